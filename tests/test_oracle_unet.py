@@ -1,0 +1,125 @@
+"""Pins of the oracle's network, unrolled loss and optimiser.
+
+conv2d is a library step; these tests pin how the oracle uses it (kernel
+orientation, padding, channel order) to brute force, the scale wrapper to
+positive homogeneity, the reference gradient to central finite differences
+(h = 1e-3, float64, 8 instances at 32x32) and AdamW to its closed form.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+import torch.nn.functional as Fnn
+
+import synth
+from oracle import helmholtz as H
+from oracle import unet as U
+
+
+def _params(seed=0):
+    flat = torch.from_numpy(synth.random_weights([s for _, s in U.PARAM_SPEC], seed=seed)).double()
+    return flat, U.unflatten(flat)
+
+
+def test_param_count():
+    # 9 * sum(Cin*Cout) over the 17 3x3 convs + biases + the 32->2 head
+    assert U.n_params() == 9 * 237664 + sum(c for _, _, c in U.CONVS) + 64
+
+
+def test_conv_orientation_brute_force():
+    """Cross-correlation with zero padding 1 and OIHW weights, by loops."""
+    rng = np.random.default_rng(0)
+    x = rng.standard_normal((1, 2, 4, 5))
+    w = rng.standard_normal((3, 2, 3, 3))
+    b = rng.standard_normal(3)
+    ref = np.zeros((1, 3, 4, 5))
+    for co in range(3):
+        for y in range(4):
+            for xx in range(5):
+                acc = b[co]
+                for ci in range(2):
+                    for dy in range(3):
+                        for dx in range(3):
+                            yy, xs = y + dy - 1, xx + dx - 1
+                            if 0 <= yy < 4 and 0 <= xs < 5:
+                                acc += w[co, ci, dy, dx] * x[0, ci, yy, xs]
+                ref[0, co, y, xx] = acc
+    got = Fnn.conv2d(torch.from_numpy(x), torch.from_numpy(w), torch.from_numpy(b), padding=1)
+    assert np.allclose(got.numpy(), ref, atol=1e-12)
+
+
+def test_pool_up_and_gelu_definitions():
+    x = torch.arange(16, dtype=torch.float64).reshape(1, 1, 4, 4)
+    p = U._pool(x)
+    assert p[0, 0, 0, 0] == (0 + 1 + 4 + 5) / 4
+    u = U._up(p)
+    assert u.shape == x.shape and u[0, 0, 1, 1] == p[0, 0, 0, 0] and u[0, 0, 2, 3] == p[0, 0, 1, 1]
+    t = torch.tensor([-1.5, 0.0, 0.7], dtype=torch.float64)
+    ref = torch.tensor([v * 0.5 * (1 + math.erf(v / math.sqrt(2))) for v in t.tolist()], dtype=torch.float64)
+    assert torch.allclose(Fnn.gelu(t), ref, atol=1e-15)
+
+
+def test_scale_wrapper_positive_homogeneity():
+    _, P = _params(1)
+    rng = np.random.default_rng(3)
+    r = torch.from_numpy(rng.standard_normal((2, 16, 16)) + 1j * rng.standard_normal((2, 16, 16)))
+    n = torch.from_numpy(1 + 0.2 * rng.standard_normal((2, 16, 16)))
+    a = U.correction(3.7 * r, n, P)
+    b = 3.7 * U.correction(r, n, P)
+    assert float((a - b).abs().max() / b.abs().max()) < 1e-12
+
+
+def _batch(count=8, N=32):
+    insts = [synth.small_instance(N, N, seed=100 + i, layer=4, ppw=8.0) for i in range(count)]
+    probs = [H.problem_from_instance(i) for i in insts]
+    V, lam, f, n = U.problems_to_batch(probs)
+    # residual snapshots from short CBS runs of different lengths
+    u0 = torch.stack([H.cbs_solve(p, tol=0, max_iter=3 * i).u for i, p in enumerate(probs)])
+    return V, lam, f, n, u0
+
+
+def test_loss_is_one_when_network_is_zero():
+    flat, _ = _params(2)
+    P = U.unflatten(torch.zeros_like(flat))
+    V, lam, f, n, u0 = _batch(2, 16)
+    assert float(U.unrolled_loss(P, V, lam, f, n, u0)) == pytest.approx(1.0, abs=1e-14)
+
+
+def test_loss_gradient_matches_central_fd():
+    """Autograd of the float64 oracle loss vs central finite differences,
+    h = 1e-3, on 8 instances at 32x32."""
+    flat, _ = _params(4)
+    V, lam, f, n, u0 = _batch(8, 32)
+    th = flat.clone().requires_grad_(True)
+    L = U.unrolled_loss(U.unflatten(th), V, lam, f, n, u0)
+    (g,) = torch.autograd.grad(L, th)
+    rng = np.random.default_rng(7)
+    # a few coordinates in each of: first conv, bottleneck, decoder, head
+    names = [nm for nm, _ in U.PARAM_SPEC]
+    offs = np.cumsum([0] + [math.prod(s) for _, s in U.PARAM_SPEC])
+    picks = []
+    for nm in ["enc0a.w", "enc0a.b", "enc3b.w", "dec0b.w", "out.w"]:
+        k = names.index(nm)
+        picks += list(rng.integers(offs[k], offs[k + 1], size=2))
+    h = 1e-3
+    for idx in picks:
+        e = torch.zeros_like(flat)
+        e[idx] = h
+        lp = float(U.unrolled_loss(U.unflatten(flat + e), V, lam, f, n, u0))
+        lm = float(U.unrolled_loss(U.unflatten(flat - e), V, lam, f, n, u0))
+        fd = (lp - lm) / (2 * h)
+        assert abs(fd - float(g[idx])) <= 1e-6 * max(1.0, abs(fd)) + 1e-9, (idx, fd, float(g[idx]))
+
+
+def test_adamw_first_step_closed_form():
+    """At step 1, mhat = g and vhat = g^2, so the update is
+    -lr * g / (|g| + eps) after decay by (1 - lr wd)."""
+    th = torch.tensor([1.0, -2.0, 0.5], dtype=torch.float64)
+    g = torch.tensor([0.3, -0.01, 0.0], dtype=torch.float64)
+    lr, wd, eps = 1e-3, 1e-2, 1e-8
+    new, m, v = U.adamw_step(th, g, torch.zeros(3, dtype=torch.float64), torch.zeros(3, dtype=torch.float64),
+                             1, lr=lr, weight_decay=wd, eps=eps)
+    expect = th * (1 - lr * wd) - lr * g / (g.abs() + eps)
+    assert torch.allclose(new, expect, atol=1e-15)
+    assert torch.allclose(m, 0.1 * g) and torch.allclose(v, 0.001 * g * g)
