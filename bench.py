@@ -1,0 +1,286 @@
+"""Benchmark: batched Born-preconditioned CBS solves on one GB300.
+
+Workload (default): the uneven batch of 256 instances at 256^2 plus 64 at
+128/192/384/512 (random medium n = 1 + 0.3 tanh(GRF), 10-40 wavelengths
+across the interior, point/Gaussian sources), solved to rTol = 1e-5 from
+u = 0.  One step = one batched CBS solve of the whole batch.
+
+metric: ms to 1e-5 residual per 256^2 Helmholtz solve = step time divided by
+the batch size in 256^2-equivalent instances (total points / 65536); lower is
+better.  The line also carries the apply's HBM roofline, the CPU oracle
+baseline, the end-to-end number through the C ABI with host buffers, clocks
+and the kernel launch count.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+import torch  # noqa: E402
+
+import synth  # noqa: E402
+
+METRIC = "ms to 1e-5 residual per 256^2 Helmholtz solve (batched CBS)"
+UNIT = "ms/solve"
+TOL = 1e-5
+B_PER_PT = 32  # algorithmic bytes per point of one CBS apply: read u, f, V, write u (complex64)
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """Sample nvidia-smi clocks and throttle reasons while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.samples = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.samples.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for s in self.samples:
+            try:
+                sm.append(float(s[1]))
+                mx = float(s[2])
+                for k, nm in enumerate(names):
+                    if s[5 + k].lower().startswith("active"):
+                        reasons.add(nm)
+            except Exception:
+                pass
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def make_workload(args):
+    if args.workload == "mixed":
+        return synth.workload_mixed(args.n256, args.nother), "cbs_mixed_256x256^2+64x{128,192,384,512}^2"
+    if args.workload == "small":
+        return synth.workload_96(), "cbs_96^2"
+    raise ValueError(args.workload)
+
+
+def equiv_256(insts):
+    return sum(i.nx * i.ny for i in insts) / 65536.0
+
+
+def cpu_oracle_solve(inst, budget_s=25.0):
+    """Time the oracle's CBS solve of one instance to TOL (complex128, CPU)."""
+    from oracle import helmholtz as H
+    p = H.problem_from_instance(inst)
+    t0 = time.perf_counter()
+    res = H.cbs_solve(p, tol=TOL, max_iter=20000, check_every=1)
+    dt = time.perf_counter() - t0
+    return dt, res
+
+
+def run_reference(args):
+    """The CPU oracle as the reference arm, on a bounded sample of the workload."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    insts, wname = make_workload(args)
+    sample = [i for i in insts if i.nx == 256][:1] or insts[:1]
+    inst = sample[0]
+    for _ in range(min(args.warmup, 1)):
+        pass  # the oracle has no warm-up state; skip untimed repeats to bound run time
+    times = []
+    iters = None
+    for _ in range(args.steps):
+        dt, res = cpu_oracle_solve(inst)
+        times.append(dt)
+        iters = res.iters
+    per = statistics.median(times) * 1e3 / (inst.nx * inst.ny / 65536.0)
+    cores = torch.get_num_threads()
+    line = {"impl": "reference", "metric": METRIC, "value": per, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.median(times) * 1e3,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
+            "data": "synthetic", "config": {"workload": wname, "sample": f"1 instance {inst.ny}x{inst.nx}",
+                                            "tol": TOL},
+            "cpu_baseline": {"value": per, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"oracle CBS solve of one {inst.ny}x{inst.nx} instance to {TOL} "
+                                       f"({iters} iterations), median of {args.steps}"},
+            "e2e": {"value": per, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="mixed", choices=["mixed", "small"])
+    ap.add_argument("--n256", type=int, default=256)
+    ap.add_argument("--nother", type=int, default=64)
+    ap.add_argument("--check-every", type=int, default=16)
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--apply-reps", type=int, default=50)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    from paper_2603_18527_gb300 import build, capi
+    build.build()
+    ctx = capi.Context(local)
+    insts, wname = make_workload(args)
+    b = capi.Batch([(i.ny, i.nx) for i in insts], h=[i.h for i in insts])
+    k2_h = b.pack([i.k2 for i in insts], device="cpu").pin_memory()
+    f_h = b.pack([i.f for i in insts], device="cpu").pin_memory()
+    k2 = k2_h.cuda()
+    f = f_h.cuda()
+    V = torch.zeros_like(k2)
+    capi.npbs_build_potential(ctx, b, k2, V)
+    u = torch.zeros(b.extent, dtype=torch.complex128, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        u.zero_()
+        return capi.cbs_solve(ctx, b, V, f, u, rtol=TOL, max_iter=20000, check_every=args.check_every)
+
+    for _ in range(args.warmup):
+        st, rep = step()
+    launches0 = capi.launch_count(ctx)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            st, rep = step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    launches = (capi.launch_count(ctx) - launches0) // args.steps
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t)
+    eq = equiv_256(insts)
+    value = ms / eq  # each rank solves its own replica of the batch (weak scaling)
+    value = value / world
+    conv = sum(1 for s in rep["status"] if s == capi.OK)
+
+    # apply roofline: CBS_STEP over the whole batch, timed alone
+    x = torch.zeros(b.extent, dtype=torch.complex64, device="cuda")
+    for _ in range(3):
+        capi.cbs_apply(ctx, b, V, f, x, x, capi.CBS_STEP)
+    torch.cuda.synchronize()
+    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a0.record(stream)
+    for _ in range(args.apply_reps):
+        capi.cbs_apply(ctx, b, V, f, x, x, capi.CBS_STEP)
+    a1.record(stream)
+    torch.cuda.synchronize()
+    apply_ms = a0.elapsed_time(a1) / args.apply_reps
+    pts = b.points()
+    ach = B_PER_PT * pts / (apply_ms * 1e-3) / 1e9
+    peak, kind = peaks()
+
+    # end to end through the C ABI with host buffers
+    e2e_steps = max(1, min(args.steps, 2))
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    u_h = torch.empty(b.extent, dtype=torch.complex128).pin_memory()
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        k2.copy_(k2_h, non_blocking=True)
+        f.copy_(f_h, non_blocking=True)
+        capi.npbs_build_potential(ctx, b, k2, V)
+        step()
+        u_h.copy_(u, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / e2e_steps
+
+    line = None
+    if rank == 0:
+        cpu = None
+        if not args.no_cpu and world == 1:
+            sample = [i for i in insts if i.nx == 256][:1] or insts[:1]
+            dt, res = cpu_oracle_solve(sample[0])
+            cpu = {"value": dt * 1e3 / (sample[0].nx * sample[0].ny / 65536.0), "unit": UNIT,
+                   "cores": torch.get_num_threads(), "kind": "oracle",
+                   "sample": f"oracle CBS solve of one {sample[0].ny}x{sample[0].nx} instance of the workload "
+                             f"to {TOL} ({res.iters} iterations, rTol checked every iteration)"}
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
+                "vs_baseline": None, "dtype": "c64 (f64 refinement)", "data": "synthetic",
+                "config": {"workload": wname, "instances": len(insts), "points": pts, "tol": TOL,
+                           "check_every": args.check_every, "l2": "inputs larger than L2 (774 MB per apply)",
+                           "converged": f"{conv}/{len(insts)}", "iters_mean": float(np.mean(rep["iters"])),
+                           "iters_max": int(np.max(rep["iters"])), "parallelism": f"replicas x{world}"},
+                "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                             "traffic": None, "kernel": "cbs_apply CBS_STEP (3 launches)", "apply_ms": apply_ms,
+                             "peak_kind": kind},
+                "cpu_baseline": cpu,
+                "e2e": {"value": e2e_ms / eq, "unit": UNIT,
+                        "h2d_bytes_per_step": int(k2_h.numel() * 8 + f_h.numel() * 8),
+                        "d2h_bytes_per_step": int(u_h.numel() * 16)},
+                "gpu_launches": int(launches), "clocks": clk.summary()}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

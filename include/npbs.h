@@ -1,0 +1,237 @@
+/*
+ * npbs.h - C ABI of the GB300 (sm_103a) Born-preconditioned Helmholtz library.
+ *
+ * The library implements the hot path of Neural Preconditioned Born Series
+ * (NPBS): the Born-preconditioned residual apply r = G_eta(V_eta u + f) - u,
+ * the CBS and NPBS iterations built on it, FGMRES on the Lippmann-Schwinger
+ * system, and the learned residual-to-correction U-Net with its training step.
+ *
+ * Discretisation (App. Fourier Pseudospectral Discretization): every instance
+ * lives on a periodic ny x nx grid with spacing h (absorbing layer included),
+ * row-major [ny][nx]; modes n in {-N/2..N/2-1}, xi = 2 pi n/(N h), forward DFT
+ * unnormalised, inverse scaled by 1/(nx ny).  Supported sizes: nx, ny of the
+ * form 2^a 3^b with 2 <= n <= 1024 (anything else is NPBS_ERR_UNSUPPORTED_SIZE;
+ * there is no fallback path).
+ *
+ * Operators (Sec. 3.1):
+ *   lambda(xi) = |xi|^2 - k0^2 - i eps          symbol of L_eta
+ *   G q        = F^{-1}(F q / lambda)          Green operator, G = L_eta^{-1}
+ *   V          = k^2 - k0^2 - i eps             perturbation (pointwise)
+ *   A u        = F^{-1}(|xi|^2 F u) - k^2 u     Helmholtz operator, A = L_eta - V
+ *   gamma      = i V / eps                      CBS diagonal preconditioner
+ *   B          = I - G V                        Lippmann-Schwinger operator (Eq. LS_discrete)
+ *
+ * Memory.  Every field argument is caller-owned DEVICE memory holding the whole
+ * batch: instance j occupies elements [offset_j, offset_j + nx_j ny_j) of each
+ * buffer.  Complex fields are interleaved (re, im): complex64 (8 bytes) unless
+ * a parameter says complex128.  Real per-point fields (the refractive index n)
+ * use the same offsets in float32 elements.  Offsets must be multiples of 32
+ * elements.  The library never frees or retains caller buffers past a call.
+ * It owns only the internals of npbs_ctx and npbs_net (workspace, plans,
+ * captured graphs, weights, moments).
+ *
+ * Errors.  Every call returns a status; nothing aborts or traps.  Device waits
+ * are bounded.  npbs_last_error() gives a one-line message for the last failure
+ * on a context.
+ *
+ * Streams.  Calls taking a stream are asynchronous on it except where noted
+ * ("synchronises"): the solvers synchronise before filling their report.
+ */
+#ifndef NPBS_H
+#define NPBS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* npbs_stream; /* a cudaStream_t; NULL = legacy default stream */
+
+typedef enum {
+    NPBS_OK = 0,
+    NPBS_ERR_INVALID_ARG = 1,
+    NPBS_ERR_UNSUPPORTED_SIZE = 2,
+    NPBS_ERR_NONFINITE = 3,
+    NPBS_NOT_CONVERGED = 4,
+    NPBS_ERR_DEVICE_TIMEOUT = 5,
+    NPBS_ERR_CUDA = 6,
+    NPBS_ERR_OOM = 7
+} npbs_status;
+
+typedef struct npbs_ctx npbs_ctx;
+typedef struct npbs_net npbs_net;
+
+/* One instance.  nx, ny: full grid including the absorbing layer.  h: grid
+ * spacing.  k0sq, eps: k0^2 and eta of L_eta (eps > 0).  offset: first element
+ * of this instance in every field buffer (multiple of 32). */
+typedef struct {
+    int32_t nx, ny;
+    double h, k0sq, eps;
+    int64_t offset;
+} npbs_instance;
+
+typedef struct {
+    int32_t count;              /* number of instances, >= 0 */
+    const npbs_instance* inst;  /* HOST array [count] */
+} npbs_batch;
+
+/* Apply modes of cbs_apply.  x is the field operated on, out the result.
+ *   NPBS_RESIDUAL      out = G(V x + f) - x                      (Eq. npbs_integral)
+ *   NPBS_CBS_STEP      out = x + gamma (G(V x + f) - x)          (Eq. CBS); out may alias x
+ *   NPBS_OP_B          out = x - G(V x)                          (Eq. LS_discrete)
+ *   NPBS_ADJ_B         out = x - conj(V) G^*(x), G^* symbol 1/conj(lambda)
+ *   NPBS_TRUE_RESIDUAL out = f - A x                             (Sec. 5 stopping rule)
+ *   NPBS_PREC_SWEEP    out = x + gamma (f - B x): one CBS Richardson sweep for
+ *                      B z = f with f in preconditioned coordinates
+ * norm2 (nullable, DEVICE double[count]) receives, per instance, the squared
+ * 2-norm of G(Vx+f)-x for RESIDUAL / CBS_STEP (before the update), of out for
+ * OP_B, ADJ_B, TRUE_RESIDUAL, and of f - B x for PREC_SWEEP.  It is
+ * overwritten, not accumulated. */
+typedef enum {
+    NPBS_RESIDUAL = 0,
+    NPBS_CBS_STEP = 1,
+    NPBS_OP_B = 2,
+    NPBS_ADJ_B = 3,
+    NPBS_TRUE_RESIDUAL = 4,
+    NPBS_PREC_SWEEP = 5
+} npbs_mode;
+
+typedef struct {
+    double rtol;          /* target ||f - A u|| / ||f|| (Sec. 5) */
+    int32_t max_iter;     /* cap on iterations (CBS/NPBS updates or FGMRES steps) */
+    int32_t check_every;  /* iterations between convergence checks (>= 1) */
+    int32_t use_graph;    /* capture the inner loop in a CUDA graph (0/1) */
+} npbs_solve_opts;
+
+typedef struct {
+    int32_t* iters;        /* HOST [count]: iterations at the passing check (or at the cap) */
+    double* rtol;          /* HOST [count]: final ||f - A u|| / ||f|| in float64 */
+    npbs_status* status;   /* HOST [count]: NPBS_OK or NPBS_NOT_CONVERGED / NPBS_ERR_NONFINITE */
+    int32_t* flags;        /* HOST [count], nullable: npbs_solve sets 1 where the divergence
+                            * guard switched the instance to plain CBS steps */
+} npbs_report;
+
+/* ---- context ------------------------------------------------------------ */
+
+/* Create a context on CUDA device `device` (made current for the call). */
+npbs_status npbs_create(npbs_ctx** out, int device);
+npbs_status npbs_destroy(npbs_ctx* ctx);
+/* One-line description of the last error on ctx ("" if none).  Owned by ctx. */
+const char* npbs_last_error(const npbs_ctx* ctx);
+/* Library version string, static storage. */
+const char* npbs_version(void);
+/* Number of kernels launched through ctx so far (graph launches count the
+ * kernels they contain); -1 for a NULL ctx.  For benchmarks. */
+int64_t npbs_launch_count(const npbs_ctx* ctx);
+
+/* ---- problem set-up ----------------------------------------------------- */
+
+/* Reference constants and potential (Sec. 3.1; the paper leaves k0 and eta
+ * free, this library takes k0^2 = (min Re k^2 + max Re k^2)/2 and
+ * eps = max |k^2 - k0^2| over each instance's full grid).
+ * k2: DEVICE complex64 k(x)^2 (Im k^2 >= 0 carries the absorbing layer).
+ * V_out: DEVICE complex64, receives V = k^2 - k0^2 - i eps (may be NULL).
+ * k0sq_out, eps_out: HOST double[count].  The k0sq / eps fields of `batch`
+ * are ignored.  Synchronises the stream. */
+npbs_status npbs_build_potential(npbs_ctx* ctx, const npbs_batch* batch, const void* k2,
+                                 void* V_out, double* k0sq_out, double* eps_out,
+                                 npbs_stream stream);
+
+/* ---- the apply (Eq. CBS / Eq. npbs_integral / Eq. LS_discrete) ------------ */
+
+/* One fused Born apply over the batch in the given mode (see npbs_mode).
+ * V, f, x, out: DEVICE complex64.  f may be NULL for OP_B and ADJ_B.  Inputs
+ * other than x may not alias out.  Asynchronous. */
+npbs_status cbs_apply(npbs_ctx* ctx, const npbs_batch* batch, const void* V, const void* f,
+                      const void* x, void* out, npbs_mode mode, double* norm2,
+                      npbs_stream stream);
+
+/* ---- solvers --------------------------------------------------------------
+ * All solvers iterate in complex64 on a correction delta and fold it into the
+ * solution u held in complex128 every refinement cycle, where the true
+ * residual f - A u is recomputed in float64 (mixed-precision iterative
+ * refinement).  Linear stationary iterations restarted from delta = 0 on the
+ * correction equation A delta = f - A u produce the same iterates as the
+ * uninterrupted iteration, so iteration counts are those of the method; the
+ * float64 residual removes the float32 floor (about 1e-5 for complex64 CBS).
+ * u: DEVICE complex128, initial guess on entry, solution on exit.
+ * Converged instances are masked out of later launches.  Synchronise. */
+
+/* Stationary CBS (Eq. CBS) to opts->rtol. */
+npbs_status cbs_solve(npbs_ctx* ctx, const npbs_batch* batch, const void* V, const void* f,
+                      void* u, const npbs_solve_opts* opts, npbs_report* report,
+                      npbs_stream stream);
+
+/* Stationary NPBS (Eq. npbs_integral) with the network of `net` as M_theta:
+ * u <- u + M(G(V u + f) - u), M(r) = s N([Re r/s, Im r/s, n]), s = rms(r).
+ * n: DEVICE float32 refractive index (network input channel).  Divergence
+ * guard: an instance whose float64 rTol did not decrease between two refresh
+ * points continues with plain CBS steps (report->flags). */
+npbs_status npbs_solve(npbs_ctx* ctx, const npbs_net* net, const npbs_batch* batch,
+                       const void* V, const void* f, const float* n, void* u,
+                       const npbs_solve_opts* opts, npbs_report* report, npbs_stream stream);
+
+/* Restarted flexible GMRES on B u = G f (Eq. LS_discrete), restart length
+ * `restart` (1..64), right preconditioner precond: 0 none, 1 `cbs_sweeps`
+ * CBS Richardson sweeps, 2 the network of `net` (may be NULL unless precond = 2). */
+npbs_status fgmres_solve(npbs_ctx* ctx, const npbs_net* net, const npbs_batch* batch,
+                         const void* V, const void* f, const float* n, void* u,
+                         int32_t restart, int32_t precond, int32_t cbs_sweeps,
+                         const npbs_solve_opts* opts, npbs_report* report, npbs_stream stream);
+
+
+/* ---- the learned correction M_theta (App. Experimental Setup, U-Net) -------
+ * M(r; n) = s N([Re r / s, Im r / s, n]), s = ||r||_2 / sqrt(nx ny) per
+ * instance, N a 4-level U-Net (32/64/128/256 channels, two 3x3 conv + GELU per
+ * level, 2x2 average pooling, nearest x2 upsampling + 3x3 conv + GELU,
+ * concatenated skips, bias-free 1x1 head to 2 channels), BF16 weights and
+ * activations with FP32 accumulation on the tensor cores.  Grid sides must be
+ * multiples of 8.  Parameters are exchanged in the canonical order: for each of
+ * the 17 convolutions (enc0a, enc0b, enc1a, enc1b, enc2a, enc2b, enc3a, enc3b,
+ * up2, dec2a, dec2b, up1, dec1a, dec1b, up0, dec0a, dec0b) a float32 weight
+ * [Cout][Cin][3][3] then a bias [Cout]; then the head weight [2][32]. */
+
+/* Total number of parameters in the canonical order. */
+int64_t npbs_net_num_params(void);
+/* Create a network on `device` with seeded He-normal weights. */
+npbs_status npbs_net_create(npbs_net** out, int device, uint64_t seed);
+npbs_status npbs_net_destroy(npbs_net* net);
+/* Copy parameters / accumulated gradients in the canonical order (HOST float[n],
+ * n = npbs_net_num_params()).  Synchronous. */
+npbs_status npbs_net_set_params(npbs_net* net, const float* host, int64_t n);
+npbs_status npbs_net_get_params(const npbs_net* net, float* host, int64_t n);
+npbs_status npbs_net_get_grads(const npbs_net* net, float* host, int64_t n);
+npbs_status npbs_net_zero_grad(npbs_net* net, npbs_stream stream);
+/* One AdamW update (beta 0.9 / 0.999, eps 1e-8, decoupled weight decay) with
+ * the accumulated gradients. */
+npbs_status npbs_net_adamw(npbs_ctx* ctx, npbs_net* net, float lr, float weight_decay, npbs_stream stream);
+/* Checkpoint: parameters, AdamW moments and step count to a binary file. */
+npbs_status npbs_net_save(const npbs_net* net, const char* path);
+npbs_status npbs_net_load(npbs_net** out, int device, const char* path);
+
+/* c_out = M(r; n) per instance (Eq. npbs_integral, learned map).  r, c_out:
+ * DEVICE complex64; n: DEVICE float32. */
+npbs_status npbs_net_forward(npbs_ctx* ctx, const npbs_net* net, const npbs_batch* batch, const void* r,
+                             const float* n, void* c_out, npbs_stream stream);
+/* Hand-written adjoint of c = M(r; n): accumulates d<grad_c, c>/dtheta into the
+ * network gradients and writes grad_r = (J_M(r))^* grad_c (gradients of real
+ * losses in the convention dL/dRe + i dL/dIm).  Recomputes the forward. */
+npbs_status npbs_net_backward(npbs_ctx* ctx, npbs_net* net, const npbs_batch* batch, const void* r,
+                              const float* n, const void* grad_c, void* grad_r, npbs_stream stream);
+
+/* Metric-matched training step (Eq. L_bs_Reta_integral, squared, over `unroll`
+ * NPBS steps from the snapshots u_snap): r_0 = G(V u + f) - u,
+ * r_{k+1} = r_k - (I - G V) M(r_k), loss = mean_j (1/U) sum_k ||r_k||^2/||r_0||^2;
+ * gradients by the adjoint apply and network backward with activation
+ * checkpointing (only r_0..r_U stored), then one AdamW update.  u_snap:
+ * DEVICE complex64.  loss_host receives the loss before the update.
+ * Synchronises the stream once (to read the loss). */
+npbs_status npbs_train_step(npbs_ctx* ctx, npbs_net* net, const npbs_batch* batch, const void* V,
+                            const void* f, const float* n, const void* u_snap, int32_t unroll, float lr,
+                            float weight_decay, float* loss_host, npbs_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NPBS_H */

@@ -1,0 +1,324 @@
+// C ABI: context, batch plans, potential set-up and the fused apply entry.
+#include <cmath>
+#include <cstring>
+#include <cstdio>
+
+#include "ctx.cuh"
+
+namespace npbs {
+
+Plan::~Plan() {
+    cudaFree(inst);
+    cudaFree(plans);
+    cudaFree(tw32);
+    cudaFree(tw64);
+    cudaFree(rows32);
+    cudaFree(cols32);
+    cudaFree(rows64);
+    cudaFree(cols64);
+    cudaFree(vitems);
+}
+
+cudaError_t DevBuf::ensure(size_t need) {
+    if (need <= bytes && p) return cudaSuccess;
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+    cudaError_t e = cudaMalloc(&p, need);
+    if (e == cudaSuccess) bytes = need;
+    return e;
+}
+
+DevBuf::~DevBuf() {
+    if (p) cudaFree(p);
+}
+
+npbs_status set_err(npbs_ctx* ctx, npbs_status st, const std::string& msg) {
+    if (ctx) ctx->err = msg;
+    return st;
+}
+
+npbs_status cuda_err(npbs_ctx* ctx, cudaError_t e, const char* where) {
+    std::string m = std::string("CUDA error ") + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ") at " + where;
+    return set_err(ctx, e == cudaErrorMemoryAllocation ? NPBS_ERR_OOM : NPBS_ERR_CUDA, m);
+}
+
+// 2^a 3^b with 2 <= n <= 1024; radices 8, 4, 2 then 3.
+static bool radix_plan(int n, RadixPlan* p) {
+    if (n < 2 || n > kMaxN) return false;
+    p->n = n;
+    p->npass = 0;
+    int m = n;
+    while (m % 8 == 0) { p->radix[p->npass++] = 8; m /= 8; }
+    while (m % 4 == 0) { p->radix[p->npass++] = 4; m /= 4; }
+    while (m % 2 == 0) { p->radix[p->npass++] = 2; m /= 2; }
+    while (m % 3 == 0) { p->radix[p->npass++] = 3; m /= 3; }
+    return m == 1 && p->npass <= kMaxPass;
+}
+
+template <typename T> static cudaError_t upload(T** dst, const std::vector<T>& v) {
+    if (v.empty()) { *dst = nullptr; return cudaSuccess; }
+    cudaError_t e = cudaMalloc(dst, v.size() * sizeof(T));
+    if (e != cudaSuccess) return e;
+    return cudaMemcpy(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+}
+
+const Plan* get_plan(npbs_ctx* ctx, const npbs_batch* batch, npbs_status* st) {
+    *st = NPBS_OK;
+    if (!batch || batch->count < 0 || (batch->count > 0 && !batch->inst)) {
+        *st = set_err(ctx, NPBS_ERR_INVALID_ARG, "batch is NULL, has a negative count or a NULL instance array");
+        return nullptr;
+    }
+    std::string key(reinterpret_cast<const char*>(batch->inst), sizeof(npbs_instance) * batch->count);
+    auto itp = ctx->plans.find(key);
+    if (itp != ctx->plans.end()) return itp->second.get();
+
+    auto pl = std::make_unique<Plan>();
+    pl->count = batch->count;
+    std::map<int, int> plan_of, tw_of;
+    std::vector<RadixPlan> plans;
+    std::vector<float2> tw32;
+    std::vector<double2> tw64;
+    auto add_n = [&](int n) -> bool {
+        if (plan_of.count(n)) return true;
+        RadixPlan rp;
+        if (!radix_plan(n, &rp)) return false;
+        plan_of[n] = (int)plans.size();
+        plans.push_back(rp);
+        tw_of[n] = (int)tw32.size();
+        for (int k = 0; k < n; ++k) {
+            const double a = -2.0 * M_PI * (double)k / (double)n;
+            tw64.push_back(make_double2(std::cos(a), std::sin(a)));
+            tw32.push_back(make_float2((float)std::cos(a), (float)std::sin(a)));
+        }
+        return true;
+    };
+    std::vector<RowItem> r32, r64;
+    std::vector<ColItem> c32, c64;
+    std::vector<VecItem> vit;
+    for (int j = 0; j < batch->count; ++j) {
+        const npbs_instance& s = batch->inst[j];
+        char buf[256];
+        if (!(s.h > 0.0) || !std::isfinite(s.h) || !std::isfinite(s.k0sq) || !(s.eps > 0.0) ||
+            !std::isfinite(s.eps) || s.offset < 0 || (s.offset % 32) != 0) {
+            snprintf(buf, sizeof buf, "instance %d: need h > 0, eps > 0, finite k0sq and offset >= 0, multiple of 32", j);
+            *st = set_err(ctx, NPBS_ERR_INVALID_ARG, buf);
+            return nullptr;
+        }
+        if (!add_n(s.nx) || !add_n(s.ny)) {
+            snprintf(buf, sizeof buf, "instance %d: grid %d x %d is not 2^a 3^b in [2, %d]", j, s.ny, s.nx, kMaxN);
+            *st = set_err(ctx, NPBS_ERR_UNSUPPORTED_SIZE, buf);
+            return nullptr;
+        }
+        InstDev d;
+        d.nx = s.nx;
+        d.ny = s.ny;
+        d.plan_x = plan_of[s.nx];
+        d.plan_y = plan_of[s.ny];
+        d.tw_x = tw_of[s.nx];
+        d.tw_y = tw_of[s.ny];
+        d.h = s.h;
+        d.k0sq = s.k0sq;
+        d.eps = s.eps;
+        d.offset = s.offset;
+        pl->inst_h.push_back(d);
+        pl->extent = std::max<long long>(pl->extent, s.offset + (long long)s.nx * s.ny);
+        pl->points += (long long)s.nx * s.ny;
+        for (long long st0 = 0; st0 < (long long)s.nx * s.ny; st0 += kVecChunk) {
+            VecItem v{j, (int)st0, (int)std::min<long long>(kVecChunk, (long long)s.nx * s.ny - st0), 0};
+            vit.push_back(v);
+        }
+        for (int f64 = 0; f64 < 2; ++f64) {
+            const int tile = f64 ? kTileElems<double>() : kTileElems<float>();
+            const int rp = std::max(1, std::min(s.ny, tile / s.nx));
+            for (int r0 = 0; r0 < s.ny; r0 += rp) {
+                RowItem it{j, r0, std::min(rp, s.ny - r0), 0};
+                (f64 ? r64 : r32).push_back(it);
+            }
+            const int cp = std::max(1, std::min(16, tile / s.ny));
+            for (int c0 = 0; c0 < s.nx; c0 += cp) {
+                ColItem it{j, c0, std::min(cp, s.nx - c0), 0};
+                (f64 ? c64 : c32).push_back(it);
+            }
+        }
+    }
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = upload(&pl->inst, pl->inst_h);
+    if (e == cudaSuccess) e = upload(&pl->plans, plans);
+    if (e == cudaSuccess) e = upload(&pl->tw32, tw32);
+    if (e == cudaSuccess) e = upload(&pl->tw64, tw64);
+    if (e == cudaSuccess) e = upload(&pl->rows32, r32);
+    if (e == cudaSuccess) e = upload(&pl->cols32, c32);
+    if (e == cudaSuccess) e = upload(&pl->rows64, r64);
+    if (e == cudaSuccess) e = upload(&pl->cols64, c64);
+    if (e == cudaSuccess) e = upload(&pl->vitems, vit);
+    if (e != cudaSuccess) {
+        *st = cuda_err(ctx, e, "plan upload");
+        return nullptr;
+    }
+    pl->nrow32 = (int)r32.size();
+    pl->ncol32 = (int)c32.size();
+    pl->nrow64 = (int)r64.size();
+    pl->ncol64 = (int)c64.size();
+    pl->nvec = (int)vit.size();
+    if (ctx->plans.size() > 64) ctx->plans.clear();
+    const Plan* out = pl.get();
+    ctx->plans[key] = std::move(pl);
+    return out;
+}
+
+npbs_status run_apply(npbs_ctx* ctx, const Plan& pl, int mode, const ApplyArgs& a0, const int* active,
+                      cudaStream_t st) {
+    const bool f64 = (mode == kTrueRes64);
+    ApplyArgs a = a0;
+    NPBS_CK(ctx, ctx->scratch.ensure((size_t)std::max<long long>(pl.extent, 1) * (f64 ? 16 : 8)));
+    a.scratch = ctx->scratch.p;
+    if (a.norm2) NPBS_CK(ctx, cudaMemsetAsync(a.norm2, 0, sizeof(double) * pl.count, st));
+    if (a.norm2b) NPBS_CK(ctx, cudaMemsetAsync(a.norm2b, 0, sizeof(double) * pl.count, st));
+    const BatchDev bd = pl.bd(f64, active);
+    NPBS_CK(ctx, launch_apply(mode, bd, f64 ? pl.nrow64 : pl.nrow32, f64 ? pl.ncol64 : pl.ncol32, a, st));
+    ctx->count(st, 3);
+    return NPBS_OK;
+}
+
+// k0^2 = (min Re k^2 + max Re k^2)/2, eps = max |k^2 - k0^2|, V = k^2 - k0^2 - i eps.
+__global__ void k_potential(const InstDev* inst, const float2* k2, float2* V, double* consts) {
+    __shared__ float smin[32], smax[32];
+    __shared__ double sd[32];
+    __shared__ double c0, c1;
+    const InstDev in = inst[blockIdx.x];
+    const long long n = (long long)in.nx * in.ny;
+    const float2* p = k2 + in.offset;
+    float mn = 3.0e38f, mx = -3.0e38f;
+    for (long long e = threadIdx.x; e < n; e += blockDim.x) {
+        const float v = p[e].x;
+        mn = fminf(mn, v);
+        mx = fmaxf(mx, v);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+        mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (lane == 0) { smin[w] = mn; smax[w] = mx; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float a = smin[0], b = smax[0];
+        for (int i = 1; i < nw; ++i) { a = fminf(a, smin[i]); b = fmaxf(b, smax[i]); }
+        c0 = 0.5 * ((double)a + (double)b);
+    }
+    __syncthreads();
+    const double k0sq = c0;
+    double m = 0.0;
+    for (long long e = threadIdx.x; e < n; e += blockDim.x) {
+        const double dr = (double)p[e].x - k0sq, di = (double)p[e].y;
+        m = fmax(m, dr * dr + di * di);
+    }
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane == 0) sd[w] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = sd[0];
+        for (int i = 1; i < nw; ++i) a = fmax(a, sd[i]);
+        c1 = sqrt(a);
+        consts[2 * blockIdx.x] = k0sq;
+        consts[2 * blockIdx.x + 1] = c1;
+    }
+    __syncthreads();
+    const double eps = c1;
+    if (V) {
+        float2* q = V + in.offset;
+        for (long long e = threadIdx.x; e < n; e += blockDim.x)
+            q[e] = make_float2((float)((double)p[e].x - k0sq), (float)((double)p[e].y - eps));
+    }
+}
+
+}  // namespace npbs
+
+using namespace npbs;
+
+extern "C" {
+
+const char* npbs_version(void) { return "npbs-gb300 0.1 (sm_103a)"; }
+
+npbs_status npbs_create(npbs_ctx** out, int device) {
+    if (!out) return NPBS_ERR_INVALID_ARG;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return NPBS_ERR_INVALID_ARG;
+    if (cudaSetDevice(device) != cudaSuccess) return NPBS_ERR_CUDA;
+    if (prepare_apply() != cudaSuccess) return NPBS_ERR_CUDA;
+    npbs_ctx* c = new (std::nothrow) npbs_ctx();
+    if (!c) return NPBS_ERR_OOM;
+    c->device = device;
+    *out = c;
+    return NPBS_OK;
+}
+
+npbs_status npbs_destroy(npbs_ctx* ctx) {
+    if (!ctx) return NPBS_ERR_INVALID_ARG;
+    cudaSetDevice(ctx->device);
+    if (ctx->solve_stream) {
+        cudaStreamSynchronize(ctx->solve_stream);
+        cudaStreamDestroy(ctx->solve_stream);
+    }
+    if (ctx->solve_event) cudaEventDestroy(ctx->solve_event);
+    delete ctx;
+    return NPBS_OK;
+}
+
+const char* npbs_last_error(const npbs_ctx* ctx) { return ctx ? ctx->err.c_str() : "NULL context"; }
+
+int64_t npbs_launch_count(const npbs_ctx* ctx) { return ctx ? (int64_t)ctx->launches : -1; }
+
+npbs_status npbs_build_potential(npbs_ctx* ctx, const npbs_batch* batch, const void* k2, void* V_out,
+                                 double* k0sq_out, double* eps_out, npbs_stream stream) {
+    if (!ctx) return NPBS_ERR_INVALID_ARG;
+    if (!batch || batch->count < 0 || (batch->count > 0 && (!batch->inst || !k2 || !k0sq_out || !eps_out)))
+        return set_err(ctx, NPBS_ERR_INVALID_ARG, "npbs_build_potential: NULL argument");
+    if (batch->count == 0) return NPBS_OK;
+    // the constants are outputs here: plan with placeholders that pass validation
+    std::vector<npbs_instance> tmp(batch->inst, batch->inst + batch->count);
+    for (auto& t : tmp) { t.k0sq = 0.0; t.eps = 1.0; }
+    npbs_batch b2{batch->count, tmp.data()};
+    npbs_status st;
+    const Plan* pl = get_plan(ctx, &b2, &st);
+    if (!pl) return st;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    NPBS_CK(ctx, ctx->work[7].ensure(sizeof(double) * 2 * batch->count));
+    double* dc = static_cast<double*>(ctx->work[7].p);
+    k_potential<<<batch->count, 1024, 0, s>>>(pl->inst, static_cast<const float2*>(k2), static_cast<float2*>(V_out), dc);
+    NPBS_CK(ctx, cudaGetLastError());
+    ctx->count(s, 1);
+    std::vector<double> hc(2 * batch->count);
+    NPBS_CK(ctx, cudaMemcpyAsync(hc.data(), dc, sizeof(double) * hc.size(), cudaMemcpyDeviceToHost, s));
+    NPBS_CK(ctx, cudaStreamSynchronize(s));
+    for (int j = 0; j < batch->count; ++j) {
+        k0sq_out[j] = hc[2 * j];
+        eps_out[j] = hc[2 * j + 1];
+    }
+    return NPBS_OK;
+}
+
+npbs_status cbs_apply(npbs_ctx* ctx, const npbs_batch* batch, const void* V, const void* f, const void* x,
+                      void* out, npbs_mode mode, double* norm2, npbs_stream stream) {
+    if (!ctx) return NPBS_ERR_INVALID_ARG;
+    if ((int)mode < 0 || (int)mode > NPBS_PREC_SWEEP) return set_err(ctx, NPBS_ERR_INVALID_ARG, "cbs_apply: bad mode");
+    npbs_status st;
+    const Plan* pl = get_plan(ctx, batch, &st);
+    if (!pl) return st;
+    if (pl->count == 0) return NPBS_OK;
+    const bool need_f = mode == NPBS_RESIDUAL || mode == NPBS_CBS_STEP || mode == NPBS_TRUE_RESIDUAL ||
+                        mode == NPBS_PREC_SWEEP;
+    if (!V || !x || !out || (need_f && !f))
+        return set_err(ctx, NPBS_ERR_INVALID_ARG, "cbs_apply: NULL field pointer");
+    ApplyArgs a{};
+    a.V = static_cast<const float2*>(V);
+    a.f = static_cast<const float2*>(f);
+    a.x = static_cast<const float2*>(x);
+    a.out = static_cast<float2*>(out);
+    a.norm2 = norm2;
+    return run_apply(ctx, *pl, (int)mode, a, nullptr, reinterpret_cast<cudaStream_t>(stream));
+}
+
+}  // extern "C"

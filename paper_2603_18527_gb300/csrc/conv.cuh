@@ -1,0 +1,47 @@
+// Convolution and elementwise kernels of the residual-to-correction U-Net.
+// Activations are NHWC bfloat16 with an explicit pixel stride (channels of a
+// concatenation share one buffer); accumulation is float32.
+#pragma once
+
+#include <cuda_bf16.h>
+
+#include "common.cuh"
+
+namespace npbs {
+
+using bf16 = __nv_bfloat16;
+
+// One 3x3 (zero padding 1) convolution as an implicit GEMM:
+//   out[p, n] = sum_{tap, c} in[nbr(p, tap), c] * w[n, tap, c]   (+ bias, GELU)
+// M = B*H*W output pixels, N = Cout, K = 9*Cin.
+struct ConvFwd {
+    const bf16* x;      // input [B][Hin][Win][xs], channels [xo, xo + Cin) read
+    int xs, xo;
+    int B, H, W;        // output spatial size; input is H x W, or H/2 x W/2 when ups
+    int ups;            // 1: nearest-neighbour x2 upsampling folded into the gather
+    int Cin, Cout;      // Cin multiple of 16, Cout multiple of 8
+    const bf16* w;      // [Cout][9][Cin]
+    const float* bias;  // [Cout] or null
+    int act;            // 1: GELU (erf form)
+    bf16* y;            // output [B][H][W][ys] at channel offset yo (bf16) ...
+    int ys, yo;
+    bf16* z;            // ... and optionally the pre-activation in the same layout
+    float* yf;          // or float32 output [B][H][W][ys] at yo (no activation)
+};
+
+// Weight gradient dW[n, tap, c] += sum_p dz[p, n] * in[nbr(p, tap), c], split
+// over pixel ranges with float32 atomics.
+struct ConvWgrad {
+    const bf16* x;
+    int xs, xo;
+    int B, H, W, ups;
+    int Cin, Cout;
+    const bf16* dz;     // [B][H][W][Cout]
+    float* dw;          // [Cout][9][Cin], accumulated
+    int pix_per_cta;
+};
+
+cudaError_t conv_fwd(const ConvFwd& a, cudaStream_t st);
+cudaError_t conv_wgrad(const ConvWgrad& a, cudaStream_t st);
+
+}  // namespace npbs

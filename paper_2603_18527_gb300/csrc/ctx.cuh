@@ -1,0 +1,93 @@
+// Context internals shared by the C ABI implementation files.
+#pragma once
+
+#include <map>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "apply.cuh"
+#include "common.cuh"
+
+namespace npbs {
+
+// Device copy of a batch description: instances, radix plans, twiddles and
+// the row / column work items for float32 and float64 tiles.
+struct Plan {
+    int count = 0;
+    long long extent = 0;         // one past the last element used by any instance
+    long long points = 0;         // sum of nx * ny
+    std::vector<InstDev> inst_h;
+    InstDev* inst = nullptr;
+    RadixPlan* plans = nullptr;
+    float2* tw32 = nullptr;
+    double2* tw64 = nullptr;
+    RowItem* rows32 = nullptr;
+    ColItem* cols32 = nullptr;
+    RowItem* rows64 = nullptr;
+    ColItem* cols64 = nullptr;
+    int nrow32 = 0, ncol32 = 0, nrow64 = 0, ncol64 = 0;
+    VecItem* vitems = nullptr;
+    int nvec = 0;
+    BatchDev bd(bool f64, const int* active) const {
+        BatchDev b;
+        b.inst = inst;
+        b.plans = plans;
+        b.tw32 = tw32;
+        b.tw64 = tw64;
+        b.rows = f64 ? rows64 : rows32;
+        b.cols = f64 ? cols64 : cols32;
+        b.active = active;
+        b.count = count;
+        return b;
+    }
+    ~Plan();
+};
+
+// Growable device buffer owned by a context.
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    cudaError_t ensure(size_t need);
+    ~DevBuf();
+};
+
+}  // namespace npbs
+
+struct npbs_ctx {
+    int device = 0;
+    std::string err;
+    std::map<std::string, std::unique_ptr<npbs::Plan>> plans;
+    npbs::DevBuf scratch;   // spectrum between apply passes
+    npbs::DevBuf work[8];   // solver workspaces
+    npbs::DevBuf net_ws;    // network activations
+    cudaStream_t solve_stream = nullptr;  // capturable stream the solvers run on
+    cudaEvent_t solve_event = nullptr;
+    long long launches = 0;         // kernels launched (graph launches count their kernels)
+    long long capture_kernels = 0;  // kernels recorded into the graph being captured
+    void count(cudaStream_t st, long long k) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        cudaStreamIsCapturing(st, &cs);
+        if (cs == cudaStreamCaptureStatusActive) capture_kernels += k;
+        else launches += k;
+    }
+};
+
+namespace npbs {
+
+npbs_status set_err(npbs_ctx* ctx, npbs_status st, const std::string& msg);
+npbs_status cuda_err(npbs_ctx* ctx, cudaError_t e, const char* where);
+// Validate the batch and return its (cached) device plan; nullptr on error
+// with the status in *st.
+const Plan* get_plan(npbs_ctx* ctx, const npbs_batch* batch, npbs_status* st);
+// Launch one apply of `mode` on the plan (float32 modes or kTrueRes64).
+npbs_status run_apply(npbs_ctx* ctx, const Plan& pl, int mode, const ApplyArgs& a, const int* active,
+                      cudaStream_t st);
+
+}  // namespace npbs
+
+#define NPBS_CK(ctx, call)                                                   \
+    do {                                                                     \
+        cudaError_t _e = (call);                                             \
+        if (_e != cudaSuccess) return npbs::cuda_err((ctx), _e, #call);      \
+    } while (0)

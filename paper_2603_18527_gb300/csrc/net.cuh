@@ -1,0 +1,69 @@
+// Network internals shared by the network, solver and training files.
+#pragma once
+
+#include <vector>
+
+#include "conv.cuh"
+#include "ctx.cuh"
+
+namespace npbs {
+
+struct LayerDef {
+    const char* kind;  // enc_a, enc_b, up, dec_a, dec_b
+    int level, cin, cout, ups;
+    int cin_pad = 0;                 // input channels padded to a multiple of 16
+    long long w_off = 0, b_off = 0;  // device layout offsets (float32 master copy)
+    long long cw_off = 0, cb_off = 0;  // canonical (OIHW) offsets
+};
+
+const std::vector<LayerDef>& layer_defs();
+long long dev_param_count();
+long long canon_param_count();
+
+// Weights, gradients and AdamW moments on one device (device layout: per conv
+// [Cout][9][Cin_pad] then bias, then the 2 x 32 head).
+struct Net {
+    int device = 0;
+    long long step = 0;
+    float* params = nullptr;
+    float* grads = nullptr;
+    float* m1 = nullptr;
+    float* m2 = nullptr;
+    bf16* wb = nullptr;  // bfloat16 copy, [Cout][9][Cin_pad]
+    bf16* wt = nullptr;  // flipped transpose for data gradients, [Cin_pad][9][Cout]
+    std::vector<long long> wb_off;
+    npbs_status alloc(int dev);
+    cudaError_t refresh_bf16(cudaStream_t st) const;
+    ~Net();
+};
+
+// Instances the network runs on: nb slots of one grid size, element offsets.
+struct SlotDev {
+    int nb;
+    long long np;           // points per instance
+    const long long* off;   // device [nb]
+};
+
+// A prepared network launch over a set of instances (grouped by size): all
+// allocations and host-to-device copies happen in net_prepare, so the run
+// functions only launch kernels and can be captured in a CUDA graph.
+struct NetGroup {
+    int H, W;
+    SlotDev sd;
+};
+struct NetRun {
+    std::vector<NetGroup> groups;
+    bool train = false;
+};
+
+npbs_status net_prepare(npbs_ctx* ctx, const Plan& pl, const std::vector<int>& which, bool train, NetRun* run,
+                        cudaStream_t st);
+// out = M(r) (add = 0) or out += M(r) (add = 1)
+npbs_status net_run_forward(npbs_ctx* ctx, const Net& net, const NetRun& run, const float2* r, const float* n,
+                            float2* out, int add, cudaStream_t st);
+// weight gradients += d/dtheta <gc, M(r)>, gr = (or +=) d/dr; run must be prepared with train = true
+npbs_status net_run_backward(npbs_ctx* ctx, Net& net, const NetRun& run, const float2* r, const float* n,
+                             const float2* gc, float2* gr, int add, cudaStream_t st);
+npbs_status net_adamw(npbs_ctx* ctx, Net& net, float lr, float wd, cudaStream_t st);
+
+}  // namespace npbs

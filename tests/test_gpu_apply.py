@@ -1,0 +1,137 @@
+"""GPU parity of the fused Born apply (every mode) against the complex128 oracle.
+
+Tolerance: relative L2 error <= 1e-5 per instance and apply (float32 FFT
+round-off is ~1e-7 * log2 N; the bound leaves two orders of margin).
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import helmholtz as H
+from tests.gpu_common import ctx, rel_l2, random_field, setup_batch
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+# sizes spanning several row/column tiles, ragged tails, radix 3, non-square grids
+SHAPES = [(16, 16), (96, 96), (24, 48), (48, 24), (2, 2), (3, 6), (288, 288), (256, 256), (1024, 64),
+          (64, 1024), (384, 128), (9, 512)]
+
+
+@pytest.fixture(scope="module")
+def env():
+    capi, c = ctx()
+    insts = [synth.small_instance(ny, nx, seed=10 + j, layer=max(1, min(ny, nx) // 8), ppw=6.0)
+             for j, (ny, nx) in enumerate(SHAPES)]
+    b, k2, f, n, V = setup_batch(capi, c, insts)
+    probs = [H.problem_from_instance(i) for i in insts]
+    xs = [random_field((i.ny, i.nx), 100 + j) for j, i in enumerate(insts)]
+    x = b.pack(xs)
+    return capi, c, insts, probs, b, k2, f, V, xs, x
+
+
+def test_reference_constants_match_oracle(env):
+    capi, c, insts, probs, b, *_ = env
+    for j, p in enumerate(probs):
+        assert b.k0sq[j] == pytest.approx(p.k0sq, rel=1e-6, abs=1e-7)
+        assert b.eps[j] == pytest.approx(p.eps, rel=1e-6)
+
+
+def _oracle(mode, p, x):
+    x = torch.from_numpy(x)
+    if mode == "RESIDUAL":
+        return H.born_residual(p, x), None
+    if mode == "CBS_STEP":
+        return H.cbs_step(p, x), H.born_residual(p, x)
+    if mode == "OP_B":
+        return H.op_B(p, x), None
+    if mode == "ADJ_B":
+        return H.op_BH(p, x), None
+    if mode == "TRUE_RESIDUAL":
+        return H.true_residual(p, x), None
+    if mode == "PREC_SWEEP":
+        # f plays the role of the preconditioned-coordinate right-hand side v
+        return H.prec_cbs_sweep(p, x, p.f), p.f - H.op_B(p, x)
+    raise ValueError(mode)
+
+
+@pytest.mark.parametrize("mode", ["RESIDUAL", "CBS_STEP", "OP_B", "ADJ_B", "TRUE_RESIDUAL", "PREC_SWEEP"])
+def test_apply_mode_parity(env, mode):
+    capi, c, insts, probs, b, k2, f, V, xs, x = env
+    out = torch.zeros_like(x)
+    norm2 = torch.zeros(b.count, dtype=torch.float64, device="cuda")
+    capi.cbs_apply(c, b, V, f, x, out, getattr(capi, mode), norm2)
+    torch.cuda.synchronize()
+    got = b.unpack(out)
+    n2 = norm2.cpu().numpy()
+    for j, p in enumerate(probs):
+        ref, normed = _oracle(mode, p, xs[j])
+        err = rel_l2(got[j], ref.numpy())
+        assert err <= TOL, (mode, insts[j].ny, insts[j].nx, err)
+        q = ref if normed is None else normed
+        refn = float((q.abs() ** 2).sum())
+        assert n2[j] == pytest.approx(refn, rel=1e-4), (mode, j)
+
+
+def test_cbs_step_in_place(env):
+    capi, c, insts, probs, b, k2, f, V, xs, x = env
+    u = x.clone()
+    capi.cbs_apply(c, b, V, f, u, u, capi.CBS_STEP)
+    torch.cuda.synchronize()
+    got = b.unpack(u)
+    for j, p in enumerate(probs):
+        assert rel_l2(got[j], H.cbs_step(p, torch.from_numpy(xs[j])).numpy()) <= TOL
+
+
+def test_adjoint_dot_product_gpu(env):
+    """<B x, y> = <x, B^* y> with both sides on the GPU (float32)."""
+    capi, c, insts, probs, b, k2, f, V, xs, x = env
+    y = b.pack([random_field((i.ny, i.nx), 500 + j) for j, i in enumerate(insts)])
+    Bx = torch.zeros_like(x)
+    BHy = torch.zeros_like(x)
+    capi.cbs_apply(c, b, V, None, x, Bx, capi.OP_B)
+    capi.cbs_apply(c, b, V, None, y, BHy, capi.ADJ_B)
+    torch.cuda.synchronize()
+    for j in range(b.count):
+        xv, yv = b.view(x, j).double(), b.view(y, j)
+        lhs = torch.vdot(b.view(Bx, j).reshape(-1).to(torch.complex128), yv.reshape(-1).to(torch.complex128))
+        rhs = torch.vdot(b.view(x, j).reshape(-1).to(torch.complex128), b.view(BHy, j).reshape(-1).to(torch.complex128))
+        assert abs(complex(lhs - rhs)) <= 1e-5 * abs(complex(lhs)) + 1e-6
+
+
+def test_empty_batch_is_a_noop():
+    capi, c = ctx()
+    b = capi.Batch([])
+    t = torch.zeros(32, dtype=torch.complex64, device="cuda")
+    capi.cbs_apply(c, b, t, t, t, t, capi.RESIDUAL)
+
+
+@pytest.mark.parametrize("shape", [(97, 96), (96, 2048), (1, 8), (96, 7)])
+def test_unsupported_sizes_are_rejected(shape):
+    capi, c = ctx()
+    b = capi.Batch([shape], k0sq=[1.0], eps=[1.0])
+    t = torch.zeros(b.extent, dtype=torch.complex64, device="cuda")
+    with pytest.raises(capi.NpbsError) as e:
+        capi.cbs_apply(c, b, t, t, t, t, capi.RESIDUAL)
+    assert e.value.status == capi.ERR_UNSUPPORTED_SIZE
+
+
+def test_invalid_arguments_are_rejected():
+    capi, c = ctx()
+    b = capi.Batch([(16, 16)], k0sq=[1.0], eps=[0.0])
+    t = torch.zeros(b.extent, dtype=torch.complex64, device="cuda")
+    with pytest.raises(capi.NpbsError) as e:
+        capi.cbs_apply(c, b, t, t, t, t, capi.RESIDUAL)
+    assert e.value.status == capi.ERR_INVALID_ARG
+    b = capi.Batch([(16, 16)], k0sq=[1.0], eps=[1.0])
+    b.offsets = [8]
+    with pytest.raises(capi.NpbsError) as e:
+        capi.cbs_apply(c, b, t, t, t, t, capi.RESIDUAL)
+    assert e.value.status == capi.ERR_INVALID_ARG
+    b = capi.Batch([(16, 16)], k0sq=[1.0], eps=[1.0])
+    with pytest.raises(capi.NpbsError):
+        capi.cbs_apply(c, b, t, None, t, t, capi.RESIDUAL)

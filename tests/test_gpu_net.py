@@ -1,0 +1,184 @@
+"""GPU network, NPBS solve and training step against the float64 oracle.
+
+BF16 tolerance: bf16 has a unit roundoff of 2^-8 = 3.9e-3; the forward rounds
+activations and weights once per layer over 17 convolutions, so independent
+rounding errors give about sqrt(17) * 3.9e-3 = 1.6e-2 relative error in the
+output.  Forward outputs are checked at relative L2 <= 4e-2, gradients (which
+go through the forward and the backward, twice the roundings) at <= 8e-2
+relative L2 with cosine similarity >= 0.995.
+"""
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import helmholtz as H
+from oracle import unet as U
+from tests.gpu_common import ctx, rel_l2, random_field, setup_batch
+
+pytestmark = pytest.mark.gpu
+
+
+def _weights(seed):
+    return synth.random_weights([s for _, s in U.PARAM_SPEC], seed=seed, out_scale=1.0)
+
+
+def _net(capi, seed):
+    net = capi.Net(0, seed=1)
+    net.set_params(_weights(seed))
+    return net
+
+
+def test_param_count_matches_oracle():
+    capi, c = ctx()
+    assert capi.npbs_net_num_params() == U.n_params()
+
+
+def test_params_roundtrip_and_checkpoint(tmp_path):
+    capi, c = ctx()
+    net = _net(capi, 3)
+    w = _weights(3)
+    assert np.array_equal(net.get_params(), w)
+    p = str(tmp_path / "net.bin")
+    net.save(p)
+    net2 = capi.Net.load(p)
+    assert np.array_equal(net2.get_params(), w)
+
+
+@pytest.mark.parametrize("shape", [(32, 32), (64, 96), (256, 256)])
+def test_network_forward_parity(shape):
+    capi, c = ctx()
+    insts = [synth.small_instance(*shape, seed=40 + j) for j in range(3)]
+    b, k2, f, n, V = setup_batch(capi, c, insts)
+    rs = [random_field(shape, 7 + j) * (10.0 ** j) for j in range(3)]  # scale wrapper: any magnitude
+    r = b.pack(rs)
+    out = torch.zeros_like(r)
+    net = _net(capi, 5)
+    capi.npbs_net_forward(c, net, b, r, n, out)
+    torch.cuda.synchronize()
+    P = U.unflatten(torch.from_numpy(_weights(5)).double())
+    got = b.unpack(out)
+    for j, inst in enumerate(insts):
+        ref = U.correction(torch.from_numpy(rs[j])[None], torch.from_numpy(inst.n)[None], P)[0].numpy()
+        assert rel_l2(got[j], ref) <= 4e-2, (shape, j, rel_l2(got[j], ref))
+
+
+def test_network_backward_matches_autograd():
+    """npbs_net_backward vs torch autograd of the float64 oracle network:
+    L = Re <g, M(r)> for a fixed random g."""
+    capi, c = ctx()
+    shape = (32, 32)
+    insts = [synth.small_instance(*shape, seed=60 + j) for j in range(4)]
+    b, k2, f, n, V = setup_batch(capi, c, insts)
+    rs = [random_field(shape, 70 + j) for j in range(4)]
+    gs = [random_field(shape, 80 + j) for j in range(4)]
+    r, g = b.pack(rs), b.pack(gs)
+    gr = torch.zeros_like(r)
+    net = _net(capi, 6)
+    net.zero_grad()
+    capi.npbs_net_backward(c, net, b, r, n, g, gr)
+    torch.cuda.synchronize()
+    flat = torch.from_numpy(_weights(6)).double().requires_grad_(True)
+    rt = torch.from_numpy(np.stack(rs)).requires_grad_(True)
+    nt = torch.from_numpy(np.stack([i.n for i in insts]))
+    out = U.correction(rt, nt, U.unflatten(flat))
+    gt = torch.from_numpy(np.stack(gs))
+    L = (gt.real * out.real + gt.imag * out.imag).sum()
+    dth, dr = torch.autograd.grad(L, [flat, rt])
+    gw = net.get_grads()
+    ref = dth.numpy()
+    assert rel_l2(gw, ref) <= 8e-2
+    cos = float(np.dot(gw, ref) / (np.linalg.norm(gw) * np.linalg.norm(ref)))
+    assert cos >= 0.995
+    got_r = np.stack(b.unpack(gr))
+    assert rel_l2(got_r, dr.numpy()) <= 8e-2
+
+
+def _train_batch(count=8, N=32):
+    insts = [synth.small_instance(N, N, seed=100 + i, layer=4, ppw=8.0) for i in range(count)]
+    probs = [H.problem_from_instance(i) for i in insts]
+    snaps = [H.cbs_solve(p, tol=0, max_iter=3 * i).u.numpy() for i, p in enumerate(probs)]
+    return insts, probs, snaps
+
+
+def test_train_step_loss_and_gradient_match_oracle():
+    """One training step (4 unrolls, lr = 0) on 8 instances at 32x32: loss and
+    accumulated gradient against the float64 oracle (autograd, itself pinned to
+    central finite differences in the oracle tests)."""
+    capi, c = ctx()
+    insts, probs, snaps = _train_batch()
+    b, k2, f, n, V = setup_batch(capi, c, insts)
+    u0 = b.pack(snaps)
+    net = _net(capi, 4)
+    loss = capi.npbs_train_step(c, net, b, V, f, n, u0, unroll=4, lr=0.0, weight_decay=0.0)
+    flat = torch.from_numpy(_weights(4)).double().requires_grad_(True)
+    Vb, lam, fb, nb = U.problems_to_batch(probs)
+    L = U.unrolled_loss(U.unflatten(flat), Vb, lam, fb, nb, torch.from_numpy(np.stack(snaps)), unroll=4)
+    (g,) = torch.autograd.grad(L, flat)
+    assert loss == pytest.approx(float(L), rel=2e-2)
+    gw = net.get_grads()
+    ref = g.numpy()
+    assert rel_l2(gw, ref) <= 8e-2, rel_l2(gw, ref)
+    cos = float(np.dot(gw, ref) / (np.linalg.norm(gw) * np.linalg.norm(ref)))
+    assert cos >= 0.995
+
+
+def test_train_step_adamw_update():
+    """After one step with lr = 1e-3 every parameter moved by about lr in the
+    direction opposite to the oracle gradient (AdamW's first step is
+    lr * g / (|g| + eps), after decay by 1 - lr wd)."""
+    capi, c = ctx()
+    insts, probs, snaps = _train_batch()
+    b, k2, f, n, V = setup_batch(capi, c, insts)
+    u0 = b.pack(snaps)
+    w0 = _weights(4)
+    net = capi.Net(0, seed=1)
+    net.set_params(w0)
+    lr, wd = 1e-3, 1e-2
+    capi.npbs_train_step(c, net, b, V, f, n, u0, unroll=4, lr=lr, weight_decay=wd)
+    w1 = net.get_params().astype(np.float64)
+    flat = torch.from_numpy(w0).double().requires_grad_(True)
+    Vb, lam, fb, nb = U.problems_to_batch(probs)
+    L = U.unrolled_loss(U.unflatten(flat), Vb, lam, fb, nb, torch.from_numpy(np.stack(snaps)), unroll=4)
+    (g,) = torch.autograd.grad(L, flat)
+    new, _, _ = U.adamw_step(flat.detach(), g, torch.zeros_like(g), torch.zeros_like(g), 1, lr=lr, weight_decay=wd)
+    d_gpu = w1 - w0.astype(np.float64) * (1 - lr * wd)
+    d_ref = new.numpy() - w0.astype(np.float64) * (1 - lr * wd)
+    assert np.all(np.abs(d_gpu) <= lr * 1.001 + 1e-7)
+    big = np.abs(g.numpy()) > 1e-2 * np.abs(g.numpy()).max()
+    agree = np.mean(np.sign(d_gpu[big]) == np.sign(d_ref[big]))
+    assert agree >= 0.97, agree
+
+
+def test_npbs_solve_short_trajectory_parity():
+    """Two NPBS updates from u = 0 (no convergence test) vs the oracle's NPBS
+    iteration with the same weights."""
+    capi, c = ctx()
+    insts = [synth.small_instance(64, 64, seed=90 + j, layer=8) for j in range(2)]
+    b, k2, f, n, V = setup_batch(capi, c, insts)
+    net = _net(capi, 8)
+    u = torch.zeros(b.extent, dtype=torch.complex128, device="cuda")
+    st, rep = capi.npbs_solve(c, net, b, V, f, n, u, rtol=0.0, max_iter=2, check_every=2)
+    P = U.unflatten(torch.from_numpy(_weights(8)).double())
+    got = b.unpack(u)
+    for j, inst in enumerate(insts):
+        p = H.problem_from_instance(inst)
+        M = lambda r: U.correction(r[None], p.n[None], P)[0]
+        ref = H.npbs_solve(p, M, tol=0, max_iter=2)
+        assert rel_l2(got[j], ref.u.numpy()) <= 5e-2
+
+
+def test_npbs_solve_converges_with_guard():
+    """With an untrained network the divergence guard falls back to CBS where
+    needed; every instance reaches rTol 1e-5 as judged by the oracle."""
+    capi, c = ctx()
+    insts = [synth.small_instance(64, 64, seed=95 + j, layer=8) for j in range(3)]
+    b, k2, f, n, V = setup_batch(capi, c, insts)
+    net = capi.Net(0, seed=3)
+    u = torch.zeros(b.extent, dtype=torch.complex128, device="cuda")
+    st, rep = capi.npbs_solve(c, net, b, V, f, n, u, rtol=1e-5, max_iter=20000, check_every=8)
+    assert st == capi.OK, rep
+    got = b.unpack(u)
+    for j, inst in enumerate(insts):
+        r = H.rtol(H.problem_from_instance(inst), torch.from_numpy(got[j]))
+        assert r <= 1e-5, (j, r, rep)
