@@ -192,7 +192,7 @@ def main():
 
     def step():
         u.zero_()
-        return capi.cbs_solve(ctx, b, V, f, u, rtol=TOL, max_iter=20000, check_every=args.check_every)
+        return capi.cbs_solve(ctx, b, k2, f, u, rtol=TOL, max_iter=20000, check_every=args.check_every)
 
     for _ in range(args.warmup):
         st, rep = step()

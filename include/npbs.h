@@ -155,11 +155,14 @@ npbs_status cbs_apply(npbs_ctx* ctx, const npbs_batch* batch, const void* V, con
  * correction equation A delta = f - A u produce the same iterates as the
  * uninterrupted iteration, so iteration counts are those of the method; the
  * float64 residual removes the float32 floor (about 1e-5 for complex64 CBS).
+ * k2: DEVICE complex64 k(x)^2 of every instance (the problem data; the solver
+ * forms V = k^2 - k0^2 - i eps from it with the batch's k0sq / eps, and uses
+ * k^2 itself, exactly, in the float64 residual f - A u).
  * u: DEVICE complex128, initial guess on entry, solution on exit.
  * Converged instances are masked out of later launches.  Synchronise. */
 
 /* Stationary CBS (Eq. CBS) to opts->rtol. */
-npbs_status cbs_solve(npbs_ctx* ctx, const npbs_batch* batch, const void* V, const void* f,
+npbs_status cbs_solve(npbs_ctx* ctx, const npbs_batch* batch, const void* k2, const void* f,
                       void* u, const npbs_solve_opts* opts, npbs_report* report,
                       npbs_stream stream);
 
@@ -169,14 +172,14 @@ npbs_status cbs_solve(npbs_ctx* ctx, const npbs_batch* batch, const void* V, con
  * guard: an instance whose float64 rTol did not decrease between two refresh
  * points continues with plain CBS steps (report->flags). */
 npbs_status npbs_solve(npbs_ctx* ctx, const npbs_net* net, const npbs_batch* batch,
-                       const void* V, const void* f, const float* n, void* u,
+                       const void* k2, const void* f, const float* n, void* u,
                        const npbs_solve_opts* opts, npbs_report* report, npbs_stream stream);
 
 /* Restarted flexible GMRES on B u = G f (Eq. LS_discrete), restart length
  * `restart` (1..64), right preconditioner precond: 0 none, 1 `cbs_sweeps`
  * CBS Richardson sweeps, 2 the network of `net` (may be NULL unless precond = 2). */
 npbs_status fgmres_solve(npbs_ctx* ctx, const npbs_net* net, const npbs_batch* batch,
-                         const void* V, const void* f, const float* n, void* u,
+                         const void* k2, const void* f, const float* n, void* u,
                          int32_t restart, int32_t precond, int32_t cbs_sweeps,
                          const npbs_solve_opts* opts, npbs_report* report, npbs_stream stream);
 

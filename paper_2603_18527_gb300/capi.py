@@ -261,23 +261,23 @@ def _opts(rtol, max_iter, check_every, use_graph):
     return npbs_solve_opts(float(rtol), int(max_iter), int(check_every), int(use_graph))
 
 
-def cbs_solve(ctx: Context, batch: Batch, V, f, u, rtol=1e-5, max_iter=2500, check_every=16, use_graph=1,
+def cbs_solve(ctx: Context, batch: Batch, k2, f, u, rtol=1e-5, max_iter=2500, check_every=16, use_graph=1,
               stream=None):
     """Returns (status, report dict); u (complex128) is updated in place."""
     rep = Report(batch.count)
     o = _opts(rtol, max_iter, check_every, use_graph)
-    st = lib().cbs_solve(ctx.handle, C.byref(batch.c_batch()), _ptr(V), _ptr(f), _ptr(u), C.byref(o),
+    st = lib().cbs_solve(ctx.handle, C.byref(batch.c_batch()), _ptr(k2), _ptr(f), _ptr(u), C.byref(o),
                          C.byref(rep.c), _stream(stream))
     if st not in (OK, NOT_CONVERGED):
         ctx.check(st)
     return st, rep.as_dict()
 
 
-def npbs_solve(ctx: Context, net: "Net", batch: Batch, V, f, n, u, rtol=1e-5, max_iter=2500, check_every=4,
+def npbs_solve(ctx: Context, net: "Net", batch: Batch, k2, f, n, u, rtol=1e-5, max_iter=2500, check_every=4,
                use_graph=1, stream=None):
     rep = Report(batch.count)
     o = _opts(rtol, max_iter, check_every, use_graph)
-    st = lib().npbs_solve(ctx.handle, net.handle, C.byref(batch.c_batch()), _ptr(V), _ptr(f), _ptr(n), _ptr(u),
+    st = lib().npbs_solve(ctx.handle, net.handle, C.byref(batch.c_batch()), _ptr(k2), _ptr(f), _ptr(n), _ptr(u),
                           C.byref(o), C.byref(rep.c), _stream(stream))
     if st not in (OK, NOT_CONVERGED):
         ctx.check(st)
@@ -287,11 +287,11 @@ def npbs_solve(ctx: Context, net: "Net", batch: Batch, V, f, n, u, rtol=1e-5, ma
 PRECOND_NONE, PRECOND_CBS, PRECOND_NPBS = 0, 1, 2
 
 
-def fgmres_solve(ctx: Context, net, batch: Batch, V, f, n, u, restart=20, precond=PRECOND_NONE, cbs_sweeps=16,
+def fgmres_solve(ctx: Context, net, batch: Batch, k2, f, n, u, restart=20, precond=PRECOND_NONE, cbs_sweeps=16,
                  rtol=1e-5, max_iter=2500, stream=None):
     rep = Report(batch.count)
     o = _opts(rtol, max_iter, 1, 0)
-    st = lib().fgmres_solve(ctx.handle, net.handle if net is not None else None, C.byref(batch.c_batch()), _ptr(V),
+    st = lib().fgmres_solve(ctx.handle, net.handle if net is not None else None, C.byref(batch.c_batch()), _ptr(k2),
                             _ptr(f), _ptr(n), _ptr(u), int(restart), int(precond), int(cbs_sweeps), C.byref(o),
                             C.byref(rep.c), _stream(stream))
     if st not in (OK, NOT_CONVERGED):

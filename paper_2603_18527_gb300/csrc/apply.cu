@@ -167,8 +167,17 @@ __global__ void __launch_bounds__(kThreads) k_rows_inverse(BatchDev bd, ApplyArg
         if constexpr (MODE == kTrueRes64) {
             // rho = f + k^2 u - z with k^2 = V + k0^2 + i eps
             const double2 u = a.uhi[g];
-            const float2 v = ld(a.V + g), f = ld(a.f + g);
-            const double kr = (double)v.x + in.k0sq, ki = (double)v.y + in.eps;
+            const float2 f = ld(a.f + g);
+            double kr, ki;
+            if (a.k2) {
+                const float2 k = ld(a.k2 + g);
+                kr = (double)k.x;
+                ki = (double)k.y;
+            } else {
+                const float2 v = ld(a.V + g);
+                kr = (double)v.x + in.k0sq;
+                ki = (double)v.y + in.eps;
+            }
             const double rr = (double)f.x + kr * u.x - ki * u.y - zr;
             const double ri = (double)f.y + kr * u.y + ki * u.x - zi;
             if (a.out) a.out[g] = make_float2((float)rr, (float)ri);

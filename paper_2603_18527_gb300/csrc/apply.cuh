@@ -23,6 +23,7 @@ struct ApplyArgs {
     void* scratch;      // spectrum between passes (complex64 or complex128 per point)
     double2* uhi;       // kTrueRes64: complex128 solution (updated in place)
     const float2* delta;  // kTrueRes64: complex64 correction folded into uhi (nullable)
+    const float2* k2;     // kTrueRes64: k^2 (nullable: then k^2 = V + k0^2 + i eps)
 };
 
 // Opt the apply kernels into their dynamic shared memory (once per device).

@@ -59,7 +59,7 @@ struct npbs_ctx {
     std::string err;
     std::map<std::string, std::unique_ptr<npbs::Plan>> plans;
     npbs::DevBuf scratch;   // spectrum between apply passes
-    npbs::DevBuf work[8];   // solver workspaces
+    npbs::DevBuf work[12];  // solver workspaces
     npbs::DevBuf net_ws;    // network activations
     cudaStream_t solve_stream = nullptr;  // capturable stream the solvers run on
     cudaEvent_t solve_event = nullptr;

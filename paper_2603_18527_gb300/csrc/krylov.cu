@@ -201,7 +201,7 @@ struct Fg {
 
 }  // namespace
 
-extern "C" npbs_status fgmres_solve(npbs_ctx* ctx, const npbs_net* net, const npbs_batch* batch, const void* V,
+extern "C" npbs_status fgmres_solve(npbs_ctx* ctx, const npbs_net* net, const npbs_batch* batch, const void* k2,
                                     const void* f, const float* n, void* u, int32_t restart, int32_t precond,
                                     int32_t cbs_sweeps, const npbs_solve_opts* opts, npbs_report* report,
                                     npbs_stream stream) {
@@ -210,7 +210,7 @@ extern "C" npbs_status fgmres_solve(npbs_ctx* ctx, const npbs_net* net, const np
     const Plan* pl = get_plan(ctx, batch, &st);
     if (!pl) return st;
     if (pl->count == 0) return NPBS_OK;
-    st = check_solve_args(ctx, opts, V, f, u);
+    st = check_solve_args(ctx, opts, k2, f, u);
     if (st != NPBS_OK) return st;
     if (restart < 1 || restart > kMaxRestart)
         return set_err(ctx, NPBS_ERR_INVALID_ARG, "fgmres_solve: restart must be in [1, 64]");
@@ -223,7 +223,10 @@ extern "C" npbs_status fgmres_solve(npbs_ctx* ctx, const npbs_net* net, const np
     const int m = restart;
     const int ldh = m + 1;
     const long long ext = std::max<long long>(pl->extent, 1);
-    const float2* Vp = static_cast<const float2*>(V);
+    const float2* K2 = static_cast<const float2*>(k2);
+    const float2* Vp = nullptr;
+    st = solver_potential(ctx, *pl, K2, s, &Vp);
+    if (st != NPBS_OK) return st;
     const float2* fp = static_cast<const float2*>(f);
     double2* up = static_cast<double2*>(u);
 
@@ -232,8 +235,17 @@ extern "C" npbs_status fgmres_solve(npbs_ctx* ctx, const npbs_net* net, const np
     NPBS_CK(ctx, ctx->work[3].ensure(sizeof(float2) * ext * (size_t)(m + 1 + nz + 1)));
     NPBS_CK(ctx, ctx->work[0].ensure(ext * sizeof(float2)));
     NPBS_CK(ctx, ctx->work[1].ensure(ext * sizeof(float2)));
-    const size_t small = sizeof(double2) * ((size_t)cnt * (ldh * m + 2 * ldh + 3 * m + 2 * ldh)) +
-                         sizeof(double) * 8 * cnt + sizeof(int) * 4 * cnt + 1024;
+    // small per-instance arrays carved from one buffer (each rounded to 256 bytes)
+    const size_t small_sizes[] = {sizeof(double2) * cnt * ldh * m, sizeof(double2) * cnt * ldh,
+                                  sizeof(double2) * cnt * ldh,     sizeof(double2) * cnt * m,
+                                  sizeof(double2) * cnt * m,       sizeof(double2) * cnt * m,
+                                  sizeof(double2) * cnt * ldh,     sizeof(double) * cnt,
+                                  sizeof(double) * cnt,            sizeof(double) * cnt,
+                                  sizeof(double) * cnt,            sizeof(double) * cnt,
+                                  sizeof(int) * cnt,               sizeof(int) * cnt,
+                                  sizeof(int) * cnt};
+    size_t small = 0;
+    for (size_t b : small_sizes) small += (b + 255) / 256 * 256;
     NPBS_CK(ctx, ctx->work[4].ensure(small));
     NPBS_CK(ctx, ctx->scratch.ensure(ext * 16));
     float2* Vb = static_cast<float2*>(ctx->work[3].p);
@@ -242,6 +254,7 @@ extern "C" npbs_status fgmres_solve(npbs_ctx* ctx, const npbs_net* net, const np
     float2* delta = static_cast<float2*>(ctx->work[0].p);
     float2* rho = static_cast<float2*>(ctx->work[1].p);
     char* sp = static_cast<char*>(ctx->work[4].p);
+    char* const sp_end = sp + small;
     auto take = [&](size_t bytes) { char* p = sp; sp += (bytes + 255) / 256 * 256; return p; };
     double2* H = reinterpret_cast<double2*>(take(sizeof(double2) * cnt * ldh * m));
     double2* h1 = reinterpret_cast<double2*>(take(sizeof(double2) * cnt * ldh));
@@ -258,6 +271,7 @@ extern "C" npbs_status fgmres_solve(npbs_ctx* ctx, const npbs_net* net, const np
     int* act_run = reinterpret_cast<int*>(take(sizeof(int) * cnt));   // instances still solving
     int* act_cyc = reinterpret_cast<int*>(take(sizeof(int) * cnt));   // instances still in this cycle
     int* ksteps = reinterpret_cast<int*>(take(sizeof(int) * cnt));
+    if (sp > sp_end) return set_err(ctx, NPBS_ERR_INVALID_ARG, "fgmres_solve: internal workspace layout error");
 
     const int vb = pl->nvec;
     const VecItem* vi = pl->vitems;
@@ -274,6 +288,7 @@ extern "C" npbs_status fgmres_solve(npbs_ctx* ctx, const npbs_net* net, const np
         a.norm2 = rho2;
         a.norm2b = f2;
         a.uhi = up;
+        a.k2 = K2;
         a.delta = fold ? delta : nullptr;
         npbs_status s2 = run_apply(ctx, *pl, kTrueRes64, a, fold ? act_run : nullptr, s);
         if (s2 != NPBS_OK) return s2;

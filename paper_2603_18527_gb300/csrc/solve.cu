@@ -28,7 +28,27 @@ struct GraphGuard {
     }
 };
 
-npbs_status refine_driver(npbs_ctx* ctx, const Plan& pl, const float2* V, const float2* f, double2* u,
+__global__ void k_build_V(const VecItem* items, const InstDev* inst, const float2* k2, float2* V) {
+    const VecItem it = items[blockIdx.x];
+    const InstDev in = inst[it.inst];
+    const long long base = in.offset + it.start;
+    for (int e = threadIdx.x; e < it.len; e += blockDim.x) {
+        const float2 k = k2[base + e];
+        V[base + e] = make_float2((float)((double)k.x - in.k0sq), (float)((double)k.y - in.eps));
+    }
+}
+
+npbs_status solver_potential(npbs_ctx* ctx, const Plan& pl, const float2* k2, cudaStream_t st, const float2** V) {
+    NPBS_CK(ctx, ctx->work[8].ensure(sizeof(float2) * (size_t)std::max<long long>(pl.extent, 1)));
+    float2* v = static_cast<float2*>(ctx->work[8].p);
+    k_build_V<<<pl.nvec, 256, 0, st>>>(pl.vitems, pl.inst, k2, v);
+    NPBS_CK(ctx, cudaGetLastError());
+    ctx->count(st, 1);
+    *V = v;
+    return NPBS_OK;
+}
+
+npbs_status refine_driver(npbs_ctx* ctx, const Plan& pl, const float2* k2, const float2* V, const float2* f, double2* u,
                           const npbs_solve_opts& o, npbs_report* rep, cudaStream_t st, const InnerStep& step,
                           RefineWork& w) {
     const int n = pl.count;
@@ -57,6 +77,7 @@ npbs_status refine_driver(npbs_ctx* ctx, const Plan& pl, const float2* V, const 
         a.norm2 = rho2;
         a.norm2b = f2;
         a.uhi = u;
+        a.k2 = k2;
         a.delta = fold ? w.delta : nullptr;
         npbs_status s = run_apply(ctx, pl, kTrueRes64, a, fold ? active : nullptr, st);
         if (s != NPBS_OK) return s;
@@ -176,7 +197,8 @@ npbs_status refine_driver(npbs_ctx* ctx, const Plan& pl, const float2* V, const 
                 }
                 const double red = std::sqrt(hnb[j] / nb_first[j]);
                 const double est = rt_cycle[j] * red;
-                if (!std::isfinite(hnb[j]) || est <= o.rtol || red <= w.max_reduction || iters[j] >= o.max_iter)
+                if (!std::isfinite(hnb[j]) || est <= o.rtol || red <= w.max_reduction || red > 2.0 ||
+                    iters[j] >= o.max_iter)
                     go = true;
             }
             if (go || cycle_its >= w.max_cycle) break;
@@ -209,10 +231,10 @@ npbs_status solve_stream_begin(npbs_ctx* ctx, cudaStream_t user, cudaStream_t* w
     return NPBS_OK;
 }
 
-npbs_status check_solve_args(npbs_ctx* ctx, const npbs_solve_opts* o, const void* V, const void* f, const void* u) {
+npbs_status check_solve_args(npbs_ctx* ctx, const npbs_solve_opts* o, const void* k2, const void* f, const void* u) {
     if (!o || !(o->rtol >= 0.0) || o->max_iter < 0 || o->check_every < 1)
         return set_err(ctx, NPBS_ERR_INVALID_ARG, "solve options: need rtol >= 0, max_iter >= 0, check_every >= 1");
-    if (!V || !f || !u) return set_err(ctx, NPBS_ERR_INVALID_ARG, "solve: NULL field pointer");
+    if (!k2 || !f || !u) return set_err(ctx, NPBS_ERR_INVALID_ARG, "solve: NULL field pointer");
     return NPBS_OK;
 }
 
@@ -220,20 +242,23 @@ npbs_status check_solve_args(npbs_ctx* ctx, const npbs_solve_opts* o, const void
 
 using namespace npbs;
 
-extern "C" npbs_status cbs_solve(npbs_ctx* ctx, const npbs_batch* batch, const void* V, const void* f, void* u,
+extern "C" npbs_status cbs_solve(npbs_ctx* ctx, const npbs_batch* batch, const void* k2, const void* f, void* u,
                                  const npbs_solve_opts* opts, npbs_report* report, npbs_stream stream) {
     if (!ctx) return NPBS_ERR_INVALID_ARG;
     npbs_status st;
     const Plan* pl = get_plan(ctx, batch, &st);
     if (!pl) return st;
     if (pl->count == 0) return NPBS_OK;
-    st = check_solve_args(ctx, opts, V, f, u);
+    st = check_solve_args(ctx, opts, k2, f, u);
     if (st != NPBS_OK) return st;
     cudaStream_t s = nullptr;
     st = solve_stream_begin(ctx, reinterpret_cast<cudaStream_t>(stream), &s);
     if (st != NPBS_OK) return st;
     RefineWork w;
-    const float2* Vp = static_cast<const float2*>(V);
+    const float2* K2 = static_cast<const float2*>(k2);
+    const float2* Vp = nullptr;
+    st = solver_potential(ctx, *pl, K2, s, &Vp);
+    if (st != NPBS_OK) return st;
     // inner step: delta <- delta + gamma (G(V delta + rho) - delta), in place
     InnerStep step = [&](bool last) -> npbs_status {
         ApplyArgs a{};
@@ -244,8 +269,8 @@ extern "C" npbs_status cbs_solve(npbs_ctx* ctx, const npbs_batch* batch, const v
         a.norm2 = last ? w.nb : nullptr;
         return run_apply(ctx, *pl, NPBS_CBS_STEP, a, w.active, s);
     };
-    return refine_driver(ctx, *pl, Vp, static_cast<const float2*>(f), static_cast<double2*>(u), *opts, report, s,
-                         step, w);
+    return refine_driver(ctx, *pl, K2, Vp, static_cast<const float2*>(f), static_cast<double2*>(u), *opts, report,
+                         s, step, w);
 }
 
 #include "net.cuh"
@@ -274,7 +299,7 @@ __global__ void k_cbs_fallback(const VecItem* items, const InstDev* inst, const 
 //   delta <- delta + M(G(V delta + rho) - delta)
 // on the correction equation; r = G(V delta + rho) - delta equals the Born
 // residual of u + delta for the original problem.
-extern "C" npbs_status npbs_solve(npbs_ctx* ctx, const npbs_net* net, const npbs_batch* batch, const void* V,
+extern "C" npbs_status npbs_solve(npbs_ctx* ctx, const npbs_net* net, const npbs_batch* batch, const void* k2,
                                   const void* f, const float* n, void* u, const npbs_solve_opts* opts,
                                   npbs_report* report, npbs_stream stream) {
     if (!ctx) return NPBS_ERR_INVALID_ARG;
@@ -283,16 +308,19 @@ extern "C" npbs_status npbs_solve(npbs_ctx* ctx, const npbs_net* net, const npbs
     const Plan* pl = get_plan(ctx, batch, &st);
     if (!pl) return st;
     if (pl->count == 0) return NPBS_OK;
-    st = check_solve_args(ctx, opts, V, f, u);
+    st = check_solve_args(ctx, opts, k2, f, u);
     if (st != NPBS_OK) return st;
     cudaStream_t s = nullptr;
     st = solve_stream_begin(ctx, reinterpret_cast<cudaStream_t>(stream), &s);
+    if (st != NPBS_OK) return st;
+    const float2* K2 = static_cast<const float2*>(k2);
+    const float2* Vp = nullptr;
+    st = solver_potential(ctx, *pl, K2, s, &Vp);
     if (st != NPBS_OK) return st;
     const size_t ext = (size_t)std::max<long long>(pl->extent, 1);
     NPBS_CK(ctx, ctx->work[6].ensure(ext * sizeof(float2)));
     float2* r = static_cast<float2*>(ctx->work[6].p);
     const Net& N = *reinterpret_cast<const Net*>(net);
-    const float2* Vp = static_cast<const float2*>(V);
     NPBS_CK(ctx, ctx->work[2].ensure(sizeof(double) * 4 * pl->count + sizeof(int) * pl->count + 64));
     NPBS_CK(ctx, ctx->work[7].ensure(sizeof(int) * pl->count + 64));
     int* cbs_mode = static_cast<int*>(ctx->work[7].p);
@@ -339,6 +367,6 @@ extern "C" npbs_status npbs_solve(npbs_ctx* ctx, const npbs_net* net, const npbs
         ctx->count(s, 1);
         return NPBS_OK;
     };
-    return refine_driver(ctx, *pl, Vp, static_cast<const float2*>(f), static_cast<double2*>(u), *opts, report, s,
-                         step, w);
+    return refine_driver(ctx, *pl, K2, Vp, static_cast<const float2*>(f), static_cast<double2*>(u), *opts, report,
+                         s, step, w);
 }

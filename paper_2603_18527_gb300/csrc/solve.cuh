@@ -37,10 +37,13 @@ using InnerStep = std::function<npbs_status(bool last)>;
 // caller's stream (which may be the legacy default stream, not capturable).
 npbs_status solve_stream_begin(npbs_ctx* ctx, cudaStream_t user, cudaStream_t* work);
 
-npbs_status refine_driver(npbs_ctx* ctx, const Plan& pl, const float2* V, const float2* f, double2* u,
+// V = k^2 - k0^2 - i eps (float32) for every instance, into a context buffer.
+npbs_status solver_potential(npbs_ctx* ctx, const Plan& pl, const float2* k2, cudaStream_t st, const float2** V);
+
+npbs_status refine_driver(npbs_ctx* ctx, const Plan& pl, const float2* k2, const float2* V, const float2* f, double2* u,
                           const npbs_solve_opts& o, npbs_report* rep, cudaStream_t st, const InnerStep& step,
                           RefineWork& w);
-npbs_status check_solve_args(npbs_ctx* ctx, const npbs_solve_opts* o, const void* V, const void* f,
+npbs_status check_solve_args(npbs_ctx* ctx, const npbs_solve_opts* o, const void* k2, const void* f,
                              const void* u);
 
 }  // namespace npbs

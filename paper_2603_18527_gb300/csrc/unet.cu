@@ -114,23 +114,23 @@ __global__ void k_pack_input(const SlotDev sd, const float2* r, const float* n, 
     }
 }
 
-// 2x2 average pooling of channels [0, C) of src (pixel stride S) -> dst [B][R/2][R/2][C]
-__global__ void k_pool(int nb, int R, int C, int S, const bf16* src, bf16* dst) {
-    const int Ro = R / 2;
+// 2x2 average pooling of channels [0, C) of src [B][R][Rw][S] -> dst [B][R/2][Rw/2][C]
+__global__ void k_pool(int nb, int R, int Rw, int C, int S, const bf16* src, bf16* dst) {
+    const int Ro = R / 2, Rwo = Rw / 2;
     const int cc = C / 8;
-    const long long total = (long long)nb * Ro * Ro * cc;
+    const long long total = (long long)nb * Ro * Rwo * cc;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
         const int c8 = (int)(i % cc);
         const long long q = i / cc;
-        const int x = (int)(q % Ro);
-        const long long t = q / Ro;
+        const int x = (int)(q % Rwo);
+        const long long t = q / Rwo;
         const int y = (int)(t % Ro), b = (int)(t / Ro);
         float acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
 #pragma unroll
         for (int dy = 0; dy < 2; ++dy)
 #pragma unroll
             for (int dx = 0; dx < 2; ++dx) {
-                const long long sp = ((long long)b * R + 2 * y + dy) * R + 2 * x + dx;
+                const long long sp = ((long long)b * R + 2 * y + dy) * Rw + 2 * x + dx;
                 const uint4 v = *reinterpret_cast<const uint4*>(src + sp * S + c8 * 8);
                 const bf16* e = reinterpret_cast<const bf16*>(&v);
 #pragma unroll
@@ -269,42 +269,42 @@ __global__ void k_gelu_bwd(long long P, int C, const float* dy, int ds, int dof,
 }
 
 // adjoint of 2x2 average pooling, accumulated: dst[b][2y+dy][2x+dx][c] (stride S)
-// += 0.25 * src[b][y][x][c]   (src [B][R][R][C], R the coarse size)
-__global__ void k_pool_adj_add(int nb, int R, int C, const float* src, float* dst, int S) {
-    const long long total = (long long)nb * R * R * C;
+// += 0.25 * src[b][y][x][c]   (src [B][R][Rw][C], R x Rw the coarse size)
+__global__ void k_pool_adj_add(int nb, int R, int Rw, int C, const float* src, float* dst, int S) {
+    const long long total = (long long)nb * R * Rw * C;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
         const int c = (int)(i % C);
         const long long q = i / C;
-        const int x = (int)(q % R);
-        const long long t = q / R;
+        const int x = (int)(q % Rw);
+        const long long t = q / Rw;
         const int y = (int)(t % R), b = (int)(t / R);
         const float v = 0.25f * src[i];
 #pragma unroll
         for (int dy = 0; dy < 2; ++dy)
 #pragma unroll
             for (int dx = 0; dx < 2; ++dx) {
-                const long long dp = ((long long)b * 2 * R + 2 * y + dy) * 2 * R + 2 * x + dx;
+                const long long dp = ((long long)b * 2 * R + 2 * y + dy) * 2 * Rw + 2 * x + dx;
                 dst[dp * S + c] += v;
             }
     }
 }
 
 // adjoint of nearest x2 upsampling: dst[b][y][x][c] = sum of the 2x2 block of src
-// (src [B][2R][2R][C], dst [B][R][R][C])
-__global__ void k_sumpool(int nb, int R, int C, const float* src, float* dst) {
-    const long long total = (long long)nb * R * R * C;
+// (src [B][2R][2Rw][C], dst [B][R][Rw][C])
+__global__ void k_sumpool(int nb, int R, int Rw, int C, const float* src, float* dst) {
+    const long long total = (long long)nb * R * Rw * C;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
         const int c = (int)(i % C);
         const long long q = i / C;
-        const int x = (int)(q % R);
-        const long long t = q / R;
+        const int x = (int)(q % Rw);
+        const long long t = q / Rw;
         const int y = (int)(t % R), b = (int)(t / R);
         float acc = 0.f;
 #pragma unroll
         for (int dy = 0; dy < 2; ++dy)
 #pragma unroll
             for (int dx = 0; dx < 2; ++dx) {
-                const long long sp = ((long long)b * 2 * R + 2 * y + dy) * 2 * R + 2 * x + dx;
+                const long long sp = ((long long)b * 2 * R + 2 * y + dy) * 2 * Rw + 2 * x + dx;
                 acc += src[sp * C + c];
             }
         dst[i] = acc;
@@ -585,7 +585,7 @@ static cudaError_t forward_body(const Net& net, const Acts& A, cudaStream_t st, 
             xs = 16;
         } else {
             const int Cp = ch[l - 1];
-            k_pool<<<grid_for((long long)nb * R * Rw * Cp / 8), 256, 0, st>>>(nb, 2 * R, Cp, 2 * Cp, A.cat[l - 1], A.in[l]);
+            k_pool<<<grid_for((long long)nb * R * Rw * Cp / 8), 256, 0, st>>>(nb, 2 * R, 2 * Rw, Cp, 2 * Cp, A.cat[l - 1], A.in[l]);
             ++k;
             xin = A.in[l];
             xs = Cp;
@@ -769,7 +769,7 @@ npbs_status net_run_backward(npbs_ctx* ctx, Net& net, const NetRun& run, const f
             if (e == cudaSuccess) e = dgrad(iu, R, Rw, A.tmp, uss, 0);
             if (e != cudaSuccess) break;
             float* dsrc = l == 2 ? A.dcat[3] : A.de[l + 1];
-            k_sumpool<<<grid_for((long long)nb * (R / 2) * (Rw / 2) * uss), 256, 0, st>>>(nb, R / 2, uss, A.tmp, dsrc);
+            k_sumpool<<<grid_for((long long)nb * (R / 2) * (Rw / 2) * uss), 256, 0, st>>>(nb, R / 2, Rw / 2, uss, A.tmp, dsrc);
             ++k;
         }
         // encoder levels 3 .. 0
@@ -793,7 +793,7 @@ npbs_status net_run_backward(npbs_ctx* ctx, Net& net, const NetRun& run, const f
                 e = dgrad(enc_a(l), R, Rw, A.din[l], ch[l - 1], 0);
                 if (e == cudaSuccess) {
                     k_pool_adj_add<<<grid_for((long long)nb * R * Rw * ch[l - 1]), 256, 0, st>>>(
-                        nb, R, ch[l - 1], A.din[l], A.dcat[l - 1], 2 * ch[l - 1]);
+                        nb, R, Rw, ch[l - 1], A.din[l], A.dcat[l - 1], 2 * ch[l - 1]);
                     ++k;
                 }
             }

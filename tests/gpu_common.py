@@ -25,6 +25,15 @@ def setup_batch(capi, c, insts):
     return b, k2, f, n, V
 
 
+def oracle_problem(inst):
+    """The oracle's problem on exactly the data handed to the GPU (k^2, f and n
+    rounded to the complex64 / float32 inputs of the library)."""
+    k2 = inst.k2.astype(np.complex64).astype(np.complex128)
+    f = inst.f.astype(np.complex64).astype(np.complex128)
+    n = inst.n.astype(np.float32).astype(np.float64)
+    return H.make_problem(k2, f, inst.h, n=n)
+
+
 def rel_l2(a, b):
     a = np.asarray(a)
     b = np.asarray(b)

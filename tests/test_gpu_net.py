@@ -14,7 +14,7 @@ import torch
 import synth
 from oracle import helmholtz as H
 from oracle import unet as U
-from tests.gpu_common import ctx, rel_l2, random_field, setup_batch
+from tests.gpu_common import oracle_problem, ctx, rel_l2, random_field, setup_batch
 
 pytestmark = pytest.mark.gpu
 
@@ -158,11 +158,11 @@ def test_npbs_solve_short_trajectory_parity():
     b, k2, f, n, V = setup_batch(capi, c, insts)
     net = _net(capi, 8)
     u = torch.zeros(b.extent, dtype=torch.complex128, device="cuda")
-    st, rep = capi.npbs_solve(c, net, b, V, f, n, u, rtol=0.0, max_iter=2, check_every=2)
+    st, rep = capi.npbs_solve(c, net, b, k2, f, n, u, rtol=0.0, max_iter=2, check_every=2)
     P = U.unflatten(torch.from_numpy(_weights(8)).double())
     got = b.unpack(u)
     for j, inst in enumerate(insts):
-        p = H.problem_from_instance(inst)
+        p = oracle_problem(inst)
         M = lambda r: U.correction(r[None], p.n[None], P)[0]
         ref = H.npbs_solve(p, M, tol=0, max_iter=2)
         assert rel_l2(got[j], ref.u.numpy()) <= 5e-2
@@ -176,9 +176,9 @@ def test_npbs_solve_converges_with_guard():
     b, k2, f, n, V = setup_batch(capi, c, insts)
     net = capi.Net(0, seed=3)
     u = torch.zeros(b.extent, dtype=torch.complex128, device="cuda")
-    st, rep = capi.npbs_solve(c, net, b, V, f, n, u, rtol=1e-5, max_iter=20000, check_every=8)
+    st, rep = capi.npbs_solve(c, net, b, k2, f, n, u, rtol=1e-5, max_iter=20000, check_every=8)
     assert st == capi.OK, rep
     got = b.unpack(u)
     for j, inst in enumerate(insts):
-        r = H.rtol(H.problem_from_instance(inst), torch.from_numpy(got[j]))
+        r = H.rtol(oracle_problem(inst), torch.from_numpy(got[j]))
         assert r <= 1e-5, (j, r, rep)

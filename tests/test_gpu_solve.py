@@ -6,7 +6,7 @@ import torch
 
 import synth
 from oracle import helmholtz as H
-from tests.gpu_common import ctx, rel_l2, setup_batch
+from tests.gpu_common import oracle_problem, ctx, rel_l2, setup_batch
 
 pytestmark = pytest.mark.gpu
 
@@ -17,11 +17,11 @@ def test_cbs_solve_96_to_1e6():
     insts = synth.workload_96() + [synth.small_instance(64, 64, seed=3, layer=8), synth.small_instance(48, 96, seed=4)]
     b, k2, f, n, V = setup_batch(capi, c, insts)
     u = torch.zeros(b.extent, dtype=torch.complex128, device="cuda")
-    st, rep = capi.cbs_solve(c, b, V, f, u, rtol=1e-6, max_iter=20000, check_every=16)
+    st, rep = capi.cbs_solve(c, b, k2, f, u, rtol=1e-6, max_iter=20000, check_every=16)
     assert st == capi.OK, rep
     got = b.unpack(u)
     for j, inst in enumerate(insts):
-        p = H.problem_from_instance(inst)
+        p = oracle_problem(inst)
         r = H.rtol(p, torch.from_numpy(got[j]))
         assert r <= 1e-6, (j, r, rep)
         assert rep["rtol"][j] == pytest.approx(r, rel=1e-3, abs=1e-9)
@@ -37,9 +37,9 @@ def test_cbs_solve_matches_oracle_iterates_without_refinement():
     insts = [synth.small_instance(96, 96, seed=7)]
     b, k2, f, n, V = setup_batch(capi, c, insts)
     u = torch.zeros(b.extent, dtype=torch.complex128, device="cuda")
-    st, rep = capi.cbs_solve(c, b, V, f, u, rtol=0.0, max_iter=10, check_every=10)
+    st, rep = capi.cbs_solve(c, b, k2, f, u, rtol=0.0, max_iter=10, check_every=10)
     assert st == capi.NOT_CONVERGED and rep["iters"][0] == 10
-    p = H.problem_from_instance(insts[0])
+    p = oracle_problem(insts[0])
     ref = H.cbs_solve(p, tol=0, max_iter=10)
     assert rel_l2(b.unpack(u)[0], ref.u.numpy()) < 1e-5
 
@@ -50,5 +50,5 @@ def test_cbs_solve_zero_source_and_graph_off():
     insts[0].f[:] = 0
     b, k2, f, n, V = setup_batch(capi, c, insts)
     u = torch.zeros(b.extent, dtype=torch.complex128, device="cuda")
-    st, rep = capi.cbs_solve(c, b, V, f, u, rtol=1e-6, max_iter=100, check_every=4, use_graph=0)
+    st, rep = capi.cbs_solve(c, b, k2, f, u, rtol=1e-6, max_iter=100, check_every=4, use_graph=0)
     assert st == capi.OK and rep["iters"][0] == 0
