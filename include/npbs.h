@@ -147,6 +147,28 @@ npbs_status cbs_apply(npbs_ctx* ctx, const npbs_batch* batch, const void* V, con
                       const void* x, void* out, npbs_mode mode, double* norm2,
                       npbs_stream stream);
 
+/* The same apply as cbs_apply for callers that cannot allocate device memory
+ * (the paper has no counterpart; this is a deployment variant).  cbs_apply
+ * allocates its spectrum scratch and batch plan through the context on first
+ * use; an application whose memory manager has reserved the whole device for
+ * its own pool, or latency-critical code that must not pay for (possibly
+ * device-synchronising) cudaMalloc / cudaFree, cannot allow that.  This entry
+ * point takes no context and allocates nothing: the scratch (2^20 complex64
+ * elements, 8 MiB) and the plan live in static device arrays that the library
+ * reserves on every GPU that loads it, until the process exits.  The caller
+ * still passes inputs and outputs (same meaning and layout as cbs_apply) on the
+ * current device.  Limits: batch extent (max offset + nx*ny) <= 2^20 elements,
+ * <= 64 instances, <= 8 distinct grid sides; larger batches return
+ * NPBS_ERR_UNSUPPORTED_SIZE.  The first call on a device resolves the static
+ * arrays' device addresses and sets kernel attributes; make that first call
+ * before any stream capture.  All calls share the static arrays: calls that
+ * overlap on the GPU (different streams or host threads) race; calls on one
+ * stream are ordered.  err (nullable, errlen bytes) receives a one-line
+ * message on failure.  Asynchronous on `stream`. */
+npbs_status cbs_apply_static(const npbs_batch* batch, const void* V, const void* f, const void* x,
+                             void* out, npbs_mode mode, double* norm2, npbs_stream stream,
+                             char* err, int32_t errlen);
+
 /* ---- solvers --------------------------------------------------------------
  * All solvers iterate in complex64 on a correction delta and fold it into the
  * solution u held in complex128 every refinement cycle, where the true

@@ -70,6 +70,8 @@ _SIGS = {
     "fgmres_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(npbs_batch), C.c_void_p, C.c_void_p,
                                C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_int32,
                                C.POINTER(npbs_solve_opts), C.POINTER(npbs_report), C.c_void_p]),
+    "cbs_apply_static": (C.c_int, [C.POINTER(npbs_batch), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
+                                   C.c_void_p, C.c_void_p, C.c_char_p, C.c_int32]),
     "npbs_net_num_params": (C.c_int64, []),
     "npbs_net_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_uint64]),
     "npbs_net_destroy": (C.c_int, [C.c_void_p]),
@@ -239,6 +241,17 @@ def cbs_apply(ctx: Context, batch: Batch, V, f, x, out, mode: int, norm2: Option
         raise ValueError("norm2 must be float64")
     ctx.check(lib().cbs_apply(ctx.handle, C.byref(batch.c_batch()), _ptr(V), _ptr(f), _ptr(x), _ptr(out),
                               int(mode), _ptr(norm2), _stream(stream)))
+
+
+def cbs_apply_static(batch: Batch, V, f, x, out, mode: int, norm2: Optional[torch.Tensor] = None, stream=None):
+    """cbs_apply without a context and without device allocation (static scratch)."""
+    if norm2 is not None and norm2.dtype != torch.float64:
+        raise ValueError("norm2 must be float64")
+    buf = C.create_string_buffer(256)
+    st = lib().cbs_apply_static(C.byref(batch.c_batch()), _ptr(V), _ptr(f), _ptr(x), _ptr(out), int(mode),
+                                _ptr(norm2), _stream(stream), buf, 256)
+    if st != OK:
+        raise NpbsError(st, buf.value.decode())
 
 
 class Report:
