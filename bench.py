@@ -163,6 +163,9 @@ def main():
     ap.add_argument("--check-every", type=int, default=16)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--apply-reps", type=int, default=50)
+    ap.add_argument("--apply-only", action="store_true",
+                    help="time only the CBS_STEP apply on the workload (for profiler captures)")
+    ap.add_argument("--mode", default="CBS_STEP", help="apply mode for --apply-only")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -189,6 +192,24 @@ def main():
     capi.npbs_build_potential(ctx, b, k2, V)
     u = torch.zeros(b.extent, dtype=torch.complex128, device="cuda")
     stream = torch.cuda.current_stream()
+    if args.apply_only:
+        x = torch.zeros(b.extent, dtype=torch.complex64, device="cuda")
+        m = getattr(capi, args.mode)
+        for _ in range(args.warmup):
+            capi.cbs_apply(ctx, b, V, f, x, x, m)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.apply_reps):
+            capi.cbs_apply(ctx, b, V, f, x, x, m)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.apply_reps
+        bpp = 24 if args.mode in ("OP_B", "ADJ_B") else 32
+        gbs = bpp * b.points() / (ms * 1e-3) / 1e9
+        print(json.dumps({"apply_only": args.mode, "workload": wname, "points": b.points(), "ms": ms,
+                          "algorithmic_GBps": gbs, "frac_of_peak": gbs / peaks()[0]}), flush=True)
+        return 0
 
     def step():
         u.zero_()

@@ -2,6 +2,7 @@
 #include <cmath>
 #include <cstring>
 #include <cstdio>
+#include <cstdlib>
 
 #include "ctx.cuh"
 
@@ -17,6 +18,9 @@ Plan::~Plan() {
     cudaFree(rows64);
     cudaFree(cols64);
     cudaFree(vitems);
+    cudaFree(rows32s);
+    cudaFree(cols32s);
+    for (auto& g : fast) cudaFree(g.list);
 }
 
 cudaError_t DevBuf::ensure(size_t need) {
@@ -96,6 +100,9 @@ const Plan* get_plan(npbs_ctx* ctx, const npbs_batch* batch, npbs_status* st) {
     std::vector<RowItem> r32, r64;
     std::vector<ColItem> c32, c64;
     std::vector<VecItem> vit;
+    std::vector<RowItem> r32s;
+    std::vector<ColItem> c32s;
+    std::map<int, std::vector<int>> fastlists;
     for (int j = 0; j < batch->count; ++j) {
         const npbs_instance& s = batch->inst[j];
         char buf[256];
@@ -128,17 +135,21 @@ const Plan* get_plan(npbs_ctx* ctx, const npbs_batch* batch, npbs_status* st) {
             VecItem v{j, (int)st0, (int)std::min<long long>(kVecChunk, (long long)s.nx * s.ny - st0), 0};
             vit.push_back(v);
         }
+        const bool fast = ctx->use_fast && s.nx == s.ny && fast_supported(s.nx);
+        if (fast) fastlists[s.nx].push_back(j);
         for (int f64 = 0; f64 < 2; ++f64) {
             const int tile = f64 ? kTileElems<double>() : kTileElems<float>();
             const int rp = std::max(1, std::min(s.ny, tile / s.nx));
             for (int r0 = 0; r0 < s.ny; r0 += rp) {
                 RowItem it{j, r0, std::min(rp, s.ny - r0), 0};
                 (f64 ? r64 : r32).push_back(it);
+                if (!f64 && !fast) r32s.push_back(it);
             }
             const int cp = std::max(1, std::min(16, tile / s.ny));
             for (int c0 = 0; c0 < s.nx; c0 += cp) {
                 ColItem it{j, c0, std::min(cp, s.nx - c0), 0};
                 (f64 ? c64 : c32).push_back(it);
+                if (!f64 && !fast) c32s.push_back(it);
             }
         }
     }
@@ -152,6 +163,16 @@ const Plan* get_plan(npbs_ctx* ctx, const npbs_batch* batch, npbs_status* st) {
     if (e == cudaSuccess) e = upload(&pl->rows64, r64);
     if (e == cudaSuccess) e = upload(&pl->cols64, c64);
     if (e == cudaSuccess) e = upload(&pl->vitems, vit);
+    if (e == cudaSuccess) e = upload(&pl->rows32s, r32s);
+    if (e == cudaSuccess) e = upload(&pl->cols32s, c32s);
+    for (auto& kv : fastlists) {
+        if (e != cudaSuccess) break;
+        Plan::FastGroup g;
+        g.n = kv.first;
+        g.count = (int)kv.second.size();
+        e = upload(&g.list, kv.second);
+        pl->fast.push_back(g);
+    }
     if (e != cudaSuccess) {
         *st = cuda_err(ctx, e, "plan upload");
         return nullptr;
@@ -161,6 +182,8 @@ const Plan* get_plan(npbs_ctx* ctx, const npbs_batch* batch, npbs_status* st) {
     pl->nrow64 = (int)r64.size();
     pl->ncol64 = (int)c64.size();
     pl->nvec = (int)vit.size();
+    pl->nrow32s = (int)r32s.size();
+    pl->ncol32s = (int)c32s.size();
     if (ctx->plans.size() > 64) ctx->plans.clear();
     const Plan* out = pl.get();
     ctx->plans[key] = std::move(pl);
@@ -175,9 +198,23 @@ npbs_status run_apply(npbs_ctx* ctx, const Plan& pl, int mode, const ApplyArgs& 
     a.scratch = ctx->scratch.p;
     if (a.norm2) NPBS_CK(ctx, cudaMemsetAsync(a.norm2, 0, sizeof(double) * pl.count, st));
     if (a.norm2b) NPBS_CK(ctx, cudaMemsetAsync(a.norm2b, 0, sizeof(double) * pl.count, st));
-    const BatchDev bd = pl.bd(f64, active);
-    NPBS_CK(ctx, launch_apply(mode, bd, f64 ? pl.nrow64 : pl.nrow32, f64 ? pl.ncol64 : pl.ncol32, a, st));
-    ctx->count(st, 3);
+    BatchDev bd = pl.bd(f64, active);
+    if (f64) {
+        NPBS_CK(ctx, launch_apply(mode, bd, pl.nrow64, pl.ncol64, a, st));
+        ctx->count(st, 3);
+        return NPBS_OK;
+    }
+    for (const auto& g : pl.fast) {
+        FastDev fd{g.list, g.count};
+        NPBS_CK(ctx, launch_apply_fast(g.n, mode, fd, bd, a, st));
+        ctx->count(st, 1);
+    }
+    if (pl.nrow32s > 0) {
+        bd.rows = pl.rows32s;
+        bd.cols = pl.cols32s;
+        NPBS_CK(ctx, launch_apply(mode, bd, pl.nrow32s, pl.ncol32s, a, st));
+        ctx->count(st, 3);
+    }
     return NPBS_OK;
 }
 
@@ -248,9 +285,12 @@ npbs_status npbs_create(npbs_ctx** out, int device) {
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return NPBS_ERR_INVALID_ARG;
     if (cudaSetDevice(device) != cudaSuccess) return NPBS_ERR_CUDA;
     if (prepare_apply() != cudaSuccess) return NPBS_ERR_CUDA;
+    if (prepare_apply_fast() != cudaSuccess) return NPBS_ERR_CUDA;
     npbs_ctx* c = new (std::nothrow) npbs_ctx();
     if (!c) return NPBS_ERR_OOM;
     c->device = device;
+    const char* env = getenv("NPBS_APPLY_PATH");
+    c->use_fast = !(env && strcmp(env, "three_pass") == 0);
     *out = c;
     return NPBS_OK;
 }

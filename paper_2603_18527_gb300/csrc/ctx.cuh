@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "apply.cuh"
+#include "apply_fast.cuh"
 #include "common.cuh"
 
 namespace npbs {
@@ -29,6 +30,17 @@ struct Plan {
     int nrow32 = 0, ncol32 = 0, nrow64 = 0, ncol64 = 0;
     VecItem* vitems = nullptr;
     int nvec = 0;
+    // float32 modes: square instances of a cluster-kernel size go to one
+    // launch per size; the rest use the three-launch path (rows32s / cols32s)
+    struct FastGroup {
+        int n = 0;
+        int* list = nullptr;
+        int count = 0;
+    };
+    std::vector<FastGroup> fast;
+    RowItem* rows32s = nullptr;
+    ColItem* cols32s = nullptr;
+    int nrow32s = 0, ncol32s = 0;
     BatchDev bd(bool f64, const int* active) const {
         BatchDev b;
         b.inst = inst;
@@ -61,6 +73,7 @@ struct npbs_ctx {
     npbs::DevBuf scratch;   // spectrum between apply passes
     npbs::DevBuf work[12];  // solver workspaces
     npbs::DevBuf net_ws;    // network activations
+    bool use_fast = true;  // cluster apply for square 128..512 grids (NPBS_APPLY_PATH=three_pass disables)
     cudaStream_t solve_stream = nullptr;  // capturable stream the solvers run on
     cudaEvent_t solve_event = nullptr;
     long long launches = 0;         // kernels launched (graph launches count their kernels)

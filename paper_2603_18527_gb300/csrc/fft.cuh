@@ -17,14 +17,14 @@
 namespace npbs {
 
 // x * (DIR * i): multiply by +i (DIR = +1) or -i (DIR = -1).
-template <int DIR, typename C> __device__ __forceinline__ C mul_i(C a) {
+template <int DIR, typename C> __host__ __device__ __forceinline__ C mul_i(C a) {
     return DIR > 0 ? mk<C>(-a.y, a.x) : mk<C>(a.y, -a.x);
 }
 
 template <int R, int DIR, typename C> struct Dft;
 
 template <int DIR, typename C> struct Dft<2, DIR, C> {
-    static __device__ __forceinline__ void run(C* v) {
+    static __host__ __device__ __forceinline__ void run(C* v) {
         C a = v[0], b = v[1];
         v[0] = a + b;
         v[1] = a - b;
@@ -32,7 +32,7 @@ template <int DIR, typename C> struct Dft<2, DIR, C> {
 };
 
 template <int DIR, typename C> struct Dft<4, DIR, C> {
-    static __device__ __forceinline__ void run(C* v) {
+    static __host__ __device__ __forceinline__ void run(C* v) {
         C t0 = v[0] + v[2], t1 = v[0] - v[2];
         C t2 = v[1] + v[3], t3 = mul_i<DIR>(v[1] - v[3]);
         v[0] = t0 + t2;
@@ -43,7 +43,7 @@ template <int DIR, typename C> struct Dft<4, DIR, C> {
 };
 
 template <int DIR, typename C> struct Dft<8, DIR, C> {
-    static __device__ __forceinline__ void run(C* v) {
+    static __host__ __device__ __forceinline__ void run(C* v) {
         using S = decltype(C::x);
         const S h = S(0.70710678118654752440);  // sqrt(2)/2
         C e[4] = {v[0], v[2], v[4], v[6]};
@@ -66,7 +66,7 @@ template <int DIR, typename C> struct Dft<8, DIR, C> {
 };
 
 template <int DIR, typename C> struct Dft<3, DIR, C> {
-    static __device__ __forceinline__ void run(C* v) {
+    static __host__ __device__ __forceinline__ void run(C* v) {
         using S = decltype(C::x);
         const S s3 = S(0.86602540378443864676);  // sqrt(3)/2
         C t = v[1] + v[2];

@@ -19,7 +19,7 @@ TOL = 1e-5
 
 # sizes spanning several row/column tiles, ragged tails, radix 3, non-square grids
 SHAPES = [(16, 16), (96, 96), (24, 48), (48, 24), (2, 2), (3, 6), (288, 288), (256, 256), (1024, 64),
-          (64, 1024), (384, 128), (9, 512)]
+          (64, 1024), (384, 128), (9, 512), (128, 128), (192, 192), (384, 384), (512, 512), (256, 256)]
 
 
 @pytest.fixture(scope="module")
@@ -135,3 +135,23 @@ def test_invalid_arguments_are_rejected():
     b = capi.Batch([(16, 16)], k0sq=[1.0], eps=[1.0])
     with pytest.raises(capi.NpbsError):
         capi.cbs_apply(c, b, t, None, t, t, capi.RESIDUAL)
+
+
+def test_cluster_path_matches_three_pass_path(env, monkeypatch):
+    """Square 128..512 grids run on the single-launch cluster kernel; a context
+    created with NPBS_APPLY_PATH=three_pass runs the three-launch kernels.  Both
+    must agree to float32 round-off for every mode."""
+    capi, c, insts, probs, b, k2, f, V, xs, x = env
+    monkeypatch.setenv("NPBS_APPLY_PATH", "three_pass")
+    c3 = capi.Context(0)
+    for mode in ["RESIDUAL", "CBS_STEP", "OP_B", "ADJ_B", "TRUE_RESIDUAL", "PREC_SWEEP"]:
+        o1, o2 = torch.zeros_like(x), torch.zeros_like(x)
+        n1 = torch.zeros(b.count, dtype=torch.float64, device="cuda")
+        n2 = torch.zeros(b.count, dtype=torch.float64, device="cuda")
+        capi.cbs_apply(c, b, V, f, x, o1, getattr(capi, mode), n1)
+        capi.cbs_apply(c3, b, V, f, x, o2, getattr(capi, mode), n2)
+        torch.cuda.synchronize()
+        A, B = b.unpack(o1), b.unpack(o2)
+        for j in range(b.count):
+            assert rel_l2(A[j], B[j]) <= 2e-6, (mode, SHAPES[j])
+        assert np.allclose(n1.cpu().numpy(), n2.cpu().numpy(), rtol=1e-5)
