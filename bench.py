@@ -98,6 +98,128 @@ class Clocks:
                 "samples": len(sm)}
 
 
+def unet_forward_flops(H: int, W: int) -> float:
+    """FLOPs of one network forward at H x W: 2 * 9 * Cin * Cout per output pixel
+    of every 3x3 convolution (the first one counted with its 3 real input
+    channels) plus the 32 -> 2 head."""
+    ch = [32, 64, 128, 256]
+    macs = 0.0
+    cin = 3
+    for l in range(4):
+        px = (H >> l) * (W >> l)
+        macs += 9 * px * (cin * ch[l] + ch[l] * ch[l])
+        cin = ch[l]
+    for l in range(2, -1, -1):
+        px = (H >> l) * (W >> l)
+        macs += 9 * px * (ch[l + 1] * ch[l] + 2 * ch[l] * ch[l] + ch[l] * ch[l])
+    macs += H * W * 32 * 2
+    return 2.0 * macs
+
+
+def tensor_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["bf16_tflops"]), float(d.get("bf16_tflops_sustained", d["bf16_tflops"])), "measured"
+    except Exception:
+        return 1900.0, 1700.0, "fallback"
+
+
+def timed(stream, fn, reps):
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def bench_learned(capi, ctx, args, stream):
+    """Network forward / training step throughput and NPBS vs CBS on the
+    contrast media law at 256^2."""
+    from paper_2603_18527_gb300 import train_unet as T
+    out = {}
+    net = None
+    if args.net and os.path.exists(args.net) and args.net.endswith(".npz"):
+        net = capi.Net(0, seed=0)
+        net.set_params(np.load(args.net)["params"].astype(np.float32))
+        out["net"] = os.path.basename(args.net)
+    elif args.net and os.path.exists(args.net):
+        net = capi.Net.load(args.net)
+        out["net"] = os.path.basename(args.net)
+    else:
+        net = capi.Net(0, seed=0)
+        out["net"] = "untrained (seed 0)"
+    # network forward at 64 x 256^2 (the NPBS inference batch)
+    insts = T.media(256, args.npbs_count, 2000)
+    pool = T.Pool(ctx, insts)
+    r = torch.randn(pool.b.extent, dtype=torch.complex64, device="cuda")
+    c = torch.zeros_like(r)
+    fwd = lambda: capi.npbs_net_forward(ctx, net, pool.b, r, pool.n, c)
+    fwd()
+    ms = timed(stream, fwd, 3)
+    fl = unet_forward_flops(256, 256) * len(insts)
+    peak, peak_s, kind = tensor_peak()
+    out["unet_forward"] = {"instances": len(insts), "ms": ms, "tflops": fl / (ms * 1e-3) / 1e12,
+                           "frac_of_bf16_peak": fl / (ms * 1e-3) / 1e12 / peak, "peak_kind": kind}
+    # training step: batch 32 at 256^2, 4 unrolls (lr = 0 keeps the weights)
+    sel = insts[:32] if len(insts) >= 32 else (insts * 32)[:32]
+    tp = T.Pool(ctx, sel)
+    u0 = torch.zeros(tp.b.extent, dtype=torch.complex64, device="cuda")
+    step = lambda: capi.npbs_train_step(ctx, net, tp.b, tp.V, tp.f, tp.n, u0, unroll=4, lr=0.0, weight_decay=0.0)
+    step()
+    ms_t = timed(stream, step, 2)
+    # forward twice (one pass for the unrolled residuals, one recomputed in the
+    # backward) + data gradient + weight gradient, each ~ one forward's FLOPs
+    flt = 4 * 4 * unet_forward_flops(256, 256) * 32
+    out["train_step"] = {"batch": 32, "grid": 256, "unroll": 4, "ms": ms_t, "tflops": flt / (ms_t * 1e-3) / 1e12,
+                         "frac_of_bf16_peak_sustained": flt / (ms_t * 1e-3) / 1e12 / peak_s}
+    # NPBS vs CBS to 1e-5 on the same batch (per-instance ms = batch time / count)
+    ev = {}
+    for name in ["cbs", "npbs"]:
+        u = torch.zeros(pool.b.extent, dtype=torch.complex128, device="cuda")
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        if name == "cbs":
+            st, rep = capi.cbs_solve(ctx, pool.b, pool.k2, pool.f, u, rtol=TOL, max_iter=args.npbs_max_iter,
+                                     check_every=16)
+        else:
+            st, rep = capi.npbs_solve(ctx, net, pool.b, pool.k2, pool.f, pool.n, u, rtol=TOL,
+                                      max_iter=args.npbs_max_iter, check_every=4)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        ev[name] = {"ms_per_solve": dt * 1e3 / len(insts), "iters_mean": float(np.mean(rep["iters"])),
+                    "converged": int(sum(1 for x in rep["status"] if x == capi.OK)),
+                    "fallback_to_cbs": int(sum(rep.get("fallback") or [0]))}
+    out["npbs_vs_cbs"] = {"workload": f"contrast media law, {len(insts)} x 256^2, tol {TOL}", **ev}
+    return out
+
+
+def bench_fgmres(capi, ctx, args):
+    """FGMRES(20) at 1024^2 on layered media: none / 16 CBS sweeps."""
+    insts = synth.workload_layered(args.fgmres_count, 1024)
+    b = capi.Batch([(i.ny, i.nx) for i in insts], h=[i.h for i in insts])
+    k2 = b.pack([i.k2 for i in insts])
+    f = b.pack([i.f for i in insts])
+    n = b.pack([i.n for i in insts], dtype=torch.float32)
+    V = torch.zeros_like(k2)
+    capi.npbs_build_potential(ctx, b, k2, V)
+    res = {"workload": f"layered media, {len(insts)} x 1024^2, restart 20, tol {TOL}"}
+    for name, pc in [("none", 0), ("cbs16", 1)]:
+        u = torch.zeros(b.extent, dtype=torch.complex128, device="cuda")
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st, rep = capi.fgmres_solve(ctx, None, b, k2, f, n, u, restart=20, precond=pc, cbs_sweeps=16, rtol=TOL,
+                                    max_iter=args.fgmres_max_iter)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        res[name] = {"ms_per_solve": dt * 1e3 / len(insts), "iters_mean": float(np.mean(rep["iters"])),
+                     "converged": int(sum(1 for x in rep["status"] if x == capi.OK))}
+    return res
+
+
 def make_workload(args):
     if args.workload == "mixed":
         return synth.workload_mixed(args.n256, args.nother), "cbs_mixed_256x256^2+64x{128,192,384,512}^2"
@@ -166,6 +288,13 @@ def main():
     ap.add_argument("--apply-only", action="store_true",
                     help="time only the CBS_STEP apply on the workload (for profiler captures)")
     ap.add_argument("--mode", default="CBS_STEP", help="apply mode for --apply-only")
+    ap.add_argument("--net", default=os.path.join(ROOT, "paper_2603_18527_gb300", "weights", "unet_contrast256.npz"),
+                    help="trained network (.npz canonical parameters or an npbs_net_save checkpoint)")
+    ap.add_argument("--npbs-count", type=int, default=16)
+    ap.add_argument("--npbs-max-iter", type=int, default=6000)
+    ap.add_argument("--fgmres-count", type=int, default=2)
+    ap.add_argument("--fgmres-max-iter", type=int, default=400)
+    ap.add_argument("--no-learned", action="store_true", help="skip the network / NPBS / FGMRES sections")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -192,6 +321,10 @@ def main():
     capi.npbs_build_potential(ctx, b, k2, V)
     u = torch.zeros(b.extent, dtype=torch.complex128, device="cuda")
     stream = torch.cuda.current_stream()
+    # autotune the cluster-kernel variant per grid side on this workload (set-up, untimed)
+    xt = torch.zeros(b.extent, dtype=torch.complex64, device="cuda")
+    tuned = capi.npbs_autotune_apply(ctx, b, V, f, xt, reps=5)
+    del xt
     if args.apply_only:
         x = torch.zeros(b.extent, dtype=torch.complex64, device="cuda")
         m = getattr(capi, args.mode)
@@ -207,7 +340,7 @@ def main():
         ms = e0.elapsed_time(e1) / args.apply_reps
         bpp = 24 if args.mode in ("OP_B", "ADJ_B") else 32
         gbs = bpp * b.points() / (ms * 1e-3) / 1e9
-        print(json.dumps({"apply_only": args.mode, "workload": wname, "points": b.points(), "ms": ms,
+        print(json.dumps({"apply_only": args.mode, "workload": wname, "points": b.points(), "ms": ms, "tuned": tuned,
                           "algorithmic_GBps": gbs, "frac_of_peak": gbs / peaks()[0]}), flush=True)
         return 0
 
@@ -271,6 +404,11 @@ def main():
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1) / e2e_steps
 
+    learned = fg = None
+    if not args.no_learned and rank == 0:
+        learned = bench_learned(capi, ctx, args, stream)
+        fg = bench_fgmres(capi, ctx, args)
+
     line = None
     if rank == 0:
         cpu = None
@@ -289,13 +427,14 @@ def main():
                            "converged": f"{conv}/{len(insts)}", "iters_mean": float(np.mean(rep["iters"])),
                            "iters_max": int(np.max(rep["iters"])), "parallelism": f"replicas x{world}"},
                 "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-                             "traffic": None, "kernel": "cbs_apply CBS_STEP (3 launches)", "apply_ms": apply_ms,
-                             "peak_kind": kind},
+                             "traffic": None, "kernel": "cbs_apply CBS_STEP (one cluster launch per grid side)",
+                             "apply_ms": apply_ms, "peak_kind": kind, "autotuned_variants": tuned},
                 "cpu_baseline": cpu,
                 "e2e": {"value": e2e_ms / eq, "unit": UNIT,
                         "h2d_bytes_per_step": int(k2_h.numel() * 8 + f_h.numel() * 8),
                         "d2h_bytes_per_step": int(u_h.numel() * 16)},
-                "gpu_launches": int(launches), "clocks": clk.summary()}
+                "gpu_launches": int(launches), "clocks": clk.summary(),
+                "learned": learned, "fgmres": fg}
         print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()

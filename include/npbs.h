@@ -125,6 +125,12 @@ const char* npbs_version(void);
  * kernels they contain); -1 for a NULL ctx.  For benchmarks. */
 int64_t npbs_launch_count(const npbs_ctx* ctx);
 
+/* Process-wide counts of network convolution launches by engine: the tcgen05
+ * tensor-core kernel (TMA-fed, TMEM accumulator) and the warp-level MMA kernel
+ * used where TMA cannot tile the geometry (upsampling convolutions, grids
+ * whose sides do not divide or are not multiples of 128).  For benchmarks. */
+void npbs_conv_stats(int64_t* tensor_core_launches, int64_t* warp_mma_launches);
+
 /* ---- problem set-up ----------------------------------------------------- */
 
 /* Reference constants and potential (Sec. 3.1; the paper leaves k0 and eta
@@ -146,6 +152,16 @@ npbs_status npbs_build_potential(npbs_ctx* ctx, const npbs_batch* batch, const v
 npbs_status cbs_apply(npbs_ctx* ctx, const npbs_batch* batch, const void* V, const void* f,
                       const void* x, void* out, npbs_mode mode, double* norm2,
                       npbs_stream stream);
+
+/* Autotuner for the single-launch cluster apply: for every square grid side
+ * of the batch that has a cluster kernel (128, 192, 256, 384, 512), time each
+ * compiled (N1 x N2 factorisation, cluster size, threads) variant over `reps`
+ * CBS_STEP applies on the caller's data and keep the fastest for later calls
+ * on ctx.  x is overwritten (it is iterated in place).  chosen (nullable, HOST
+ * int32 per grid side present, in increasing side order) receives
+ * side * 16 + variant.  Synchronises the stream. */
+npbs_status npbs_autotune_apply(npbs_ctx* ctx, const npbs_batch* batch, const void* V, const void* f,
+                                void* x, int32_t reps, int32_t* chosen, npbs_stream stream);
 
 /* The same apply as cbs_apply for callers that cannot allocate device memory
  * (the paper has no counterpart; this is a deployment variant).  cbs_apply

@@ -58,6 +58,7 @@ _SIGS = {
     "npbs_destroy": (C.c_int, [C.c_void_p]),
     "npbs_last_error": (C.c_char_p, [C.c_void_p]),
     "npbs_launch_count": (C.c_int64, [C.c_void_p]),
+    "npbs_conv_stats": (None, [C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "npbs_build_potential": (C.c_int, [C.c_void_p, C.POINTER(npbs_batch), C.c_void_p, C.c_void_p,
                                        C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_void_p]),
     "cbs_apply": (C.c_int, [C.c_void_p, C.POINTER(npbs_batch), C.c_void_p, C.c_void_p, C.c_void_p,
@@ -70,6 +71,8 @@ _SIGS = {
     "fgmres_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(npbs_batch), C.c_void_p, C.c_void_p,
                                C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_int32,
                                C.POINTER(npbs_solve_opts), C.POINTER(npbs_report), C.c_void_p]),
+    "npbs_autotune_apply": (C.c_int, [C.c_void_p, C.POINTER(npbs_batch), C.c_void_p, C.c_void_p, C.c_void_p,
+                                      C.c_int32, C.c_void_p, C.c_void_p]),
     "cbs_apply_static": (C.c_int, [C.POINTER(npbs_batch), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
                                    C.c_void_p, C.c_void_p, C.c_char_p, C.c_int32]),
     "npbs_net_num_params": (C.c_int64, []),
@@ -218,6 +221,12 @@ def npbs_version() -> str:
     return lib().npbs_version().decode()
 
 
+def npbs_conv_stats() -> dict:
+    tc, mma = C.c_int64(0), C.c_int64(0)
+    lib().npbs_conv_stats(C.byref(tc), C.byref(mma))
+    return {"tensor_core": int(tc.value), "warp_mma": int(mma.value)}
+
+
 def launch_count(ctx: Context) -> int:
     return int(lib().npbs_launch_count(ctx.handle))
 
@@ -241,6 +250,14 @@ def cbs_apply(ctx: Context, batch: Batch, V, f, x, out, mode: int, norm2: Option
         raise ValueError("norm2 must be float64")
     ctx.check(lib().cbs_apply(ctx.handle, C.byref(batch.c_batch()), _ptr(V), _ptr(f), _ptr(x), _ptr(out),
                               int(mode), _ptr(norm2), _stream(stream)))
+
+
+def npbs_autotune_apply(ctx: Context, batch: Batch, V, f, x, reps=5, stream=None) -> dict:
+    """Pick the fastest cluster-kernel variant per grid side; returns {side: variant}."""
+    out = (C.c_int32 * 8)()
+    ctx.check(lib().npbs_autotune_apply(ctx.handle, C.byref(batch.c_batch()), _ptr(V), _ptr(f), _ptr(x), int(reps),
+                                        out, _stream(stream)))
+    return {int(v) // 16: int(v) % 16 for v in out if v > 0}
 
 
 def cbs_apply_static(batch: Batch, V, f, x, out, mode: int, norm2: Optional[torch.Tensor] = None, stream=None):

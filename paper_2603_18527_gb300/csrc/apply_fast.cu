@@ -1,392 +1,49 @@
-// Single-launch Born apply for square N x N instances, one thread-block
-// cluster per instance (the hot path of every CBS / NPBS / FGMRES step).
-//
-// CTA `rank` of a cluster of CS CTAs owns rows [rank*ROWS, (rank+1)*ROWS) of
-// the instance in shared memory (ROWS = N / CS).  Each 1D transform of length
-// N = N1 * N2 is a four-step FFT done in registers (n = N2 n1 + n2,
-// k = k1 + N1 k2):
-//   pass 1: N2 DFTs of length N1 over stride-N2 elements, twiddle W_N^{n2 k1};
-//   pass 2: N1 DFTs of length N2 over contiguous blocks,
-// which leaves the spectrum in "digit order" (position N2 k1 + k2 holds
-// frequency k1 + N1 k2).  The Green symbol is applied in that order (App.
-// Pseudospectral: lambda = |xi|^2 - k0^2 - i eps, step 2), and the inverse
-// transform consumes digit order and returns natural order, so no reordering
-// pass exists.  The row -> column and column -> row transposes go through
-// distributed shared memory: each thread stores its register results directly
-// into the owning CTA's slab between two cluster barriers.
-//
-// DRAM traffic is the algorithmic minimum: the prologue reads x, V, f once
-// (Eq. CBS: q = V x + f), the epilogue re-reads x and V (they are still in L2)
-// and writes out once.  Phases per apply:
-//   P1 row pass 1 (from global, prologue)   P2 row pass 2 -> DSMEM transpose
-//   P3 column pass 1                         P4 column pass 2, symbol, inverse pass A
-//   P5 column inverse pass B -> DSMEM        P6 row inverse pass A
-//   P7 row inverse pass B, epilogue (to global), per-instance norm
-#include <cooperative_groups.h>
-
-#include "apply.cuh"
+// Single-launch cluster apply: size dispatch and the per-size variant tables
+// (the kernel itself is in apply_fast_impl.cuh, instantiated per grid size in
+// apply_fast_<N>.cu so the sizes compile in parallel).
 #include "apply_fast.cuh"
-#include "dftreg.cuh"
-
-namespace cg = cooperative_groups;
 
 namespace npbs {
 
-namespace {
+#define NPBS_FAST_SIZES(X) X(128) X(192) X(256) X(384) X(512)
+#define NPBS_DECL(n)                                                                                        \
+    int fast_variants_##n();                                                                              \
+    cudaError_t prepare_fast_##n();                                                                       \
+    cudaError_t launch_fast_##n(int variant, int mode, const FastDev& fd, const BatchDev& bd, const ApplyArgs& a, \
+                                cudaStream_t st);
+NPBS_FAST_SIZES(NPBS_DECL)
+#undef NPBS_DECL
 
-template <int N2> __device__ __forceinline__ int pad(int p) { return p + p / N2; }
-
-__device__ __forceinline__ double warp_sum_d(double v) {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
-template <int N1, int N2, int CS, int T, int MODE>
-__global__ void __launch_bounds__(T) k_apply_cluster(FastDev fd, BatchDev bd, ApplyArgs a) {
-    constexpr int N = N1 * N2;
-    constexpr int ROWS = N / CS;
-    constexpr int LD = N + N1 + 1;
-    constexpr int J1 = (ROWS * N2 + T - 1) / T;  // jobs per thread, passes over N1 (P1, P3, P5, P7)
-    constexpr int J2 = (ROWS * N1 + T - 1) / T;  // jobs per thread, passes over N2 (P2, P4, P6)
-    static_assert(N % CS == 0 && ROWS % N2 == 0, "slab must hold whole N2 blocks");
-    extern __shared__ __align__(16) float2 smem[];
-    float2* S = smem;               // [ROWS][LD]: row slab, then column slab
-    float2* tw = smem + ROWS * LD;  // W_N^j = exp(-2 pi i j / N)
-    __shared__ double red[T / 32];
-
-    cg::cluster_group cluster = cg::this_cluster();
-    const int rank = (int)cluster.block_rank();
-    const int instx = fd.list[blockIdx.x / CS];
-    if (bd.active && !bd.active[instx]) return;  // uniform over the cluster
-    const InstDev in = bd.inst[instx];
-    const int tid = threadIdx.x;
-    for (int j = tid; j < N; j += T) tw[j] = bd.tw32[in.tw_x + j];
-    const long long base = in.offset;
-    __syncthreads();
-
-    // ---------------- P1: row pass 1 from global with the prologue
-#pragma unroll
-    for (int s = 0; s < J1; ++s) {
-        const int j = tid + s * T;
-        if (j < ROWS * N2) {
-            const int n2 = j % N2, r = j / N2;
-            const long long g0 = base + (long long)(rank * ROWS + r) * N + n2;
-            float2 v[N1];
-#pragma unroll
-            for (int m = 0; m < N1; ++m) {
-                const long long g = g0 + N2 * m;
-                const float2 x = __ldg(a.x + g);
-                if constexpr (MODE == NPBS_RESIDUAL || MODE == NPBS_CBS_STEP) {
-                    const float2 V = __ldg(a.V + g), f = __ldg(a.f + g);
-                    v[m] = make_float2(V.x * x.x - V.y * x.y + f.x, V.x * x.y + V.y * x.x + f.y);
-                } else if constexpr (MODE == NPBS_OP_B || MODE == NPBS_PREC_SWEEP) {
-                    const float2 V = __ldg(a.V + g);
-                    v[m] = make_float2(V.x * x.x - V.y * x.y, V.x * x.y + V.y * x.x);
-                } else {
-                    v[m] = x;
-                }
-            }
-            DftR<N1, -1>::run(v);
-#pragma unroll
-            for (int k1 = 0; k1 < N1; ++k1) {
-                const float2 w = tw[(n2 * k1) % N];
-                const float2 t = v[k1];
-                S[r * LD + pad<N2>(N2 * k1 + n2)] = make_float2(t.x * w.x - t.y * w.y, t.x * w.y + t.y * w.x);
-            }
-        }
-    }
-    __syncthreads();
-
-    // ---------------- P2: row pass 2, results held for the transpose
-    float2 h2[J2][N2];
-#pragma unroll
-    for (int s = 0; s < J2; ++s) {
-        const int j = tid + s * T;
-        if (j < ROWS * N1) {
-            const int r = j % ROWS, k1 = j / ROWS;
-#pragma unroll
-            for (int i = 0; i < N2; ++i) h2[s][i] = S[r * LD + pad<N2>(N2 * k1 + i)];
-            DftR<N2, -1>::run(h2[s]);
-        }
-    }
-    cluster.sync();
-#pragma unroll
-    for (int s = 0; s < J2; ++s) {
-        const int j = tid + s * T;
-        if (j < ROWS * N1) {
-            const int r = j % ROWS, k1 = j / ROWS;
-            const int p0 = N2 * k1;
-            const int d = p0 / ROWS, pl = p0 - d * ROWS;
-            float2* dst = cluster.map_shared_rank(S, d);
-            const int R = rank * ROWS + r;
-#pragma unroll
-            for (int i = 0; i < N2; ++i) dst[(pl + i) * LD + pad<N2>(R)] = h2[s][i];
-        }
-    }
-    cluster.sync();
-
-    // ---------------- P3: column pass 1 (slab now [ROWS columns][N rows])
-#pragma unroll
-    for (int s = 0; s < J1; ++s) {
-        const int j = tid + s * T;
-        if (j < ROWS * N2) {
-            const int n2 = j % N2, c = j / N2;
-            float2 v[N1];
-#pragma unroll
-            for (int m = 0; m < N1; ++m) v[m] = S[c * LD + pad<N2>(n2 + N2 * m)];
-            DftR<N1, -1>::run(v);
-#pragma unroll
-            for (int k1 = 0; k1 < N1; ++k1) {
-                const float2 w = tw[(n2 * k1) % N];
-                const float2 t = v[k1];
-                S[c * LD + pad<N2>(N2 * k1 + n2)] = make_float2(t.x * w.x - t.y * w.y, t.x * w.y + t.y * w.x);
-            }
-        }
-    }
-    __syncthreads();
-
-    // ---------------- P4: column pass 2, Green symbol, inverse pass A
-    {
-        const float cxi = (float)(6.283185307179586476925 / ((double)N * in.h));
-        const float k0sq = (float)in.k0sq, eps = (float)in.eps;
-#pragma unroll
-        for (int s = 0; s < J2; ++s) {
-            const int j = tid + s * T;
-            if (j < ROWS * N1) {
-                const int k1 = j % N1, c = j / N1;
-                float2 v[N2];
-#pragma unroll
-                for (int i = 0; i < N2; ++i) v[i] = S[c * LD + pad<N2>(N2 * k1 + i)];
-                DftR<N2, -1>::run(v);
-                const int px = rank * ROWS + c;
-                const int kx = signed_mode(px / N2 + N1 * (px % N2), N);
-                const float xx = cxi * (float)kx;
-#pragma unroll
-                for (int k2 = 0; k2 < N2; ++k2) {
-                    const int ky = signed_mode(k1 + N1 * k2, N);
-                    const float xy = cxi * (float)ky;
-                    const float xi2 = xx * xx + xy * xy;
-                    const float2 t = v[k2];
-                    if constexpr (MODE == NPBS_TRUE_RESIDUAL) {
-                        v[k2] = make_float2(t.x * xi2, t.y * xi2);
-                    } else {
-                        const float lr = xi2 - k0sq;
-                        const float li = (MODE == NPBS_ADJ_B) ? eps : -eps;
-                        const float inv = 1.f / (lr * lr + li * li);
-                        v[k2] = make_float2((t.x * lr + t.y * li) * inv, (t.y * lr - t.x * li) * inv);
-                    }
-                }
-                DftR<N2, +1>::run(v);
-#pragma unroll
-                for (int n2 = 0; n2 < N2; ++n2) {
-                    const float2 w = tw[(n2 * k1) % N];  // conjugate twiddle for the inverse
-                    const float2 t = v[n2];
-                    S[c * LD + pad<N2>(N2 * k1 + n2)] = make_float2(t.x * w.x + t.y * w.y, t.y * w.x - t.x * w.y);
-                }
-            }
-        }
-    }
-    __syncthreads();
-
-    // ---------------- P5: column inverse pass B, results held for the transpose back
-    float2 h5[J1][N1];
-#pragma unroll
-    for (int s = 0; s < J1; ++s) {
-        const int j = tid + s * T;
-        if (j < ROWS * N2) {
-            const int c = j % ROWS, n2 = j / ROWS;
-#pragma unroll
-            for (int k1 = 0; k1 < N1; ++k1) h5[s][k1] = S[c * LD + pad<N2>(N2 * k1 + n2)];
-            DftR<N1, +1>::run(h5[s]);
-        }
-    }
-    cluster.sync();
-#pragma unroll
-    for (int s = 0; s < J1; ++s) {
-        const int j = tid + s * T;
-        if (j < ROWS * N2) {
-            const int c = j % ROWS, n2 = j / ROWS;
-            const int px = rank * ROWS + c;
-#pragma unroll
-            for (int n1 = 0; n1 < N1; ++n1) {
-                const int Ry = N2 * n1 + n2;
-                const int d = Ry / ROWS, rl = Ry - d * ROWS;
-                float2* dst = cluster.map_shared_rank(S, d);
-                dst[rl * LD + pad<N2>(px)] = h5[s][n1];
-            }
-        }
-    }
-    cluster.sync();
-
-    // ---------------- P6: row inverse pass A
-#pragma unroll
-    for (int s = 0; s < J2; ++s) {
-        const int j = tid + s * T;
-        if (j < ROWS * N1) {
-            const int k1 = j % N1, r = j / N1;
-            float2 v[N2];
-#pragma unroll
-            for (int i = 0; i < N2; ++i) v[i] = S[r * LD + pad<N2>(N2 * k1 + i)];
-            DftR<N2, +1>::run(v);
-#pragma unroll
-            for (int n2 = 0; n2 < N2; ++n2) {
-                const float2 w = tw[(n2 * k1) % N];
-                const float2 t = v[n2];
-                S[r * LD + pad<N2>(N2 * k1 + n2)] = make_float2(t.x * w.x + t.y * w.y, t.y * w.x - t.x * w.y);
-            }
-        }
-    }
-    __syncthreads();
-
-    // ---------------- P7: row inverse pass B and the epilogue
-    const float scale = 1.f / ((float)N * (float)N);
-    const float ie = (float)(1.0 / in.eps);
-    double acc = 0.0;
-#pragma unroll
-    for (int s = 0; s < J1; ++s) {
-        const int j = tid + s * T;
-        if (j < ROWS * N2) {
-            const int n2 = j % N2, r = j / N2;
-            float2 v[N1];
-#pragma unroll
-            for (int k1 = 0; k1 < N1; ++k1) v[k1] = S[r * LD + pad<N2>(N2 * k1 + n2)];
-            DftR<N1, +1>::run(v);
-            const long long g0 = base + (long long)(rank * ROWS + r) * N + n2;
-#pragma unroll
-            for (int n1 = 0; n1 < N1; ++n1) {
-                const long long g = g0 + N2 * n1;
-                const float zr = v[n1].x * scale, zi = v[n1].y * scale;
-                const float2 x = a.x[g];  // plain load: out may alias x
-                float rr, ri;
-                float2 o;
-                if constexpr (MODE == NPBS_RESIDUAL) {
-                    rr = zr - x.x;
-                    ri = zi - x.y;
-                    o = make_float2(rr, ri);
-                } else if constexpr (MODE == NPBS_CBS_STEP) {
-                    rr = zr - x.x;
-                    ri = zi - x.y;
-                    const float2 V = __ldg(a.V + g);
-                    const float gr = -V.y * ie, gi = V.x * ie;
-                    o = make_float2(x.x + gr * rr - gi * ri, x.y + gr * ri + gi * rr);
-                } else if constexpr (MODE == NPBS_OP_B) {
-                    rr = x.x - zr;
-                    ri = x.y - zi;
-                    o = make_float2(rr, ri);
-                } else if constexpr (MODE == NPBS_ADJ_B) {
-                    const float2 V = __ldg(a.V + g);
-                    rr = x.x - (V.x * zr + V.y * zi);
-                    ri = x.y - (V.x * zi - V.y * zr);
-                    o = make_float2(rr, ri);
-                } else if constexpr (MODE == NPBS_TRUE_RESIDUAL) {
-                    const float2 V = __ldg(a.V + g), f = __ldg(a.f + g);
-                    const float kr = V.x + (float)in.k0sq, ki = V.y + (float)in.eps;
-                    rr = f.x + kr * x.x - ki * x.y - zr;
-                    ri = f.y + kr * x.y + ki * x.x - zi;
-                    o = make_float2(rr, ri);
-                } else {  // PREC_SWEEP
-                    const float2 V = __ldg(a.V + g), f = __ldg(a.f + g);
-                    rr = f.x - x.x + zr;
-                    ri = f.y - x.y + zi;
-                    const float gr = -V.y * ie, gi = V.x * ie;
-                    o = make_float2(x.x + gr * rr - gi * ri, x.y + gr * ri + gi * rr);
-                }
-                a.out[g] = o;
-                acc += (double)(rr * rr + ri * ri);
-            }
-        }
-    }
-    if (a.norm2) {
-        acc = warp_sum_d(acc);
-        if ((tid & 31) == 0) red[tid >> 5] = acc;
-        __syncthreads();
-        if (tid == 0) {
-            double t = 0.0;
-            for (int w = 0; w < T / 32; ++w) t += red[w];
-            atomicAdd(a.norm2 + instx, t);
-        }
-    }
-}
-
-template <int N1, int N2, int CS, int T> constexpr size_t fast_smem() {
-    return sizeof(float2) * ((size_t)(N1 * N2 / CS) * (N1 * N2 + N1 + 1) + N1 * N2);
-}
-
-template <int N1, int N2, int CS, int T, int MODE>
-cudaError_t set_attr_one() {
-    auto k = k_apply_cluster<N1, N2, CS, T, MODE>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fast_smem<N1, N2, CS, T>());
-    if (e == cudaSuccess && CS > 8) e = cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    return e;
-}
-
-template <int N1, int N2, int CS, int T>
-cudaError_t set_attr_size() {
-    cudaError_t e = cudaSuccess;
-    if (e == cudaSuccess) e = set_attr_one<N1, N2, CS, T, NPBS_RESIDUAL>();
-    if (e == cudaSuccess) e = set_attr_one<N1, N2, CS, T, NPBS_CBS_STEP>();
-    if (e == cudaSuccess) e = set_attr_one<N1, N2, CS, T, NPBS_OP_B>();
-    if (e == cudaSuccess) e = set_attr_one<N1, N2, CS, T, NPBS_ADJ_B>();
-    if (e == cudaSuccess) e = set_attr_one<N1, N2, CS, T, NPBS_TRUE_RESIDUAL>();
-    if (e == cudaSuccess) e = set_attr_one<N1, N2, CS, T, NPBS_PREC_SWEEP>();
-    return e;
-}
-
-template <int N1, int N2, int CS, int T, int MODE>
-cudaError_t launch_one(const FastDev& fd, const BatchDev& bd, const ApplyArgs& a, cudaStream_t st) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)(fd.count * CS), 1, 1);
-    cfg.blockDim = dim3(T, 1, 1);
-    cfg.dynamicSmemBytes = fast_smem<N1, N2, CS, T>();
-    cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = CS;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_apply_cluster<N1, N2, CS, T, MODE>, fd, bd, a);
-}
-
-template <int N1, int N2, int CS, int T>
-cudaError_t launch_size(int mode, const FastDev& fd, const BatchDev& bd, const ApplyArgs& a, cudaStream_t st) {
-    switch (mode) {
-        case NPBS_RESIDUAL: return launch_one<N1, N2, CS, T, NPBS_RESIDUAL>(fd, bd, a, st);
-        case NPBS_CBS_STEP: return launch_one<N1, N2, CS, T, NPBS_CBS_STEP>(fd, bd, a, st);
-        case NPBS_OP_B: return launch_one<N1, N2, CS, T, NPBS_OP_B>(fd, bd, a, st);
-        case NPBS_ADJ_B: return launch_one<N1, N2, CS, T, NPBS_ADJ_B>(fd, bd, a, st);
-        case NPBS_TRUE_RESIDUAL: return launch_one<N1, N2, CS, T, NPBS_TRUE_RESIDUAL>(fd, bd, a, st);
-        case NPBS_PREC_SWEEP: return launch_one<N1, N2, CS, T, NPBS_PREC_SWEEP>(fd, bd, a, st);
-        default: return cudaErrorInvalidValue;
-    }
-}
-
-}  // namespace
-
-// Supported sizes: N -> (N1, N2, cluster size, threads).  Other grids use the
-// three-launch path.
 bool fast_supported(int n) { return n == 128 || n == 192 || n == 256 || n == 384 || n == 512; }
+
+int fast_variants(int n) {
+    switch (n) {
+        case 128: return fast_variants_128();
+        case 192: return fast_variants_192();
+        case 256: return fast_variants_256();
+        case 384: return fast_variants_384();
+        case 512: return fast_variants_512();
+        default: return 0;
+    }
+}
 
 cudaError_t prepare_apply_fast() {
     cudaError_t e = cudaSuccess;
-    if (e == cudaSuccess) e = set_attr_size<16, 8, 4, 256>();
-    if (e == cudaSuccess) e = set_attr_size<16, 12, 4, 384>();
-    if (e == cudaSuccess) e = set_attr_size<16, 16, 8, 256>();
-    if (e == cudaSuccess) e = set_attr_size<16, 24, 16, 384>();
-    if (e == cudaSuccess) e = set_attr_size<16, 32, 16, 512>();
+#define NPBS_PREP(n) \
+    if (e == cudaSuccess) e = prepare_fast_##n();
+    NPBS_FAST_SIZES(NPBS_PREP)
+#undef NPBS_PREP
     return e;
 }
 
-cudaError_t launch_apply_fast(int n, int mode, const FastDev& fd, const BatchDev& bd, const ApplyArgs& a,
+cudaError_t launch_apply_fast(int n, int variant, int mode, const FastDev& fd, const BatchDev& bd, const ApplyArgs& a,
                               cudaStream_t st) {
     if (fd.count == 0) return cudaSuccess;
     switch (n) {
-        case 128: return launch_size<16, 8, 4, 256>(mode, fd, bd, a, st);
-        case 192: return launch_size<16, 12, 4, 384>(mode, fd, bd, a, st);
-        case 256: return launch_size<16, 16, 8, 256>(mode, fd, bd, a, st);
-        case 384: return launch_size<16, 24, 16, 384>(mode, fd, bd, a, st);
-        case 512: return launch_size<16, 32, 16, 512>(mode, fd, bd, a, st);
+#define NPBS_CASE(n) \
+    case n: return launch_fast_##n(variant, mode, fd, bd, a, st);
+        NPBS_FAST_SIZES(NPBS_CASE)
+#undef NPBS_CASE
         default: return cudaErrorInvalidValue;
     }
 }

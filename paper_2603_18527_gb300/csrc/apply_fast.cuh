@@ -12,8 +12,10 @@ struct FastDev {
 };
 
 bool fast_supported(int n);
+// number of compiled (N1, N2, cluster, threads) variants for grid side n
+int fast_variants(int n);
 cudaError_t prepare_apply_fast();
-cudaError_t launch_apply_fast(int n, int mode, const FastDev& fd, const BatchDev& bd, const ApplyArgs& a,
+cudaError_t launch_apply_fast(int n, int variant, int mode, const FastDev& fd, const BatchDev& bd, const ApplyArgs& a,
                               cudaStream_t st);
 
 }  // namespace npbs

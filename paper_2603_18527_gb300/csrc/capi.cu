@@ -4,6 +4,7 @@
 #include <cstdio>
 #include <cstdlib>
 
+#include "conv.cuh"
 #include "ctx.cuh"
 
 namespace npbs {
@@ -75,7 +76,10 @@ const Plan* get_plan(npbs_ctx* ctx, const npbs_batch* batch, npbs_status* st) {
     }
     std::string key(reinterpret_cast<const char*>(batch->inst), sizeof(npbs_instance) * batch->count);
     auto itp = ctx->plans.find(key);
-    if (itp != ctx->plans.end()) return itp->second.get();
+    if (itp != ctx->plans.end()) {
+        itp->second->last_use = ++ctx->plan_clock;
+        return itp->second.get();
+    }
 
     auto pl = std::make_unique<Plan>();
     pl->count = batch->count;
@@ -184,7 +188,15 @@ const Plan* get_plan(npbs_ctx* ctx, const npbs_batch* batch, npbs_status* st) {
     pl->nvec = (int)vit.size();
     pl->nrow32s = (int)r32s.size();
     pl->ncol32s = (int)c32s.size();
-    if (ctx->plans.size() > 64) ctx->plans.clear();
+    // bounded cache: evict the least recently used plan (no call is in flight
+    // across this point, and captured graphs never outlive the call that made them)
+    if (ctx->plans.size() >= 256) {
+        auto victim = ctx->plans.begin();
+        for (auto it = ctx->plans.begin(); it != ctx->plans.end(); ++it)
+            if (it->second->last_use < victim->second->last_use) victim = it;
+        ctx->plans.erase(victim);
+    }
+    pl->last_use = ++ctx->plan_clock;
     const Plan* out = pl.get();
     ctx->plans[key] = std::move(pl);
     return out;
@@ -206,7 +218,9 @@ npbs_status run_apply(npbs_ctx* ctx, const Plan& pl, int mode, const ApplyArgs& 
     }
     for (const auto& g : pl.fast) {
         FastDev fd{g.list, g.count};
-        NPBS_CK(ctx, launch_apply_fast(g.n, mode, fd, bd, a, st));
+        auto itv = ctx->fast_variant.find(g.n);
+        const int var = itv == ctx->fast_variant.end() ? 0 : itv->second;
+        NPBS_CK(ctx, launch_apply_fast(g.n, var, mode, fd, bd, a, st));
         ctx->count(st, 1);
     }
     if (pl.nrow32s > 0) {
@@ -286,11 +300,22 @@ npbs_status npbs_create(npbs_ctx** out, int device) {
     if (cudaSetDevice(device) != cudaSuccess) return NPBS_ERR_CUDA;
     if (prepare_apply() != cudaSuccess) return NPBS_ERR_CUDA;
     if (prepare_apply_fast() != cudaSuccess) return NPBS_ERR_CUDA;
+    if (prepare_conv_tc() != cudaSuccess) return NPBS_ERR_CUDA;
     npbs_ctx* c = new (std::nothrow) npbs_ctx();
     if (!c) return NPBS_ERR_OOM;
     c->device = device;
     const char* env = getenv("NPBS_APPLY_PATH");
     c->use_fast = !(env && strcmp(env, "three_pass") == 0);
+    // NPBS_FAST_VARIANT="256:1,512:0" pins cluster-kernel variants
+    if (const char* fv = getenv("NPBS_FAST_VARIANT")) {
+        int n = 0, v = 0, used = 0;
+        while (sscanf(fv, "%d:%d%n", &n, &v, &used) == 2) {
+            if (v >= 0 && v < fast_variants(n)) c->fast_variant[n] = v;
+            fv += used;
+            if (*fv != ',') break;
+            ++fv;
+        }
+    }
     *out = c;
     return NPBS_OK;
 }
@@ -337,6 +362,57 @@ npbs_status npbs_build_potential(npbs_ctx* ctx, const npbs_batch* batch, const v
         k0sq_out[j] = hc[2 * j];
         eps_out[j] = hc[2 * j + 1];
     }
+    return NPBS_OK;
+}
+
+npbs_status npbs_autotune_apply(npbs_ctx* ctx, const npbs_batch* batch, const void* V, const void* f, void* x,
+                                int32_t reps, int32_t* chosen, npbs_stream stream) {
+    if (!ctx) return NPBS_ERR_INVALID_ARG;
+    npbs_status st;
+    const Plan* pl = get_plan(ctx, batch, &st);
+    if (!pl) return st;
+    if (!V || !f || !x || reps < 1) return set_err(ctx, NPBS_ERR_INVALID_ARG, "npbs_autotune_apply: bad argument");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    NPBS_CK(ctx, ctx->scratch.ensure((size_t)std::max<long long>(pl->extent, 1) * 8));
+    ApplyArgs a{};
+    a.V = static_cast<const float2*>(V);
+    a.f = static_cast<const float2*>(f);
+    a.x = static_cast<const float2*>(x);
+    a.out = static_cast<float2*>(x);
+    a.scratch = ctx->scratch.p;
+    const BatchDev bd = pl->bd(false, nullptr);
+    cudaEvent_t e0, e1;
+    NPBS_CK(ctx, cudaEventCreate(&e0));
+    NPBS_CK(ctx, cudaEventCreate(&e1));
+    int gi = 0;
+    for (const auto& g : pl->fast) {
+        FastDev fd{g.list, g.count};
+        float best = 1e30f;
+        int bestv = 0;
+        for (int v = 0; v < fast_variants(g.n); ++v) {
+            cudaError_t e = launch_apply_fast(g.n, v, NPBS_CBS_STEP, fd, bd, a, s);  // warm-up
+            for (int r = 0; r < reps && e == cudaSuccess; ++r) {
+                if (r == 0) e = cudaEventRecord(e0, s);
+                if (e == cudaSuccess) e = launch_apply_fast(g.n, v, NPBS_CBS_STEP, fd, bd, a, s);
+            }
+            if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float ms = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e != cudaSuccess) {
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+                return cuda_err(ctx, e, "npbs_autotune_apply");
+            }
+            ctx->count(s, reps + 1);
+            if (ms < best) { best = ms; bestv = v; }
+        }
+        ctx->fast_variant[g.n] = bestv;
+        if (chosen) chosen[gi] = g.n * 16 + bestv;
+        ++gi;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
     return NPBS_OK;
 }
 

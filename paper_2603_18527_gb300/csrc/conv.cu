@@ -2,6 +2,10 @@
 // kernel with transformed weights / weight gradient) on the warp-level tensor
 // core MMA (m16n8k16, float32 accumulate), cp.async double buffering and
 // ldmatrix fragment loads.
+#include <atomic>
+#include <cstdlib>
+#include <cstring>
+
 #include "conv.cuh"
 
 namespace npbs {
@@ -271,9 +275,17 @@ __global__ void __launch_bounds__(kConvThreads) k_conv_wgrad(ConvWgrad a) {
 
 }  // namespace
 
+std::atomic<long long> g_conv_tc_launches{0}, g_conv_mma_launches{0};
+
 cudaError_t conv_fwd(const ConvFwd& a, cudaStream_t st) {
     const long long M = (long long)a.B * a.H * a.W;
     if (M == 0) return cudaSuccess;
+    const char* force = getenv("NPBS_CONV");
+    if (!(force && strcmp(force, "mma") == 0) && conv_tc_supported(a)) {
+        g_conv_tc_launches++;
+        return conv_fwd_tc(a, st);
+    }
+    g_conv_mma_launches++;
     if (a.Cin % 16 || a.Cout % 8 || a.xs % 8 || a.xo % 8 || a.ys % 2 || a.yo % 2) return cudaErrorInvalidValue;
     const unsigned gm = (unsigned)((M + kBM - 1) / kBM);
     const bool bk32 = a.Cin % 32 == 0;
@@ -306,3 +318,8 @@ cudaError_t conv_wgrad(const ConvWgrad& a, cudaStream_t st) {
 }
 
 }  // namespace npbs
+
+extern "C" void npbs_conv_stats(int64_t* tensor_core_launches, int64_t* warp_mma_launches) {
+    if (tensor_core_launches) *tensor_core_launches = npbs::g_conv_tc_launches.load();
+    if (warp_mma_launches) *warp_mma_launches = npbs::g_conv_mma_launches.load();
+}

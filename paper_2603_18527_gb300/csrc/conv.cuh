@@ -44,4 +44,12 @@ struct ConvWgrad {
 cudaError_t conv_fwd(const ConvFwd& a, cudaStream_t st);
 cudaError_t conv_wgrad(const ConvWgrad& a, cudaStream_t st);
 
+// tcgen05 path (conv_tc.cu): used by conv_fwd when the geometry allows TMA
+// tiling (no upsampling, W a multiple of 128 or a divisor of 128 with H*W a
+// multiple of 128, Cout a multiple of 16 up to 256).
+bool conv_tc_supported(const ConvFwd& a);
+cudaError_t conv_fwd_tc(const ConvFwd& a, cudaStream_t st);
+cudaError_t prepare_conv_tc();
+int conv_tc_timeout_flag();
+
 }  // namespace npbs

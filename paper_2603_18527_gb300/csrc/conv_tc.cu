@@ -1,0 +1,374 @@
+// 3x3 convolution (implicit GEMM) on the 5th-generation tensor cores:
+// TMA loads of the shifted input tile and of the weights into swizzled shared
+// memory, tcgen05.mma (BF16 x BF16 -> FP32) accumulating in tensor memory,
+// tcgen05.ld for the bias / GELU / BF16 epilogue.
+//
+// One CTA computes a 128-pixel x Cout tile (Cout <= 256, all output channels,
+// so each input tile is read once).  K = 9 taps x Cin in chunks of BK channels
+// (BK = 64 with the 128-byte swizzle, or 32 / 16 for narrow inputs).  The
+// 128 output pixels are a run of one image row (W >= 128) or whole rows
+// (W < 128): for tap (dy, dx) the input tile is the same run shifted by
+// (dy, dx), which a 4D TMA box [1][rows][cols][BK] at (c0, x0 + dx, y0 + dy, b)
+// fetches with hardware zero fill outside the image (the convolution's zero
+// padding).  Pipeline: 4 stages, thread 0 issues TMA, thread 32 issues MMAs
+// and commits stage releases; all 128 threads (one warpgroup, TMEM lanes
+// 0..127 = tile rows) run the epilogue.  Every mbarrier wait is bounded; a
+// timeout sets g_conv_tc_timeout and the CTA cleans up and returns.
+#include <cuda.h>
+
+#include <cstring>
+#include <mutex>
+
+#include "conv.cuh"
+
+namespace npbs {
+
+__device__ int g_conv_tc_timeout = 0;
+
+namespace {
+
+constexpr int kStages = 4;
+constexpr int kTM = 128;
+constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz
+
+__device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait: false (and the global flag set) after about two seconds.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+    if (mbar_try(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (!mbar_try(bar, parity)) {
+        if (clock64() - t0 > kWaitCycles) {
+            atomicExch(&g_conv_tc_timeout, 1);
+            return false;
+        }
+    }
+    return true;
+}
+
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map, uint32_t bar, int c0, int c1, int c2,
+                                            int c3) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5, %6}], "
+        "[%2];" ::"r"(dst),
+        "l"(map), "r"(bar), "r"(c0), "r"(c1), "r"(c2), "r"(c3)
+        : "memory");
+}
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, uint32_t bar, int c0, int c1) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
+            dst),
+        "l"(map), "r"(bar), "r"(c0), "r"(c1)
+        : "memory");
+}
+
+// K-major shared-memory matrix descriptor with swizzle (rows of `row_bytes`,
+// 8-row atoms `8 * row_bytes` apart).
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, int row_bytes) {
+    const uint64_t layout = row_bytes == 128 ? 2ull : row_bytes == 64 ? 4ull : 6ull;  // SW128 / SW64 / SW32
+    const uint64_t sbo = (uint64_t)(8 * row_bytes) >> 4;
+    uint64_t d = 0;
+    d |= (uint64_t)((addr >> 4) & 0x3FFF);
+    d |= (uint64_t)1 << 16;  // leading byte offset (unused for swizzled K-major)
+    d |= (sbo & 0x3FFF) << 32;
+    d |= (uint64_t)1 << 46;  // descriptor version
+    d |= layout << 61;
+    return d;
+}
+
+// Instruction descriptor: BF16 x BF16 -> F32, both K-major, M = 128, N = n.
+__device__ __forceinline__ uint32_t instr_desc(int n) {
+    uint32_t d = 0;
+    d |= 1u << 4;                      // D format F32
+    d |= 1u << 7;                      // A format BF16
+    d |= 1u << 10;                     // B format BF16
+    d |= (uint32_t)(n >> 3) << 17;     // N / 8
+    d |= (uint32_t)(kTM >> 4) << 24;   // M / 16
+    return d;
+}
+
+__device__ __forceinline__ void umma(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+        : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.f + erff(z * 0.70710678118654752f)); }
+
+struct TcArgs {
+    int B, H, W, Cin, Cout, BK;
+    int rows_per_tile;      // output rows per 128-pixel tile (W < 128), else 1
+    int tiles_per_row;      // W / 128 when W >= 128, else 1
+    const float* bias;
+    int act;
+    bf16* y;
+    bf16* z;
+    float* yf;
+    int ys, yo;
+    int xo;                 // channel offset of the input slice
+    int bn;                 // N of the MMA (Cout rounded up to 16)
+    int tmem_cols;
+};
+
+__global__ void __launch_bounds__(128, 1) k_conv_tc(const __grid_constant__ CUtensorMap mapx,
+                                                    const __grid_constant__ CUtensorMap mapw, TcArgs a) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    // 1024-byte aligned stage buffers (swizzle atoms), then barriers
+    unsigned char* base = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const int a_bytes = kTM * a.BK * 2;
+    const int b_bytes = a.bn * a.BK * 2;
+    const int stage_bytes = a_bytes + b_bytes;
+    unsigned char* stage0 = base;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(base + kStages * stage_bytes);  // full[4], empty[4], done
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kStages + 1);
+
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const long long m0 = (long long)blockIdx.x * kTM;
+    // tile origin
+    const long long HW = (long long)a.H * a.W;
+    const int b = (int)(m0 / HW);
+    const long long rem = m0 - (long long)b * HW;
+    const int y0 = (int)(rem / a.W);
+    const int x0 = (int)(rem % a.W);
+
+    if (tid == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(su32(&bars[s]), 1);
+            mbar_init(su32(&bars[kStages + s]), 1);
+        }
+        mbar_init(su32(&bars[2 * kStages]), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)),
+                     "r"(a.tmem_cols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+
+    const int nck = a.Cin / a.BK;
+    const int KT = 9 * nck;
+    bool ok = true;
+    if (tid == 0) {
+        // TMA producer
+        for (int kt = 0; kt < KT && ok; ++kt) {
+            const int s = kt % kStages;
+            if (kt >= kStages) ok = mbar_wait(su32(&bars[kStages + s]), ((kt / kStages) - 1) & 1);
+            if (!ok) break;
+            const int tap = kt / nck, c0 = (kt % nck) * a.BK;
+            const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+            const uint32_t full = su32(&bars[s]);
+            mbar_expect_tx(full, (uint32_t)stage_bytes);
+            unsigned char* st = stage0 + s * stage_bytes;
+            tma_load_4d(su32(st), &mapx, full, a.xo + c0, x0 + dx, y0 + dy, b);
+            tma_load_2d(su32(st + a_bytes), &mapw, full, tap * a.Cin + c0, 0);
+        }
+    } else if (tid == 32) {
+        // MMA issuer
+        const uint32_t idesc = instr_desc(a.bn);
+        const int row_bytes = a.BK * 2;
+        for (int kt = 0; kt < KT && ok; ++kt) {
+            const int s = kt % kStages;
+            ok = mbar_wait(su32(&bars[s]), (kt / kStages) & 1);
+            if (!ok) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            unsigned char* st = stage0 + s * stage_bytes;
+            const uint32_t abase = su32(st), bbase = su32(st + a_bytes);
+            for (int kk = 0; kk < a.BK / 16; ++kk) {
+                const uint64_t ad = smem_desc(abase + kk * 32, row_bytes);
+                const uint64_t bd = smem_desc(bbase + kk * 32, row_bytes);
+                umma(tmem, ad, bd, idesc, (kt > 0 || kk > 0) ? 1u : 0u);
+            }
+            umma_commit(su32(&bars[kStages + s]));  // stage s free once these MMAs complete
+        }
+        umma_commit(su32(&bars[2 * kStages]));  // accumulator complete
+    }
+    __syncwarp();
+    // epilogue: every thread owns one tile row (TMEM lane = tid)
+    const bool done = mbar_wait(su32(&bars[2 * kStages]), 0);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const long long p = m0 + tid;
+    const long long P = (long long)a.B * HW;
+    if (done) {
+        for (int c = 0; c < a.bn; c += 16) {
+            uint32_t r[16];
+            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c;
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                : "r"(taddr)
+                : "memory");
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (p >= P) continue;
+            float v[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                v[j] = __uint_as_float(r[j]);
+                if (a.bias && c + j < a.Cout) v[j] += a.bias[c + j];
+            }
+            const long long o = p * a.ys + a.yo + c;
+            if (a.yf) {
+#pragma unroll
+                for (int j = 0; j < 16; j += 4)
+                    if (c + j < a.Cout) *reinterpret_cast<float4*>(a.yf + o + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+                continue;
+            }
+            __align__(16) bf16 zb[16], yb[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                zb[j] = __float2bfloat16_rn(v[j]);
+                yb[j] = __float2bfloat16_rn(a.act ? gelu(v[j]) : v[j]);
+            }
+            if (c + 16 <= a.Cout) {
+                uint4* yd = reinterpret_cast<uint4*>(a.y + o);
+                yd[0] = reinterpret_cast<uint4*>(yb)[0];
+                yd[1] = reinterpret_cast<uint4*>(yb)[1];
+                if (a.z) {
+                    uint4* zd = reinterpret_cast<uint4*>(a.z + o);
+                    zd[0] = reinterpret_cast<uint4*>(zb)[0];
+                    zd[1] = reinterpret_cast<uint4*>(zb)[1];
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(a.tmem_cols) : "memory");
+    }
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encoder() {
+    static EncodeTiledFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    });
+    return fn;
+}
+
+size_t tc_smem(int bn, int bk) { return (size_t)kStages * (kTM + bn) * bk * 2 + 1024 + 256; }
+
+}  // namespace
+
+// Whether the tensor-core path takes this convolution (else the caller uses
+// the warp-level MMA kernel).
+bool conv_tc_supported(const ConvFwd& a) {
+    if (a.ups || !encoder()) return false;
+    if (!(a.Cin == 16 || a.Cin == 32 || a.Cin % 64 == 0)) return false;
+    if (a.Cout % 16 || a.Cout > 256 || a.Cout < 16) return false;
+    if (a.xs % 8 || a.xo % 8 || (reinterpret_cast<uintptr_t>(a.x) & 15)) return false;
+    if (a.ys % 8 || a.yo % 8) return false;
+    const long long HW = (long long)a.H * a.W;
+    if (a.W >= kTM) {
+        if (a.W % kTM) return false;
+    } else {
+        if (kTM % a.W || HW % kTM) return false;
+    }
+    return true;
+}
+
+cudaError_t conv_fwd_tc(const ConvFwd& a, cudaStream_t st) {
+    const int bk = a.Cin >= 64 ? 64 : a.Cin;
+    const int bn = a.Cout;
+    int tcols = 32;
+    while (tcols < bn) tcols <<= 1;
+    CUtensorMapSwizzle sw = bk == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : bk == 32 ? CU_TENSOR_MAP_SWIZZLE_64B
+                                                                                : CU_TENSOR_MAP_SWIZZLE_32B;
+    // input: dims (C, W, H, B), box (bk, cols, rows, 1)
+    const int cols = a.W >= kTM ? kTM : a.W;
+    const int rows = a.W >= kTM ? 1 : kTM / a.W;
+    CUtensorMap mx, mw;
+    {
+        cuuint64_t dims[4] = {(cuuint64_t)a.xs, (cuuint64_t)a.W, (cuuint64_t)a.H, (cuuint64_t)a.B};
+        cuuint64_t strides[3] = {(cuuint64_t)a.xs * 2, (cuuint64_t)a.xs * 2 * a.W, (cuuint64_t)a.xs * 2 * a.W * a.H};
+        cuuint32_t box[4] = {(cuuint32_t)bk, (cuuint32_t)cols, (cuuint32_t)rows, 1};
+        cuuint32_t es[4] = {1, 1, 1, 1};
+        if (encoder()(&mx, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<bf16*>(a.x), dims, strides, box, es,
+                      CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return cudaErrorInvalidValue;
+    }
+    {
+        cuuint64_t dims[2] = {(cuuint64_t)9 * a.Cin, (cuuint64_t)a.Cout};
+        cuuint64_t strides[1] = {(cuuint64_t)9 * a.Cin * 2};
+        cuuint32_t box[2] = {(cuuint32_t)bk, (cuuint32_t)bn};
+        cuuint32_t es[2] = {1, 1};
+        if (encoder()(&mw, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<bf16*>(a.w), dims, strides, box, es,
+                      CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return cudaErrorInvalidValue;
+    }
+    TcArgs t{};
+    t.B = a.B;
+    t.H = a.H;
+    t.W = a.W;
+    t.Cin = a.Cin;
+    t.Cout = a.Cout;
+    t.BK = bk;
+    t.rows_per_tile = rows;
+    t.tiles_per_row = a.W >= kTM ? a.W / kTM : 1;
+    t.bias = a.bias;
+    t.act = a.act;
+    t.y = a.y;
+    t.z = a.z;
+    t.yf = a.yf;
+    t.ys = a.ys;
+    t.yo = a.yo;
+    t.xo = a.xo;
+    t.bn = bn;
+    t.tmem_cols = tcols;
+    const size_t smem = tc_smem(bn, bk);
+    const long long M = (long long)a.B * a.H * a.W;
+    k_conv_tc<<<(unsigned)((M + kTM - 1) / kTM), 128, smem, st>>>(mx, mw, t);
+    return cudaGetLastError();
+}
+
+cudaError_t prepare_conv_tc() {
+    encoder();
+    return cudaFuncSetAttribute(k_conv_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem(256, 64));
+}
+
+int conv_tc_timeout_flag() {
+    int v = 0;
+    cudaMemcpyFromSymbol(&v, g_conv_tc_timeout, sizeof(int));
+    return v;
+}
+
+}  // namespace npbs

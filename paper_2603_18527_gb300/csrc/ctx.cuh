@@ -41,6 +41,7 @@ struct Plan {
     RowItem* rows32s = nullptr;
     ColItem* cols32s = nullptr;
     int nrow32s = 0, ncol32s = 0;
+    long long last_use = 0;  // LRU stamp in the context's plan cache
     BatchDev bd(bool f64, const int* active) const {
         BatchDev b;
         b.inst = inst;
@@ -70,10 +71,12 @@ struct npbs_ctx {
     int device = 0;
     std::string err;
     std::map<std::string, std::unique_ptr<npbs::Plan>> plans;
+    long long plan_clock = 0;
     npbs::DevBuf scratch;   // spectrum between apply passes
     npbs::DevBuf work[12];  // solver workspaces
     npbs::DevBuf net_ws;    // network activations
     bool use_fast = true;  // cluster apply for square 128..512 grids (NPBS_APPLY_PATH=three_pass disables)
+    std::map<int, int> fast_variant;  // grid side -> chosen cluster-kernel variant (autotuned; default 0)
     cudaStream_t solve_stream = nullptr;  // capturable stream the solvers run on
     cudaEvent_t solve_event = nullptr;
     long long launches = 0;         // kernels launched (graph launches count their kernels)

@@ -1,0 +1,168 @@
+"""Train the residual-to-correction U-Net with the library's own kernels.
+
+Training tuples (medium, source, residual) come from the method itself
+(the metric-matched objective, Eq. L_bs_Reta_integral): a pool of instances
+of the contrast media law is iterated with plain CBS (``cbs_apply`` CBS_STEP)
+and its iterates are banked at log-spaced iteration counts; every training
+batch draws instances and snapshot counts from that bank, and
+``npbs_train_step`` unrolls the NPBS iteration from those snapshots.
+Evaluation compares ``npbs_solve`` with ``cbs_solve`` (iterations and time to
+the rTol target) on held-out seeds.  Every step runs on the GPU in the
+library; this module only marshals arguments.
+
+    python -m paper_2603_18527_gb300.train_unet --grid 64 --steps 2000 --out net.bin
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import sys
+import time
+
+import numpy as np
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+from paper_2603_18527_gb300 import build, capi  # noqa: E402
+
+
+def coefficient_channel(inst, scale_by_omega: bool) -> np.ndarray:
+    """Third network input: n(x), or the local wavenumber omega n(x) so that one
+    network serves several frequencies."""
+    return inst.n * (inst.omega if scale_by_omega else 1.0)
+
+
+class Pool:
+    """A packed batch of instances with the library-side potential."""
+
+    def __init__(self, ctx, insts, scale_by_omega=True):
+        self.insts = insts
+        self.b = capi.Batch([(i.ny, i.nx) for i in insts], h=[i.h for i in insts])
+        self.k2 = self.b.pack([i.k2 for i in insts])
+        self.f = self.b.pack([i.f for i in insts])
+        self.n = self.b.pack([coefficient_channel(i, scale_by_omega) for i in insts], dtype=torch.float32)
+        self.V = torch.zeros_like(self.k2)
+        capi.npbs_build_potential(ctx, self.b, self.k2, self.V)
+
+
+def snapshot_bank(ctx, pool: Pool, max_snap: int = 2048) -> tuple[list[int], torch.Tensor]:
+    """CBS iterates of every pool instance at log-spaced iteration counts
+    0, 1, 3, 7, ..., up to max_snap (one pass of in-place complex64 CBS_STEP
+    applies over the whole pool); returns (counts, bank[count_index, extent])."""
+    counts = [0]
+    while counts[-1] * 2 + 1 <= max_snap:
+        counts.append(counts[-1] * 2 + 1)
+    u = torch.zeros(pool.b.extent, dtype=torch.complex64, device="cuda")
+    bank = torch.zeros((len(counts), pool.b.extent), dtype=torch.complex64, device="cuda")
+    done = 0
+    for ci, m in enumerate(counts):
+        while done < m:
+            capi.cbs_apply(ctx, pool.b, pool.V, pool.f, u, u, capi.CBS_STEP)
+            done += 1
+        bank[ci].copy_(u)
+    return counts, bank
+
+
+def media(grid: int, count: int, seed0: int, waves=(20.0, 40.0)):
+    """Contrast media law at any grid size (seed block seed0)."""
+    out = []
+    for i in range(count):
+        rng = np.random.default_rng(seed0 + i)
+        N = grid
+        W = max(2, N // 16)
+        g = synth.grf(rng, N, N, max(2.0, 16.0 * N / 256))
+        na, nb = rng.uniform(0.7, 1.6, size=2)
+        n = na + (nb - na) * 0.5 * (1.0 + np.tanh(g / 0.25))
+        wl = rng.uniform(*waves) * N / 256.0
+        omega = 2.0 * math.pi * wl / (N - 2 * W)
+        cy, cx = int(rng.integers(W, N - W)), int(rng.integers(W, N - W))
+        yy, xx = np.mgrid[0:N, 0:N]
+        f = np.exp(-((yy - cy) ** 2 + (xx - cx) ** 2) / (2 * 1.5 ** 2)).astype(np.complex128)
+        out.append(synth.make_instance(n, omega, W, f, seed=seed0 + i, source_kind="gaussian"))
+    return out
+
+
+def train(ctx, net, grid=64, steps=1000, batch=32, unroll=4, lr=1e-3, wd=1e-6, pool_size=256, seed=3000,
+          max_snap=2048, log_every=50, log=print):
+    """Metric-matched training on a pool of contrast media; each step draws
+    `batch` instances and, for each, a CBS snapshot at a log-uniform iteration
+    count, and runs one npbs_train_step (4 unrolled NPBS steps, AdamW)."""
+    rng = np.random.default_rng(seed)
+    insts = media(grid, pool_size, seed)
+    pool = Pool(ctx, insts)
+    counts, bank = snapshot_bank(ctx, pool, max_snap)
+    np_ = grid * grid
+    if pool.b.extent != pool_size * np_:
+        raise ValueError("grid * grid must be a multiple of 32 (packed pool layout)")
+    pV, pf = pool.V.view(pool_size, np_), pool.f.view(pool_size, np_)
+    pn, pb = pool.n.view(pool_size, np_), bank.view(len(counts), pool_size, np_)
+    history = []
+    t0 = time.time()
+    sb = capi.Batch([(grid, grid)] * batch, h=[1.0] * batch)
+    for step in range(steps):
+        idx = rng.choice(pool_size, size=batch, replace=False)
+        ci = rng.integers(0, len(counts), size=batch)
+        it = torch.from_numpy(idx).cuda()
+        V = pV.index_select(0, it).reshape(-1)
+        f = pf.index_select(0, it).reshape(-1)
+        n = pn.index_select(0, it).reshape(-1)
+        u0 = pb[torch.from_numpy(ci).cuda(), it].reshape(-1)
+        sb.k0sq = [pool.b.k0sq[i] for i in idx]
+        sb.eps = [pool.b.eps[i] for i in idx]
+        loss = capi.npbs_train_step(ctx, net, sb, V, f, n, u0, unroll=unroll, lr=lr, weight_decay=wd)
+        history.append(loss)
+        if log and (step % log_every == 0 or step == steps - 1):
+            log(json.dumps({"step": step, "loss": loss, "mean_last": float(np.mean(history[-log_every:])),
+                            "elapsed_s": round(time.time() - t0, 1)}))
+    return history
+
+
+def evaluate(ctx, net, grid=64, count=16, seed=9000, tol=1e-5, max_iter=20000):
+    insts = media(grid, count, seed)
+    pool = Pool(ctx, insts)
+    res = {}
+    for name in ["cbs", "npbs"]:
+        u = torch.zeros(pool.b.extent, dtype=torch.complex128, device="cuda")
+        torch.cuda.synchronize()
+        t = time.time()
+        if name == "cbs":
+            st, rep = capi.cbs_solve(ctx, pool.b, pool.k2, pool.f, u, rtol=tol, max_iter=max_iter, check_every=16)
+        else:
+            st, rep = capi.npbs_solve(ctx, net, pool.b, pool.k2, pool.f, pool.n, u, rtol=tol, max_iter=max_iter,
+                                      check_every=4)
+        torch.cuda.synchronize()
+        res[name] = {"iters": rep["iters"], "rtol": rep["rtol"], "status": rep["status"],
+                     "fallback": rep.get("fallback"), "seconds": time.time() - t}
+    return res
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--grid", type=int, default=64)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--batch", type=int, default=32)
+    ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--out", default="")
+    ap.add_argument("--eval", type=int, default=16)
+    ap.add_argument("--max-snap", type=int, default=2048)
+    args = ap.parse_args()
+    build.build()
+    ctx = capi.Context(0)
+    net = capi.Net(0, seed=args.seed)
+    train(ctx, net, grid=args.grid, steps=args.steps, batch=args.batch, lr=args.lr, max_snap=args.max_snap)
+    if args.out:
+        net.save(args.out)
+    if args.eval:
+        print(json.dumps(evaluate(ctx, net, grid=args.grid, count=args.eval)))
+
+
+if __name__ == "__main__":
+    main()

@@ -155,3 +155,36 @@ def test_cluster_path_matches_three_pass_path(env, monkeypatch):
         for j in range(b.count):
             assert rel_l2(A[j], B[j]) <= 2e-6, (mode, SHAPES[j])
         assert np.allclose(n1.cpu().numpy(), n2.cpu().numpy(), rtol=1e-5)
+
+
+@pytest.mark.parametrize("side,variants", [(128, 3), (192, 3), (256, 3), (384, 1), (512, 2)])
+def test_every_cluster_variant_matches_three_pass(side, variants, monkeypatch):
+    """Each compiled (factorisation, cluster size, threads) variant that the
+    autotuner may pick gives the three-launch result for every mode."""
+    capi, c0 = ctx()
+    insts = [synth.small_instance(side, side, seed=200 + j, layer=side // 16) for j in range(2)]
+    b, k2, f, n, V = setup_batch(capi, c0, insts)
+    x = b.pack([random_field((side, side), 210 + j) for j in range(2)])
+    monkeypatch.setenv("NPBS_APPLY_PATH", "three_pass")
+    c3 = capi.Context(0)
+    monkeypatch.delenv("NPBS_APPLY_PATH")
+    for v in range(variants):
+        monkeypatch.setenv("NPBS_FAST_VARIANT", f"{side}:{v}")
+        cv = capi.Context(0)
+        for mode in ["RESIDUAL", "CBS_STEP", "OP_B", "ADJ_B", "TRUE_RESIDUAL", "PREC_SWEEP"]:
+            o1, o2 = torch.zeros_like(x), torch.zeros_like(x)
+            capi.cbs_apply(cv, b, V, f, x, o1, getattr(capi, mode))
+            capi.cbs_apply(c3, b, V, f, x, o2, getattr(capi, mode))
+            torch.cuda.synchronize()
+            A, B = b.unpack(o1), b.unpack(o2)
+            for j in range(2):
+                assert rel_l2(A[j], B[j]) <= 2e-6, (side, v, mode)
+
+
+def test_autotuner_picks_a_valid_variant():
+    capi, c = ctx()
+    insts = [synth.small_instance(256, 256, seed=230 + j, layer=16) for j in range(4)]
+    b, k2, f, n, V = setup_batch(capi, c, insts)
+    x = torch.zeros(b.extent, dtype=torch.complex64, device="cuda")
+    tuned = capi.npbs_autotune_apply(c, b, V, f, x, reps=2)
+    assert set(tuned) == {256} and 0 <= tuned[256] < 3
