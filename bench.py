@@ -295,9 +295,28 @@ def main():
     ap.add_argument("--fgmres-count", type=int, default=2)
     ap.add_argument("--fgmres-max-iter", type=int, default=400)
     ap.add_argument("--no-learned", action="store_true", help="skip the network / NPBS / FGMRES sections")
+    ap.add_argument("--net-forward-only", action="store_true",
+                    help="time only the network forward on --npbs-count 256^2 instances (for profiler captures)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.net_forward_only:
+        from paper_2603_18527_gb300 import build, capi
+        from paper_2603_18527_gb300 import train_unet as T
+        build.build()
+        ctx = capi.Context(0)
+        net = capi.Net(0, seed=0)
+        pool = T.Pool(ctx, T.media(256, args.npbs_count, 2000))
+        r = torch.randn(pool.b.extent, dtype=torch.complex64, device="cuda")
+        c = torch.zeros_like(r)
+        fwd = lambda: capi.npbs_net_forward(ctx, net, pool.b, r, pool.n, c)
+        for _ in range(args.warmup):
+            fwd()
+        ms = timed(torch.cuda.current_stream(), fwd, max(1, args.steps))
+        fl = unet_forward_flops(256, 256) * args.npbs_count
+        print(json.dumps({"net_forward_only": args.npbs_count, "ms": ms, "tflops": fl / (ms * 1e-3) / 1e12,
+                          "conv_launches": capi.npbs_conv_stats()}), flush=True)
+        return 0
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

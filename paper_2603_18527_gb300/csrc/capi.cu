@@ -21,7 +21,10 @@ Plan::~Plan() {
     cudaFree(vitems);
     cudaFree(rows32s);
     cudaFree(cols32s);
-    for (auto& g : fast) cudaFree(g.list);
+    for (auto& g : fast) {
+        cudaFree(g.list);
+        cudaFree(g.alist);
+    }
 }
 
 cudaError_t DevBuf::ensure(size_t need) {
@@ -174,7 +177,10 @@ const Plan* get_plan(npbs_ctx* ctx, const npbs_batch* batch, npbs_status* st) {
         Plan::FastGroup g;
         g.n = kv.first;
         g.count = (int)kv.second.size();
+        g.list_h = kv.second;
         e = upload(&g.list, kv.second);
+        if (e == cudaSuccess) e = upload(&g.alist, kv.second);
+        g.acount = g.count;
         pl->fast.push_back(g);
     }
     if (e != cudaSuccess) {
@@ -216,8 +222,10 @@ npbs_status run_apply(npbs_ctx* ctx, const Plan& pl, int mode, const ApplyArgs& 
         ctx->count(st, 3);
         return NPBS_OK;
     }
+    const bool compact = active && active == pl.alist_mask;
     for (const auto& g : pl.fast) {
-        FastDev fd{g.list, g.count};
+        FastDev fd{compact ? g.alist : g.list, compact ? g.acount : g.count};
+        if (fd.count == 0) continue;
         auto itv = ctx->fast_variant.find(g.n);
         const int var = itv == ctx->fast_variant.end() ? 0 : itv->second;
         NPBS_CK(ctx, launch_apply_fast(g.n, var, mode, fd, bd, a, st));
@@ -229,6 +237,18 @@ npbs_status run_apply(npbs_ctx* ctx, const Plan& pl, int mode, const ApplyArgs& 
         NPBS_CK(ctx, launch_apply(mode, bd, pl.nrow32s, pl.ncol32s, a, st));
         ctx->count(st, 3);
     }
+    return NPBS_OK;
+}
+
+npbs_status set_active_lists(npbs_ctx* ctx, const Plan& pl, const std::vector<int>& act, const int* active_dev) {
+    for (const auto& g : pl.fast) {
+        std::vector<int> l;
+        for (int j : g.list_h)
+            if (act[j]) l.push_back(j);
+        if (!l.empty()) NPBS_CK(ctx, cudaMemcpy(g.alist, l.data(), sizeof(int) * l.size(), cudaMemcpyHostToDevice));
+        g.acount = (int)l.size();
+    }
+    pl.alist_mask = active_dev;
     return NPBS_OK;
 }
 

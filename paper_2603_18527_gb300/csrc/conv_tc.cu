@@ -16,6 +16,8 @@
 // timeout sets g_conv_tc_timeout and the CTA cleans up and returns.
 #include <cuda.h>
 
+#include <algorithm>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 
@@ -266,6 +268,165 @@ __global__ void __launch_bounds__(128, 1) k_conv_tc(const __grid_constant__ CUte
     }
 }
 
+
+// Persistent, warp-specialised variant: warps 0-3 drain TMEM (epilogue),
+// warp 4 issues TMA, warp 5 issues MMAs.  Each CTA walks tiles
+// blockIdx.x, blockIdx.x + gridDim.x, ...; the smem pipeline runs across tile
+// boundaries and two TMEM accumulators let the epilogue of one tile overlap
+// the MMAs of the next.
+__global__ void __launch_bounds__(192, 1) k_conv_tc_persist(const __grid_constant__ CUtensorMap mapx,
+                                                            const __grid_constant__ CUtensorMap mapw, TcArgs a,
+                                                            int ntiles) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* base = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const int a_bytes = kTM * a.BK * 2;
+    const int b_bytes = a.bn * a.BK * 2;
+    const int stage_bytes = a_bytes + b_bytes;
+    unsigned char* stage0 = base;
+    // full[S], empty[S], tfull[2], tempty[2]
+    uint64_t* bars = reinterpret_cast<uint64_t*>(base + kStages * stage_bytes);
+    uint64_t* full = bars;
+    uint64_t* empty = bars + kStages;
+    uint64_t* tfull = bars + 2 * kStages;
+    uint64_t* tempty = bars + 2 * kStages + 2;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kStages + 4);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const long long HW = (long long)a.H * a.W;
+    if (tid == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(su32(&full[s]), 1);
+            mbar_init(su32(&empty[s]), 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(su32(&tfull[b]), 1);
+            mbar_init(su32(&tempty[b]), 128);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 4) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)),
+                     "r"(a.tmem_cols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+    const int nck = a.Cin / a.BK;
+    const int KT = 9 * nck;
+    const int my_tiles = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+
+    if (warp == 4) {
+        if (lane == 0) {
+            bool ok = true;
+            long long g = 0;
+            for (int i = 0; i < my_tiles && ok; ++i) {
+                const long long m0 = (long long)(blockIdx.x + (long long)i * gridDim.x) * kTM;
+                const int b = (int)(m0 / HW);
+                const long long rem = m0 - (long long)b * HW;
+                const int y0 = (int)(rem / a.W), x0 = (int)(rem % a.W);
+                for (int kt = 0; kt < KT && ok; ++kt, ++g) {
+                    const int s = (int)(g % kStages);
+                    if (g >= kStages) ok = mbar_wait(su32(&empty[s]), (uint32_t)(((g / kStages) - 1) & 1));
+                    if (!ok) break;
+                    const int tap = kt / nck, c0 = (kt % nck) * a.BK;
+                    mbar_expect_tx(su32(&full[s]), (uint32_t)stage_bytes);
+                    unsigned char* st = stage0 + s * stage_bytes;
+                    tma_load_4d(su32(st), &mapx, su32(&full[s]), a.xo + c0, x0 + tap % 3 - 1, y0 + tap / 3 - 1, b);
+                    tma_load_2d(su32(st + a_bytes), &mapw, su32(&full[s]), tap * a.Cin + c0, 0);
+                }
+            }
+        }
+    } else if (warp == 5) {
+        if (lane == 0) {
+            const uint32_t idesc = instr_desc(a.bn);
+            const int row_bytes = a.BK * 2;
+            bool ok = true;
+            long long g = 0;
+            for (int i = 0; i < my_tiles && ok; ++i) {
+                const int buf = i & 1;
+                if (i >= 2) ok = mbar_wait(su32(&tempty[buf]), (uint32_t)(((i >> 1) - 1) & 1));
+                if (!ok) break;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t acc_addr = tmem + (uint32_t)(buf * a.bn);
+                for (int kt = 0; kt < KT && ok; ++kt, ++g) {
+                    const int s = (int)(g % kStages);
+                    ok = mbar_wait(su32(&full[s]), (uint32_t)((g / kStages) & 1));
+                    if (!ok) break;
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    unsigned char* st = stage0 + s * stage_bytes;
+                    const uint32_t abase = su32(st), bbase = su32(st + a_bytes);
+                    for (int kk = 0; kk < a.BK / 16; ++kk)
+                        umma(acc_addr, smem_desc(abase + kk * 32, row_bytes), smem_desc(bbase + kk * 32, row_bytes), idesc,
+                             (kt > 0 || kk > 0) ? 1u : 0u);
+                    umma_commit(su32(&empty[s]));
+                }
+                umma_commit(su32(&tfull[buf]));
+            }
+        }
+    } else {
+        // epilogue warps 0..3: TMEM lanes 32 * warp .. 32 * warp + 31
+        const long long P = (long long)a.B * HW;
+        for (int i = 0; i < my_tiles; ++i) {
+            const int buf = i & 1;
+            if (!mbar_wait(su32(&tfull[buf]), (uint32_t)((i >> 1) & 1))) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const long long p = (long long)(blockIdx.x + (long long)i * gridDim.x) * kTM + tid;
+            for (int c = 0; c < a.bn; c += 16) {
+                uint32_t r[16];
+                const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(buf * a.bn + c);
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                    : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                      "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                    : "r"(taddr)
+                    : "memory");
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                if (p >= P) continue;
+                float v[16];
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    v[j] = __uint_as_float(r[j]);
+                    if (a.bias && c + j < a.Cout) v[j] += a.bias[c + j];
+                }
+                const long long o = p * a.ys + a.yo + c;
+                if (a.yf) {
+#pragma unroll
+                    for (int j = 0; j < 16; j += 4)
+                        if (c + j < a.Cout)
+                            *reinterpret_cast<float4*>(a.yf + o + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+                    continue;
+                }
+                __align__(16) bf16 zb[16], yb[16];
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    zb[j] = __float2bfloat16_rn(v[j]);
+                    yb[j] = __float2bfloat16_rn(a.act ? gelu(v[j]) : v[j]);
+                }
+                if (c + 16 <= a.Cout) {
+                    uint4* yd = reinterpret_cast<uint4*>(a.y + o);
+                    yd[0] = reinterpret_cast<uint4*>(yb)[0];
+                    yd[1] = reinterpret_cast<uint4*>(yb)[1];
+                    if (a.z) {
+                        uint4* zd = reinterpret_cast<uint4*>(a.z + o);
+                        zd[0] = reinterpret_cast<uint4*>(zb)[0];
+                        zd[1] = reinterpret_cast<uint4*>(zb)[1];
+                    }
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(&tempty[buf])) : "memory");
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 4) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(a.tmem_cols) : "memory");
+    }
+}
+
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -284,6 +445,9 @@ EncodeTiledFn encoder() {
 }
 
 size_t tc_smem(int bn, int bk) { return (size_t)kStages * (kTM + bn) * bk * 2 + 1024 + 256; }
+
+bool g_tc_persistent = true;
+int g_tc_blocks_per_sm_cap = 4;
 
 }  // namespace
 
@@ -356,13 +520,31 @@ cudaError_t conv_fwd_tc(const ConvFwd& a, cudaStream_t st) {
     t.tmem_cols = tcols;
     const size_t smem = tc_smem(bn, bk);
     const long long M = (long long)a.B * a.H * a.W;
-    k_conv_tc<<<(unsigned)((M + kTM - 1) / kTM), 128, smem, st>>>(mx, mw, t);
+    const int ntiles = (int)((M + kTM - 1) / kTM);
+    if (g_tc_persistent) {
+        int tc2 = 32;
+        while (tc2 < 2 * bn) tc2 <<= 1;
+        t.tmem_cols = tc2;
+        const int per_sm = std::max(1, std::min(512 / tc2, g_tc_blocks_per_sm_cap));
+        int dev = 0, nsm = 0, occ = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_conv_tc_persist, 192, smem);
+        const int grid = std::max(1, std::min(ntiles, nsm * std::max(1, std::min(occ, per_sm))));
+        k_conv_tc_persist<<<grid, 192, smem, st>>>(mx, mw, t, ntiles);
+        return cudaGetLastError();
+    }
+    k_conv_tc<<<(unsigned)ntiles, 128, smem, st>>>(mx, mw, t);
     return cudaGetLastError();
 }
 
 cudaError_t prepare_conv_tc() {
     encoder();
-    return cudaFuncSetAttribute(k_conv_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem(256, 64));
+    if (const char* e = getenv("NPBS_CONV_TC")) g_tc_persistent = strcmp(e, "tile") != 0;
+    cudaError_t e = cudaFuncSetAttribute(k_conv_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem(256, 64));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_conv_tc_persist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem(256, 64));
+    return e;
 }
 
 int conv_tc_timeout_flag() {

@@ -36,7 +36,12 @@ struct Plan {
         int n = 0;
         int* list = nullptr;
         int count = 0;
+        std::vector<int> list_h;
+        // compacted active subset for the mask `alist_mask` (set_active_lists)
+        int* alist = nullptr;
+        mutable int acount = 0;
     };
+    mutable const int* alist_mask = nullptr;
     std::vector<FastGroup> fast;
     RowItem* rows32s = nullptr;
     ColItem* cols32s = nullptr;
@@ -99,6 +104,12 @@ const Plan* get_plan(npbs_ctx* ctx, const npbs_batch* batch, npbs_status* st);
 // Launch one apply of `mode` on the plan (float32 modes or kTrueRes64).
 npbs_status run_apply(npbs_ctx* ctx, const Plan& pl, int mode, const ApplyArgs& a, const int* active,
                       cudaStream_t st);
+// Record which instances the device mask `active_dev` currently enables (host
+// copy `act`): cluster-kernel launches under that mask then cover only those
+// instances and skip empty size groups.  Call outside stream capture whenever
+// an instance becomes active again; deactivations only make the lists loose
+// (the kernels still check the mask).  Synchronous.
+npbs_status set_active_lists(npbs_ctx* ctx, const Plan& pl, const std::vector<int>& act, const int* active_dev);
 
 }  // namespace npbs
 

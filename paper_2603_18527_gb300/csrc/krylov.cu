@@ -364,6 +364,9 @@ extern "C" npbs_status fgmres_solve(npbs_ctx* ctx, const npbs_net* net, const np
         }
         NPBS_CK(ctx, cudaMemcpyAsync(g, g0.data(), sizeof(double2) * cnt * ldh, cudaMemcpyHostToDevice, s));
         NPBS_CK(ctx, cudaMemcpyAsync(act_cyc, cyc.data(), sizeof(int) * cnt, cudaMemcpyHostToDevice, s));
+        NPBS_CK(ctx, cudaStreamSynchronize(s));
+        r = set_active_lists(ctx, *pl, cyc, act_cyc);
+        if (r != NPBS_OK) return r;
         for (int j = 0; j < m; ++j) {
             float2* vj = Vb + ext * j;
             float2* zj = nz ? Zb + ext * j : vj;
@@ -403,6 +406,9 @@ extern "C" npbs_status fgmres_solve(npbs_ctx* ctx, const npbs_net* net, const np
             }
             if (!any_c) break;
             NPBS_CK(ctx, cudaMemcpyAsync(act_cyc, cyc.data(), sizeof(int) * cnt, cudaMemcpyHostToDevice, s));
+            NPBS_CK(ctx, cudaStreamSynchronize(s));
+            r = set_active_lists(ctx, *pl, cyc, act_cyc);
+            if (r != NPBS_OK) return r;
         }
         // delta = Z y
         NPBS_CK(ctx, cudaMemcpyAsync(ksteps, ks.data(), sizeof(int) * cnt, cudaMemcpyHostToDevice, s));

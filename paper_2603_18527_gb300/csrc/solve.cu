@@ -164,6 +164,10 @@ npbs_status refine_driver(npbs_ctx* ctx, const Plan& pl, const float2* k2, const
         if (!any) break;
         {
             shape_changed = false;
+            // the device mask was just uploaded by the refresh: compact the
+            // per-size launch lists to the instances still iterating
+            s = set_active_lists(ctx, pl, act, active);
+            if (s != NPBS_OK) return s;
             s = notify();
             if (s != NPBS_OK) return s;
             if (shape_changed && graph_ready) {
