@@ -220,6 +220,19 @@ def bench_fgmres(capi, ctx, args):
     return res
 
 
+def aggregate_over_ranks(ms_local: float, units_local: float, dist=None, device=None):
+    """Replica aggregation: the step time is the max over ranks (a barrier
+    brackets the timed region) and the work is the sum over ranks.  Returns
+    (ms_max, units_total).  Without a process group it is the identity."""
+    if dist is None or not dist.is_initialized():
+        return ms_local, units_local
+    t = torch.tensor([ms_local, units_local], dtype=torch.float64, device=device)
+    m = t.clone()
+    dist.all_reduce(m, op=dist.ReduceOp.MAX)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(m[0]), float(t[1])
+
+
 def make_workload(args):
     if args.workload == "mixed":
         return synth.workload_mixed(args.n256, args.nother), "cbs_mixed_256x256^2+64x{128,192,384,512}^2"
@@ -382,13 +395,11 @@ def main():
         torch.cuda.synchronize()
     ms = ev0.elapsed_time(ev1) / args.steps
     launches = (capi.launch_count(ctx) - launches0) // args.steps
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t)
+    # each rank solves its own replica of the batch (weak scaling): the job
+    # solved world x eq instances in the slowest rank's time
+    ms, eq_total = aggregate_over_ranks(ms, equiv_256(insts), dist, torch.device("cuda"))
     eq = equiv_256(insts)
-    value = ms / eq  # each rank solves its own replica of the batch (weak scaling)
-    value = value / world
+    value = ms / eq_total
     conv = sum(1 for s in rep["status"] if s == capi.OK)
 
     # apply roofline: CBS_STEP over the whole batch, timed alone

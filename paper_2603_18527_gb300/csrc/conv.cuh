@@ -21,6 +21,7 @@ struct ConvFwd {
     int ups;            // 1: nearest-neighbour x2 upsampling folded into the gather
     int Cin, Cout;      // Cin multiple of 16, Cout multiple of 8
     const bf16* w;      // [Cout][9][Cin]
+    const bf16* w_sub;  // ups only (nullable): [parity py*2+px][Cout][4][Cin], 2x2 sub-pixel weights
     const float* bias;  // [Cout] or null
     int act;            // 1: GELU (erf form)
     bf16* y;            // output [B][H][W][ys] at channel offset yo (bf16) ...

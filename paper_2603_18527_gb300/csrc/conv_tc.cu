@@ -121,7 +121,10 @@ __device__ __forceinline__ void umma_commit(uint32_t bar) {
 __device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.f + erff(z * 0.70710678118654752f)); }
 
 struct TcArgs {
-    int B, H, W, Cin, Cout, BK;
+    int B, H, W, Cin, Cout, BK;   // H, W: the grid the 128-pixel tiles walk (half resolution for sub-pixel)
+    int ntaps;                    // 9 (3x3) or 4 (2x2 sub-pixel convolution)
+    int tdy[9], tdx[9];           // input offsets of each tap
+    int sub, py, px, Ho, Wo;      // sub-pixel output: pixel (Y, X) of the tile grid -> (2Y + py, 2X + px) of Ho x Wo
     int rows_per_tile;      // output rows per 128-pixel tile (W < 128), else 1
     int tiles_per_row;      // W / 128 when W >= 128, else 1
     const float* bias;
@@ -176,7 +179,7 @@ __global__ void __launch_bounds__(128, 1) k_conv_tc(const __grid_constant__ CUte
     const uint32_t tmem = *tmem_slot;
 
     const int nck = a.Cin / a.BK;
-    const int KT = 9 * nck;
+    const int KT = a.ntaps * nck;
     bool ok = true;
     if (tid == 0) {
         // TMA producer
@@ -185,7 +188,7 @@ __global__ void __launch_bounds__(128, 1) k_conv_tc(const __grid_constant__ CUte
             if (kt >= kStages) ok = mbar_wait(su32(&bars[kStages + s]), ((kt / kStages) - 1) & 1);
             if (!ok) break;
             const int tap = kt / nck, c0 = (kt % nck) * a.BK;
-            const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+            const int dy = a.tdy[tap], dx = a.tdx[tap];
             const uint32_t full = su32(&bars[s]);
             mbar_expect_tx(full, (uint32_t)stage_bytes);
             unsigned char* st = stage0 + s * stage_bytes;
@@ -216,8 +219,14 @@ __global__ void __launch_bounds__(128, 1) k_conv_tc(const __grid_constant__ CUte
     // epilogue: every thread owns one tile row (TMEM lane = tid)
     const bool done = mbar_wait(su32(&bars[2 * kStages]), 0);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const long long p = m0 + tid;
+    const long long q = m0 + tid;
     const long long P = (long long)a.B * HW;
+    long long p = q;
+    if (a.sub) {
+        const int qb = (int)(q / HW);
+        const long long qr = q - (long long)qb * HW;
+        p = ((long long)qb * a.Ho + 2 * (qr / a.W) + a.py) * a.Wo + 2 * (qr % a.W) + a.px;
+    }
     if (done) {
         for (int c = 0; c < a.bn; c += 16) {
             uint32_t r[16];
@@ -229,7 +238,7 @@ __global__ void __launch_bounds__(128, 1) k_conv_tc(const __grid_constant__ CUte
                 : "r"(taddr)
                 : "memory");
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            if (p >= P) continue;
+            if (q >= P) continue;
             float v[16];
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
@@ -315,7 +324,7 @@ __global__ void __launch_bounds__(192, 1) k_conv_tc_persist(const __grid_constan
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tmem_slot;
     const int nck = a.Cin / a.BK;
-    const int KT = 9 * nck;
+    const int KT = a.ntaps * nck;
     const int my_tiles = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
 
     if (warp == 4) {
@@ -334,7 +343,7 @@ __global__ void __launch_bounds__(192, 1) k_conv_tc_persist(const __grid_constan
                     const int tap = kt / nck, c0 = (kt % nck) * a.BK;
                     mbar_expect_tx(su32(&full[s]), (uint32_t)stage_bytes);
                     unsigned char* st = stage0 + s * stage_bytes;
-                    tma_load_4d(su32(st), &mapx, su32(&full[s]), a.xo + c0, x0 + tap % 3 - 1, y0 + tap / 3 - 1, b);
+                    tma_load_4d(su32(st), &mapx, su32(&full[s]), a.xo + c0, x0 + a.tdx[tap], y0 + a.tdy[tap], b);
                     tma_load_2d(su32(st + a_bytes), &mapw, su32(&full[s]), tap * a.Cin + c0, 0);
                 }
             }
@@ -373,7 +382,13 @@ __global__ void __launch_bounds__(192, 1) k_conv_tc_persist(const __grid_constan
             const int buf = i & 1;
             if (!mbar_wait(su32(&tfull[buf]), (uint32_t)((i >> 1) & 1))) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const long long p = (long long)(blockIdx.x + (long long)i * gridDim.x) * kTM + tid;
+            const long long q = (long long)(blockIdx.x + (long long)i * gridDim.x) * kTM + tid;
+            long long p = q;
+            if (a.sub) {
+                const int qb = (int)(q / HW);
+                const long long qr = q - (long long)qb * HW;
+                p = ((long long)qb * a.Ho + 2 * (qr / a.W) + a.py) * a.Wo + 2 * (qr % a.W) + a.px;
+            }
             for (int c = 0; c < a.bn; c += 16) {
                 uint32_t r[16];
                 const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(buf * a.bn + c);
@@ -384,7 +399,7 @@ __global__ void __launch_bounds__(192, 1) k_conv_tc_persist(const __grid_constan
                     : "r"(taddr)
                     : "memory");
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                if (p >= P) continue;
+                if (q >= P) continue;
                 float v[16];
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
@@ -453,22 +468,48 @@ int g_tc_blocks_per_sm_cap = 4;
 
 // Whether the tensor-core path takes this convolution (else the caller uses
 // the warp-level MMA kernel).
+static bool tc_grid_ok(int H, int W) {
+    const long long HW = (long long)H * W;
+    if (W >= kTM) return W % kTM == 0;
+    return kTM % W == 0 && HW % kTM == 0;
+}
+
 bool conv_tc_supported(const ConvFwd& a) {
-    if (a.ups || !encoder()) return false;
+    if (!encoder()) return false;
+    if (a.ups) {
+        if (!a.w_sub || (a.H & 1) || (a.W & 1) || !tc_grid_ok(a.H / 2, a.W / 2)) return false;
+    } else if (!tc_grid_ok(a.H, a.W)) {
+        return false;
+    }
     if (!(a.Cin == 16 || a.Cin == 32 || a.Cin % 64 == 0)) return false;
     if (a.Cout % 16 || a.Cout > 256 || a.Cout < 16) return false;
     if (a.xs % 8 || a.xo % 8 || (reinterpret_cast<uintptr_t>(a.x) & 15)) return false;
     if (a.ys % 8 || a.yo % 8) return false;
-    const long long HW = (long long)a.H * a.W;
-    if (a.W >= kTM) {
-        if (a.W % kTM) return false;
-    } else {
-        if (kTM % a.W || HW % kTM) return false;
-    }
     return true;
 }
 
+static cudaError_t conv_fwd_tc_one(const ConvFwd& a, cudaStream_t st, int sub, int py, int px);
+
 cudaError_t conv_fwd_tc(const ConvFwd& a, cudaStream_t st) {
+    if (!a.ups) return conv_fwd_tc_one(a, st, 0, 0, 0);
+    // nearest x2 upsampling + 3x3 conv == four 2x2 convolutions of the half-res
+    // input (one per output parity) with pre-summed weights
+    for (int py = 0; py < 2; ++py)
+        for (int px = 0; px < 2; ++px) {
+            cudaError_t e = conv_fwd_tc_one(a, st, 1, py, px);
+            if (e != cudaSuccess) return e;
+        }
+    return cudaSuccess;
+}
+
+static cudaError_t conv_fwd_tc_one(const ConvFwd& a0, cudaStream_t st, int sub, int py, int px) {
+    ConvFwd a = a0;
+    const int ntaps = sub ? 4 : 9;
+    if (sub) {
+        a.H = a0.H / 2;
+        a.W = a0.W / 2;
+        a.w = a0.w_sub + (size_t)(py * 2 + px) * a0.Cout * 4 * a0.Cin;
+    }
     const int bk = a.Cin >= 64 ? 64 : a.Cin;
     const int bn = a.Cout;
     int tcols = 32;
@@ -490,8 +531,8 @@ cudaError_t conv_fwd_tc(const ConvFwd& a, cudaStream_t st) {
             return cudaErrorInvalidValue;
     }
     {
-        cuuint64_t dims[2] = {(cuuint64_t)9 * a.Cin, (cuuint64_t)a.Cout};
-        cuuint64_t strides[1] = {(cuuint64_t)9 * a.Cin * 2};
+        cuuint64_t dims[2] = {(cuuint64_t)ntaps * a.Cin, (cuuint64_t)a.Cout};
+        cuuint64_t strides[1] = {(cuuint64_t)ntaps * a.Cin * 2};
         cuuint32_t box[2] = {(cuuint32_t)bk, (cuuint32_t)bn};
         cuuint32_t es[2] = {1, 1};
         if (encoder()(&mw, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<bf16*>(a.w), dims, strides, box, es,
@@ -506,6 +547,22 @@ cudaError_t conv_fwd_tc(const ConvFwd& a, cudaStream_t st) {
     t.Cin = a.Cin;
     t.Cout = a.Cout;
     t.BK = bk;
+    t.ntaps = ntaps;
+    for (int k = 0; k < ntaps; ++k) {
+        if (sub) {
+            // offsets {p - 1, p} at half resolution for output parity p
+            t.tdy[k] = (k >> 1) + py - 1;
+            t.tdx[k] = (k & 1) + px - 1;
+        } else {
+            t.tdy[k] = k / 3 - 1;
+            t.tdx[k] = k % 3 - 1;
+        }
+    }
+    t.sub = sub;
+    t.py = py;
+    t.px = px;
+    t.Ho = a0.H;
+    t.Wo = a0.W;
     t.rows_per_tile = rows;
     t.tiles_per_row = a.W >= kTM ? a.W / kTM : 1;
     t.bias = a.bias;

@@ -31,7 +31,9 @@ struct Net {
     float* m2 = nullptr;
     bf16* wb = nullptr;  // bfloat16 copy, [Cout][9][Cin_pad]
     bf16* wt = nullptr;  // flipped transpose for data gradients, [Cin_pad][9][Cout]
+    bf16* wsub = nullptr;  // upsampling convs: 2x2 sub-pixel weights [4 parities][Cout][4][Cin_pad]
     std::vector<long long> wb_off;
+    std::vector<long long> wsub_off;  // -1 for convs without upsampling
     npbs_status alloc(int dev);
     cudaError_t refresh_bf16(cudaStream_t st) const;
     ~Net();

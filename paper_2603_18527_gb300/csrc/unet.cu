@@ -71,13 +71,12 @@ __device__ __forceinline__ float gelu_grad(float z) {
     return 0.5f * (1.f + erff(z * 0.70710678118654752f)) + z * 0.39894228040143268f * expf(-0.5f * z * z);
 }
 
-// s[slot] = sqrt(mean |r|^2) over the slot's instance
-__global__ void k_slot_rms(const SlotDev sd, const float2* r, float* s) {
-    const int slot = blockIdx.x;
+// acc[slot] += sum |r|^2 over a chunk of the slot's instance (grid: chunks x slots)
+__global__ void k_slot_sumsq(const SlotDev sd, const float2* r, double* acc2) {
+    const int slot = blockIdx.y;
     const long long base = sd.off[slot];
-    const long long np = sd.np;
     double acc = 0.0;
-    for (long long e = threadIdx.x; e < np; e += blockDim.x) {
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < sd.np; e += (long long)gridDim.x * blockDim.x) {
         const float2 v = r[base + e];
         acc += (double)v.x * v.x + (double)v.y * v.y;
     }
@@ -88,8 +87,23 @@ __global__ void k_slot_rms(const SlotDev sd, const float2* r, float* s) {
     if (threadIdx.x == 0) {
         double t = 0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
-        s[slot] = (float)sqrt(t / (double)np);
+        atomicAdd(acc2 + slot, t);
     }
+}
+
+// s[slot] = sqrt(mean |r|^2)
+__global__ void k_slot_rms_finish(int nb, long long np, const double* acc2, float* s) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nb) s[i] = (float)sqrt(acc2[i] / (double)np);
+}
+
+static cudaError_t slot_rms(const SlotDev& sd, const float2* r, double* acc2, float* s, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(acc2, 0, sizeof(double) * sd.nb, st);
+    if (e != cudaSuccess) return e;
+    dim3 g((unsigned)std::max<long long>(1, std::min<long long>(64, (sd.np + 255) / 256)), sd.nb);
+    k_slot_sumsq<<<g, 256, 0, st>>>(sd, r, acc2);
+    k_slot_rms_finish<<<(sd.nb + 127) / 128, 128, 0, st>>>(sd.nb, sd.np, acc2, s);
+    return cudaGetLastError();
 }
 
 // net input [slot][H][W][16]: Re r / s, Im r / s, n, zeros
@@ -378,6 +392,34 @@ __global__ void k_weights_bf16(const float* w, int cout, int cinp, bf16* wb, bf1
     }
 }
 
+// 2x2 sub-pixel weights of an upsampling conv: for output parity (py, px) and
+// tap (a, b) at half-resolution offsets (a + py - 1, b + px - 1), the sum of the
+// 3x3 weights whose input falls on that half-resolution pixel.
+__device__ __forceinline__ void dy_range(int p, int a, int* lo, int* hi) {
+    // p = 0: a = 0 <- {-1}, a = 1 <- {0, 1};  p = 1: a = 0 <- {-1, 0}, a = 1 <- {1}
+    if (p == 0) { *lo = a == 0 ? -1 : 0; *hi = a == 0 ? -1 : 1; }
+    else { *lo = a == 0 ? -1 : 1; *hi = a == 0 ? 0 : 1; }
+}
+__global__ void k_weights_subpixel(const float* w, int cout, int cinp, bf16* ws) {
+    const long long total = 4LL * cout * 4 * cinp;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+        const int ci = (int)(i % cinp);
+        long long q = i / cinp;
+        const int k = (int)(q % 4);
+        q /= 4;
+        const int co = (int)(q % cout);
+        const int par = (int)(q / cout);
+        const int py = par >> 1, px = par & 1, a = k >> 1, b = k & 1;
+        int y0, y1, x0, x1;
+        dy_range(py, a, &y0, &y1);
+        dy_range(px, b, &x0, &x1);
+        float acc = 0.f;
+        for (int dy = y0; dy <= y1; ++dy)
+            for (int dx = x0; dx <= x1; ++dx) acc += w[((long long)co * 9 + (dy + 1) * 3 + (dx + 1)) * cinp + ci];
+        ws[i] = __float2bfloat16_rn(acc);
+    }
+}
+
 __global__ void k_adamw(long long n, float* p, const float* g, float* m, float* v, float lr, float b1, float b2,
                         float eps, float wd, float bc1, float bc2) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
@@ -411,6 +453,12 @@ npbs_status Net::alloc(int dev) {
     if (cudaMalloc(&m2, sizeof(float) * P) != cudaSuccess) return NPBS_ERR_OOM;
     if (cudaMalloc(&wb, sizeof(bf16) * nbf) != cudaSuccess) return NPBS_ERR_OOM;
     if (cudaMalloc(&wt, sizeof(bf16) * nbf) != cudaSuccess) return NPBS_ERR_OOM;
+    long long nsub = 0;
+    for (auto& L : d) {
+        wsub_off.push_back(L.ups ? nsub : -1);
+        if (L.ups) nsub += 4LL * L.cout * 4 * L.cin_pad;
+    }
+    if (nsub && cudaMalloc(&wsub, sizeof(bf16) * nsub) != cudaSuccess) return NPBS_ERR_OOM;
     cudaMemset(params, 0, sizeof(float) * P);
     cudaMemset(grads, 0, sizeof(float) * P);
     cudaMemset(m1, 0, sizeof(float) * P);
@@ -430,6 +478,7 @@ Net::~Net() {
     cudaFree(m2);
     cudaFree(wb);
     cudaFree(wt);
+    cudaFree(wsub);
 }
 
 cudaError_t Net::refresh_bf16(cudaStream_t st) const {
@@ -438,6 +487,9 @@ cudaError_t Net::refresh_bf16(cudaStream_t st) const {
         const auto& L = d[i];
         const long long n = (long long)L.cout * 9 * L.cin_pad;
         k_weights_bf16<<<grid_for(n), 256, 0, st>>>(params + L.w_off, L.cout, L.cin_pad, wb + wb_off[i], wt + wb_off[i]);
+        if (L.ups)
+            k_weights_subpixel<<<grid_for(16LL * L.cout * L.cin_pad), 256, 0, st>>>(params + L.w_off, L.cout, L.cin_pad,
+                                                                                    wsub + wsub_off[i]);
     }
     return cudaGetLastError();
 }
@@ -555,6 +607,7 @@ static cudaError_t conv(const Net& net, int li, const bf16* x, int xs, int xo, i
     a.Cin = L.cin_pad;
     a.Cout = L.cout;
     a.w = net.wb + net.wb_off[li];
+    a.w_sub = L.ups ? net.wsub + net.wsub_off[li] : nullptr;
     a.bias = net.params + L.b_off;
     a.act = 1;
     a.y = y;
@@ -659,7 +712,7 @@ npbs_status net_run_forward(npbs_ctx* ctx, const Net& net, const NetRun& run, co
     for (const NetGroup& g : run.groups) {
         Acts A = acts_of(ctx, g, false);
         const SlotDev sd = g.sd;
-        k_slot_rms<<<sd.nb, 256, 0, st>>>(sd, r, A.s);
+        NPBS_CK(ctx, slot_rms(sd, r, A.S2, A.s, st));
         k_pack_input<<<grid_for((long long)sd.nb * sd.np), 256, 0, st>>>(sd, r, n, A.s, A.netin);
         long long k = 2;
         NPBS_CK(ctx, forward_body(net, A, st, &k));
@@ -683,7 +736,7 @@ npbs_status net_run_backward(npbs_ctx* ctx, Net& net, const NetRun& run, const f
         const SlotDev sd = grp.sd;
         const int nb = sd.nb;
         long long k = 0;
-        k_slot_rms<<<nb, 256, 0, st>>>(sd, r, A.s);
+        NPBS_CK(ctx, slot_rms(sd, r, A.S2, A.s, st));
         k_pack_input<<<grid_for((long long)nb * sd.np), 256, 0, st>>>(sd, r, n, A.s, A.netin);
         k += 2;
         NPBS_CK(ctx, forward_body(net, A, st, &k));

@@ -182,3 +182,25 @@ def test_npbs_solve_converges_with_guard():
     for j, inst in enumerate(insts):
         r = H.rtol(oracle_problem(inst), torch.from_numpy(got[j]))
         assert r <= 1e-5, (j, r, rep)
+
+
+def test_tensor_core_network_matches_warp_mma_network(monkeypatch):
+    """At 256^2 the convolutions run on tcgen05 (upsampling convs as four 2x2
+    sub-pixel convolutions); NPBS_CONV=mma forces the warp-level kernels.  Both
+    engines give the same correction to bf16 rounding."""
+    capi, c = ctx()
+    insts = [synth.small_instance(256, 256, seed=70 + j) for j in range(2)]
+    b, k2, f, n, V = setup_batch(capi, c, insts)
+    r = b.pack([random_field((256, 256), 71 + j) for j in range(2)])
+    net = _net(capi, 9)
+    o_tc, o_mma = torch.zeros_like(r), torch.zeros_like(r)
+    s0 = capi.npbs_conv_stats()
+    capi.npbs_net_forward(c, net, b, r, n, o_tc)
+    torch.cuda.synchronize()
+    s1 = capi.npbs_conv_stats()
+    assert s1["tensor_core"] - s0["tensor_core"] == 17 and s1["warp_mma"] == s0["warp_mma"]
+    monkeypatch.setenv("NPBS_CONV", "mma")
+    capi.npbs_net_forward(c, net, b, r, n, o_mma)
+    torch.cuda.synchronize()
+    for j in range(2):
+        assert rel_l2(b.unpack(o_tc)[j], b.unpack(o_mma)[j]) <= 2e-2
