@@ -308,11 +308,30 @@ def main():
     ap.add_argument("--fgmres-count", type=int, default=2)
     ap.add_argument("--fgmres-max-iter", type=int, default=400)
     ap.add_argument("--no-learned", action="store_true", help="skip the network / NPBS / FGMRES sections")
+    ap.add_argument("--train-step-only", action="store_true",
+                    help="time only npbs_train_step (batch --train-batch at 256^2, 4 unrolls) for profiler captures")
+    ap.add_argument("--train-batch", type=int, default=32)
     ap.add_argument("--net-forward-only", action="store_true",
                     help="time only the network forward on --npbs-count 256^2 instances (for profiler captures)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.train_step_only:
+        from paper_2603_18527_gb300 import build, capi
+        from paper_2603_18527_gb300 import train_unet as T
+        build.build()
+        ctx = capi.Context(0)
+        net = capi.Net(0, seed=0)
+        pool = T.Pool(ctx, T.media(256, args.train_batch, 3000))
+        u0 = torch.zeros(pool.b.extent, dtype=torch.complex64, device="cuda")
+        step = lambda: capi.npbs_train_step(ctx, net, pool.b, pool.V, pool.f, pool.n, u0, unroll=4, lr=0.0)
+        for _ in range(args.warmup):
+            step()
+        ms = timed(torch.cuda.current_stream(), step, max(1, args.steps))
+        fl = 4 * 4 * unet_forward_flops(256, 256) * args.train_batch
+        print(json.dumps({"train_step_only": args.train_batch, "ms": ms, "tflops": fl / (ms * 1e-3) / 1e12,
+                          "conv_launches": capi.npbs_conv_stats()}), flush=True)
+        return 0
     if args.net_forward_only:
         from paper_2603_18527_gb300 import build, capi
         from paper_2603_18527_gb300 import train_unet as T
