@@ -220,6 +220,37 @@ def bench_fgmres(capi, ctx, args):
     return res
 
 
+def library_fft_apply_ms(b, insts, V, f, stream, reps):
+    """Context for the apply's roofline: the same CBS step (u + gamma (G(V u + f)
+    - u), complex64) written with torch.fft (cuFFT) on per-size stacks of the
+    batch, timed the same way.  Not part of the library's path."""
+    groups = {}
+    for j, i in enumerate(insts):
+        groups.setdefault((i.ny, i.nx, i.h), []).append(j)
+    data = []
+    for (ny, nx, h), js in groups.items():
+        Vg = torch.stack([b.view(V, j) for j in js])
+        fg = torch.stack([b.view(f, j) for j in js])
+        k0 = torch.tensor([b.k0sq[j] for j in js], dtype=torch.float64, device="cuda")[:, None, None]
+        ep = torch.tensor([b.eps[j] for j in js], dtype=torch.float64, device="cuda")[:, None, None]
+        ky = 2 * np.pi * torch.fft.fftfreq(ny, d=h, dtype=torch.float64, device="cuda")
+        kx = 2 * np.pi * torch.fft.fftfreq(nx, d=h, dtype=torch.float64, device="cuda")
+        xi2 = (ky[:, None] ** 2 + kx[None, :] ** 2)[None]
+        il = (1.0 / (xi2 - k0 - 1j * ep)).to(torch.complex64)
+        gam = (1j * Vg / ep.to(torch.float32)).to(torch.complex64)
+        data.append([torch.zeros_like(Vg), Vg, fg, il, gam])
+
+    def once():
+        for d in data:
+            x, Vg, fg, il, gam = d
+            y = torch.fft.ifft2(torch.fft.fft2(Vg * x + fg) * il)
+            d[0] = x + gam * (y - x)
+
+    for _ in range(3):
+        once()
+    return timed(stream, once, reps)
+
+
 def aggregate_over_ranks(ms_local: float, units_local: float, dist=None, device=None):
     """Replica aggregation: the step time is the max over ranks (a barrier
     brackets the timed region) and the work is the sum over ranks.  Returns
@@ -391,8 +422,10 @@ def main():
         ms = e0.elapsed_time(e1) / args.apply_reps
         bpp = 24 if args.mode in ("OP_B", "ADJ_B") else 32
         gbs = bpp * b.points() / (ms * 1e-3) / 1e9
+        lib = library_fft_apply_ms(b, insts, V, f, stream, 10) if args.mode == "CBS_STEP" else None
         print(json.dumps({"apply_only": args.mode, "workload": wname, "points": b.points(), "ms": ms, "tuned": tuned,
-                          "algorithmic_GBps": gbs, "frac_of_peak": gbs / peaks()[0]}), flush=True)
+                          "algorithmic_GBps": gbs, "frac_of_peak": gbs / peaks()[0], "cufft_same_step_ms": lib}),
+              flush=True)
         return 0
 
     def step():
@@ -436,6 +469,7 @@ def main():
     pts = b.points()
     ach = B_PER_PT * pts / (apply_ms * 1e-3) / 1e9
     peak, kind = peaks()
+    lib_ms = library_fft_apply_ms(b, insts, V, f, stream, max(3, args.apply_reps // 5)) if rank == 0 else None
 
     # end to end through the C ABI with host buffers
     e2e_steps = max(1, min(args.steps, 2))
@@ -477,7 +511,8 @@ def main():
                            "iters_max": int(np.max(rep["iters"])), "parallelism": f"replicas x{world}"},
                 "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
                              "traffic": None, "kernel": "cbs_apply CBS_STEP (one cluster launch per grid side)",
-                             "apply_ms": apply_ms, "peak_kind": kind, "autotuned_variants": tuned},
+                             "apply_ms": apply_ms, "peak_kind": kind, "autotuned_variants": tuned,
+                             "cufft_same_step_ms": lib_ms},
                 "cpu_baseline": cpu,
                 "e2e": {"value": e2e_ms / eq, "unit": UNIT,
                         "h2d_bytes_per_step": int(k2_h.numel() * 8 + f_h.numel() * 8),

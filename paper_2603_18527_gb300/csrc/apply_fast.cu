@@ -16,7 +16,7 @@ NPBS_FAST_SIZES(NPBS_DECL)
 
 bool fast_supported(int n) { return n == 128 || n == 192 || n == 256 || n == 384 || n == 512; }
 
-int fast_variants(int n) {
+static int kernel_variants(int n) {
     switch (n) {
         case 128: return fast_variants_128();
         case 192: return fast_variants_192();
@@ -26,6 +26,8 @@ int fast_variants(int n) {
         default: return 0;
     }
 }
+
+int fast_variants(int n) { return 2 * kernel_variants(n); }
 
 cudaError_t prepare_apply_fast() {
     cudaError_t e = cudaSuccess;
@@ -39,9 +41,14 @@ cudaError_t prepare_apply_fast() {
 cudaError_t launch_apply_fast(int n, int variant, int mode, const FastDev& fd, const BatchDev& bd, const ApplyArgs& a,
                               cudaStream_t st) {
     if (fd.count == 0) return cudaSuccess;
+    const int nv = kernel_variants(n);
+    if (variant < 0 || variant >= 2 * nv) return cudaErrorInvalidValue;
+    FastDev f2 = fd;
+    f2.ahead = variant >= nv ? 1 : 0;  // launch_one replaces 1 by the resident cluster count
+    variant %= nv;
     switch (n) {
 #define NPBS_CASE(n) \
-    case n: return launch_fast_##n(variant, mode, fd, bd, a, st);
+    case n: return launch_fast_##n(variant, mode, f2, bd, a, st);
         NPBS_FAST_SIZES(NPBS_CASE)
 #undef NPBS_CASE
         default: return cudaErrorInvalidValue;

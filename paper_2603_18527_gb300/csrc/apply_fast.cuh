@@ -9,10 +9,13 @@ namespace npbs {
 struct FastDev {
     const int* list;  // device [count]: instance indices
     int count;
+    int ahead;        // > 0: after its loads, cluster c prefetches into L2 the rows of list[c + ahead]
 };
 
 bool fast_supported(int n);
-// number of compiled (N1, N2, cluster, threads) variants for grid side n
+// number of variants V for grid side n: every compiled (N1, N2, cluster,
+// threads, min CTAs) configuration, without (variant < V/2) and with
+// (variant >= V/2) the L2 prefetch of the instance each cluster slot runs next
 int fast_variants(int n);
 cudaError_t prepare_apply_fast();
 cudaError_t launch_apply_fast(int n, int variant, int mode, const FastDev& fd, const BatchDev& bd, const ApplyArgs& a,

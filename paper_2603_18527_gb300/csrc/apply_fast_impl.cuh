@@ -49,9 +49,32 @@ __device__ __forceinline__ double warp_sum_d(double v) {
     return v;
 }
 
+// Hint the L2 to fetch this CTA's rows of instance `next` (the operands the
+// apply of MODE reads: x and V always, f where the mode uses it) while the
+// current instance is transformed on chip; one bulk prefetch per chunk of
+// about 16 KB, issued by one thread each.  Skipped unless 16-byte aligned.
+template <int N, int ROWS, int MODE>
+__device__ __forceinline__ void prefetch_rows(const int next, const int rank, const BatchDev& bd, const ApplyArgs& a) {
+    constexpr int BYTES = ROWS * N * 8;
+    constexpr int CH = BYTES >= 32768 ? BYTES / 16384 : 1;
+    constexpr int CB = BYTES / CH;
+    static_assert(BYTES % (16 * CH) == 0, "prefetch chunks must be multiples of 16 bytes");
+    constexpr bool USE_F = MODE == NPBS_RESIDUAL || MODE == NPBS_CBS_STEP || MODE == NPBS_TRUE_RESIDUAL ||
+                           MODE == NPBS_PREC_SWEEP;
+    const int t = threadIdx.x;
+    if (t >= (USE_F ? 3 : 2) * CH) return;
+    const int arr = t / CH, ch = t - arr * CH;
+    const float2* base = arr == 0 ? a.x : (arr == 1 ? a.V : a.f);
+    const char* p = reinterpret_cast<const char*>(base + bd.inst[next].offset + (long long)rank * ROWS * N) +
+                    (long long)ch * CB;
+    if ((reinterpret_cast<unsigned long long>(p) & 15ull) != 0) return;
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(__cvta_generic_to_global(p)), "r"(CB)
+                 : "memory");
+}
+
 template <int N1, int N2, int CS, int T, int MODE>
 __device__ __forceinline__ void cluster_apply_one(const int instx, const BatchDev& bd, const ApplyArgs& a,
-                                                  float2* smem, double* red) {
+                                                  float2* smem, double* red, const int next = -1) {
     constexpr int N = N1 * N2;
     constexpr int ROWS = N / CS;
     constexpr int LD = N + N1 + 1;
@@ -106,6 +129,7 @@ __device__ __forceinline__ void cluster_apply_one(const int instx, const BatchDe
         }
     }
     __syncthreads();
+    if (next >= 0) prefetch_rows<N, ROWS, MODE>(next, rank, bd, a);
 
     NPBS_PHASE_MARK(1);
     // ---------------- P2: row pass 2, results held for the transpose
@@ -341,9 +365,23 @@ template <int N1, int N2, int CS, int T, int MODE, int MINB = 1>
 __global__ void __launch_bounds__(T, MINB) k_apply_cluster(FastDev fd, BatchDev bd, ApplyArgs a) {
     extern __shared__ __align__(16) float2 smem[];
     __shared__ double red[T / 32];
-    const int instx = fd.list[blockIdx.x / CS];
+    const int cl = blockIdx.x / CS;
+    const int instx = fd.list[cl];
     if (bd.active && !bd.active[instx]) return;  // uniform over the cluster
-    cluster_apply_one<N1, N2, CS, T, MODE>(instx, bd, a, smem, red);
+    int next = -1;
+    if (fd.ahead > 0 && cl + fd.ahead < fd.count) {
+        next = fd.list[cl + fd.ahead];
+        if (bd.active && !bd.active[next]) next = -1;
+    }
+    cluster_apply_one<N1, N2, CS, T, MODE>(instx, bd, a, smem, red, next);
+}
+
+// Clusters of one variant resident on the device at once (set when the
+// attributes are; 0 when unknown, which disables the prefetch).
+template <int N1, int N2, int CS, int T, int MODE, int MINB>
+int& resident_clusters() {
+    static int v = 0;
+    return v;
 }
 
 template <int N1, int N2, int CS, int T> constexpr size_t fast_smem() {
@@ -355,6 +393,22 @@ cudaError_t set_attr_one() {
     auto k = k_apply_cluster<N1, N2, CS, T, MODE, MINB>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fast_smem<N1, N2, CS, T>());
     if (e == cudaSuccess && CS > 8) e = cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e == cudaSuccess) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(CS, 1, 1);
+        cfg.blockDim = dim3(T, 1, 1);
+        cfg.dynamicSmemBytes = fast_smem<N1, N2, CS, T>();
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = CS;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int n = 0;
+        if (cudaOccupancyMaxActiveClusters(&n, k, &cfg) == cudaSuccess) resident_clusters<N1, N2, CS, T, MODE, MINB>() = n;
+        else (void)cudaGetLastError();
+    }
     return e;
 }
 
@@ -384,7 +438,9 @@ cudaError_t launch_one(const FastDev& fd, const BatchDev& bd, const ApplyArgs& a
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_apply_cluster<N1, N2, CS, T, MODE, MINB>, fd, bd, a);
+    FastDev f2 = fd;
+    f2.ahead = fd.ahead > 0 ? resident_clusters<N1, N2, CS, T, MODE, MINB>() : 0;
+    return cudaLaunchKernelEx(&cfg, k_apply_cluster<N1, N2, CS, T, MODE, MINB>, f2, bd, a);
 }
 
 template <int N1, int N2, int CS, int T, int MINB>

@@ -1,4 +1,5 @@
 // C ABI: context, batch plans, potential set-up and the fused apply entry.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <cstdio>
@@ -223,14 +224,28 @@ npbs_status run_apply(npbs_ctx* ctx, const Plan& pl, int mode, const ApplyArgs& 
         return NPBS_OK;
     }
     const bool compact = active && active == pl.alist_mask;
+    // grid sides with work, largest first: each side is one cluster launch;
+    // with several sides the larger ones go to side streams so that the
+    // few-wave launches of the large grids overlap the others
+    std::vector<std::pair<int, FastDev>> todo;
     for (const auto& g : pl.fast) {
         FastDev fd{compact ? g.alist : g.list, compact ? g.acount : g.count};
-        if (fd.count == 0) continue;
-        auto itv = ctx->fast_variant.find(g.n);
-        const int var = itv == ctx->fast_variant.end() ? 0 : itv->second;
-        NPBS_CK(ctx, launch_apply_fast(g.n, var, mode, fd, bd, a, st));
-        ctx->count(st, 1);
+        if (fd.count > 0) todo.emplace_back(g.n, fd);
     }
+    std::sort(todo.begin(), todo.end(), [](const auto& x, const auto& y) { return x.first > y.first; });
+    const int nside = (int)todo.size() > 1 && ctx->fork_ev ? std::min<int>((int)todo.size() - 1, npbs_ctx::kAux) : 0;
+    if (nside > 0) NPBS_CK(ctx, cudaEventRecord(ctx->fork_ev, st));
+    for (int i = 0; i < (int)todo.size(); ++i) {
+        const int n = todo[i].first;
+        auto itv = ctx->fast_variant.find(n);
+        const int var = itv == ctx->fast_variant.end() ? 0 : itv->second;
+        cudaStream_t s = i < nside ? ctx->aux[i] : st;
+        if (i < nside) NPBS_CK(ctx, cudaStreamWaitEvent(s, ctx->fork_ev, 0));
+        NPBS_CK(ctx, launch_apply_fast(n, var, mode, todo[i].second, bd, a, s));
+        ctx->count(st, 1);
+        if (i < nside) NPBS_CK(ctx, cudaEventRecord(ctx->join_ev[i], s));
+    }
+    for (int i = 0; i < nside; ++i) NPBS_CK(ctx, cudaStreamWaitEvent(st, ctx->join_ev[i], 0));
     if (pl.nrow32s > 0) {
         bd.rows = pl.rows32s;
         bd.cols = pl.cols32s;
@@ -324,6 +339,16 @@ npbs_status npbs_create(npbs_ctx** out, int device) {
     npbs_ctx* c = new (std::nothrow) npbs_ctx();
     if (!c) return NPBS_ERR_OOM;
     c->device = device;
+    {
+        bool ok = cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming) == cudaSuccess;
+        for (int i = 0; i < npbs_ctx::kAux && ok; ++i)
+            ok = cudaStreamCreateWithFlags(&c->aux[i], cudaStreamNonBlocking) == cudaSuccess &&
+                 cudaEventCreateWithFlags(&c->join_ev[i], cudaEventDisableTiming) == cudaSuccess;
+        if (!ok) {
+            npbs_destroy(c);
+            return NPBS_ERR_CUDA;
+        }
+    }
     const char* env = getenv("NPBS_APPLY_PATH");
     c->use_fast = !(env && strcmp(env, "three_pass") == 0);
     // NPBS_FAST_VARIANT="256:1,512:0" pins cluster-kernel variants
@@ -348,6 +373,14 @@ npbs_status npbs_destroy(npbs_ctx* ctx) {
         cudaStreamDestroy(ctx->solve_stream);
     }
     if (ctx->solve_event) cudaEventDestroy(ctx->solve_event);
+    for (int i = 0; i < npbs_ctx::kAux; ++i) {
+        if (ctx->aux[i]) {
+            cudaStreamSynchronize(ctx->aux[i]);
+            cudaStreamDestroy(ctx->aux[i]);
+        }
+        if (ctx->join_ev[i]) cudaEventDestroy(ctx->join_ev[i]);
+    }
+    if (ctx->fork_ev) cudaEventDestroy(ctx->fork_ev);
     delete ctx;
     return NPBS_OK;
 }

@@ -84,6 +84,11 @@ struct npbs_ctx {
     std::map<int, int> fast_variant;  // grid side -> chosen cluster-kernel variant (autotuned; default 0)
     cudaStream_t solve_stream = nullptr;  // capturable stream the solvers run on
     cudaEvent_t solve_event = nullptr;
+    // side streams on which the cluster applies of different grid sides run
+    // concurrently (fork / join by events, so they also work under capture)
+    static constexpr int kAux = 4;
+    cudaStream_t aux[kAux] = {};
+    cudaEvent_t fork_ev = nullptr, join_ev[kAux] = {};
     long long launches = 0;         // kernels launched (graph launches count their kernels)
     long long capture_kernels = 0;  // kernels recorded into the graph being captured
     void count(cudaStream_t st, long long k) {

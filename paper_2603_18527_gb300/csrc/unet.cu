@@ -326,13 +326,30 @@ __global__ void k_sumpool(int nb, int R, int Rw, int C, const float* src, float*
 }
 
 // db[c] += sum_p dz[p][c]
-__global__ void k_bias_grad(long long P, int C, const bf16* dz, float* db, int pix_per_block) {
-    const long long p0 = (long long)blockIdx.x * pix_per_block;
-    const long long p1 = min(P, p0 + pix_per_block);
+// db[c] += sum_p dz[p, c]: each thread sums 8 channels (one 16-byte load) of
+// a strided set of pixels, the block reduces its pixel lanes in shared memory
+// and adds one partial per channel.  C is a multiple of 8, at most 8 * 256.
+__global__ void k_bias_grad(long long P, int C, const bf16* dz, float* db) {
+    __shared__ float red[256 * 8];
+    const int cg = C / 8;
+    const int lanes = blockDim.x / cg;
+    const int g = threadIdx.x % cg, l = threadIdx.x / cg;
+    float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (l < lanes) {
+        for (long long p = (long long)blockIdx.x * lanes + l; p < P; p += (long long)gridDim.x * lanes) {
+            const uint4 v = *reinterpret_cast<const uint4*>(dz + p * C + g * 8);
+            const bf16* e = reinterpret_cast<const bf16*>(&v);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) acc[k] += __bfloat162float(e[k]);
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) red[l * C + g * 8 + k] = acc[k];
+    }
+    __syncthreads();
     for (int c = threadIdx.x; c < C; c += blockDim.x) {
-        float acc = 0.f;
-        for (long long p = p0; p < p1; ++p) acc += __bfloat162float(dz[p * C + c]);
-        atomicAdd(db + c, acc);
+        float t = 0.f;
+        for (int j = 0; j < lanes; ++j) t += red[j * C + c];
+        atomicAdd(db + c, t);
     }
 }
 
@@ -771,8 +788,9 @@ npbs_status net_run_backward(npbs_ctx* ctx, Net& net, const NetRun& run, const f
             w.pix_per_cta = (int)std::min<long long>(ppc, 1 << 20);
             cudaError_t e = conv_wgrad(w, st);
             if (e != cudaSuccess) return e;
-            const int ppb = 1024;
-            k_bias_grad<<<(unsigned)((P + ppb - 1) / ppb), 256, 0, st>>>(P, L.cout, A.dz, net.grads + L.b_off, ppb);
+            const int lanes = 256 / (L.cout / 8);
+            const long long nblk = std::min<long long>((P + lanes - 1) / lanes, 152LL * 8);
+            k_bias_grad<<<(unsigned)nblk, 256, 0, st>>>(P, L.cout, A.dz, net.grads + L.b_off);
             k += 2;
             return cudaGetLastError();
         };

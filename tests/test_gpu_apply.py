@@ -157,10 +157,16 @@ def test_cluster_path_matches_three_pass_path(env, monkeypatch):
         assert np.allclose(n1.cpu().numpy(), n2.cpu().numpy(), rtol=1e-5)
 
 
-@pytest.mark.parametrize("side,variants", [(128, 3), (192, 3), (256, 3), (384, 1), (512, 2)])
+# compiled (N1, N2, cluster, threads, min CTAs) configurations per side; each
+# also exists with the L2 prefetch of the next instance (variant + count)
+KERNEL_VARIANTS = {128: 3, 192: 3, 256: 3, 384: 3, 512: 2}
+
+
+@pytest.mark.parametrize("side,variants", [(s, 2 * v) for s, v in KERNEL_VARIANTS.items()])
 def test_every_cluster_variant_matches_three_pass(side, variants, monkeypatch):
     """Each compiled (factorisation, cluster size, threads) variant that the
-    autotuner may pick gives the three-launch result for every mode."""
+    autotuner may pick, with and without the L2 prefetch, gives the
+    three-launch result for every mode."""
     capi, c0 = ctx()
     insts = [synth.small_instance(side, side, seed=200 + j, layer=side // 16) for j in range(2)]
     b, k2, f, n, V = setup_batch(capi, c0, insts)
@@ -187,4 +193,34 @@ def test_autotuner_picks_a_valid_variant():
     b, k2, f, n, V = setup_batch(capi, c, insts)
     x = torch.zeros(b.extent, dtype=torch.complex64, device="cuda")
     tuned = capi.npbs_autotune_apply(c, b, V, f, x, reps=2)
-    assert set(tuned) == {256} and 0 <= tuned[256] < 3
+    assert set(tuned) == {256} and 0 <= tuned[256] < 2 * KERNEL_VARIANTS[256]
+
+
+@pytest.mark.parametrize("side", [128, 256])
+def test_prefetch_variants_identical_on_batches_beyond_residency(side, monkeypatch):
+    """With more instances than clusters resident at once, every cluster slot
+    prefetches the instance it runs next; a prefetch is only a cache hint, so
+    every mode's output is bit-identical to the same kernel without it (the
+    per-instance norms are summed by float64 atomics in any order)."""
+    capi, c0 = ctx()
+    count = 200 if side == 128 else 96
+    insts = [synth.small_instance(side, side, seed=400 + j, layer=side // 16) for j in range(count)]
+    b, k2, f, n, V = setup_batch(capi, c0, insts)
+    x = b.pack([random_field((side, side), 500 + j) for j in range(count)])
+    nv = KERNEL_VARIANTS[side]
+    for v in range(nv):
+        outs = []
+        for vv in (v, v + nv):
+            monkeypatch.setenv("NPBS_FAST_VARIANT", f"{side}:{vv}")
+            cv = capi.Context(0)
+            res = []
+            for mode in ["CBS_STEP", "ADJ_B", "TRUE_RESIDUAL"]:
+                o = torch.zeros_like(x)
+                nrm = torch.zeros(b.count, dtype=torch.float64, device="cuda")
+                capi.cbs_apply(cv, b, V, f, x, o, getattr(capi, mode), nrm)
+                res.append((o, nrm))
+            torch.cuda.synchronize()
+            outs.append(res)
+        for (o1, n1), (o2, n2) in zip(*outs):
+            assert torch.equal(o1, o2), (side, v)
+            assert torch.allclose(n1, n2, rtol=1e-12, atol=0), (side, v)
