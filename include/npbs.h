@@ -155,11 +155,15 @@ npbs_status cbs_apply(npbs_ctx* ctx, const npbs_batch* batch, const void* V, con
 
 /* Autotuner for the single-launch cluster apply: for every square grid side
  * of the batch that has a cluster kernel (128, 192, 256, 384, 512), time each
- * compiled (N1 x N2 factorisation, cluster size, threads) variant over `reps`
- * CBS_STEP applies on the caller's data and keep the fastest for later calls
- * on ctx.  x is overwritten (it is iterated in place).  chosen (nullable, HOST
- * int32 per grid side present, in increasing side order) receives
- * side * 16 + variant.  Synchronises the stream. */
+ * compiled (N1 x N2 factorisation, cluster size, threads, with or without the
+ * L2 prefetch of the next instance) variant over `reps` CBS_STEP applies on
+ * the caller's data and keep the fastest for later calls on ctx.  It also
+ * times one instance per variant and keeps the lowest-latency variant for
+ * launches of at most the largest power-of-two count of instances for which
+ * it stays faster (the few unconverged instances late in a solve).  x is
+ * overwritten (it is iterated in place).  chosen (nullable, HOST int32 per
+ * grid side present, in increasing side order) receives side * 16 + variant
+ * of the throughput choice.  Synchronises the stream. */
 npbs_status npbs_autotune_apply(npbs_ctx* ctx, const npbs_batch* batch, const void* V, const void* f,
                                 void* x, int32_t reps, int32_t* chosen, npbs_stream stream);
 

@@ -4,13 +4,14 @@
 namespace npbs {
 using namespace fastimpl;
 
-int fast_variants_384() { return 3; }
+int fast_variants_384() { return 4; }
 
 cudaError_t prepare_fast_384() {
     cudaError_t e = cudaSuccess;
     if (e == cudaSuccess) e = set_attr_size<16, 24, 16, 384, 1>();
     if (e == cudaSuccess) e = set_attr_size<16, 24, 16, 192, 2>();
     if (e == cudaSuccess) e = set_attr_size<16, 24, 8, 384, 1>();
+    if (e == cudaSuccess) e = set_attr_size<16, 24, 16, 576, 1>();
     return e;
 }
 
@@ -20,6 +21,7 @@ cudaError_t launch_fast_384(int variant, int mode, const FastDev& fd, const Batc
         case 0: return launch_size<16, 24, 16, 384, 1>(mode, fd, bd, a, st);
         case 1: return launch_size<16, 24, 16, 192, 2>(mode, fd, bd, a, st);
         case 2: return launch_size<16, 24, 8, 384, 1>(mode, fd, bd, a, st);
+        case 3: return launch_size<16, 24, 16, 576, 1>(mode, fd, bd, a, st);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -238,7 +238,9 @@ npbs_status run_apply(npbs_ctx* ctx, const Plan& pl, int mode, const ApplyArgs& 
     for (int i = 0; i < (int)todo.size(); ++i) {
         const int n = todo[i].first;
         auto itv = ctx->fast_variant.find(n);
-        const int var = itv == ctx->fast_variant.end() ? 0 : itv->second;
+        int var = itv == ctx->fast_variant.end() ? 0 : itv->second;
+        auto itt = ctx->fast_tail.find(n);
+        if (itt != ctx->fast_tail.end() && todo[i].second.count <= itt->second.second) var = itt->second.first;
         cudaStream_t s = i < nside ? ctx->aux[i] : st;
         if (i < nside) NPBS_CK(ctx, cudaStreamWaitEvent(s, ctx->fork_ev, 0));
         NPBS_CK(ctx, launch_apply_fast(n, var, mode, todo[i].second, bd, a, s));
@@ -437,32 +439,60 @@ npbs_status npbs_autotune_apply(npbs_ctx* ctx, const npbs_batch* batch, const vo
     cudaEvent_t e0, e1;
     NPBS_CK(ctx, cudaEventCreate(&e0));
     NPBS_CK(ctx, cudaEventCreate(&e1));
-    int gi = 0;
-    for (const auto& g : pl->fast) {
-        FastDev fd{g.list, g.count};
-        float best = 1e30f;
-        int bestv = 0;
-        for (int v = 0; v < fast_variants(g.n); ++v) {
-            cudaError_t e = launch_apply_fast(g.n, v, NPBS_CBS_STEP, fd, bd, a, s);  // warm-up
-            for (int r = 0; r < reps && e == cudaSuccess; ++r) {
-                if (r == 0) e = cudaEventRecord(e0, s);
-                if (e == cudaSuccess) e = launch_apply_fast(g.n, v, NPBS_CBS_STEP, fd, bd, a, s);
-            }
-            if (e == cudaSuccess) e = cudaEventRecord(e1, s);
-            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-            float ms = 0.f;
-            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-            if (e != cudaSuccess) {
-                cudaEventDestroy(e0);
-                cudaEventDestroy(e1);
-                return cuda_err(ctx, e, "npbs_autotune_apply");
-            }
-            ctx->count(s, reps + 1);
-            if (ms < best) { best = ms; bestv = v; }
+    // milliseconds per launch of variant v over the first cnt instances of g
+    auto time_v = [&](const Plan::FastGroup& g, int v, int cnt, int nrep, float* ms) -> cudaError_t {
+        FastDev fd{g.list, cnt};
+        cudaError_t e = launch_apply_fast(g.n, v, NPBS_CBS_STEP, fd, bd, a, s);  // warm-up
+        for (int r = 0; r < nrep && e == cudaSuccess; ++r) {
+            if (r == 0) e = cudaEventRecord(e0, s);
+            if (e == cudaSuccess) e = launch_apply_fast(g.n, v, NPBS_CBS_STEP, fd, bd, a, s);
         }
+        if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(ms, e0, e1);
+        ctx->count(s, nrep + 1);
+        *ms /= (float)nrep;
+        return e;
+    };
+    int gi = 0;
+    cudaError_t e = cudaSuccess;
+    for (const auto& g : pl->fast) {
+        // throughput: the whole group
+        float best = 1e30f, ms = 0.f;
+        int bestv = 0;
+        for (int v = 0; v < fast_variants(g.n) && e == cudaSuccess; ++v) {
+            e = time_v(g, v, g.count, reps, &ms);
+            if (e == cudaSuccess && ms < best) { best = ms; bestv = v; }
+        }
+        // latency: one instance; then the largest power-of-two count up to
+        // which the lowest-latency variant still beats the throughput one
+        const int lreps = std::max(reps, 20);
+        float lbest = 1e30f;
+        int tailv = bestv, tailmax = 0;
+        for (int v = 0; v < fast_variants(g.n) && e == cudaSuccess; ++v) {
+            e = time_v(g, v, 1, lreps, &ms);
+            if (e == cudaSuccess && ms < lbest) { lbest = ms; tailv = v; }
+        }
+        if (tailv != bestv) {
+            for (int k = 1; k < g.count && e == cudaSuccess; k *= 2) {
+                float mt = 0.f, mb = 0.f;
+                e = time_v(g, tailv, k, lreps, &mt);
+                if (e == cudaSuccess) e = time_v(g, bestv, k, lreps, &mb);
+                if (e != cudaSuccess || mt >= mb) break;
+                tailmax = k;
+            }
+        }
+        if (e != cudaSuccess) break;
         ctx->fast_variant[g.n] = bestv;
+        if (tailmax > 0) ctx->fast_tail[g.n] = {tailv, tailmax};
+        else ctx->fast_tail.erase(g.n);
         if (chosen) chosen[gi] = g.n * 16 + bestv;
         ++gi;
+    }
+    if (e != cudaSuccess) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        return cuda_err(ctx, e, "npbs_autotune_apply");
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);

@@ -82,6 +82,10 @@ struct npbs_ctx {
     npbs::DevBuf net_ws;    // network activations
     bool use_fast = true;  // cluster apply for square 128..512 grids (NPBS_APPLY_PATH=three_pass disables)
     std::map<int, int> fast_variant;  // grid side -> chosen cluster-kernel variant (autotuned; default 0)
+    // grid side -> (variant, max count): the lowest-latency variant, used
+    // instead when at most `max count` instances of that side are launched
+    // (the few-instance tail of a solve); autotuned
+    std::map<int, std::pair<int, int>> fast_tail;
     cudaStream_t solve_stream = nullptr;  // capturable stream the solvers run on
     cudaEvent_t solve_event = nullptr;
     // side streams on which the cluster applies of different grid sides run

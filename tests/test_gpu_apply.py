@@ -159,7 +159,7 @@ def test_cluster_path_matches_three_pass_path(env, monkeypatch):
 
 # compiled (N1, N2, cluster, threads, min CTAs) configurations per side; each
 # also exists with the L2 prefetch of the next instance (variant + count)
-KERNEL_VARIANTS = {128: 3, 192: 3, 256: 3, 384: 3, 512: 2}
+KERNEL_VARIANTS = {128: 3, 192: 3, 256: 4, 384: 4, 512: 2}
 
 
 @pytest.mark.parametrize("side,variants", [(s, 2 * v) for s, v in KERNEL_VARIANTS.items()])
