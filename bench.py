@@ -329,6 +329,8 @@ def main():
     ap.add_argument("--check-every", type=int, default=16)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--apply-reps", type=int, default=50)
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the default (or NPBS_FAST_VARIANT-pinned) cluster-kernel variants")
     ap.add_argument("--apply-only", action="store_true",
                     help="time only the CBS_STEP apply on the workload (for profiler captures)")
     ap.add_argument("--mode", default="CBS_STEP", help="apply mode for --apply-only")
@@ -405,7 +407,7 @@ def main():
     stream = torch.cuda.current_stream()
     # autotune the cluster-kernel variant per grid side on this workload (set-up, untimed)
     xt = torch.zeros(b.extent, dtype=torch.complex64, device="cuda")
-    tuned = capi.npbs_autotune_apply(ctx, b, V, f, xt, reps=5)
+    tuned = None if args.no_autotune else capi.npbs_autotune_apply(ctx, b, V, f, xt, reps=5)
     del xt
     if args.apply_only:
         x = torch.zeros(b.extent, dtype=torch.complex64, device="cuda")

@@ -41,8 +41,11 @@ namespace npbs {
 namespace fastimpl {
 
 template <int N2> __device__ __forceinline__ int pad(int p) { return p + p / N2; }
-// twiddle table index with one pad element per 16 (strided reads hit distinct banks)
-__device__ __forceinline__ int tpad(int i) { return i + (i >> 4); }
+// Twiddle table W_N^{n2 k1} stored as [k1][n2] with row stride N2 + 1: the
+// first passes read it with n2 varying across a warp (consecutive words), the
+// second passes with k1 varying (stride N2 + 1, odd for every factorisation
+// here), so neither pattern has shared-memory bank conflicts.
+template <int N2> __device__ __forceinline__ int twi(int k1, int n2) { return k1 * (N2 + 1) + n2; }
 
 __device__ __forceinline__ double warp_sum_d(double v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -82,12 +85,15 @@ __device__ __forceinline__ void cluster_apply_one(const int instx, const BatchDe
     constexpr int J2 = (ROWS * N1 + T - 1) / T;  // jobs per thread, passes over N2 (P2, P4, P6)
     static_assert(N % CS == 0 && ROWS % N2 == 0, "slab must hold whole N2 blocks");
     float2* S = smem;               // [ROWS][LD]: row slab, then column slab
-    float2* tw = smem + ROWS * LD;  // W_N^j = exp(-2 pi i j / N)
+    float2* tw = smem + ROWS * LD;  // [N1][N2 + 1]: W_N^{n2 k1}, W_N^j = exp(-2 pi i j / N)
     cg::cluster_group cluster = cg::this_cluster();
     const int rank = (int)cluster.block_rank();
     const InstDev in = bd.inst[instx];
     const int tid = threadIdx.x;
-    for (int j = tid; j < N; j += T) tw[tpad(j)] = bd.tw32[in.tw_x + j];
+    for (int e = tid; e < N; e += T) {
+        const int k1 = e / N2, n2 = e - k1 * N2;
+        tw[twi<N2>(k1, n2)] = bd.tw32[in.tw_x + n2 * k1];
+    }
     const long long base = in.offset;
     __syncthreads();
 
@@ -122,7 +128,7 @@ __device__ __forceinline__ void cluster_apply_one(const int instx, const BatchDe
             DftR<N1, -1>::run(v);
 #pragma unroll
             for (int k1 = 0; k1 < N1; ++k1) {
-                const float2 w = tw[tpad(n2 * k1)];
+                const float2 w = tw[twi<N2>(k1, n2)];
                 const float2 t = v[k1];
                 S[r * LD + pad<N2>(N2 * k1 + n2)] = make_float2(t.x * w.x - t.y * w.y, t.x * w.y + t.y * w.x);
             }
@@ -173,7 +179,7 @@ __device__ __forceinline__ void cluster_apply_one(const int instx, const BatchDe
             DftR<N1, -1>::run(v);
 #pragma unroll
             for (int k1 = 0; k1 < N1; ++k1) {
-                const float2 w = tw[tpad(n2 * k1)];
+                const float2 w = tw[twi<N2>(k1, n2)];
                 const float2 t = v[k1];
                 S[c * LD + pad<N2>(N2 * k1 + n2)] = make_float2(t.x * w.x - t.y * w.y, t.x * w.y + t.y * w.x);
             }
@@ -216,7 +222,7 @@ __device__ __forceinline__ void cluster_apply_one(const int instx, const BatchDe
                 DftR<N2, +1>::run(v);
 #pragma unroll
                 for (int n2 = 0; n2 < N2; ++n2) {
-                    const float2 w = tw[tpad(n2 * k1)];  // conjugate twiddle for the inverse
+                    const float2 w = tw[twi<N2>(k1, n2)];  // conjugate twiddle for the inverse
                     const float2 t = v[n2];
                     S[c * LD + pad<N2>(N2 * k1 + n2)] = make_float2(t.x * w.x + t.y * w.y, t.y * w.x - t.x * w.y);
                 }
@@ -269,7 +275,7 @@ __device__ __forceinline__ void cluster_apply_one(const int instx, const BatchDe
             DftR<N2, +1>::run(v);
 #pragma unroll
             for (int n2 = 0; n2 < N2; ++n2) {
-                const float2 w = tw[tpad(n2 * k1)];
+                const float2 w = tw[twi<N2>(k1, n2)];
                 const float2 t = v[n2];
                 S[r * LD + pad<N2>(N2 * k1 + n2)] = make_float2(t.x * w.x + t.y * w.y, t.y * w.x - t.x * w.y);
             }
@@ -385,7 +391,7 @@ int& resident_clusters() {
 }
 
 template <int N1, int N2, int CS, int T> constexpr size_t fast_smem() {
-    return sizeof(float2) * ((size_t)(N1 * N2 / CS) * (N1 * N2 + N1 + 1) + N1 * N2 + N1 * N2 / 16 + 1);
+    return sizeof(float2) * ((size_t)(N1 * N2 / CS) * (N1 * N2 + N1 + 1) + (size_t)N1 * (N2 + 1));
 }
 
 template <int N1, int N2, int CS, int T, int MODE, int MINB = 1>

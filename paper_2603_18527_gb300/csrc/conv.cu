@@ -304,6 +304,12 @@ cudaError_t conv_fwd(const ConvFwd& a, cudaStream_t st) {
 cudaError_t conv_wgrad(const ConvWgrad& a, cudaStream_t st) {
     const long long P = (long long)a.B * a.H * a.W;
     if (P == 0) return cudaSuccess;
+    const char* force = getenv("NPBS_WGRAD");
+    if (!(force && strcmp(force, "mma") == 0) && conv_wgrad_tc_supported(a)) {
+        g_conv_tc_launches++;
+        return conv_wgrad_tc(a, st);
+    }
+    g_conv_mma_launches++;
     if (a.Cin % 8 || a.Cout % 8 || a.xs % 8 || a.xo % 8 || a.pix_per_cta <= 0) return cudaErrorInvalidValue;
     const unsigned gz = (unsigned)((P + a.pix_per_cta - 1) / a.pix_per_cta);
     const int NT = 9 * a.Cin;

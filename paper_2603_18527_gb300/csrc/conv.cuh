@@ -50,6 +50,12 @@ cudaError_t conv_wgrad(const ConvWgrad& a, cudaStream_t st);
 // multiple of 128, Cout a multiple of 16 up to 256).
 bool conv_tc_supported(const ConvFwd& a);
 cudaError_t conv_fwd_tc(const ConvFwd& a, cudaStream_t st);
+// tcgen05 weight gradient (conv_tc.cu): used by conv_wgrad when there is no
+// upsampling in the gather, the grid splits into 64-pixel runs (W a multiple
+// of 64, or whole rows), Cin is 16, 32 or a multiple of 64 and Cout 32 or a
+// multiple of 64 up to 256.  NPBS_WGRAD=mma forces the warp-level kernel.
+bool conv_wgrad_tc_supported(const ConvWgrad& a);
+cudaError_t conv_wgrad_tc(const ConvWgrad& a, cudaStream_t st);
 cudaError_t prepare_conv_tc();
 int conv_tc_timeout_flag();
 

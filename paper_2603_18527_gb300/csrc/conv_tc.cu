@@ -442,6 +442,176 @@ __global__ void __launch_bounds__(192, 1) k_conv_tc_persist(const __grid_constan
     }
 }
 
+// ---------------------------------------------------------------- weight gradient
+//
+// dW[n][tap][c] = sum_p x[nbr(p, tap)][c] * dz[p][n] as one GEMM per tap with
+// K = pixels: D[m][n] = sum_k A[m][k] B[k][n], A = the tap-shifted input (m =
+// input channel), B = dz (n = output channel).  Both operands sit in memory
+// channel-contiguous per pixel, i.e. MN-major: a TMA box of 64 pixels x BC
+// channels lands as 64 rows of 2*BC bytes, the canonical MN-major swizzled
+// layout (8-row atoms SBO apart along K, BC-element blocks LBO apart along
+// M/N), so no transpose is needed.  The 128 rows of one M-tile are 128/BC
+// (tap, channel block) pairs: narrow inputs pack several taps into one MMA.
+// A CTA owns up to three M-tiles (accumulators side by side in TMEM, sharing
+// each dz tile) over a range of 64-pixel K-tiles; ranges are combined with
+// float32 atomics (coalesced along the input channel).  Warp 4 issues TMA,
+// warp 5 the MMAs, warps 0-3 drain TMEM; every wait is bounded.
+
+constexpr int kWKP = 64;  // pixels per K-tile
+
+// MN-major swizzled descriptor: rows of `row_bytes` along K (8-row atoms
+// 8 * row_bytes apart = SBO), MN blocks of row_bytes / 2 elements `lbo` apart.
+__device__ __forceinline__ uint64_t smem_desc_mn(uint32_t addr, int row_bytes, int lbo) {
+    const uint64_t layout = row_bytes == 128 ? 2ull : row_bytes == 64 ? 4ull : 6ull;
+    uint64_t d = 0;
+    d |= (uint64_t)((addr >> 4) & 0x3FFF);
+    d |= (uint64_t)(((uint32_t)lbo >> 4) & 0x3FFF) << 16;
+    d |= (uint64_t)(((uint32_t)(8 * row_bytes) >> 4) & 0x3FFF) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= layout << 61;
+    return d;
+}
+
+// BF16 x BF16 -> F32, A and B MN-major, M = 128, N = n.
+__device__ __forceinline__ uint32_t instr_desc_mn(int n) {
+    return instr_desc(n) | (1u << 15) | (1u << 16);
+}
+
+struct WgArgs {
+    int H, W;            // grid of the convolution (input = output resolution)
+    int Cin, Cout, xo;   // Cin channels read at channel offset xo; dW is [Cout][9][Cin]
+    int BC, cpb;         // channels per x box (16 / 32 / 64), boxes per tap (Cin / BC)
+    int pairs;           // 9 * cpb (tap, channel block) pairs
+    int per_tile;        // 128 / BC pairs per M-tile
+    int nm, MT;          // M-tiles in total, per CTA
+    int bnw, nbox_b;     // dz box width (channels) and boxes per K-tile
+    int KT, ktp;         // K-tiles in total, per CTA (blockIdx.y)
+    int stages, stage_bytes, a_bytes;
+    int tmem_cols;
+    float* dw;
+};
+
+__global__ void __launch_bounds__(192, 1) k_wgrad_tc(const __grid_constant__ CUtensorMap mapx,
+                                                     const __grid_constant__ CUtensorMap mapd, WgArgs a) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* base = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const int S = a.stages;
+    uint64_t* full = reinterpret_cast<uint64_t*>(base + S * a.stage_bytes);
+    uint64_t* empty = full + S;
+    uint64_t* done = full + 2 * S;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(full + 2 * S + 1);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int mt0 = blockIdx.x * a.MT;
+    const int mtn = min(a.MT, a.nm - mt0);
+    const int kb = blockIdx.y * a.ktp, ke = min(a.KT, kb + a.ktp);
+    if (tid == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(su32(&full[s]), 1);
+            mbar_init(su32(&empty[s]), 1);
+        }
+        mbar_init(su32(done), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 4) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)),
+                     "r"(a.tmem_cols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+    const long long HW = (long long)a.H * a.W;
+    const int xbox = a.BC * kWKP * 2, dbox = a.bnw * kWKP * 2;
+
+    if (warp == 4) {
+        if (lane == 0) {
+            int nx = 0;  // x boxes per K-tile
+            for (int t = 0; t < mtn; ++t) nx += min(a.per_tile, a.pairs - (mt0 + t) * a.per_tile);
+            const uint32_t bytes = (uint32_t)(a.nbox_b * dbox + nx * xbox);
+            bool ok = true;
+            for (int kt = kb; kt < ke && ok; ++kt) {
+                const int i = kt - kb, s = i % S;
+                if (i >= S) ok = mbar_wait(su32(&empty[s]), (uint32_t)(((i / S) - 1) & 1));
+                if (!ok) break;
+                const long long p0 = (long long)kt * kWKP;
+                const int b = (int)(p0 / HW);
+                const long long rem = p0 - (long long)b * HW;
+                const int y0 = (int)(rem / a.W), x0 = (int)(rem % a.W);
+                unsigned char* st = base + s * a.stage_bytes;
+                mbar_expect_tx(su32(&full[s]), bytes);
+                for (int k = 0; k < a.nbox_b; ++k)
+                    tma_load_2d(su32(st + a.a_bytes + k * dbox), &mapd, su32(&full[s]), k * a.bnw, (int)p0);
+                for (int t = 0; t < mtn; ++t)
+                    for (int j = 0; j < a.per_tile; ++j) {
+                        const int q = (mt0 + t) * a.per_tile + j;
+                        if (q >= a.pairs) break;
+                        const int tap = q / a.cpb, cb = q - tap * a.cpb;
+                        tma_load_4d(su32(st + t * (kTM * kWKP * 2) + j * xbox), &mapx, su32(&full[s]),
+                                    a.xo + cb * a.BC, x0 + tap % 3 - 1, y0 + tap / 3 - 1, b);
+                    }
+            }
+        }
+    } else if (warp == 5) {
+        if (lane == 0) {
+            const uint32_t idesc = instr_desc_mn(a.Cout);
+            const int ra = 2 * a.BC, rb = 2 * a.bnw;
+            bool ok = true;
+            for (int kt = kb; kt < ke && ok; ++kt) {
+                const int i = kt - kb, s = i % S;
+                ok = mbar_wait(su32(&full[s]), (uint32_t)((i / S) & 1));
+                if (!ok) break;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                unsigned char* st = base + s * a.stage_bytes;
+                const uint32_t abase = su32(st), bbase = su32(st + a.a_bytes);
+                for (int t = 0; t < mtn; ++t)
+                    for (int kk = 0; kk < kWKP / 16; ++kk)
+                        umma(tmem + (uint32_t)(t * a.Cout),
+                             smem_desc_mn(abase + t * (kTM * kWKP * 2) + kk * 16 * ra, ra, kWKP * ra),
+                             smem_desc_mn(bbase + kk * 16 * rb, rb, kWKP * rb), idesc, (i > 0 || kk > 0) ? 1u : 0u);
+                umma_commit(su32(&empty[s]));
+            }
+            if (ok) umma_commit(su32(done));
+        }
+    } else {
+        // epilogue warps 0..3: TMEM lane m = tid is row m of each M-tile
+        const bool okd = ke > kb && mbar_wait(su32(done), 0);
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (okd) {
+            const int j = tid / a.BC, c = tid - j * a.BC;
+            for (int t = 0; t < mtn; ++t) {
+                const int q = (mt0 + t) * a.per_tile + j;
+                const bool valid = q < a.pairs;
+                const int tap = valid ? q / a.cpb : 0;
+                const int ci = valid ? (q - tap * a.cpb) * a.BC + c : 0;
+                for (int n0 = 0; n0 < a.Cout; n0 += 16) {
+                    uint32_t r[16];
+                    const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(t * a.Cout + n0);
+                    asm volatile(
+                        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                        "[%16];"
+                        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+                          "=r"(r[14]), "=r"(r[15])
+                        : "r"(taddr)
+                        : "memory");
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                    if (!valid) continue;
+                    float* d = a.dw + ((long long)n0 * 9 + tap) * a.Cin + ci;
+#pragma unroll
+                    for (int jj = 0; jj < 16; ++jj) atomicAdd(d + (long long)jj * 9 * a.Cin, __uint_as_float(r[jj]));
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 4) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(a.tmem_cols) : "memory");
+    }
+}
+
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -595,12 +765,97 @@ static cudaError_t conv_fwd_tc_one(const ConvFwd& a0, cudaStream_t st, int sub, 
     return cudaGetLastError();
 }
 
+// 64-pixel K-tiles: a run of one row (W a multiple of 64) or whole rows.
+static bool wg_grid_ok(int H, int W) {
+    if (W % kWKP == 0) return true;
+    return kWKP % W == 0 && H % (kWKP / W) == 0;
+}
+
+bool conv_wgrad_tc_supported(const ConvWgrad& a) {
+    if (!encoder() || a.ups) return false;
+    if (!wg_grid_ok(a.H, a.W)) return false;
+    if (!(a.Cin == 16 || a.Cin == 32 || a.Cin % 64 == 0)) return false;
+    if (!(a.Cout == 32 || a.Cout % 64 == 0) || a.Cout > 256) return false;
+    if (a.xs % 8 || a.xo % 8 || (reinterpret_cast<uintptr_t>(a.x) & 15) || (reinterpret_cast<uintptr_t>(a.dz) & 15))
+        return false;
+    return true;
+}
+
+static constexpr size_t kWgSmemMax = 200 * 1024 + 2048;
+
+cudaError_t conv_wgrad_tc(const ConvWgrad& a, cudaStream_t st) {
+    const long long P = (long long)a.B * a.H * a.W;
+    WgArgs t{};
+    t.H = a.H;
+    t.W = a.W;
+    t.Cin = a.Cin;
+    t.Cout = a.Cout;
+    t.xo = a.xo;
+    t.BC = a.Cin >= 64 ? 64 : a.Cin;
+    t.cpb = a.Cin / t.BC;
+    t.pairs = 9 * t.cpb;
+    t.per_tile = kTM / t.BC;
+    t.nm = (t.pairs + t.per_tile - 1) / t.per_tile;
+    t.MT = std::min(std::min(3, t.nm), 512 / a.Cout);
+    t.bnw = a.Cout >= 64 ? 64 : a.Cout;
+    t.nbox_b = a.Cout / t.bnw;
+    t.a_bytes = t.MT * kTM * kWKP * 2;
+    t.stage_bytes = t.a_bytes + a.Cout * kWKP * 2;
+    t.stages = (int)std::max<size_t>(2, std::min<size_t>(4, (200 * 1024) / (size_t)t.stage_bytes));
+    int cols = 32;
+    while (cols < t.MT * a.Cout) cols <<= 1;
+    t.tmem_cols = cols;
+    t.dw = a.dw;
+    t.KT = (int)(P / kWKP);
+    const int G = (t.nm + t.MT - 1) / t.MT;
+    int nsm = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const int want = std::max(1, (2 * std::max(nsm, 1) + G - 1) / G);
+    int S = std::max(1, std::min(t.KT / 8, want));
+    t.ktp = (t.KT + S - 1) / S;
+    S = (t.KT + t.ktp - 1) / t.ktp;
+    const size_t smem = (size_t)t.stages * t.stage_bytes + 1024 + 256;
+    if (smem > kWgSmemMax) return cudaErrorInvalidValue;
+    CUtensorMap mx, md;
+    const CUtensorMapSwizzle swx = t.BC == 64 ? CU_TENSOR_MAP_SWIZZLE_128B
+                                   : t.BC == 32 ? CU_TENSOR_MAP_SWIZZLE_64B
+                                                : CU_TENSOR_MAP_SWIZZLE_32B;
+    {
+        const int cols_ = a.W >= kWKP ? kWKP : a.W;
+        const int rows_ = a.W >= kWKP ? 1 : kWKP / a.W;
+        cuuint64_t dims[4] = {(cuuint64_t)a.xs, (cuuint64_t)a.W, (cuuint64_t)a.H, (cuuint64_t)a.B};
+        cuuint64_t strides[3] = {(cuuint64_t)a.xs * 2, (cuuint64_t)a.xs * 2 * a.W, (cuuint64_t)a.xs * 2 * a.W * a.H};
+        cuuint32_t box[4] = {(cuuint32_t)t.BC, (cuuint32_t)cols_, (cuuint32_t)rows_, 1};
+        cuuint32_t es[4] = {1, 1, 1, 1};
+        if (encoder()(&mx, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<bf16*>(a.x), dims, strides, box, es,
+                      CU_TENSOR_MAP_INTERLEAVE_NONE, swx, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return cudaErrorInvalidValue;
+    }
+    {
+        cuuint64_t dims[2] = {(cuuint64_t)a.Cout, (cuuint64_t)P};
+        cuuint64_t strides[1] = {(cuuint64_t)a.Cout * 2};
+        cuuint32_t box[2] = {(cuuint32_t)t.bnw, (cuuint32_t)kWKP};
+        cuuint32_t es[2] = {1, 1};
+        const CUtensorMapSwizzle swd = t.bnw == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B;
+        if (encoder()(&md, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<bf16*>(a.dz), dims, strides, box, es,
+                      CU_TENSOR_MAP_INTERLEAVE_NONE, swd, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return cudaErrorInvalidValue;
+    }
+    k_wgrad_tc<<<dim3((unsigned)G, (unsigned)S), 192, smem, st>>>(mx, md, t);
+    return cudaGetLastError();
+}
+
 cudaError_t prepare_conv_tc() {
     encoder();
     if (const char* e = getenv("NPBS_CONV_TC")) g_tc_persistent = strcmp(e, "tile") != 0;
     cudaError_t e = cudaFuncSetAttribute(k_conv_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem(256, 64));
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_conv_tc_persist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem(256, 64));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_wgrad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWgSmemMax);
     return e;
 }
 

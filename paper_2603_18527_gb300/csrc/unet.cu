@@ -10,6 +10,7 @@
 // of the C ABI live here.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstdio>
 #include <cstring>
 #include <map>
@@ -350,6 +351,22 @@ __global__ void k_bias_grad(long long P, int C, const bf16* dz, float* db) {
         float t = 0.f;
         for (int j = 0; j < lanes; ++j) t += red[j * C + c];
         atomicAdd(db + c, t);
+    }
+}
+
+// dst[b][y][x][0..C) = src[b][y/2][x/2][0..C): the nearest x2 upsampling the
+// up convolutions fold into their gather, written out (R x Rw the fine size)
+__global__ void k_upsample2(int nb, int R, int Rw, int C, const bf16* src, bf16* dst) {
+    const int c8n = C / 8;
+    const long long total = (long long)nb * R * Rw * c8n;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+        const long long p = i / c8n;
+        const int c8 = (int)(i - p * c8n);
+        const int x = (int)(p % Rw);
+        const long long t = p / Rw;
+        const int y = (int)(t % R), b = (int)(t / R);
+        const long long q = ((long long)b * (R / 2) + y / 2) * (Rw / 2) + x / 2;
+        *reinterpret_cast<uint4*>(dst + p * C + c8 * 8) = *reinterpret_cast<const uint4*>(src + q * C + c8 * 8);
     }
 }
 
@@ -782,6 +799,23 @@ npbs_status net_run_backward(npbs_ctx* ctx, Net& net, const NetRun& run, const f
             w.dz = A.dz;
             w.dw = net.grads + L.w_off;
             const long long P = (long long)nb * R * Rw;
+            if (L.ups) {
+                // the tensor-core kernel reads TMA boxes of the input: write the
+                // upsampled input out first (into the up conv's dgrad scratch,
+                // which is free until the dgrad that follows)
+                ConvWgrad w2 = w;
+                w2.ups = 0;
+                w2.x = reinterpret_cast<const bf16*>(A.tmp);
+                w2.xs = L.cin_pad;
+                w2.xo = 0;
+                const char* force = getenv("NPBS_WGRAD");
+                if (!(force && strcmp(force, "mma") == 0) && xs == L.cin_pad && xo == 0 && conv_wgrad_tc_supported(w2)) {
+                    k_upsample2<<<grid_for(P * L.cin_pad / 8), 256, 0, st>>>(nb, R, Rw, L.cin_pad, x,
+                                                                            reinterpret_cast<bf16*>(A.tmp));
+                    ++k;
+                    w = w2;
+                }
+            }
             const long long tiles = (long long)((9 * L.cin_pad + 63) / 64) * ((L.cout + 63) / 64);
             long long ppc = std::max<long long>(256, (P * tiles + 1215) / 1216);  // ~8 CTAs per SM
             ppc = (ppc + 31) / 32 * 32;

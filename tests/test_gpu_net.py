@@ -63,11 +63,12 @@ def test_network_forward_parity(shape):
         assert rel_l2(got[j], ref) <= 4e-2, (shape, j, rel_l2(got[j], ref))
 
 
-def test_network_backward_matches_autograd():
+@pytest.mark.parametrize("shape", [(32, 32), (64, 64)])
+def test_network_backward_matches_autograd(shape):
     """npbs_net_backward vs torch autograd of the float64 oracle network:
-    L = Re <g, M(r)> for a fixed random g."""
+    L = Re <g, M(r)> for a fixed random g.  At 64^2 every weight gradient
+    runs on the tensor cores; at 32^2 the 4^2 level takes the warp kernel."""
     capi, c = ctx()
-    shape = (32, 32)
     insts = [synth.small_instance(*shape, seed=60 + j) for j in range(4)]
     b, k2, f, n, V = setup_batch(capi, c, insts)
     rs = [random_field(shape, 70 + j) for j in range(4)]
@@ -204,3 +205,37 @@ def test_tensor_core_network_matches_warp_mma_network(monkeypatch):
     torch.cuda.synchronize()
     for j in range(2):
         assert rel_l2(b.unpack(o_tc)[j], b.unpack(o_mma)[j]) <= 2e-2
+
+
+@pytest.mark.parametrize("N", [64, 256])
+def test_tensor_core_weight_gradient_matches_warp_mma(N, monkeypatch):
+    """The tcgen05 weight gradient (MN-major operands, several taps packed
+    into the 128 rows of an MMA, upsampling convs on their materialised
+    input) against the warp-level kernel (NPBS_WGRAD=mma) in the same
+    backward pass: the same bf16 products summed in float32 in another
+    order, so every parameter block agrees to float32 rounding."""
+    capi, c = ctx()
+    insts = [synth.small_instance(N, N, seed=90 + j) for j in range(2)]
+    b, k2, f, n, V = setup_batch(capi, c, insts)
+    r = b.pack([random_field((N, N), 91 + j) for j in range(2)])
+    g = b.pack([random_field((N, N), 93 + j) for j in range(2)])
+    net = _net(capi, 11)
+    out = []
+    for mode in (None, "mma"):
+        if mode:
+            monkeypatch.setenv("NPBS_WGRAD", mode)
+        gr = torch.zeros_like(r)
+        net.zero_grad()
+        s0 = capi.npbs_conv_stats()
+        capi.npbs_net_backward(c, net, b, r, n, g, gr)
+        torch.cuda.synchronize()
+        s1 = capi.npbs_conv_stats()
+        out.append((net.get_grads(), s1["warp_mma"] - s0["warp_mma"], gr.clone()))
+    (gt, mt, rt), (gm, mm, rm) = out
+    assert mm - mt == 17, (mt, mm)  # all 17 weight gradients moved between engines
+    assert torch.equal(rt, rm)
+    o = 0
+    for name, shp in U.PARAM_SPEC:
+        k = int(np.prod(shp))
+        assert rel_l2(gt[o:o + k], gm[o:o + k]) <= 5e-4, (name, rel_l2(gt[o:o + k], gm[o:o + k]))
+        o += k
