@@ -38,6 +38,14 @@ __global__ void k_build_V(const VecItem* items, const InstDev* inst, const float
     }
 }
 
+// delta = 0 on the instances with mask[inst] set
+__global__ void k_zero_masked(const VecItem* items, const InstDev* inst, const int* mask, float2* delta) {
+    const VecItem it = items[blockIdx.x];
+    if (!mask[it.inst]) return;
+    const long long base = inst[it.inst].offset + it.start;
+    for (int e = threadIdx.x; e < it.len; e += blockDim.x) delta[base + e] = make_float2(0.f, 0.f);
+}
+
 npbs_status solver_potential(npbs_ctx* ctx, const Plan& pl, const float2* k2, cudaStream_t st, const float2** V) {
     NPBS_CK(ctx, ctx->work[8].ensure(sizeof(float2) * (size_t)std::max<long long>(pl.extent, 1)));
     float2* v = static_cast<float2*>(ctx->work[8].p);
@@ -55,21 +63,29 @@ npbs_status refine_driver(npbs_ctx* ctx, const Plan& pl, const float2* k2, const
     const size_t ext = (size_t)std::max<long long>(pl.extent, 1);
     NPBS_CK(ctx, ctx->work[0].ensure(ext * sizeof(float2)));  // delta
     NPBS_CK(ctx, ctx->work[1].ensure(ext * sizeof(float2)));  // rho
-    NPBS_CK(ctx, ctx->work[2].ensure(sizeof(double) * 4 * n + sizeof(int) * n + 64));
+    NPBS_CK(ctx, ctx->work[2].ensure(sizeof(double) * 4 * n + sizeof(int) * 2 * n + 64));
     w.delta = static_cast<float2*>(ctx->work[0].p);
     w.rho = static_cast<float2*>(ctx->work[1].p);
     double* rho2 = static_cast<double*>(ctx->work[2].p);
     double* f2 = rho2 + n;
     w.nb = f2 + n;            // inner Born residual norms^2 (written by the inner step)
     int* active = reinterpret_cast<int*>(w.nb + 2 * n);
+    int* rmask = active + n;  // instances refreshed by the current float64 apply
     w.active = active;
     NPBS_CK(ctx, ctx->scratch.ensure(ext * 16));
 
-    std::vector<int> iters(n, 0), act(n, 0);
-    std::vector<double> rt(n, 0.0), hrho2(n), hf2(n), hnb(n), nb_first(n, 0.0), rt_cycle(n, 0.0);
+    // Every instance runs its own refinement cycles: the inner iteration of one
+    // instance never reads another's correction, so an instance whose cycle
+    // ends (its estimate reached the tolerance, its residual fell by
+    // max_reduction or grew, or max_cycle iterations passed) is refreshed in
+    // float64 and restarted alone while the others keep iterating.
+    std::vector<int> iters(n, 0), act(n, 0), need(n, 0), cycle_its(n, 0);
+    std::vector<double> rt(n, 0.0), hrho2(n), hf2(n), hnb(n), nb_first(n, -1.0), rt_cycle(n, 0.0);
     std::vector<npbs_status> stat(n, NPBS_OK);
 
+    // float64 refresh of the instances with need[j] (all of them when !fold)
     auto refresh = [&](bool fold) -> npbs_status {
+        NPBS_CK(ctx, cudaMemcpyAsync(rmask, need.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st));
         ApplyArgs a{};
         a.V = V;
         a.f = f;
@@ -79,13 +95,19 @@ npbs_status refine_driver(npbs_ctx* ctx, const Plan& pl, const float2* k2, const
         a.uhi = u;
         a.k2 = k2;
         a.delta = fold ? w.delta : nullptr;
-        npbs_status s = run_apply(ctx, pl, kTrueRes64, a, fold ? active : nullptr, st);
+        npbs_status s = run_apply(ctx, pl, kTrueRes64, a, rmask, st);
         if (s != NPBS_OK) return s;
+        if (fold) {
+            // the folded corrections restart from zero
+            k_zero_masked<<<pl.nvec, 256, 0, st>>>(pl.vitems, pl.inst, rmask, w.delta);
+            NPBS_CK(ctx, cudaGetLastError());
+            ctx->count(st, 1);
+        }
         NPBS_CK(ctx, cudaMemcpyAsync(hrho2.data(), rho2, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
         NPBS_CK(ctx, cudaMemcpyAsync(hf2.data(), f2, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
         NPBS_CK(ctx, cudaStreamSynchronize(st));
         for (int j = 0; j < n; ++j) {
-            if (fold && !act[j]) continue;
+            if (!need[j]) continue;
             const double fn = std::sqrt(hf2[j]);
             const double rn = std::sqrt(hrho2[j]);
             rt[j] = fn > 0 ? rn / fn : rn;
@@ -101,26 +123,36 @@ npbs_status refine_driver(npbs_ctx* ctx, const Plan& pl, const float2* k2, const
             } else {
                 act[j] = 1;
             }
+            nb_first[j] = -1.0;
+            rt_cycle[j] = rt[j];
+            cycle_its[j] = 0;
         }
         NPBS_CK(ctx, cudaMemcpyAsync(active, act.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st));
         return NPBS_OK;
     };
 
-    for (int j = 0; j < n; ++j) act[j] = 1;
+    for (int j = 0; j < n; ++j) need[j] = 1;
+    NPBS_CK(ctx, cudaMemsetAsync(w.delta, 0, ext * sizeof(float2), st));
     npbs_status s = refresh(false);
     if (s != NPBS_OK) return s;
     std::vector<int> act_prev;
-    bool shape_changed = false;
     bool first_notify = true;
-    auto notify = [&]() -> npbs_status {
+    // after every refresh: tell the solver which instances were refreshed;
+    // returns whether the inner step's launch shapes changed
+    auto notify = [&](bool* changed) -> npbs_status {
         std::vector<int> list;
         for (int j = 0; j < n; ++j)
             if (act[j]) list.push_back(j);
-        const bool shape = w.on_refresh ? w.on_refresh(rt, act) : false;
+        const bool shape = w.on_refresh ? w.on_refresh(rt, act, need) : false;
+        *changed = false;
         if (list == act_prev && !shape && !first_notify) return NPBS_OK;
         first_notify = false;
         act_prev = list;
-        shape_changed = true;
+        *changed = true;
+        // the device mask was just uploaded by the refresh: compact the
+        // per-size launch lists to the instances still iterating
+        npbs_status s2 = set_active_lists(ctx, pl, act, active);
+        if (s2 != NPBS_OK) return s2;
         return w.on_active ? w.on_active(list) : NPBS_OK;
     };
 
@@ -162,37 +194,29 @@ npbs_status refine_driver(npbs_ctx* ctx, const Plan& pl, const float2* k2, const
         bool any = false;
         for (int j = 0; j < n; ++j) any |= act[j] != 0;
         if (!any) break;
-        {
-            shape_changed = false;
-            // the device mask was just uploaded by the refresh: compact the
-            // per-size launch lists to the instances still iterating
-            s = set_active_lists(ctx, pl, act, active);
-            if (s != NPBS_OK) return s;
-            s = notify();
-            if (s != NPBS_OK) return s;
-            if (shape_changed && graph_ready) {
-                // the active set changed: launch shapes of the inner step may differ
-                if (graph.e) cudaGraphExecDestroy(graph.e);
-                if (graph.g) cudaGraphDestroy(graph.g);
-                graph.e = nullptr;
-                graph.g = nullptr;
-                graph_ready = false;
-            }
+        bool changed = false;
+        s = notify(&changed);
+        if (s != NPBS_OK) return s;
+        if (changed && graph_ready) {
+            // the active set changed: launch shapes of the inner step may differ
+            if (graph.e) cudaGraphExecDestroy(graph.e);
+            if (graph.g) cudaGraphDestroy(graph.g);
+            graph.e = nullptr;
+            graph.g = nullptr;
+            graph_ready = false;
         }
-        // new cycle: correction starts at zero, source is rho
-        NPBS_CK(ctx, cudaMemsetAsync(w.delta, 0, ext * sizeof(float2), st));
-        for (int j = 0; j < n; ++j) { nb_first[j] = -1.0; rt_cycle[j] = rt[j]; }
-        int cycle_its = 0;
-        while (true) {
+        // inner chunks until at least one instance ends its cycle
+        bool go = false;
+        while (!go) {
             s = run_chunk();
             if (s != NPBS_OK) return s;
-            cycle_its += chunk;
             NPBS_CK(ctx, cudaMemcpyAsync(hnb.data(), w.nb, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
             NPBS_CK(ctx, cudaStreamSynchronize(st));
-            bool go = false;
             for (int j = 0; j < n; ++j) {
+                need[j] = 0;
                 if (!act[j]) continue;
                 iters[j] += chunk;
+                cycle_its[j] += chunk;
                 if (nb_first[j] < 0) {
                     // the reported norm precedes the last update of the chunk; scale
                     // from the first chunk's value (the cycle's starting residual
@@ -202,10 +226,11 @@ npbs_status refine_driver(npbs_ctx* ctx, const Plan& pl, const float2* k2, const
                 const double red = std::sqrt(hnb[j] / nb_first[j]);
                 const double est = rt_cycle[j] * red;
                 if (!std::isfinite(hnb[j]) || est <= o.rtol || red <= w.max_reduction || red > 2.0 ||
-                    iters[j] >= o.max_iter)
+                    iters[j] >= o.max_iter || cycle_its[j] >= w.max_cycle) {
+                    need[j] = 1;
                     go = true;
+                }
             }
-            if (go || cycle_its >= w.max_cycle) break;
         }
         s = refresh(true);
         if (s != NPBS_OK) return s;
@@ -336,9 +361,11 @@ extern "C" npbs_status npbs_solve(npbs_ctx* ctx, const npbs_net* net, const npbs
     w.flags.assign(cnt, 0);
     // divergence guard: an instance whose float64 rTol grew since the previous
     // refresh continues with plain CBS steps (and is flagged in the report)
-    w.on_refresh = [&](const std::vector<double>& rt, const std::vector<int>& act) -> bool {
+    w.on_refresh = [&](const std::vector<double>& rt, const std::vector<int>& act,
+                       const std::vector<int>& refreshed) -> bool {
         bool changed = false;
         for (int j = 0; j < cnt; ++j) {
+            if (!refreshed[j]) continue;
             if (act[j] && mode[j] == 0 && last_rt[j] >= 0.0 && !(rt[j] < last_rt[j])) {
                 mode[j] = 1;
                 w.flags[j] = 1;

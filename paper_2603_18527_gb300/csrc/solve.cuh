@@ -22,10 +22,11 @@ struct RefineWork {
     // called (outside any capture) with the active instances whenever the set
     // changes; the captured inner-chunk graph is rebuilt afterwards
     std::function<npbs_status(const std::vector<int>&)> on_active;
-    // called after every float64 refresh with the per-instance rTol and the
-    // active mask; returns true when the inner step changed shape (forces the
-    // graph and on_active to be redone)
-    std::function<bool(const std::vector<double>&, const std::vector<int>&)> on_refresh;
+    // called after every float64 refresh with the per-instance rTol, the
+    // active mask and the mask of instances this refresh updated; returns true
+    // when the inner step changed shape (forces the graph and on_active to be
+    // redone)
+    std::function<bool(const std::vector<double>&, const std::vector<int>&, const std::vector<int>&)> on_refresh;
     std::vector<int> flags;  // per-instance flags reported to the caller
 };
 
