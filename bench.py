@@ -36,6 +36,10 @@ METRIC = "ms to 1e-5 residual per 256^2 Helmholtz solve (batched CBS)"
 UNIT = "ms/solve"
 TOL = 1e-5
 B_PER_PT = 32  # algorithmic bytes per point of one CBS apply: read u, f, V, write u (complex64)
+# DRAM bytes per point of the cluster apply (dram__bytes_read + dram__bytes_write) from one ncu
+# capture of a 64 x 256^2 CBS_STEP launch: 102.94 MB + 3.66 MB over 4,194,304 points.  Scaled
+# to the bench batch by its point count; set to None whenever the apply kernel changes.
+TRAFFIC_B_PER_PT = (102.94e6 + 3.66e6) / 4194304
 
 
 def peaks():
@@ -512,7 +516,9 @@ def main():
                            "converged": f"{conv}/{len(insts)}", "iters_mean": float(np.mean(rep["iters"])),
                            "iters_max": int(np.max(rep["iters"])), "parallelism": f"replicas x{world}"},
                 "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-                             "traffic": None, "kernel": "cbs_apply CBS_STEP (one cluster launch per grid side)",
+                             "traffic": None if TRAFFIC_B_PER_PT is None else TRAFFIC_B_PER_PT * pts,
+                             "traffic_note": "bytes per apply, ncu dram read+write of a 64x256^2 launch scaled "
+                                             "by points", "kernel": "cbs_apply CBS_STEP (one cluster launch per grid side)",
                              "apply_ms": apply_ms, "peak_kind": kind, "autotuned_variants": tuned,
                              "cufft_same_step_ms": lib_ms},
                 "cpu_baseline": cpu,

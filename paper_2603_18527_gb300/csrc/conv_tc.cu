@@ -452,9 +452,10 @@ __global__ void __launch_bounds__(192, 1) k_conv_tc_persist(const __grid_constan
 // layout (8-row atoms SBO apart along K, BC-element blocks LBO apart along
 // M/N), so no transpose is needed.  The 128 rows of one M-tile are 128/BC
 // (tap, channel block) pairs: narrow inputs pack several taps into one MMA.
-// A CTA owns up to three M-tiles (accumulators side by side in TMEM, sharing
-// each dz tile) over a range of 64-pixel K-tiles; ranges are combined with
-// float32 atomics (coalesced along the input channel).  Warp 4 issues TMA,
+// A CTA owns MT M-tiles (accumulators side by side in TMEM, sharing each dz
+// tile; the host uses MT = 1 so that two short pipelines share an SM) over a
+// range of 64-pixel K-tiles; ranges are combined with float32 atomics
+// (coalesced along the input channel).  Warp 4 issues TMA,
 // warp 5 the MMAs, warps 0-3 drain TMEM; every wait is bounded.
 
 constexpr int kWKP = 64;  // pixels per K-tile
@@ -491,7 +492,7 @@ struct WgArgs {
     float* dw;
 };
 
-__global__ void __launch_bounds__(192, 1) k_wgrad_tc(const __grid_constant__ CUtensorMap mapx,
+__global__ void __launch_bounds__(192, 2) k_wgrad_tc(const __grid_constant__ CUtensorMap mapx,
                                                      const __grid_constant__ CUtensorMap mapd, WgArgs a) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* base = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -796,12 +797,15 @@ cudaError_t conv_wgrad_tc(const ConvWgrad& a, cudaStream_t st) {
     t.pairs = 9 * t.cpb;
     t.per_tile = kTM / t.BC;
     t.nm = (t.pairs + t.per_tile - 1) / t.per_tile;
-    t.MT = std::min(std::min(3, t.nm), 512 / a.Cout);
+    // one M-tile per CTA and a pipeline sized so that two CTAs share an SM:
+    // the kernel is bound by TMA round trips, not by the tensor pipe, so
+    // more independent pipelines beat sharing each dz tile across M-tiles
+    t.MT = 1;
     t.bnw = a.Cout >= 64 ? 64 : a.Cout;
     t.nbox_b = a.Cout / t.bnw;
     t.a_bytes = t.MT * kTM * kWKP * 2;
     t.stage_bytes = t.a_bytes + a.Cout * kWKP * 2;
-    t.stages = (int)std::max<size_t>(2, std::min<size_t>(4, (200 * 1024) / (size_t)t.stage_bytes));
+    t.stages = (int)std::max<size_t>(2, std::min<size_t>(6, (100 * 1024) / (size_t)t.stage_bytes));
     int cols = 32;
     while (cols < t.MT * a.Cout) cols <<= 1;
     t.tmem_cols = cols;
@@ -811,7 +815,7 @@ cudaError_t conv_wgrad_tc(const ConvWgrad& a, cudaStream_t st) {
     int nsm = 0, dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    const int want = std::max(1, (2 * std::max(nsm, 1) + G - 1) / G);
+    const int want = std::max(1, (4 * std::max(nsm, 1) + G - 1) / G);
     int S = std::max(1, std::min(t.KT / 8, want));
     t.ktp = (t.KT + S - 1) / S;
     S = (t.KT + t.ktp - 1) / t.ktp;
