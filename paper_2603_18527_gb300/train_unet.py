@@ -90,10 +90,11 @@ def media(grid: int, count: int, seed0: int, waves=(20.0, 40.0)):
 
 
 def train(ctx, net, grid=64, steps=1000, batch=32, unroll=4, lr=1e-3, wd=1e-6, pool_size=256, seed=3000,
-          max_snap=2048, log_every=50, log=print):
+          max_snap=2048, log_every=50, log=print, lr_min=None):
     """Metric-matched training on a pool of contrast media; each step draws
     `batch` instances and, for each, a CBS snapshot at a log-uniform iteration
-    count, and runs one npbs_train_step (4 unrolled NPBS steps, AdamW)."""
+    count, and runs one npbs_train_step (4 unrolled NPBS steps, AdamW).  With
+    lr_min the learning rate follows a cosine from lr down to lr_min."""
     rng = np.random.default_rng(seed)
     insts = media(grid, pool_size, seed)
     pool = Pool(ctx, insts)
@@ -116,7 +117,8 @@ def train(ctx, net, grid=64, steps=1000, batch=32, unroll=4, lr=1e-3, wd=1e-6, p
         u0 = pb[torch.from_numpy(ci).cuda(), it].reshape(-1)
         sb.k0sq = [pool.b.k0sq[i] for i in idx]
         sb.eps = [pool.b.eps[i] for i in idx]
-        loss = capi.npbs_train_step(ctx, net, sb, V, f, n, u0, unroll=unroll, lr=lr, weight_decay=wd)
+        lr_t = lr if lr_min is None else lr_min + 0.5 * (lr - lr_min) * (1.0 + math.cos(math.pi * step / max(1, steps)))
+        loss = capi.npbs_train_step(ctx, net, sb, V, f, n, u0, unroll=unroll, lr=lr_t, weight_decay=wd)
         history.append(loss)
         if log and (step % log_every == 0 or step == steps - 1):
             log(json.dumps({"step": step, "loss": loss, "mean_last": float(np.mean(history[-log_every:])),
@@ -149,6 +151,9 @@ def main():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--batch", type=int, default=32)
     ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--lr-min", type=float, default=None, help="cosine decay of the learning rate down to this")
+    ap.add_argument("--init", default="", help="start from these weights (.npz with 'params' or a saved network)")
+    ap.add_argument("--pool", type=int, default=256)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--out", default="")
     ap.add_argument("--eval", type=int, default=16)
@@ -156,9 +161,18 @@ def main():
     args = ap.parse_args()
     build.build()
     ctx = capi.Context(0)
-    net = capi.Net(0, seed=args.seed)
-    train(ctx, net, grid=args.grid, steps=args.steps, batch=args.batch, lr=args.lr, max_snap=args.max_snap)
-    if args.out:
+    if args.init.endswith(".npz"):
+        net = capi.Net(0, seed=args.seed)
+        net.set_params(np.load(args.init)["params"].astype(np.float32))
+    elif args.init:
+        net = capi.Net.load(args.init)
+    else:
+        net = capi.Net(0, seed=args.seed)
+    train(ctx, net, grid=args.grid, steps=args.steps, batch=args.batch, lr=args.lr, max_snap=args.max_snap,
+          pool_size=args.pool, lr_min=args.lr_min)
+    if args.out.endswith(".npz"):
+        np.savez_compressed(args.out, params=net.get_params().astype(np.float16))
+    elif args.out:
         net.save(args.out)
     if args.eval:
         print(json.dumps(evaluate(ctx, net, grid=args.grid, count=args.eval)))
