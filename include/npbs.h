@@ -153,6 +153,24 @@ npbs_status cbs_apply(npbs_ctx* ctx, const npbs_batch* batch, const void* V, con
                       const void* x, void* out, npbs_mode mode, double* norm2,
                       npbs_stream stream);
 
+/* `steps` consecutive in-place CBS steps (Eq. CBS: u <- u + gamma (G(V u + f)
+ * - u)) or preconditioner sweeps (PREC_SWEEP: z <- z + gamma (v - B z), with v
+ * in f) on every instance: the same arithmetic as `steps` cbs_apply calls
+ * whose output feeds the next call's x (bit-identical results).  For the
+ * square sides 128..512 a grid side with few instances (at most an
+ * autotuned count, 8 before npbs_autotune_apply) runs all steps in one
+ * cluster launch, so that after the first step the operands come from L2 and
+ * no launch gaps remain; larger groups, which fill the GPU, run one launch
+ * per step.
+ * Step 0 reads x, later steps read out; x may alias out.  mode: CBS_STEP or
+ * PREC_SWEEP (anything else: NPBS_ERR_INVALID_ARG); steps >= 0 (0: nothing).
+ * norm2 (nullable, DEVICE float64 [count], zeroed by the call) receives the
+ * squared norm of the last step's residual G(V x + f) - x (PREC_SWEEP: v - B x).
+ * V, f, x, out: DEVICE complex64 with the batch layout.  Asynchronous. */
+npbs_status cbs_steps(npbs_ctx* ctx, const npbs_batch* batch, const void* V, const void* f,
+                      const void* x, void* out, npbs_mode mode, int32_t steps, double* norm2,
+                      npbs_stream stream);
+
 /* Autotuner for the single-launch cluster apply: for every square grid side
  * of the batch that has a cluster kernel (128, 192, 256, 384, 512), time each
  * compiled (N1 x N2 factorisation, cluster size, threads, with or without the
@@ -160,7 +178,9 @@ npbs_status cbs_apply(npbs_ctx* ctx, const npbs_batch* batch, const void* V, con
  * the caller's data and keep the fastest for later calls on ctx.  It also
  * times one instance per variant and keeps the lowest-latency variant for
  * launches of at most the largest power-of-two count of instances for which
- * it stays faster (the few unconverged instances late in a solve).  x is
+ * it stays faster (the few unconverged instances late in a solve), and the
+ * largest instance count for which a launch of fused steps (cbs_steps and
+ * the solvers' inner chunks) beats one launch per step.  x is
  * overwritten (it is iterated in place).  chosen (nullable, HOST int32 per
  * grid side present, in increasing side order) receives side * 16 + variant
  * of the throughput choice.  Synchronises the stream. */

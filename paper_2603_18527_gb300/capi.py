@@ -63,6 +63,8 @@ _SIGS = {
                                        C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_void_p]),
     "cbs_apply": (C.c_int, [C.c_void_p, C.POINTER(npbs_batch), C.c_void_p, C.c_void_p, C.c_void_p,
                             C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
+    "cbs_steps": (C.c_int, [C.c_void_p, C.POINTER(npbs_batch), C.c_void_p, C.c_void_p, C.c_void_p,
+                            C.c_void_p, C.c_int, C.c_int32, C.c_void_p, C.c_void_p]),
     "cbs_solve": (C.c_int, [C.c_void_p, C.POINTER(npbs_batch), C.c_void_p, C.c_void_p, C.c_void_p,
                             C.POINTER(npbs_solve_opts), C.POINTER(npbs_report), C.c_void_p]),
     "npbs_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(npbs_batch), C.c_void_p, C.c_void_p,
@@ -250,6 +252,15 @@ def cbs_apply(ctx: Context, batch: Batch, V, f, x, out, mode: int, norm2: Option
         raise ValueError("norm2 must be float64")
     ctx.check(lib().cbs_apply(ctx.handle, C.byref(batch.c_batch()), _ptr(V), _ptr(f), _ptr(x), _ptr(out),
                               int(mode), _ptr(norm2), _stream(stream)))
+
+
+def cbs_steps(ctx: Context, batch: Batch, V, f, x, out, mode: int, steps: int,
+              norm2: Optional[torch.Tensor] = None, stream=None):
+    """`steps` consecutive in-place CBS_STEP / PREC_SWEEP applies in one launch per grid side."""
+    if norm2 is not None and norm2.dtype != torch.float64:
+        raise ValueError("norm2 must be float64")
+    ctx.check(lib().cbs_steps(ctx.handle, C.byref(batch.c_batch()), _ptr(V), _ptr(f), _ptr(x), _ptr(out),
+                              int(mode), int(steps), _ptr(norm2), _stream(stream)))
 
 
 def npbs_autotune_apply(ctx: Context, batch: Batch, V, f, x, reps=5, stream=None) -> dict:

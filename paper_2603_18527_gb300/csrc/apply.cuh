@@ -24,6 +24,8 @@ struct ApplyArgs {
     double2* uhi;       // kTrueRes64: complex128 solution (updated in place)
     const float2* delta;  // kTrueRes64: complex64 correction folded into uhi (nullable)
     const float2* k2;     // kTrueRes64: k^2 (nullable: then k^2 = V + k0^2 + i eps)
+    int steps;            // CBS_STEP / PREC_SWEEP: consecutive in-place steps (0 or 1: one); step
+                          // k >= 1 reads x from out; norm2 is the last step's
 };
 
 // Opt the apply kernels into their dynamic shared memory (once per device).

@@ -75,27 +75,22 @@ __device__ __forceinline__ void prefetch_rows(const int next, const int rank, co
                  : "memory");
 }
 
-template <int N1, int N2, int CS, int T, int MODE>
-__device__ __forceinline__ void cluster_apply_one(const int instx, const BatchDev& bd, const ApplyArgs& a,
-                                                  float2* smem, double* red, const int next = -1) {
+// One apply (phases P1..P7) of instance `in` by this CTA; returns this
+// thread's share of the squared residual norm when `last`.  CBS_STEP and
+// PREC_SWEEP may run several steps in place: a step with !first reads x from
+// out (each thread reads back exactly the points it wrote in the previous
+// step, so the thread's own program order suffices; coherent loads, never the
+// read-only path, since out changes during the kernel).
+template <int N1, int N2, int CS, int T, int MODE, bool first, bool last>
+__device__ __forceinline__ double cluster_step(const InstDev& in, const BatchDev& bd, const ApplyArgs& a, float2* S,
+                                               const float2* tw, const int rank, const int tid, const int next) {
     constexpr int N = N1 * N2;
     constexpr int ROWS = N / CS;
     constexpr int LD = N + N1 + 1;
     constexpr int J1 = (ROWS * N2 + T - 1) / T;  // jobs per thread, passes over N1 (P1, P3, P5, P7)
     constexpr int J2 = (ROWS * N1 + T - 1) / T;  // jobs per thread, passes over N2 (P2, P4, P6)
-    static_assert(N % CS == 0 && ROWS % N2 == 0, "slab must hold whole N2 blocks");
-    float2* S = smem;               // [ROWS][LD]: row slab, then column slab
-    float2* tw = smem + ROWS * LD;  // [N1][N2 + 1]: W_N^{n2 k1}, W_N^j = exp(-2 pi i j / N)
     cg::cluster_group cluster = cg::this_cluster();
-    const int rank = (int)cluster.block_rank();
-    const InstDev in = bd.inst[instx];
-    const int tid = threadIdx.x;
-    for (int e = tid; e < N; e += T) {
-        const int k1 = e / N2, n2 = e - k1 * N2;
-        tw[twi<N2>(k1, n2)] = bd.tw32[in.tw_x + n2 * k1];
-    }
     const long long base = in.offset;
-    __syncthreads();
 
     NPBS_PHASE_MARK(0);
     // ---------------- P1: row pass 1 from global with the prologue
@@ -111,7 +106,7 @@ __device__ __forceinline__ void cluster_apply_one(const int instx, const BatchDe
 #pragma unroll
                 for (int m = 0; m < N1; ++m) {
                     const long long g = g0 + N2 * m;
-                    v[m] = __ldg(a.x + g);
+                    v[m] = first ? __ldg(a.x + g) : __ldcg(a.out + g);
                     if constexpr (MODE != NPBS_ADJ_B && MODE != NPBS_TRUE_RESIDUAL) Vs[m] = __ldg(a.V + g);
                     if constexpr (MODE == NPBS_RESIDUAL || MODE == NPBS_CBS_STEP) fs[m] = __ldg(a.f + g);
                 }
@@ -304,7 +299,7 @@ __device__ __forceinline__ void cluster_apply_one(const int instx, const BatchDe
 #pragma unroll
             for (int n1 = 0; n1 < N1; ++n1) {
                 const long long g = g0 + N2 * n1;
-                xs[n1] = a.x[g];
+                xs[n1] = first ? a.x[g] : a.out[g];
                 if constexpr (MODE != NPBS_RESIDUAL && MODE != NPBS_OP_B) Vs[n1] = __ldg(a.V + g);
                 if constexpr (MODE == NPBS_TRUE_RESIDUAL || MODE == NPBS_PREC_SWEEP) fs[n1] = __ldg(a.f + g);
             }
@@ -348,11 +343,55 @@ __device__ __forceinline__ void cluster_apply_one(const int instx, const BatchDe
                     o = make_float2(x.x + gr * rr - gi * ri, x.y + gr * ri + gi * rr);
                 }
                 a.out[g] = o;
-                acc += (double)(rr * rr + ri * ri);
+                if (last) acc += (double)(rr * rr + ri * ri);
             }
         }
     }
     NPBS_PHASE_MARK(7);
+    return acc;
+}
+
+// The same step compiled as a separate function: the fused multi-step loop
+// calls it, so nothing loop-invariant (addresses, the symbol 1/lambda,
+// twiddles) is hoisted out of the loop and kept live across the phases.
+template <int N1, int N2, int CS, int T, int MODE, bool first, bool last>
+__device__ __noinline__ double cluster_step_call(const InstDev& in, const BatchDev& bd, const ApplyArgs& a, float2* S,
+                                                 const float2* tw, const int rank, const int tid) {
+    return cluster_step<N1, N2, CS, T, MODE, first, last>(in, bd, a, S, tw, rank, tid, -1);
+}
+
+template <int N1, int N2, int CS, int T, int MODE>
+__device__ __forceinline__ void cluster_apply_one(const int instx, const BatchDev& bd, const ApplyArgs& a,
+                                                  float2* smem, double* red, const int next = -1) {
+    constexpr int N = N1 * N2;
+    constexpr int ROWS = N / CS;
+    constexpr int LD = N + N1 + 1;
+    static_assert(N % CS == 0 && ROWS % N2 == 0, "slab must hold whole N2 blocks");
+    float2* S = smem;               // [ROWS][LD]: row slab, then column slab
+    float2* tw = smem + ROWS * LD;  // [N1][N2 + 1]: W_N^{n2 k1}, W_N^j = exp(-2 pi i j / N)
+    cg::cluster_group cluster = cg::this_cluster();
+    const int rank = (int)cluster.block_rank();
+    const InstDev in = bd.inst[instx];
+    const int tid = threadIdx.x;
+    for (int e = tid; e < N; e += T) {
+        const int k1 = e / N2, n2 = e - k1 * N2;
+        tw[twi<N2>(k1, n2)] = bd.tw32[in.tw_x + n2 * k1];
+    }
+    __syncthreads();
+    double acc;
+    constexpr bool ITER = MODE == NPBS_CBS_STEP || MODE == NPBS_PREC_SWEEP;
+    if (!ITER || a.steps <= 1) {
+        acc = cluster_step<N1, N2, CS, T, MODE, true, true>(in, bd, a, S, tw, rank, tid, next);
+    } else if constexpr (ITER) {
+        // fused steps: after the first, u, V and f of the instance come from L2
+        cluster_step_call<N1, N2, CS, T, MODE, true, false>(in, bd, a, S, tw, rank, tid);
+        __syncthreads();  // the next step rewrites the slab
+        for (int it = 1; it < a.steps - 1; ++it) {
+            cluster_step_call<N1, N2, CS, T, MODE, false, false>(in, bd, a, S, tw, rank, tid);
+            __syncthreads();
+        }
+        acc = cluster_step_call<N1, N2, CS, T, MODE, false, true>(in, bd, a, S, tw, rank, tid);
+    }
     if (a.norm2) {
         acc = warp_sum_d(acc);
         if ((tid & 31) == 0) red[tid >> 5] = acc;

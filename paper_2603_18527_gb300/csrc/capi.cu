@@ -243,16 +243,40 @@ npbs_status run_apply(npbs_ctx* ctx, const Plan& pl, int mode, const ApplyArgs& 
         if (itt != ctx->fast_tail.end() && todo[i].second.count <= itt->second.second) var = itt->second.first;
         cudaStream_t s = i < nside ? ctx->aux[i] : st;
         if (i < nside) NPBS_CK(ctx, cudaStreamWaitEvent(s, ctx->fork_ev, 0));
-        NPBS_CK(ctx, launch_apply_fast(n, var, mode, todo[i].second, bd, a, s));
-        ctx->count(st, 1);
+        // fused steps pay off while a group is a single latency-bound wave;
+        // larger groups run one launch per step
+        const bool iter = mode == NPBS_CBS_STEP || mode == NPBS_PREC_SWEEP;
+        auto itf = ctx->fast_fused_max.find(n);
+        const int fmax = itf == ctx->fast_fused_max.end() ? npbs_ctx::kDefaultFusedMax : itf->second;
+        if (iter && a.steps > 1 && todo[i].second.count > fmax) {
+            for (int k = 0; k < a.steps; ++k) {
+                ApplyArgs ak = a;
+                ak.steps = 1;
+                if (k > 0) ak.x = a.out;
+                if (k < a.steps - 1) ak.norm2 = nullptr;
+                NPBS_CK(ctx, launch_apply_fast(n, var, mode, todo[i].second, bd, ak, s));
+            }
+            ctx->count(st, a.steps);
+        } else {
+            NPBS_CK(ctx, launch_apply_fast(n, var, mode, todo[i].second, bd, a, s));
+            ctx->count(st, 1);
+        }
         if (i < nside) NPBS_CK(ctx, cudaEventRecord(ctx->join_ev[i], s));
     }
     for (int i = 0; i < nside; ++i) NPBS_CK(ctx, cudaStreamWaitEvent(st, ctx->join_ev[i], 0));
     if (pl.nrow32s > 0) {
         bd.rows = pl.rows32s;
         bd.cols = pl.cols32s;
-        NPBS_CK(ctx, launch_apply(mode, bd, pl.nrow32s, pl.ncol32s, a, st));
-        ctx->count(st, 3);
+        // the three-launch path takes fused steps one apply at a time
+        const bool iter = mode == NPBS_CBS_STEP || mode == NPBS_PREC_SWEEP;
+        const int nsteps = iter ? std::max(1, a.steps) : 1;
+        for (int k = 0; k < nsteps; ++k) {
+            ApplyArgs ak = a;
+            if (k > 0) ak.x = a.out;
+            if (k < nsteps - 1) ak.norm2 = nullptr;
+            NPBS_CK(ctx, launch_apply(mode, bd, pl.nrow32s, pl.ncol32s, ak, st));
+            ctx->count(st, 3);
+        }
     }
     return NPBS_OK;
 }
@@ -440,12 +464,15 @@ npbs_status npbs_autotune_apply(npbs_ctx* ctx, const npbs_batch* batch, const vo
     NPBS_CK(ctx, cudaEventCreate(&e0));
     NPBS_CK(ctx, cudaEventCreate(&e1));
     // milliseconds per launch of variant v over the first cnt instances of g
-    auto time_v = [&](const Plan::FastGroup& g, int v, int cnt, int nrep, float* ms) -> cudaError_t {
+    // (`steps` fused CBS steps per launch)
+    auto time_v = [&](const Plan::FastGroup& g, int v, int cnt, int nrep, float* ms, int steps = 1) -> cudaError_t {
         FastDev fd{g.list, cnt};
-        cudaError_t e = launch_apply_fast(g.n, v, NPBS_CBS_STEP, fd, bd, a, s);  // warm-up
+        ApplyArgs as = a;
+        as.steps = steps;
+        cudaError_t e = launch_apply_fast(g.n, v, NPBS_CBS_STEP, fd, bd, as, s);  // warm-up
         for (int r = 0; r < nrep && e == cudaSuccess; ++r) {
             if (r == 0) e = cudaEventRecord(e0, s);
-            if (e == cudaSuccess) e = launch_apply_fast(g.n, v, NPBS_CBS_STEP, fd, bd, a, s);
+            if (e == cudaSuccess) e = launch_apply_fast(g.n, v, NPBS_CBS_STEP, fd, bd, as, s);
         }
         if (e == cudaSuccess) e = cudaEventRecord(e1, s);
         if (e == cudaSuccess) e = cudaEventSynchronize(e1);
@@ -482,10 +509,24 @@ npbs_status npbs_autotune_apply(npbs_ctx* ctx, const npbs_batch* batch, const vo
                 tailmax = k;
             }
         }
+        // fused steps: the largest power-of-two count (or the whole group) for
+        // which one launch of kFs fused steps beats kFs launches
+        constexpr int kFs = 8;
+        int fusedmax = 0;
+        for (int k = 1; e == cudaSuccess; k = std::min(2 * k, g.count)) {
+            const int v = k <= tailmax ? tailv : bestv;
+            float mf = 0.f, ms1 = 0.f;
+            e = time_v(g, v, k, std::max(reps, 4), &mf, kFs);
+            if (e == cudaSuccess) e = time_v(g, v, k, kFs * std::max(reps, 4), &ms1, 1);
+            if (e != cudaSuccess || mf >= kFs * ms1) break;
+            fusedmax = k;
+            if (k == g.count) break;
+        }
         if (e != cudaSuccess) break;
         ctx->fast_variant[g.n] = bestv;
         if (tailmax > 0) ctx->fast_tail[g.n] = {tailv, tailmax};
         else ctx->fast_tail.erase(g.n);
+        ctx->fast_fused_max[g.n] = fusedmax;
         if (chosen) chosen[gi] = g.n * 16 + bestv;
         ++gi;
     }
@@ -517,6 +558,27 @@ npbs_status cbs_apply(npbs_ctx* ctx, const npbs_batch* batch, const void* V, con
     a.x = static_cast<const float2*>(x);
     a.out = static_cast<float2*>(out);
     a.norm2 = norm2;
+    return run_apply(ctx, *pl, (int)mode, a, nullptr, reinterpret_cast<cudaStream_t>(stream));
+}
+
+npbs_status cbs_steps(npbs_ctx* ctx, const npbs_batch* batch, const void* V, const void* f, const void* x,
+                      void* out, npbs_mode mode, int32_t steps, double* norm2, npbs_stream stream) {
+    if (!ctx) return NPBS_ERR_INVALID_ARG;
+    if (mode != NPBS_CBS_STEP && mode != NPBS_PREC_SWEEP)
+        return set_err(ctx, NPBS_ERR_INVALID_ARG, "cbs_steps: mode must be CBS_STEP or PREC_SWEEP");
+    if (steps < 0) return set_err(ctx, NPBS_ERR_INVALID_ARG, "cbs_steps: steps < 0");
+    npbs_status st;
+    const Plan* pl = get_plan(ctx, batch, &st);
+    if (!pl) return st;
+    if (pl->count == 0 || steps == 0) return NPBS_OK;
+    if (!V || !f || !x || !out) return set_err(ctx, NPBS_ERR_INVALID_ARG, "cbs_steps: NULL field pointer");
+    ApplyArgs a{};
+    a.V = static_cast<const float2*>(V);
+    a.f = static_cast<const float2*>(f);
+    a.x = static_cast<const float2*>(x);
+    a.out = static_cast<float2*>(out);
+    a.norm2 = norm2;
+    a.steps = steps;
     return run_apply(ctx, *pl, (int)mode, a, nullptr, reinterpret_cast<cudaStream_t>(stream));
 }
 

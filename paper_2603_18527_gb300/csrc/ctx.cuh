@@ -86,6 +86,11 @@ struct npbs_ctx {
     // instead when at most `max count` instances of that side are launched
     // (the few-instance tail of a solve); autotuned
     std::map<int, std::pair<int, int>> fast_tail;
+    // grid side -> largest instance count for which a chunk of fused steps
+    // (cbs_steps, the solvers' inner chunks) runs as one launch; larger groups
+    // take one launch per step.  Autotuned; kDefaultFusedMax until then.
+    std::map<int, int> fast_fused_max;
+    static constexpr int kDefaultFusedMax = 8;
     cudaStream_t solve_stream = nullptr;  // capturable stream the solvers run on
     cudaEvent_t solve_event = nullptr;
     // side streams on which the cluster applies of different grid sides run

@@ -311,16 +311,14 @@ extern "C" npbs_status fgmres_solve(npbs_ctx* ctx, const npbs_net* net, const np
     auto precondition = [&](const float2* v, float2* z) -> npbs_status {
         if (precond == 1) {
             NPBS_CK(ctx, cudaMemsetAsync(z, 0, sizeof(float2) * ext, s));
-            for (int k = 0; k < cbs_sweeps; ++k) {
-                ApplyArgs a{};
-                a.V = Vp;
-                a.f = v;
-                a.x = z;
-                a.out = z;
-                npbs_status s2 = run_apply(ctx, *pl, NPBS_PREC_SWEEP, a, act_cyc, s);
-                if (s2 != NPBS_OK) return s2;
-            }
-            return NPBS_OK;
+            // all sweeps fused into one launch per grid side
+            ApplyArgs a{};
+            a.V = Vp;
+            a.f = v;
+            a.x = z;
+            a.out = z;
+            a.steps = cbs_sweeps;
+            return run_apply(ctx, *pl, NPBS_PREC_SWEEP, a, act_cyc, s);
         }
         std::vector<int> which;
         for (int q = 0; q < cnt; ++q)

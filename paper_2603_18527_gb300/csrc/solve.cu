@@ -166,7 +166,9 @@ npbs_status refine_driver(npbs_ctx* ctx, const Plan& pl, const float2* k2, const
                 ctx->capture_kernels = 0;
                 NPBS_CK(ctx, cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
                 npbs_status s2 = NPBS_OK;
-                for (int i = 0; i < chunk && s2 == NPBS_OK; ++i) s2 = step(i == chunk - 1);
+                if (w.fused) s2 = w.fused(chunk);
+                else
+                    for (int i = 0; i < chunk && s2 == NPBS_OK; ++i) s2 = step(i == chunk - 1);
                 cudaGraph_t g = nullptr;
                 cudaError_t e = cudaStreamEndCapture(st, &g);
                 if (s2 != NPBS_OK) {
@@ -183,6 +185,7 @@ npbs_status refine_driver(npbs_ctx* ctx, const Plan& pl, const float2* k2, const
             ctx->launches += graph_kernels;
             return NPBS_OK;
         }
+        if (w.fused) return w.fused(chunk);
         for (int i = 0; i < chunk; ++i) {
             npbs_status s2 = step(i == chunk - 1);
             if (s2 != NPBS_OK) return s2;
@@ -296,6 +299,17 @@ extern "C" npbs_status cbs_solve(npbs_ctx* ctx, const npbs_batch* batch, const v
         a.x = w.delta;
         a.out = w.delta;
         a.norm2 = last ? w.nb : nullptr;
+        return run_apply(ctx, *pl, NPBS_CBS_STEP, a, w.active, s);
+    };
+    // a chunk of inner iterations as one fused launch per grid side
+    w.fused = [&](int steps) -> npbs_status {
+        ApplyArgs a{};
+        a.V = Vp;
+        a.f = w.rho;
+        a.x = w.delta;
+        a.out = w.delta;
+        a.norm2 = w.nb;
+        a.steps = steps;
         return run_apply(ctx, *pl, NPBS_CBS_STEP, a, w.active, s);
     };
     return refine_driver(ctx, *pl, K2, Vp, static_cast<const float2*>(f), static_cast<double2*>(u), *opts, report,

@@ -28,6 +28,9 @@ struct RefineWork {
     // redone)
     std::function<bool(const std::vector<double>&, const std::vector<int>&, const std::vector<int>&)> on_refresh;
     std::vector<int> flags;  // per-instance flags reported to the caller
+    // optional: a whole chunk of `steps` inner iterations in one call (the last
+    // writes nb), used instead of `steps` InnerStep calls when set
+    std::function<npbs_status(int steps)> fused;
 };
 
 // One inner iteration on delta; `last` asks it to write the squared Born

@@ -224,3 +224,33 @@ def test_prefetch_variants_identical_on_batches_beyond_residency(side, monkeypat
         for (o1, n1), (o2, n2) in zip(*outs):
             assert torch.equal(o1, o2), (side, v)
             assert torch.allclose(n1, n2, rtol=1e-12, atol=0), (side, v)
+
+
+@pytest.mark.parametrize("side,count", [(96, 3), (128, 3), (128, 10), (192, 3), (256, 3), (384, 3), (512, 3)])
+def test_fused_steps_bit_identical_to_repeated_applies(side, count, monkeypatch):
+    """cbs_steps(K) is K in-place CBS_STEP (or PREC_SWEEP) applies, fused into
+    one launch per grid side for small groups (3 instances) and one launch per
+    step for groups above the fused count (10 > 8): every compiled variant
+    gives exactly the output of K separate cbs_apply calls (96^2 takes the
+    three-launch path)."""
+    capi, c0 = ctx()
+    insts = [synth.small_instance(side, side, seed=600 + j, layer=side // 16) for j in range(count)]
+    b, k2, f, n, V = setup_batch(capi, c0, insts)
+    x0 = b.pack([random_field((side, side), 610 + j) for j in range(count)])
+    K = 5
+    for v in range(2 * KERNEL_VARIANTS.get(side, 0) or 1):
+        if side in KERNEL_VARIANTS:
+            monkeypatch.setenv("NPBS_FAST_VARIANT", f"{side}:{v}")
+        cv = capi.Context(0)
+        for mode in ("CBS_STEP", "PREC_SWEEP"):
+            m = getattr(capi, mode)
+            ref = x0.clone()
+            n_ref = torch.zeros(b.count, dtype=torch.float64, device="cuda")
+            for k in range(K):
+                capi.cbs_apply(cv, b, V, f, ref, ref, m, n_ref if k == K - 1 else None)
+            got = torch.zeros_like(x0)
+            n_got = torch.zeros(b.count, dtype=torch.float64, device="cuda")
+            capi.cbs_steps(cv, b, V, f, x0, got, m, K, n_got)  # out of place: step 0 reads x0
+            torch.cuda.synchronize()
+            assert torch.equal(got, ref), (side, v, mode)
+            assert torch.allclose(n_got, n_ref, rtol=1e-12, atol=0), (side, v, mode)
