@@ -144,18 +144,8 @@ def bench_learned(capi, ctx, args, stream):
     """Network forward / training step throughput and NPBS vs CBS on the
     contrast media law at 256^2."""
     from paper_2603_18527_gb300 import train_unet as T
-    out = {}
-    net = None
-    if args.net and os.path.exists(args.net) and args.net.endswith(".npz"):
-        net = capi.Net(0, seed=0)
-        net.set_params(np.load(args.net)["params"].astype(np.float32))
-        out["net"] = os.path.basename(args.net)
-    elif args.net and os.path.exists(args.net):
-        net = capi.Net.load(args.net)
-        out["net"] = os.path.basename(args.net)
-    else:
-        net = capi.Net(0, seed=0)
-        out["net"] = "untrained (seed 0)"
+    net, name = load_net(capi, args)
+    out = {"net": name}
     # network forward at 64 x 256^2 (the NPBS inference batch)
     insts = T.media(256, args.npbs_count, 2000)
     pool = T.Pool(ctx, insts)
@@ -201,8 +191,43 @@ def bench_learned(capi, ctx, args, stream):
     return out
 
 
+def load_net(capi, args):
+    """The network of --net (.npz params or a saved network), else untrained; (net, name)."""
+    if args.net and os.path.exists(args.net) and args.net.endswith(".npz"):
+        net = capi.Net(0, seed=0)
+        net.set_params(np.load(args.net)["params"].astype(np.float32))
+        return net, os.path.basename(args.net)
+    if args.net and os.path.exists(args.net):
+        return capi.Net.load(args.net), os.path.basename(args.net)
+    return capi.Net(0, seed=0), "untrained (seed 0)"
+
+
+def fgmres_case(capi, ctx, net, b, k2, f, n, precs, max_iter):
+    res = {}
+    for name, pc in precs:
+        u = torch.zeros(b.extent, dtype=torch.complex128, device="cuda")
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st, rep = capi.fgmres_solve(ctx, net if pc == 2 else None, b, k2, f, n, u, restart=20, precond=pc,
+                                    cbs_sweeps=16, rtol=TOL, max_iter=max_iter)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        res[name] = {"ms_per_solve": dt * 1e3 / b.count, "iters_mean": float(np.mean(rep["iters"])),
+                     "converged": int(sum(1 for x in rep["status"] if x == capi.OK))}
+    return res
+
+
 def bench_fgmres(capi, ctx, args):
-    """FGMRES(20) at 1024^2 on layered media: none / 16 CBS sweeps."""
+    """FGMRES(20): 16 x 256^2 contrast media (the network's distribution) with
+    no / 16-sweep CBS / network preconditioning, and 1024^2 layered media with
+    no / CBS preconditioning."""
+    from paper_2603_18527_gb300 import train_unet as T
+    net, name = load_net(capi, args)
+    pool = T.Pool(ctx, T.media(256, args.npbs_count, 2000))
+    out = {"contrast": {"workload": f"contrast media law, {args.npbs_count} x 256^2, restart 20, tol {TOL}, "
+                                    f"network {name}",
+                        **fgmres_case(capi, ctx, net, pool.b, pool.k2, pool.f, pool.n,
+                                      [("none", 0), ("cbs16", 1), ("npbs", 2)], args.fgmres_max_iter)}}
     insts = synth.workload_layered(args.fgmres_count, 1024)
     b = capi.Batch([(i.ny, i.nx) for i in insts], h=[i.h for i in insts])
     k2 = b.pack([i.k2 for i in insts])
@@ -210,18 +235,10 @@ def bench_fgmres(capi, ctx, args):
     n = b.pack([i.n for i in insts], dtype=torch.float32)
     V = torch.zeros_like(k2)
     capi.npbs_build_potential(ctx, b, k2, V)
-    res = {"workload": f"layered media, {len(insts)} x 1024^2, restart 20, tol {TOL}"}
-    for name, pc in [("none", 0), ("cbs16", 1)]:
-        u = torch.zeros(b.extent, dtype=torch.complex128, device="cuda")
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        st, rep = capi.fgmres_solve(ctx, None, b, k2, f, n, u, restart=20, precond=pc, cbs_sweeps=16, rtol=TOL,
-                                    max_iter=args.fgmres_max_iter)
-        torch.cuda.synchronize()
-        dt = time.perf_counter() - t0
-        res[name] = {"ms_per_solve": dt * 1e3 / len(insts), "iters_mean": float(np.mean(rep["iters"])),
-                     "converged": int(sum(1 for x in rep["status"] if x == capi.OK))}
-    return res
+    out["layered"] = {"workload": f"layered media, {len(insts)} x 1024^2, restart 20, tol {TOL}",
+                      **fgmres_case(capi, ctx, None, b, k2, f, n, [("none", 0), ("cbs16", 1)],
+                                    args.fgmres_max_iter)}
+    return out
 
 
 def library_fft_apply_ms(b, insts, V, f, stream, reps):
