@@ -304,12 +304,14 @@ def _opts(rtol, max_iter, check_every, use_graph):
 
 def cbs_solve(ctx: Context, batch: Batch, k2, f, u, rtol=1e-5, max_iter=2500, check_every=16, use_graph=1,
               stream=None):
-    """Returns (status, report dict); u (complex128) is updated in place."""
+    """Returns (status, report dict); u (complex128) is updated in place.  OK,
+    NOT_CONVERGED and ERR_NONFINITE come with the per-instance report; other
+    statuses raise NpbsError."""
     rep = Report(batch.count)
     o = _opts(rtol, max_iter, check_every, use_graph)
     st = lib().cbs_solve(ctx.handle, C.byref(batch.c_batch()), _ptr(k2), _ptr(f), _ptr(u), C.byref(o),
                          C.byref(rep.c), _stream(stream))
-    if st not in (OK, NOT_CONVERGED):
+    if st not in (OK, NOT_CONVERGED, ERR_NONFINITE):  # these fill the per-instance report
         ctx.check(st)
     return st, rep.as_dict()
 
@@ -320,7 +322,7 @@ def npbs_solve(ctx: Context, net: "Net", batch: Batch, k2, f, n, u, rtol=1e-5, m
     o = _opts(rtol, max_iter, check_every, use_graph)
     st = lib().npbs_solve(ctx.handle, net.handle, C.byref(batch.c_batch()), _ptr(k2), _ptr(f), _ptr(n), _ptr(u),
                           C.byref(o), C.byref(rep.c), _stream(stream))
-    if st not in (OK, NOT_CONVERGED):
+    if st not in (OK, NOT_CONVERGED, ERR_NONFINITE):  # these fill the per-instance report
         ctx.check(st)
     return st, rep.as_dict()
 
@@ -335,7 +337,7 @@ def fgmres_solve(ctx: Context, net, batch: Batch, k2, f, n, u, restart=20, preco
     st = lib().fgmres_solve(ctx.handle, net.handle if net is not None else None, C.byref(batch.c_batch()), _ptr(k2),
                             _ptr(f), _ptr(n), _ptr(u), int(restart), int(precond), int(cbs_sweeps), C.byref(o),
                             C.byref(rep.c), _stream(stream))
-    if st not in (OK, NOT_CONVERGED):
+    if st not in (OK, NOT_CONVERGED, ERR_NONFINITE):  # these fill the per-instance report
         ctx.check(st)
     return st, rep.as_dict()
 

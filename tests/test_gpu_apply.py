@@ -19,7 +19,8 @@ TOL = 1e-5
 
 # sizes spanning several row/column tiles, ragged tails, radix 3, non-square grids
 SHAPES = [(16, 16), (96, 96), (24, 48), (48, 24), (2, 2), (3, 6), (288, 288), (256, 256), (1024, 64),
-          (64, 1024), (384, 128), (9, 512), (128, 128), (192, 192), (384, 384), (512, 512), (256, 256)]
+          (64, 1024), (384, 128), (9, 512), (128, 128), (192, 192), (384, 384), (512, 512), (256, 256),
+          (1024, 1024)]
 
 
 @pytest.fixture(scope="module")
@@ -97,7 +98,7 @@ def test_adjoint_dot_product_gpu(env):
     capi.cbs_apply(c, b, V, None, y, BHy, capi.ADJ_B)
     torch.cuda.synchronize()
     for j in range(b.count):
-        xv, yv = b.view(x, j).double(), b.view(y, j)
+        yv = b.view(y, j)
         lhs = torch.vdot(b.view(Bx, j).reshape(-1).to(torch.complex128), yv.reshape(-1).to(torch.complex128))
         rhs = torch.vdot(b.view(x, j).reshape(-1).to(torch.complex128), b.view(BHy, j).reshape(-1).to(torch.complex128))
         assert abs(complex(lhs - rhs)) <= 1e-5 * abs(complex(lhs)) + 1e-6
@@ -254,3 +255,13 @@ def test_fused_steps_bit_identical_to_repeated_applies(side, count, monkeypatch)
             torch.cuda.synchronize()
             assert torch.equal(got, ref), (side, v, mode)
             assert torch.allclose(n_got, n_ref, rtol=1e-12, atol=0), (side, v, mode)
+
+
+def test_zero_fused_steps_is_a_noop(env):
+    capi, c, insts, probs, b, k2, f, V, xs, x = env
+    out = torch.full_like(x, 7.0)
+    capi.cbs_steps(c, b, V, f, x, out, capi.CBS_STEP, 0)
+    torch.cuda.synchronize()
+    assert bool((out == 7.0).all())
+    with pytest.raises(capi.NpbsError):
+        capi.cbs_steps(c, b, V, f, x, out, capi.OP_B, 3)

@@ -52,3 +52,34 @@ def test_cbs_solve_zero_source_and_graph_off():
     u = torch.zeros(b.extent, dtype=torch.complex128, device="cuda")
     st, rep = capi.cbs_solve(c, b, k2, f, u, rtol=1e-6, max_iter=100, check_every=4, use_graph=0)
     assert st == capi.OK and rep["iters"][0] == 0
+
+
+def test_nonfinite_instance_is_isolated():
+    """A NaN in one instance's source marks that instance NONFINITE at the first
+    float64 check; the other instances of the batch still converge."""
+    capi, c = ctx()
+    insts = [synth.small_instance(64, 64, seed=20 + j, layer=8) for j in range(3)]
+    insts[1].f[5, 7] = np.nan
+    b, k2, f, n, V = setup_batch(capi, c, insts)
+    u = torch.zeros(b.extent, dtype=torch.complex128, device="cuda")
+    st, rep = capi.cbs_solve(c, b, k2, f, u, rtol=1e-5, max_iter=20000, check_every=16)
+    assert st == capi.ERR_NONFINITE
+    assert rep["status"][1] == capi.ERR_NONFINITE and rep["iters"][1] == 0
+    for j in (0, 2):
+        assert rep["status"][j] == capi.OK
+        assert H.rtol(oracle_problem(insts[j]), torch.from_numpy(b.unpack(u)[j])) <= 1e-5
+
+
+def test_warm_start_from_a_converged_solution():
+    """u is an input as well: a solve started from a converged solution
+    returns after the first float64 check with no iterations."""
+    capi, c = ctx()
+    insts = [synth.small_instance(64, 64, seed=30 + j, layer=8) for j in range(2)]
+    b, k2, f, n, V = setup_batch(capi, c, insts)
+    u = torch.zeros(b.extent, dtype=torch.complex128, device="cuda")
+    st, rep = capi.cbs_solve(c, b, k2, f, u, rtol=1e-6, max_iter=20000, check_every=16)
+    assert st == capi.OK
+    u0 = u.clone()
+    st, rep2 = capi.cbs_solve(c, b, k2, f, u, rtol=1e-5, max_iter=20000, check_every=16)
+    assert st == capi.OK and rep2["iters"] == [0, 0]
+    assert torch.equal(u, u0)
