@@ -223,3 +223,21 @@ def npbs_solve(p: Problem, M: Callable[[torch.Tensor], torch.Tensor], tol: float
             r = rtol(p, u)
             hist.append(r)
     return SolveResult(u=u, iters=it, rtol=r, history=hist, converged=r <= tol)
+
+
+def direct_solve(p: Problem, M: Callable[[torch.Tensor], torch.Tensor], tol: float = 1e-6,
+                 max_iter: int = 2500, u0=None, check_every: int = 1) -> SolveResult:
+    """Learned iteration in unpreconditioned residual coordinates,
+    u <- u + M(f - A u) (Eq. direct_iter), the baseline format of Sec. 4."""
+    u = torch.zeros_like(p.f) if u0 is None else as_c128(u0).clone()
+    hist = []
+    it = 0
+    r = rtol(p, u)
+    hist.append(r)
+    while r > tol and it < max_iter:
+        u = u + M(true_residual(p, u))
+        it += 1
+        if it % check_every == 0 or it == max_iter:
+            r = rtol(p, u)
+            hist.append(r)
+    return SolveResult(u=u, iters=it, rtol=r, history=hist, converged=r <= tol)

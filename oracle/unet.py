@@ -26,7 +26,7 @@ weight only.
 from __future__ import annotations
 
 import math
-from typing import Dict, List, Sequence, Tuple
+from typing import Callable, Dict, List, Sequence, Tuple
 
 import torch
 import torch.nn.functional as Fnn
@@ -162,6 +162,51 @@ def problems_to_batch(problems: Sequence[H.Problem]):
     f = torch.stack([p.f for p in problems])
     n = torch.stack([p.n for p in problems])
     return V, lam, f, n
+
+
+def batched_apply_A(k2: torch.Tensor, xi2: torch.Tensor, x: torch.Tensor) -> torch.Tensor:
+    """A x = -Delta x - k^2 x (Eq. helm) for a batch: k2, x [B, H, W]; xi2 [H, W] = |xi|^2."""
+    return torch.fft.ifft2(xi2 * torch.fft.fft2(x)) - k2 * x
+
+
+def batched_green(lam: torch.Tensor, x: torch.Tensor) -> torch.Tensor:
+    """G x = F^{-1}(F x / lambda) for a batch."""
+    return torch.fft.ifft2(torch.fft.fft2(x) / lam)
+
+
+LOSS_KINDS = ("bs_reta", "bs_l2", "dir")
+
+
+def unrolled_loss_kind(M: Callable[[torch.Tensor], torch.Tensor], kind: str, V, lam, k2, xi2, f, u0,
+                       unroll: int = 4) -> torch.Tensor:
+    """The three training objectives of Sec. 4 in the unrolled squared form.
+
+    With the true residual t = f - A u as the state, one unrolled step is
+    x_k = P_in t_k, c_k = M(x_k), t_{k+1} = t_k - A c_k (u_{k+1} = u_k + c_k),
+    and the loss is the batch mean of (1/unroll) sum_k ||P_out t_{k+1}||^2 /
+    ||P_out t_0||^2, where
+      dir      (Eq. L_dir):            P_in = I, P_out = I (the Direct format, Eq. direct_iter);
+      bs_l2    (Eq. L_bs_l2):          P_in = G, P_out = I;
+      bs_reta  (Eq. L_bs_Reta_integral): P_in = G, P_out = G (the metric-matched objective).
+    For bs_reta, G t is the Born residual and G A = I - G V (Eq. key_identity), so
+    this equals ``unrolled_loss`` written in Born-residual coordinates.
+    """
+    if kind not in LOSS_KINDS:
+        raise ValueError(kind)
+    t = f - batched_apply_A(k2, xi2, u0)
+    proj_in = (lambda v: v) if kind == "dir" else (lambda v: batched_green(lam, v))
+    proj_out = (lambda v: batched_green(lam, v)) if kind == "bs_reta" else (lambda v: v)
+
+    def sq(v):
+        return (v.real ** 2 + v.imag ** 2).sum(dim=(-2, -1))
+
+    t0n = sq(proj_out(t))
+    acc = torch.zeros_like(t0n)
+    for _ in range(unroll):
+        c = M(proj_in(t))
+        t = t - batched_apply_A(k2, xi2, c)
+        acc = acc + sq(proj_out(t)) / t0n
+    return (acc / unroll).mean()
 
 
 def adamw_step(theta: torch.Tensor, grad: torch.Tensor, m: torch.Tensor, v: torch.Tensor,

@@ -184,6 +184,29 @@ def test_npbs_with_exact_inverse_one_step(tiny):
     assert _rel(_vec(res.u), ustar) < 1e-11
 
 
+def test_direct_solve_with_exact_inverse_one_step(tiny):
+    """Eq. direct_iter with M = A^{-1}: the exact solution after one step."""
+    inst, p, ops = tiny
+    Ainv = np.linalg.inv(ops["A"])
+    M = lambda r: torch.from_numpy((Ainv @ _vec(r)).reshape(8, 12))
+    res = H.direct_solve(p, M, tol=1e-12, max_iter=1)
+    ustar = np.linalg.solve(ops["A"], inst.f.reshape(-1))
+    assert res.iters == 1 and _rel(_vec(res.u), ustar) < 1e-11
+
+
+def test_direct_solve_with_scaled_identity_is_richardson(tiny):
+    """Eq. direct_iter with M = alpha I is Richardson's iteration on A u = f:
+    five steps against the same recurrence on the dense matrix."""
+    inst, p, ops = tiny
+    alpha = 0.01 + 0.002j
+    res = H.direct_solve(p, lambda r: alpha * r, tol=0, max_iter=5)
+    u = np.zeros(96, dtype=np.complex128)
+    f = inst.f.reshape(-1)
+    for _ in range(5):
+        u = u + alpha * (f - ops["A"] @ u)
+    assert _rel(_vec(res.u), u) < 1e-12
+
+
 def test_riesz_equivalence(tiny):
     """Prop. 3.2: ||(I - G V) c - G r|| / ||G r|| = ||A c - r||_R / ||r||_R with
     ||x||_R = ||G x||_2, for arbitrary c and r."""

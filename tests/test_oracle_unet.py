@@ -112,6 +112,85 @@ def test_loss_gradient_matches_central_fd():
         assert abs(fd - float(g[idx])) <= 1e-6 * max(1.0, abs(fd)) + 1e-9, (idx, fd, float(g[idx]))
 
 
+def _batch_kinds(count=2, N=16):
+    insts = [synth.small_instance(N, N, seed=200 + i, layer=3, ppw=6.0) for i in range(count)]
+    probs = [H.problem_from_instance(i) for i in insts]
+    V, lam, f, n = U.problems_to_batch(probs)
+    k2 = torch.stack([p.k2 for p in probs])
+    xi2 = H.xi_squared(N, N, 1.0).to(torch.complex128)
+    u0 = torch.stack([H.cbs_solve(p, tol=0, max_iter=2 + 3 * i).u for i, p in enumerate(probs)])
+    return insts, probs, V, lam, k2, xi2, f, n, u0
+
+
+@pytest.mark.parametrize("kind", U.LOSS_KINDS)
+def test_loss_kinds_are_one_for_a_zero_network(kind):
+    insts, probs, V, lam, k2, xi2, f, n, u0 = _batch_kinds()
+    L = U.unrolled_loss_kind(lambda x: torch.zeros_like(x), kind, V, lam, k2, xi2, f, u0)
+    assert float(L) == pytest.approx(1.0, abs=1e-14)
+
+
+def test_loss_kinds_vanish_for_the_exact_inverse_of_their_format():
+    """Each objective is zero for the operator its format asks the network to
+    learn (Sec. 4): A^{-1} for Eq. L_dir (input: the plain residual), (G A)^{-1}
+    for Eq. L_bs_l2 and (I - G V)^{-1} for Eq. L_bs_Reta_integral (input: the
+    Born residual).  Dense inverses from the DFT definition, 8 x 12 grid."""
+    from oracle import dense as D
+    inst = synth.small_instance(8, 12, seed=3, layer=2, ppw=5.0)
+    p = H.problem_from_instance(inst)
+    ops = D.operators(inst.k2, 1.0, p.k0sq, p.eps)
+    V, lam, f, n = U.problems_to_batch([p])
+    k2 = p.k2[None]
+    xi2 = H.xi_squared(8, 12, 1.0).to(torch.complex128)
+    u0 = H.cbs_solve(p, tol=0, max_iter=3).u[None]
+    inv = {"dir": np.linalg.inv(ops["A"]), "bs_l2": np.linalg.inv(ops["G"] @ ops["A"]),
+           "bs_reta": np.linalg.inv(ops["B"])}
+    for kind in U.LOSS_KINDS:
+        Mi = inv[kind]
+        M = lambda x, Mi=Mi: torch.from_numpy((Mi @ x[0].numpy().reshape(-1)).reshape(1, 8, 12))
+        L = float(U.unrolled_loss_kind(M, kind, V, lam, k2, xi2, f, u0, unroll=2))
+        assert L < 1e-20, (kind, L)
+        # and the other formats' inverses do not zero it
+        for other in U.LOSS_KINDS:
+            if other != kind and not (kind != "dir" and other != "dir"):
+                Mo = inv[other]
+                Mx = lambda x, Mo=Mo: torch.from_numpy((Mo @ x[0].numpy().reshape(-1)).reshape(1, 8, 12))
+                assert float(U.unrolled_loss_kind(Mx, kind, V, lam, k2, xi2, f, u0, unroll=2)) > 1e-6
+
+
+def test_reta_kind_in_true_residual_coordinates_equals_born_state_loss():
+    """Eq. L_bs_Reta_integral through the true residual t (x = G t, metric
+    ||G t||) equals the Born-state form r_{k+1} = r_k - (I - G V) c_k used for
+    training: the key identity G A = I - G V (Eq. key_identity) inside the loss."""
+    flat, P = _params(5)
+    insts, probs, V, lam, k2, xi2, f, n, u0 = _batch_kinds(3, 16)
+    a = U.unrolled_loss_kind(lambda x: U.correction(x, n, P), "bs_reta", V, lam, k2, xi2, f, u0)
+    b = U.unrolled_loss(P, V, lam, f, n, u0)
+    assert float(abs(a - b) / b) < 1e-12
+
+
+@pytest.mark.parametrize("kind", ["dir", "bs_l2"])
+def test_loss_kind_gradient_matches_central_fd(kind):
+    """Autograd of the float64 oracle objective vs central differences, h = 1e-3."""
+    flat, _ = _params(6)
+    insts, probs, V, lam, k2, xi2, f, n, u0 = _batch_kinds(2, 16)
+    th = flat.clone().requires_grad_(True)
+    loss = lambda t: U.unrolled_loss_kind(lambda x: U.correction(x, n, U.unflatten(t)), kind, V, lam, k2, xi2, f,
+                                          u0, unroll=2)
+    (g,) = torch.autograd.grad(loss(th), th)
+    names = [nm for nm, _ in U.PARAM_SPEC]
+    offs = np.cumsum([0] + [math.prod(s) for _, s in U.PARAM_SPEC])
+    rng = np.random.default_rng(9)
+    picks = [int(rng.integers(offs[names.index(nm)], offs[names.index(nm) + 1])) for nm in
+             ["enc0a.w", "enc2b.w", "dec1a.b", "out.w"]]
+    h = 1e-3
+    with torch.no_grad():
+        for idx in picks:
+            e = torch.zeros_like(flat)
+            e[idx] = h
+            fd = (float(loss(flat + e)) - float(loss(flat - e))) / (2 * h)
+            assert abs(fd - float(g[idx])) <= 1e-6 * max(1.0, abs(fd)) + 1e-9, (kind, idx, fd, float(g[idx]))
+
+
 def test_adamw_first_step_closed_form():
     """At step 1, mhat = g and vhat = g^2, so the update is
     -lr * g / (|g| + eps) after decay by (1 - lr wd)."""
