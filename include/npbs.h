@@ -237,6 +237,14 @@ npbs_status npbs_solve(npbs_ctx* ctx, const npbs_net* net, const npbs_batch* bat
                        const void* k2, const void* f, const float* n, void* u,
                        const npbs_solve_opts* opts, npbs_report* report, npbs_stream stream);
 
+/* The Direct format (Eq. direct_iter), the baseline of Sec. 4: u <- u + M(f - A u)
+ * with the network fed the unpreconditioned residual (scale wrapper as in
+ * npbs_solve).  Same mixed-precision refinement, arguments and report as
+ * npbs_solve; no CBS guard (this format has no Born residual to step with). */
+npbs_status npbs_solve_direct(npbs_ctx* ctx, const npbs_net* net, const npbs_batch* batch,
+                              const void* k2, const void* f, const float* n, void* u,
+                              const npbs_solve_opts* opts, npbs_report* report, npbs_stream stream);
+
 /* Restarted flexible GMRES on B u = G f (Eq. LS_discrete), restart length
  * `restart` (1..64), right preconditioner precond: 0 none, 1 `cbs_sweeps`
  * CBS Richardson sweeps, 2 the network of `net` (may be NULL unless precond = 2). */
@@ -295,6 +303,25 @@ npbs_status npbs_net_backward(npbs_ctx* ctx, npbs_net* net, const npbs_batch* ba
 npbs_status npbs_train_step(npbs_ctx* ctx, npbs_net* net, const npbs_batch* batch, const void* V,
                             const void* f, const float* n, const void* u_snap, int32_t unroll, float lr,
                             float weight_decay, float* loss_host, npbs_stream stream);
+
+/* Training objectives of Sec. 4 (the format/loss ablation). */
+typedef enum {
+    NPBS_LOSS_BS_RETA = 0, /* Eq. L_bs_Reta_integral: NPBS input G r, residual measured with G (npbs_train_step) */
+    NPBS_LOSS_BS_L2 = 1,   /* Eq. L_bs_l2: NPBS input G r, Euclidean residual of A */
+    NPBS_LOSS_DIR = 2      /* Eq. L_dir: Direct-format input r = f - A u, Euclidean residual */
+} npbs_loss;
+
+/* npbs_train_step with a choice of objective, each in the squared unrolled
+ * form: for BS_L2 and DIR the state is the true residual t_0 = f - A u_snap,
+ * x_k = G t_k (BS_L2) or t_k (DIR), t_{k+1} = t_k - A M(x_k), loss =
+ * mean_j (1/U) sum_k ||t_k||^2/||t_0||^2, with the adjoints A^* and G^*
+ * (A and G are complex symmetric: A^* y = conj(A conj(y))).  BS_RETA is
+ * npbs_train_step.  Other arguments as there; an unknown kind returns
+ * NPBS_ERR_INVALID_ARG. */
+npbs_status npbs_train_step_loss(npbs_ctx* ctx, npbs_net* net, const npbs_batch* batch, const void* V,
+                                 const void* f, const float* n, const void* u_snap, int32_t unroll,
+                                 npbs_loss kind, float lr, float weight_decay, float* loss_host,
+                                 npbs_stream stream);
 
 #ifdef __cplusplus
 }

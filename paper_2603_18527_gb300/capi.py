@@ -70,6 +70,9 @@ _SIGS = {
     "npbs_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(npbs_batch), C.c_void_p, C.c_void_p,
                              C.c_void_p, C.c_void_p, C.POINTER(npbs_solve_opts), C.POINTER(npbs_report),
                              C.c_void_p]),
+    "npbs_solve_direct": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(npbs_batch), C.c_void_p, C.c_void_p,
+                                    C.c_void_p, C.c_void_p, C.POINTER(npbs_solve_opts), C.POINTER(npbs_report),
+                                    C.c_void_p]),
     "fgmres_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(npbs_batch), C.c_void_p, C.c_void_p,
                                C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_int32,
                                C.POINTER(npbs_solve_opts), C.POINTER(npbs_report), C.c_void_p]),
@@ -94,6 +97,9 @@ _SIGS = {
     "npbs_train_step": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(npbs_batch), C.c_void_p, C.c_void_p,
                                   C.c_void_p, C.c_void_p, C.c_int32, C.c_float, C.c_float,
                                   C.POINTER(C.c_float), C.c_void_p]),
+    "npbs_train_step_loss": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(npbs_batch), C.c_void_p, C.c_void_p,
+                                       C.c_void_p, C.c_void_p, C.c_int32, C.c_int, C.c_float, C.c_float,
+                                       C.POINTER(C.c_float), C.c_void_p]),
 }
 
 
@@ -327,7 +333,21 @@ def npbs_solve(ctx: Context, net: "Net", batch: Batch, k2, f, n, u, rtol=1e-5, m
     return st, rep.as_dict()
 
 
+def npbs_solve_direct(ctx: Context, net: "Net", batch: Batch, k2, f, n, u, rtol=1e-5, max_iter=2500,
+                      check_every=4, use_graph=1, stream=None):
+    """The Direct format u <- u + M(f - A u) (no CBS guard); as npbs_solve otherwise."""
+    rep = Report(batch.count)
+    o = _opts(rtol, max_iter, check_every, use_graph)
+    st = lib().npbs_solve_direct(ctx.handle, net.handle, C.byref(batch.c_batch()), _ptr(k2), _ptr(f), _ptr(n),
+                                 _ptr(u), C.byref(o), C.byref(rep.c), _stream(stream))
+    if st not in (OK, NOT_CONVERGED, ERR_NONFINITE):
+        ctx.check(st)
+    return st, rep.as_dict()
+
+
 PRECOND_NONE, PRECOND_CBS, PRECOND_NPBS = 0, 1, 2
+LOSS_BS_RETA, LOSS_BS_L2, LOSS_DIR = 0, 1, 2
+LOSS_KINDS = {"bs_reta": LOSS_BS_RETA, "bs_l2": LOSS_BS_L2, "dir": LOSS_DIR}
 
 
 def fgmres_solve(ctx: Context, net, batch: Batch, k2, f, n, u, restart=20, precond=PRECOND_NONE, cbs_sweeps=16,
@@ -428,9 +448,15 @@ def npbs_net_adamw(ctx: Context, net: Net, lr: float, weight_decay: float, strea
 
 
 def npbs_train_step(ctx: Context, net: Net, batch: Batch, V, f, n, u_snap, unroll=4, lr=1e-3, weight_decay=1e-6,
-                    stream=None) -> float:
-    loss = C.c_float(0.0)
-    ctx.check(lib().npbs_train_step(ctx.handle, net.handle, C.byref(batch.c_batch()), _ptr(V), _ptr(f), _ptr(n),
-                                    _ptr(u_snap), int(unroll), float(lr), float(weight_decay), C.byref(loss),
-                                    _stream(stream)))
-    return float(loss.value)
+                    stream=None, loss: str = "bs_reta") -> float:
+    """One training step; loss "bs_reta" (metric-matched), "bs_l2" or "dir"."""
+    out = C.c_float(0.0)
+    if loss == "bs_reta":
+        ctx.check(lib().npbs_train_step(ctx.handle, net.handle, C.byref(batch.c_batch()), _ptr(V), _ptr(f), _ptr(n),
+                                        _ptr(u_snap), int(unroll), float(lr), float(weight_decay), C.byref(out),
+                                        _stream(stream)))
+    else:
+        ctx.check(lib().npbs_train_step_loss(ctx.handle, net.handle, C.byref(batch.c_batch()), _ptr(V), _ptr(f),
+                                             _ptr(n), _ptr(u_snap), int(unroll), LOSS_KINDS[loss], float(lr),
+                                             float(weight_decay), C.byref(out), _stream(stream)))
+    return float(out.value)

@@ -342,9 +342,12 @@ __global__ void k_cbs_fallback(const VecItem* items, const InstDev* inst, const 
 //   delta <- delta + M(G(V delta + rho) - delta)
 // on the correction equation; r = G(V delta + rho) - delta equals the Born
 // residual of u + delta for the original problem.
-extern "C" npbs_status npbs_solve(npbs_ctx* ctx, const npbs_net* net, const npbs_batch* batch, const void* k2,
-                                  const void* f, const float* n, void* u, const npbs_solve_opts* opts,
-                                  npbs_report* report, npbs_stream stream) {
+// Learned stationary iteration in either format: Born (Eq. npbs_integral,
+// with the CBS guard) or direct (Eq. direct_iter: r = rho - A delta from the
+// TRUE_RESIDUAL apply, no guard).
+static npbs_status learned_solve(npbs_ctx* ctx, const npbs_net* net, const npbs_batch* batch, const void* k2,
+                                 const void* f, const float* n, void* u, const npbs_solve_opts* opts,
+                                 npbs_report* report, npbs_stream stream, bool direct) {
     if (!ctx) return NPBS_ERR_INVALID_ARG;
     if (!net || !n) return set_err(ctx, NPBS_ERR_INVALID_ARG, "npbs_solve: NULL network or refractive index");
     npbs_status st;
@@ -377,6 +380,7 @@ extern "C" npbs_status npbs_solve(npbs_ctx* ctx, const npbs_net* net, const npbs
     // refresh continues with plain CBS steps (and is flagged in the report)
     w.on_refresh = [&](const std::vector<double>& rt, const std::vector<int>& act,
                        const std::vector<int>& refreshed) -> bool {
+        if (direct) return false;
         bool changed = false;
         for (int j = 0; j < cnt; ++j) {
             if (!refreshed[j]) continue;
@@ -403,10 +407,11 @@ extern "C" npbs_status npbs_solve(npbs_ctx* ctx, const npbs_net* net, const npbs
         a.x = w.delta;
         a.out = r;
         a.norm2 = last ? w.nb : nullptr;
-        npbs_status s2 = run_apply(ctx, *pl, NPBS_RESIDUAL, a, w.active, s);
+        npbs_status s2 = run_apply(ctx, *pl, direct ? NPBS_TRUE_RESIDUAL : NPBS_RESIDUAL, a, w.active, s);
         if (s2 != NPBS_OK) return s2;
         s2 = net_run_forward(ctx, N, run, r, n, w.delta, 1, s);
         if (s2 != NPBS_OK) return s2;
+        if (direct) return NPBS_OK;
         k_cbs_fallback<<<pl->nvec, 256, 0, s>>>(pl->vitems, pl->inst, w.active, cbs_mode, Vp, r, w.delta);
         NPBS_CK(ctx, cudaGetLastError());
         ctx->count(s, 1);
@@ -414,4 +419,16 @@ extern "C" npbs_status npbs_solve(npbs_ctx* ctx, const npbs_net* net, const npbs
     };
     return refine_driver(ctx, *pl, K2, Vp, static_cast<const float2*>(f), static_cast<double2*>(u), *opts, report,
                          s, step, w);
+}
+
+extern "C" npbs_status npbs_solve(npbs_ctx* ctx, const npbs_net* net, const npbs_batch* batch, const void* k2,
+                                  const void* f, const float* n, void* u, const npbs_solve_opts* opts,
+                                  npbs_report* report, npbs_stream stream) {
+    return learned_solve(ctx, net, batch, k2, f, n, u, opts, report, stream, false);
+}
+
+extern "C" npbs_status npbs_solve_direct(npbs_ctx* ctx, const npbs_net* net, const npbs_batch* batch, const void* k2,
+                                         const void* f, const float* n, void* u, const npbs_solve_opts* opts,
+                                         npbs_report* report, npbs_stream stream) {
+    return learned_solve(ctx, net, batch, k2, f, n, u, opts, report, stream, true);
 }

@@ -1,12 +1,26 @@
-// Metric-matched training step (Eq. L_bs_Reta_integral) over unrolled NPBS
-// steps with activation checkpointing:
+// Training step over unrolled learned iterations with activation
+// checkpointing, for the three objectives of Sec. 4.
+//
+// Metric-matched (Eq. L_bs_Reta_integral), in Born-residual coordinates:
 //   r_0 = G(V u + f) - u,  c_k = M(r_k),  r_{k+1} = r_k - (I - G V) c_k,
-//   loss = mean over instances of (1/U) sum_{k=1..U} ||r_k||^2 / ||r_0||^2.
-// Only r_0..r_U are kept; the network activations are recomputed during the
-// backward sweep, which runs the hand-written adjoints in reverse:
+//   loss = mean over instances of (1/U) sum_{k=1..U} ||r_k||^2 / ||r_0||^2,
+// backward with the hand-written adjoints in reverse:
 //   g_{r_U} = 2 w r_U,  g_{c_k} = -(I - G V)^* g_{r_{k+1}}  (ADJ_B apply),
 //   g_{r_k} = g_{r_{k+1}} + J_M(r_k)^* g_{c_k} + 2 w r_k (k >= 1),
-// with w = 1 / (U * count * ||r_0||^2), then one AdamW update.
+// with w = 1 / (U * count * ||r_0||^2).
+//
+// Euclidean objectives (Eq. L_bs_l2 and Eq. L_dir), in true-residual
+// coordinates t = f - A u:
+//   x_k = P t_k (P = G for L_bs_l2, I for L_dir), c_k = M(x_k),
+//   t_{k+1} = t_k - A c_k,  loss = mean of (1/U) sum ||t_k||^2 / ||t_0||^2,
+//   g_{t_U} = 2 w t_U,  g_{c_k} = -A^* g_{t_{k+1}},
+//   g_{t_k} = g_{t_{k+1}} + P^* J_M(x_k)^* g_{c_k} + 2 w t_k (k >= 1).
+// A x is minus the TRUE_RESIDUAL apply with f = 0, G x the RESIDUAL apply
+// with x = 0 and f = x; A and G are complex symmetric (their symbols are even
+// in xi and their potentials diagonal), so A^* y = conj(A conj(y)) and
+// likewise for G.  Only the states (and for L_bs_l2 the network inputs) are
+// kept; the network activations are recomputed in the backward sweep.  One
+// AdamW update ends the step.
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -15,14 +29,15 @@
 
 namespace npbs {
 
+// out = a + sb * b and norm2[inst] += ||out||^2
 __global__ void k_sub_norm(const VecItem* items, const InstDev* inst, const float2* a, const float2* b, float2* out,
-                           double* norm2) {
+                           double* norm2, float sb = -1.f) {
     const VecItem it = items[blockIdx.x];
     const long long base = inst[it.inst].offset + it.start;
     double acc = 0.0;
     for (int e = threadIdx.x; e < it.len; e += blockDim.x) {
         const float2 x = a[base + e], y = b[base + e];
-        const float2 o = make_float2(x.x - y.x, x.y - y.y);
+        const float2 o = make_float2(x.x + sb * y.x, x.y + sb * y.y);
         out[base + e] = o;
         acc += (double)o.x * o.x + (double)o.y * o.y;
     }
@@ -60,18 +75,35 @@ __global__ void k_axpby_inst(const VecItem* items, const InstDev* inst, const fl
     }
 }
 
+// out = conj(x)
+__global__ void k_conj(const VecItem* items, const InstDev* inst, const float2* x, float2* out) {
+    const VecItem it = items[blockIdx.x];
+    const long long base = inst[it.inst].offset + it.start;
+    for (int e = threadIdx.x; e < it.len; e += blockDim.x) {
+        const float2 v = x[base + e];
+        out[base + e] = make_float2(v.x, -v.y);
+    }
+}
+
 }  // namespace npbs
 
 using namespace npbs;
 
-extern "C" npbs_status npbs_train_step(npbs_ctx* ctx, npbs_net* net, const npbs_batch* batch, const void* V,
-                                       const void* f, const float* n, const void* u_snap, int32_t unroll, float lr,
-                                       float weight_decay, float* loss_host, npbs_stream stream) {
+static npbs_status train_step_euclid(npbs_ctx* ctx, Net& N, const Plan* pl, const float2* V, const float2* f,
+                                     const float* n, const float2* u_snap, int U, bool green_input, float lr,
+                                     float weight_decay, float* loss_host, cudaStream_t s);
+
+extern "C" npbs_status npbs_train_step_loss(npbs_ctx* ctx, npbs_net* net, const npbs_batch* batch, const void* V,
+                                            const void* f, const float* n, const void* u_snap, int32_t unroll,
+                                            npbs_loss kind, float lr, float weight_decay, float* loss_host,
+                                            npbs_stream stream) {
     if (!ctx) return NPBS_ERR_INVALID_ARG;
     if (!net || !V || !f || !n || !u_snap || !loss_host)
         return set_err(ctx, NPBS_ERR_INVALID_ARG, "npbs_train_step: NULL argument");
     if (unroll < 1 || unroll > 16 || !(lr >= 0.f) || !(weight_decay >= 0.f))
         return set_err(ctx, NPBS_ERR_INVALID_ARG, "npbs_train_step: need 1 <= unroll <= 16, lr >= 0, weight_decay >= 0");
+    if (kind != NPBS_LOSS_BS_RETA && kind != NPBS_LOSS_BS_L2 && kind != NPBS_LOSS_DIR)
+        return set_err(ctx, NPBS_ERR_INVALID_ARG, "npbs_train_step: unknown loss");
     npbs_status st;
     const Plan* pl = get_plan(ctx, batch, &st);
     if (!pl) return st;
@@ -80,6 +112,10 @@ extern "C" npbs_status npbs_train_step(npbs_ctx* ctx, npbs_net* net, const npbs_
     if (cnt == 0) return NPBS_OK;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     Net& N = *reinterpret_cast<Net*>(net);
+    if (kind != NPBS_LOSS_BS_RETA)
+        return train_step_euclid(ctx, N, pl, static_cast<const float2*>(V), static_cast<const float2*>(f), n,
+                                 static_cast<const float2*>(u_snap), unroll, kind == NPBS_LOSS_BS_L2, lr,
+                                 weight_decay, loss_host, s);
     const int U = unroll;
     const size_t ext = (size_t)std::max<long long>(pl->extent, 1);
     NPBS_CK(ctx, ctx->work[6].ensure(ext * sizeof(float2) * (size_t)(U + 1 + 4)));
@@ -159,6 +195,126 @@ extern "C" npbs_status npbs_train_step(npbs_ctx* ctx, npbs_net* net, const npbs_
         if (k > 0) {
             // g_r <- g_r + J^* g_c + 2 w r_k
             k_axpby_inst<<<vb, 256, 0, s>>>(vi, pl->inst, Rk(k), wgt, 2.f, gr, gn, gr);
+            ctx->count(s, 1);
+        }
+    }
+    NPBS_CK(ctx, cudaGetLastError());
+    return net_adamw(ctx, N, lr, weight_decay, s);
+}
+
+extern "C" npbs_status npbs_train_step(npbs_ctx* ctx, npbs_net* net, const npbs_batch* batch, const void* V,
+                                       const void* f, const float* n, const void* u_snap, int32_t unroll, float lr,
+                                       float weight_decay, float* loss_host, npbs_stream stream) {
+    return npbs_train_step_loss(ctx, net, batch, V, f, n, u_snap, unroll, NPBS_LOSS_BS_RETA, lr, weight_decay,
+                                loss_host, stream);
+}
+
+// Eq. L_bs_l2 (green_input) and Eq. L_dir in true-residual coordinates.
+static npbs_status train_step_euclid(npbs_ctx* ctx, Net& N, const Plan* pl, const float2* V, const float2* f,
+                                     const float* n, const float2* u_snap, int U, bool green_input, float lr,
+                                     float weight_decay, float* loss_host, cudaStream_t s) {
+    const int cnt = pl->count;
+    const size_t ext = (size_t)std::max<long long>(pl->extent, 1);
+    // states t_0..t_U, network inputs x_0..x_{U-1} (green_input only), c, wv, gr, gn, zero
+    const size_t nbuf = (size_t)(U + 1) + (green_input ? (size_t)U : 0) + 5;
+    NPBS_CK(ctx, ctx->work[6].ensure(ext * sizeof(float2) * nbuf));
+    NPBS_CK(ctx, ctx->work[7].ensure(sizeof(double) * (size_t)cnt * (U + 3) + 256));
+    float2* T = static_cast<float2*>(ctx->work[6].p);
+    float2* X = T + ext * (U + 1);
+    float2* c = X + (green_input ? ext * U : 0);
+    float2* wv = c + ext;
+    float2* gr = wv + ext;
+    float2* gn = gr + ext;
+    float2* zero = gn + ext;
+    double* t0n2 = static_cast<double*>(ctx->work[7].p);
+    double* nk2 = t0n2 + cnt;
+    double* wgt = nk2 + (size_t)cnt * U;
+    const VecItem* vi = pl->vitems;
+    const int vb = pl->nvec;
+    auto Tk = [&](int k) { return T + ext * k; };
+    auto Xk = [&](int k) { return green_input ? X + ext * k : Tk(k); };
+    npbs_status st;
+    std::vector<int> which(cnt);
+    for (int j = 0; j < cnt; ++j) which[j] = j;
+    NetRun run;
+    st = net_prepare(ctx, *pl, which, true, &run, s);
+    if (st != NPBS_OK) return st;
+    NPBS_CK(ctx, cudaMemsetAsync(N.grads, 0, sizeof(float) * dev_param_count(), s));
+    NPBS_CK(ctx, cudaMemsetAsync(nk2, 0, sizeof(double) * cnt * U, s));
+    NPBS_CK(ctx, cudaMemsetAsync(zero, 0, sizeof(float2) * ext, s));
+    // out = f_in - A x (TRUE_RESIDUAL); with f_in = 0 it is -A x
+    auto minusA = [&](const float2* x, const float2* f_in, float2* out, double* norm2) -> npbs_status {
+        ApplyArgs a{};
+        a.V = V;
+        a.f = f_in;
+        a.x = x;
+        a.out = out;
+        a.norm2 = norm2;
+        return run_apply(ctx, *pl, NPBS_TRUE_RESIDUAL, a, nullptr, s);
+    };
+    // out = G x (RESIDUAL with x = 0 and f = x)
+    auto green = [&](const float2* x, float2* out) -> npbs_status {
+        ApplyArgs a{};
+        a.V = V;
+        a.f = x;
+        a.x = zero;
+        a.out = out;
+        return run_apply(ctx, *pl, NPBS_RESIDUAL, a, nullptr, s);
+    };
+    auto conj = [&](const float2* x, float2* out) {
+        k_conj<<<vb, 256, 0, s>>>(vi, pl->inst, x, out);
+        ctx->count(s, 1);
+    };
+
+    // forward
+    st = minusA(u_snap, f, Tk(0), t0n2);  // t_0 = f - A u
+    if (st != NPBS_OK) return st;
+    for (int k = 0; k < U; ++k) {
+        if (green_input) {
+            st = green(Tk(k), Xk(k));
+            if (st != NPBS_OK) return st;
+        }
+        st = net_run_forward(ctx, N, run, Xk(k), n, c, 0, s);
+        if (st != NPBS_OK) return st;
+        st = minusA(c, zero, wv, nullptr);  // -A c
+        if (st != NPBS_OK) return st;
+        k_sub_norm<<<vb, 256, 0, s>>>(vi, pl->inst, Tk(k), wv, Tk(k + 1), nk2 + (size_t)k * cnt, 1.f);
+        ctx->count(s, 1);
+    }
+    std::vector<double> h0(cnt), hk((size_t)cnt * U), hw(cnt);
+    NPBS_CK(ctx, cudaMemcpyAsync(h0.data(), t0n2, sizeof(double) * cnt, cudaMemcpyDeviceToHost, s));
+    NPBS_CK(ctx, cudaMemcpyAsync(hk.data(), nk2, sizeof(double) * cnt * U, cudaMemcpyDeviceToHost, s));
+    NPBS_CK(ctx, cudaStreamSynchronize(s));
+    double loss = 0.0;
+    for (int j = 0; j < cnt; ++j) {
+        hw[j] = h0[j] > 0 ? 1.0 / ((double)U * cnt * h0[j]) : 0.0;
+        for (int k = 0; k < U; ++k) loss += hk[(size_t)k * cnt + j] * hw[j];
+    }
+    if (!std::isfinite(loss)) return set_err(ctx, NPBS_ERR_NONFINITE, "npbs_train_step: non-finite loss");
+    *loss_host = (float)loss;
+    NPBS_CK(ctx, cudaMemcpyAsync(wgt, hw.data(), sizeof(double) * cnt, cudaMemcpyHostToDevice, s));
+
+    // backward sweep
+    k_axpby_inst<<<vb, 256, 0, s>>>(vi, pl->inst, Tk(U), wgt, 2.f, nullptr, nullptr, gr);
+    ctx->count(s, 1);
+    for (int k = U - 1; k >= 0; --k) {
+        // g_c = -A^* g_t = conj(-A conj(g_t))
+        conj(gr, c);
+        st = minusA(c, zero, wv, nullptr);
+        if (st != NPBS_OK) return st;
+        conj(wv, c);
+        st = net_run_backward(ctx, N, run, Xk(k), n, c, gn, 0, s);
+        if (st != NPBS_OK) return st;
+        if (green_input) {
+            // G^* gn = conj(G conj(gn))
+            conj(gn, c);
+            st = green(c, wv);
+            if (st != NPBS_OK) return st;
+            conj(wv, gn);
+        }
+        if (k > 0) {
+            // g_t <- g_t + P^* J^* g_c + 2 w t_k
+            k_axpby_inst<<<vb, 256, 0, s>>>(vi, pl->inst, Tk(k), wgt, 2.f, gr, gn, gr);
             ctx->count(s, 1);
         }
     }

@@ -90,7 +90,7 @@ def media(grid: int, count: int, seed0: int, waves=(20.0, 40.0)):
 
 
 def train(ctx, net, grid=64, steps=1000, batch=32, unroll=4, lr=1e-3, wd=1e-6, pool_size=256, seed=3000,
-          max_snap=2048, log_every=50, log=print, lr_min=None):
+          max_snap=2048, log_every=50, log=print, lr_min=None, loss="bs_reta"):
     """Metric-matched training on a pool of contrast media; each step draws
     `batch` instances and, for each, a CBS snapshot at a log-uniform iteration
     count, and runs one npbs_train_step (4 unrolled NPBS steps, AdamW).  With
@@ -118,24 +118,29 @@ def train(ctx, net, grid=64, steps=1000, batch=32, unroll=4, lr=1e-3, wd=1e-6, p
         sb.k0sq = [pool.b.k0sq[i] for i in idx]
         sb.eps = [pool.b.eps[i] for i in idx]
         lr_t = lr if lr_min is None else lr_min + 0.5 * (lr - lr_min) * (1.0 + math.cos(math.pi * step / max(1, steps)))
-        loss = capi.npbs_train_step(ctx, net, sb, V, f, n, u0, unroll=unroll, lr=lr_t, weight_decay=wd)
-        history.append(loss)
+        val = capi.npbs_train_step(ctx, net, sb, V, f, n, u0, unroll=unroll, lr=lr_t, weight_decay=wd, loss=loss)
+        history.append(val)
         if log and (step % log_every == 0 or step == steps - 1):
-            log(json.dumps({"step": step, "loss": loss, "mean_last": float(np.mean(history[-log_every:])),
+            log(json.dumps({"step": step, "loss": val, "mean_last": float(np.mean(history[-log_every:])),
                             "elapsed_s": round(time.time() - t0, 1)}))
     return history
 
 
-def evaluate(ctx, net, grid=64, count=16, seed=9000, tol=1e-5, max_iter=20000):
+def evaluate(ctx, net, grid=64, count=16, seed=9000, tol=1e-5, max_iter=20000, solvers=("cbs", "npbs")):
+    """Iterations and time to `tol` on held-out media for CBS, NPBS (Eq.
+    npbs_integral) and/or the Direct format (Eq. direct_iter, "direct")."""
     insts = media(grid, count, seed)
     pool = Pool(ctx, insts)
     res = {}
-    for name in ["cbs", "npbs"]:
+    for name in solvers:
         u = torch.zeros(pool.b.extent, dtype=torch.complex128, device="cuda")
         torch.cuda.synchronize()
         t = time.time()
         if name == "cbs":
             st, rep = capi.cbs_solve(ctx, pool.b, pool.k2, pool.f, u, rtol=tol, max_iter=max_iter, check_every=16)
+        elif name == "direct":
+            st, rep = capi.npbs_solve_direct(ctx, net, pool.b, pool.k2, pool.f, pool.n, u, rtol=tol,
+                                             max_iter=max_iter, check_every=4)
         else:
             st, rep = capi.npbs_solve(ctx, net, pool.b, pool.k2, pool.f, pool.n, u, rtol=tol, max_iter=max_iter,
                                       check_every=4)
@@ -154,6 +159,8 @@ def main():
     ap.add_argument("--lr-min", type=float, default=None, help="cosine decay of the learning rate down to this")
     ap.add_argument("--init", default="", help="start from these weights (.npz with 'params' or a saved network)")
     ap.add_argument("--pool", type=int, default=256)
+    ap.add_argument("--loss", default="bs_reta", choices=["bs_reta", "bs_l2", "dir"],
+                    help="training objective (Sec. 4): metric-matched, Euclidean bs, or Direct")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--out", default="")
     ap.add_argument("--eval", type=int, default=16)
@@ -169,13 +176,14 @@ def main():
     else:
         net = capi.Net(0, seed=args.seed)
     train(ctx, net, grid=args.grid, steps=args.steps, batch=args.batch, lr=args.lr, max_snap=args.max_snap,
-          pool_size=args.pool, lr_min=args.lr_min)
+          pool_size=args.pool, lr_min=args.lr_min, loss=args.loss)
     if args.out.endswith(".npz"):
         np.savez_compressed(args.out, params=net.get_params().astype(np.float16))
     elif args.out:
         net.save(args.out)
     if args.eval:
-        print(json.dumps(evaluate(ctx, net, grid=args.grid, count=args.eval)))
+        solvers = ("cbs", "direct") if args.loss == "dir" else ("cbs", "npbs")
+        print(json.dumps(evaluate(ctx, net, grid=args.grid, count=args.eval, solvers=solvers)))
 
 
 if __name__ == "__main__":
