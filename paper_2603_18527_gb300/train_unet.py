@@ -150,6 +150,33 @@ def evaluate(ctx, net, grid=64, count=16, seed=9000, tol=1e-5, max_iter=20000, s
     return res
 
 
+def ablation(ctx, grid=256, steps=2000, count=32, tol=1e-5, max_iter=2500, log=print):
+    """The format / objective ablation of Sec. 4 (Table 2's U-Net row): three
+    networks from the same initialisation on the same media pool and snapshot
+    bank, trained with Eq. L_dir (Direct format), Eq. L_bs_l2 and Eq.
+    L_bs_Reta_integral (NPBS format), each evaluated in its own format on
+    `count` held-out media against CBS."""
+    out = {}
+    for kind in ("dir", "bs_l2", "bs_reta"):
+        net = capi.Net(0, seed=0)
+        t = time.time()
+        hist = train(ctx, net, grid=grid, steps=steps, batch=32, pool_size=256, seed=5000, lr=1e-3, lr_min=2e-5,
+                     log_every=max(1, steps // 4), log=log, loss=kind)
+        solver = "direct" if kind == "dir" else "npbs"
+        r = evaluate(ctx, net, grid=grid, count=count, seed=2000, tol=tol, max_iter=max_iter, solvers=("cbs", solver))
+        res = {"train_s": round(time.time() - t, 1), "final_loss": float(np.mean(hist[-200:]))}
+        for name, v in r.items():
+            it = np.array(v["iters"])
+            ok = np.array(v["status"]) == capi.OK
+            res[name] = {"converged": int(ok.sum()), "iters_mean_converged": float(it[ok].mean()) if ok.any() else None,
+                         "iters_median": float(np.median(it)), "seconds": round(v["seconds"], 3),
+                         "fallback": int(sum(v.get("fallback") or [0]))}
+        out[kind] = res
+        if log:
+            log(json.dumps({kind: res}))
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--grid", type=int, default=64)
@@ -165,9 +192,14 @@ def main():
     ap.add_argument("--out", default="")
     ap.add_argument("--eval", type=int, default=16)
     ap.add_argument("--max-snap", type=int, default=2048)
+    ap.add_argument("--ablation", action="store_true",
+                    help="train and evaluate the three objectives (Direct+L_dir, NPBS+L_bs_l2, NPBS+L_bs_Reta)")
     args = ap.parse_args()
     build.build()
     ctx = capi.Context(0)
+    if args.ablation:
+        print(json.dumps(ablation(ctx, grid=args.grid, steps=args.steps)))
+        return
     if args.init.endswith(".npz"):
         net = capi.Net(0, seed=args.seed)
         net.set_params(np.load(args.init)["params"].astype(np.float32))
