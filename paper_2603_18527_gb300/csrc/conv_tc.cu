@@ -633,7 +633,30 @@ EncodeTiledFn encoder() {
 size_t tc_smem(int bn, int bk) { return (size_t)kStages * (kTM + bn) * bk * 2 + 1024 + 256; }
 
 bool g_tc_persistent = true;
-int g_tc_blocks_per_sm_cap = 4;
+// CTAs of the persistent convolution per SM: two by default (measured: the
+// network forward of 16 x 256^2 takes 1.66 / 1.25 / 1.30 / 1.32 ms with 1 / 2 /
+// 3 / 4), fewer where registers or shared memory do not fit them.
+int g_tc_blocks_per_sm_cap = 2;
+bool g_tc_blocks_forced = false;  // NPBS_CONV_CTAS_PER_SM given: size the grid by it alone
+
+// CTAs of the persistent convolution that fit on one SM with `smem` bytes of
+// dynamic shared memory, from the kernel's registers and the SM's register
+// file, shared memory and thread limits.  (The occupancy query reports one CTA
+// for this kernel whatever the launch's shared memory, which left SMs idle.)
+int conv_tc_blocks_per_sm(size_t smem) {
+    cudaFuncAttributes fa{};
+    int dev = 0, regs_sm = 65536, smem_sm = 228 * 1024;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    if (cudaFuncGetAttributes(&fa, k_conv_tc_persist) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return 1;
+    }
+    const int by_regs = regs_sm / std::max(1, fa.numRegs * 192);
+    const int by_smem = (int)(smem_sm / (smem + fa.sharedSizeBytes + 1024));
+    return std::max(1, std::min(std::min(by_regs, by_smem), 2048 / 192));
+}
 
 }  // namespace
 
@@ -757,7 +780,7 @@ static cudaError_t conv_fwd_tc_one(const ConvFwd& a0, cudaStream_t st, int sub, 
         int dev = 0, nsm = 0, occ = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_conv_tc_persist, 192, smem);
+        occ = g_tc_blocks_forced ? g_tc_blocks_per_sm_cap : conv_tc_blocks_per_sm(smem);
         const int grid = std::max(1, std::min(ntiles, nsm * std::max(1, std::min(occ, per_sm))));
         k_conv_tc_persist<<<grid, 192, smem, st>>>(mx, mw, t, ntiles);
         return cudaGetLastError();
@@ -855,6 +878,11 @@ cudaError_t conv_wgrad_tc(const ConvWgrad& a, cudaStream_t st) {
 cudaError_t prepare_conv_tc() {
     encoder();
     if (const char* e = getenv("NPBS_CONV_TC")) g_tc_persistent = strcmp(e, "tile") != 0;
+    // NPBS_CONV_CTAS_PER_SM=k launches k CTAs of the persistent convolution per SM (default: 2 where they fit)
+    if (const char* e = getenv("NPBS_CONV_CTAS_PER_SM")) {
+        g_tc_blocks_per_sm_cap = std::max(1, atoi(e));
+        g_tc_blocks_forced = true;
+    }
     cudaError_t e = cudaFuncSetAttribute(k_conv_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem(256, 64));
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_conv_tc_persist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem(256, 64));
