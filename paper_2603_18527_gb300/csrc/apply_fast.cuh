@@ -10,6 +10,7 @@ struct FastDev {
     const int* list;  // device [count]: instance indices
     int count;
     int ahead;        // > 0: after its loads, cluster c prefetches into L2 the rows of list[c + ahead]
+                      // (the launcher sets a third of the resident cluster count)
 };
 
 bool fast_supported(int n);
