@@ -37,9 +37,9 @@ UNIT = "ms/solve"
 TOL = 1e-5
 B_PER_PT = 32  # algorithmic bytes per point of one CBS apply: read u, f, V, write u (complex64)
 # DRAM bytes per point of the cluster apply (dram__bytes_read + dram__bytes_write) from one ncu
-# capture of a 64 x 256^2 CBS_STEP launch: 102.94 MB + 3.66 MB over 4,194,304 points.  Scaled
+# capture of a 64 x 256^2 CBS_STEP launch: 106.18 MB + 17.81 MB over 4,194,304 points.  Scaled
 # to the bench batch by its point count; set to None whenever the apply kernel changes.
-TRAFFIC_B_PER_PT = (102.94e6 + 3.66e6) / 4194304
+TRAFFIC_B_PER_PT = (106.18e6 + 17.81e6) / 4194304
 
 
 def peaks():
