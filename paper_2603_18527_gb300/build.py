@@ -44,6 +44,20 @@ def _stale() -> bool:
 def build(force: bool = False, verbose: bool = False, extra=()) -> str:
     if not force and not _stale():
         return LIB
+    # one builder at a time (several ranks of a job may call this together);
+    # whoever waited re-checks, the library may be fresh by then
+    import fcntl
+    with open(LIB + ".lock", "w") as lock:
+        fcntl.flock(lock, fcntl.LOCK_EX)
+        try:
+            if not force and not _stale():
+                return LIB
+            return _build_locked(verbose, extra)
+        finally:
+            fcntl.flock(lock, fcntl.LOCK_UN)
+
+
+def _build_locked(verbose: bool, extra) -> str:
     os.makedirs(OUT_DIR, exist_ok=True)
     cc = nvcc()
     srcs = sources()
