@@ -136,7 +136,24 @@ struct TcArgs {
     int xo;                 // channel offset of the input slice
     int bn;                 // N of the MMA (Cout rounded up to 16)
     int tmem_cols;
+    int halo;               // 1: halo rows (one per dy, shared by the three dx taps), see k_conv_tc_persist
 };
+
+// Halo mode: one TMA box of kHaloRows pixels (x0 - 4 .. x0 + 131) x 8 channels
+// per dy row and 8-channel slice of a K chunk, unswizzled, so that the A
+// operand of tap dx starts at pixel row 4 + dx of the box (16-byte steps).
+constexpr int kHaloRows = 136;
+
+// K-major shared-memory descriptor without swizzle: 8-row x 16-byte core
+// matrices, `lbo` bytes apart along K, `sbo` bytes apart along M / N.
+__device__ __forceinline__ uint64_t smem_desc_nosw(uint32_t addr, int lbo, int sbo) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr >> 4) & 0x3FFF);
+    d |= (uint64_t)(((uint32_t)lbo >> 4) & 0x3FFF) << 16;
+    d |= (uint64_t)(((uint32_t)sbo >> 4) & 0x3FFF) << 32;
+    d |= (uint64_t)1 << 46;  // descriptor version; layout type 0 = no swizzle
+    return d;
+}
 
 __global__ void __launch_bounds__(128, 1) k_conv_tc(const __grid_constant__ CUtensorMap mapx,
                                                     const __grid_constant__ CUtensorMap mapw, TcArgs a) {
@@ -288,8 +305,10 @@ __global__ void __launch_bounds__(192, 1) k_conv_tc_persist(const __grid_constan
                                                             int ntiles) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* base = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    const int a_bytes = kTM * a.BK * 2;
-    const int b_bytes = a.bn * a.BK * 2;
+    // halo mode: A = BK/8 boxes of 8 channels x kHaloRows pixels, B = the three
+    // dx taps' weights for BK channels; K step = (dy, BK-channel chunk)
+    const int a_bytes = a.halo ? (a.BK / 8) * kHaloRows * 16 : kTM * a.BK * 2;
+    const int b_bytes = a.halo ? 3 * a.bn * a.BK * 2 : a.bn * a.BK * 2;
     const int stage_bytes = a_bytes + b_bytes;
     unsigned char* stage0 = base;
     // full[S], empty[S], tfull[2], tempty[2]
@@ -324,7 +343,7 @@ __global__ void __launch_bounds__(192, 1) k_conv_tc_persist(const __grid_constan
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tmem_slot;
     const int nck = a.Cin / a.BK;
-    const int KT = a.ntaps * nck;
+    const int KT = a.halo ? 3 * nck : a.ntaps * nck;
     const int my_tiles = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
 
     if (warp == 4) {
@@ -340,11 +359,21 @@ __global__ void __launch_bounds__(192, 1) k_conv_tc_persist(const __grid_constan
                     const int s = (int)(g % kStages);
                     if (g >= kStages) ok = mbar_wait(su32(&empty[s]), (uint32_t)(((g / kStages) - 1) & 1));
                     if (!ok) break;
-                    const int tap = kt / nck, c0 = (kt % nck) * a.BK;
                     mbar_expect_tx(su32(&full[s]), (uint32_t)stage_bytes);
                     unsigned char* st = stage0 + s * stage_bytes;
-                    tma_load_4d(su32(st), &mapx, su32(&full[s]), a.xo + c0, x0 + a.tdx[tap], y0 + a.tdy[tap], b);
-                    tma_load_2d(su32(st + a_bytes), &mapw, su32(&full[s]), tap * a.Cin + c0, 0);
+                    if (a.halo) {
+                        const int dyi = kt / nck, c0 = (kt % nck) * a.BK;
+                        for (int hh = 0; hh < a.BK / 8; ++hh)
+                            tma_load_4d(su32(st + hh * kHaloRows * 16), &mapx, su32(&full[s]), a.xo + c0 + 8 * hh,
+                                        x0 - 4, y0 + dyi - 1, b);
+                        for (int dxi = 0; dxi < 3; ++dxi)
+                            tma_load_2d(su32(st + a_bytes + dxi * a.bn * a.BK * 2), &mapw, su32(&full[s]),
+                                        (3 * dyi + dxi) * a.Cin + c0, 0);
+                    } else {
+                        const int tap = kt / nck, c0 = (kt % nck) * a.BK;
+                        tma_load_4d(su32(st), &mapx, su32(&full[s]), a.xo + c0, x0 + a.tdx[tap], y0 + a.tdy[tap], b);
+                        tma_load_2d(su32(st + a_bytes), &mapw, su32(&full[s]), tap * a.Cin + c0, 0);
+                    }
                 }
             }
         }
@@ -367,9 +396,20 @@ __global__ void __launch_bounds__(192, 1) k_conv_tc_persist(const __grid_constan
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                     unsigned char* st = stage0 + s * stage_bytes;
                     const uint32_t abase = su32(st), bbase = su32(st + a_bytes);
-                    for (int kk = 0; kk < a.BK / 16; ++kk)
-                        umma(acc_addr, smem_desc(abase + kk * 32, row_bytes), smem_desc(bbase + kk * 32, row_bytes), idesc,
-                             (kt > 0 || kk > 0) ? 1u : 0u);
+                    if (a.halo) {
+                        // tap dx = dxi - 1 reads pixel rows 3 + dxi .. 130 + dxi of the halo
+                        // boxes; K sub-step kk takes boxes 2 kk and 2 kk + 1 (16 channels)
+                        for (int dxi = 0; dxi < 3; ++dxi)
+                            for (int kk = 0; kk < a.BK / 16; ++kk)
+                                umma(acc_addr,
+                                     smem_desc_nosw(abase + kk * 2 * kHaloRows * 16 + (3 + dxi) * 16, kHaloRows * 16, 128),
+                                     smem_desc(bbase + dxi * a.bn * a.BK * 2 + kk * 32, row_bytes), idesc,
+                                     (kt > 0 || dxi > 0 || kk > 0) ? 1u : 0u);
+                    } else {
+                        for (int kk = 0; kk < a.BK / 16; ++kk)
+                            umma(acc_addr, smem_desc(abase + kk * 32, row_bytes), smem_desc(bbase + kk * 32, row_bytes),
+                                 idesc, (kt > 0 || kk > 0) ? 1u : 0u);
+                    }
                     umma_commit(su32(&empty[s]));
                 }
                 umma_commit(su32(&tfull[buf]));
@@ -633,6 +673,7 @@ EncodeTiledFn encoder() {
 size_t tc_smem(int bn, int bk) { return (size_t)kStages * (kTM + bn) * bk * 2 + 1024 + 256; }
 
 bool g_tc_persistent = true;
+bool g_tc_halo = true;  // NPBS_CONV_HALO=0 disables the halo mode
 // CTAs of the persistent convolution per SM: two by default (measured: the
 // network forward of 16 x 256^2 takes 1.66 / 1.25 / 1.30 / 1.32 ms with 1 / 2 /
 // 3 / 4), fewer where registers or shared memory do not fit them.
@@ -704,13 +745,16 @@ static cudaError_t conv_fwd_tc_one(const ConvFwd& a0, cudaStream_t st, int sub, 
         a.W = a0.W / 2;
         a.w = a0.w_sub + (size_t)(py * 2 + px) * a0.Cout * 4 * a0.Cin;
     }
+    // halo rows for 3x3 convolutions over whole 128-pixel row runs with narrow
+    // inputs (the level-0/1 convolutions, bound by the tap tiles' L2 stream)
+    const bool halo = g_tc_persistent && g_tc_halo && !sub && a.W % kTM == 0 && a.Cin % 16 == 0 && a.Cin <= 32;
     const int bk = a.Cin >= 64 ? 64 : a.Cin;
     const int bn = a.Cout;
     int tcols = 32;
     while (tcols < bn) tcols <<= 1;
     CUtensorMapSwizzle sw = bk == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : bk == 32 ? CU_TENSOR_MAP_SWIZZLE_64B
                                                                                 : CU_TENSOR_MAP_SWIZZLE_32B;
-    // input: dims (C, W, H, B), box (bk, cols, rows, 1)
+    // input: dims (C, W, H, B), box (bk, cols, rows, 1); halo: (8, kHaloRows, 1, 1) unswizzled
     const int cols = a.W >= kTM ? kTM : a.W;
     const int rows = a.W >= kTM ? 1 : kTM / a.W;
     CUtensorMap mx, mw;
@@ -718,10 +762,14 @@ static cudaError_t conv_fwd_tc_one(const ConvFwd& a0, cudaStream_t st, int sub, 
         cuuint64_t dims[4] = {(cuuint64_t)a.xs, (cuuint64_t)a.W, (cuuint64_t)a.H, (cuuint64_t)a.B};
         cuuint64_t strides[3] = {(cuuint64_t)a.xs * 2, (cuuint64_t)a.xs * 2 * a.W, (cuuint64_t)a.xs * 2 * a.W * a.H};
         cuuint32_t box[4] = {(cuuint32_t)bk, (cuuint32_t)cols, (cuuint32_t)rows, 1};
+        if (halo) {
+            box[0] = 8;
+            box[1] = kHaloRows;
+        }
         cuuint32_t es[4] = {1, 1, 1, 1};
         if (encoder()(&mx, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<bf16*>(a.x), dims, strides, box, es,
-                      CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+                      CU_TENSOR_MAP_INTERLEAVE_NONE, halo ? CU_TENSOR_MAP_SWIZZLE_NONE : sw,
+                      CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
             return cudaErrorInvalidValue;
     }
     {
@@ -769,7 +817,9 @@ static cudaError_t conv_fwd_tc_one(const ConvFwd& a0, cudaStream_t st, int sub, 
     t.xo = a.xo;
     t.bn = bn;
     t.tmem_cols = tcols;
-    const size_t smem = tc_smem(bn, bk);
+    t.halo = halo ? 1 : 0;
+    const size_t smem = halo ? (size_t)kStages * ((bk / 8) * kHaloRows * 16 + 3 * bn * bk * 2) + 1024 + 256
+                             : tc_smem(bn, bk);
     const long long M = (long long)a.B * a.H * a.W;
     const int ntiles = (int)((M + kTM - 1) / kTM);
     if (g_tc_persistent) {
@@ -878,6 +928,7 @@ cudaError_t conv_wgrad_tc(const ConvWgrad& a, cudaStream_t st) {
 cudaError_t prepare_conv_tc() {
     encoder();
     if (const char* e = getenv("NPBS_CONV_TC")) g_tc_persistent = strcmp(e, "tile") != 0;
+    if (const char* e = getenv("NPBS_CONV_HALO")) g_tc_halo = strcmp(e, "0") != 0;
     // NPBS_CONV_CTAS_PER_SM=k launches k CTAs of the persistent convolution per SM (default: 2 where they fit)
     if (const char* e = getenv("NPBS_CONV_CTAS_PER_SM")) {
         g_tc_blocks_per_sm_cap = std::max(1, atoi(e));
