@@ -56,3 +56,31 @@ def test_fgmres_network_preconditioner_is_flexible_minimal_residual():
     # float32 Arnoldi: allow rounding-level increases
     assert all(born[i + 1] <= born[i] * (1 + 1e-4) for i in range(len(born) - 1)), born
     assert born[-1] < born[0]
+
+
+@pytest.mark.parametrize("precond", [0, 1])
+def test_fgmres_short_trajectory_matches_oracle(precond):
+    """Six FGMRES steps inside one restart cycle (Arnoldi, Givens, least
+    squares) with no preconditioner or 16 CBS sweeps: the GPU iterate is the
+    oracle's minimal-residual iterate over the same Krylov space (float32 basis
+    against float64: agreement to ~1e-5)."""
+    capi, c = ctx()
+    insts = [synth.small_instance(64, 64, seed=140 + j, layer=8, ppw=8.0) for j in range(2)]
+    b, k2, f, n, V = setup_batch(capi, c, insts)
+    u = torch.zeros(b.extent, dtype=torch.complex128, device="cuda")
+    st, rep = capi.fgmres_solve(c, None, b, k2, f, n, u, restart=20, precond=precond, cbs_sweeps=16, rtol=1e-12,
+                                max_iter=6)
+    assert rep["iters"] == [6, 6], rep
+    got = b.unpack(u)
+    for j, inst in enumerate(insts):
+        p = oracle_problem(inst)
+
+        def cbs16(v, p=p):
+            z = torch.zeros_like(v)
+            for _ in range(16):
+                z = H.prec_cbs_sweep(p, z, v)
+            return z
+
+        ref = FG.fgmres_solve(p, cbs16 if precond == 1 else None, restart=20, tol=1e-12, max_iter=6)
+        err = float(np.linalg.norm(got[j] - ref.u.numpy()) / np.linalg.norm(ref.u.numpy()))
+        assert err <= 1e-4, (precond, j, err)
