@@ -48,3 +48,19 @@ def test_version_string_without_gpu(libpath):
     lib = ctypes.CDLL(libpath)
     lib.npbs_version.restype = ctypes.c_char_p
     assert b"sm_103a" in lib.npbs_version()
+
+
+def test_header_is_plain_c(tmp_path):
+    """include/npbs.h is a C header: a C99 translation unit that includes it
+    compiles warning-free (no C++-only constructs in the ABI)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if not cc:
+        pytest.skip("no C compiler")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    src = tmp_path / "use_header.c"
+    src.write_text('#include "npbs.h"\nint main(void) { npbs_ctx* c = 0; (void)c; return (int)NPBS_OK; }\n')
+    r = subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I", os.path.join(root, "include"),
+                        "-c", str(src), "-o", str(tmp_path / "use_header.o")], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
