@@ -11,7 +11,7 @@ import torch
 
 import synth
 from oracle import helmholtz as H
-from tests.gpu_common import ctx, rel_l2, random_field, setup_batch
+from tests.gpu_common import ctx, oracle_problem, rel_l2, random_field, setup_batch
 
 pytestmark = pytest.mark.gpu
 
@@ -265,3 +265,27 @@ def test_zero_fused_steps_is_a_noop(env):
     assert bool((out == 7.0).all())
     with pytest.raises(capi.NpbsError):
         capi.cbs_steps(c, b, V, f, x, out, capi.OP_B, 3)
+
+
+@pytest.mark.parametrize("mode", ["RESIDUAL", "CBS_STEP", "ADJ_B", "TRUE_RESIDUAL"])
+def test_apply_parity_with_grid_spacing(mode):
+    """h != 1 (xi = 2 pi n / (N h), App. Pseudospectral): every instance of a
+    batch carries its own h, on cluster (128^2, 192^2) and three-launch
+    (96 x 48) grids; a dropped or misplaced 1/h fails this."""
+    import dataclasses
+    capi, c = ctx()
+    base = [synth.small_instance(128, 128, seed=60, layer=8), synth.small_instance(192, 192, seed=61, layer=12),
+            synth.small_instance(96, 48, seed=62, layer=6), synth.small_instance(128, 128, seed=63, layer=8)]
+    hs = [0.5, 2.5, 0.5, 1.7]
+    insts = [dataclasses.replace(i, h=h) for i, h in zip(base, hs)]
+    b, k2, f, n, V = setup_batch(capi, c, insts)
+    xs = [random_field((i.ny, i.nx), 70 + j) for j, i in enumerate(insts)]
+    x = b.pack(xs)
+    out = torch.zeros_like(x)
+    capi.cbs_apply(c, b, V, f, x, out, getattr(capi, mode))
+    torch.cuda.synchronize()
+    got = b.unpack(out)
+    for j, inst in enumerate(insts):
+        p = oracle_problem(inst)
+        ref, _ = _oracle(mode, p, xs[j].astype(np.complex128))
+        assert rel_l2(got[j], ref.numpy()) <= TOL, (mode, j, inst.h, rel_l2(got[j], ref.numpy()))
