@@ -289,3 +289,62 @@ def test_apply_parity_with_grid_spacing(mode):
         p = oracle_problem(inst)
         ref, _ = _oracle(mode, p, xs[j].astype(np.complex128))
         assert rel_l2(got[j], ref.numpy()) <= TOL, (mode, j, inst.h, rel_l2(got[j], ref.numpy()))
+
+
+def test_custom_offsets_with_gaps_leave_gaps_untouched():
+    """The batch layout is the caller's (offsets multiples of 32, any order,
+    holes allowed): reversed instances with holes give bit-identical results
+    to the packed layout, and nothing is written into the holes (applies,
+    fused steps, a CBS solve)."""
+    capi, c = ctx()
+    insts = [synth.small_instance(128, 128, seed=80, layer=8), synth.small_instance(96, 48, seed=81, layer=6),
+             synth.small_instance(128, 128, seed=82, layer=8)]
+    b0, k2_0, f_0, n_0, V_0 = setup_batch(capi, c, insts)
+    x0 = b0.pack([random_field((i.ny, i.nx), 90 + j) for j, i in enumerate(insts)])
+    # the same instances, reversed, with 64- and 96-element holes
+    bg = capi.Batch([(i.ny, i.nx) for i in insts], h=[i.h for i in insts])
+    sizes = [i.ny * i.nx for i in insts]
+    bg.offsets = [64 + sizes[2] + 96 + sizes[1] + 64, 64 + sizes[2] + 96, 64]
+    bg.extent = bg.offsets[0] + sizes[0] + 32
+    hole = torch.ones(bg.extent, dtype=torch.bool)
+    for o, sz in zip(bg.offsets, sizes):
+        hole[o:o + sz] = False
+    hole = hole.cuda()
+
+    def regap(t, fill):
+        out = torch.full((bg.extent,), fill, dtype=t.dtype, device="cuda")
+        for j in range(len(insts)):
+            bg.view(out, j).copy_(b0.view(t, j))
+        return out
+
+    SENT = complex(7.0, -3.0)
+    k2_g, f_g, x_g = regap(k2_0, SENT), regap(f_0, SENT), regap(x0, SENT)
+    V_g = torch.full_like(k2_g, SENT)
+    capi.npbs_build_potential(c, bg, k2_g, V_g)
+    assert bool((V_g[hole] == SENT).all())
+    for mode in ["RESIDUAL", "CBS_STEP", "OP_B", "ADJ_B", "TRUE_RESIDUAL", "PREC_SWEEP"]:
+        o0 = torch.zeros_like(x0)
+        capi.cbs_apply(c, b0, V_0, f_0, x0, o0, getattr(capi, mode))
+        og = torch.full_like(x_g, SENT)
+        capi.cbs_apply(c, bg, V_g, f_g, x_g, og, getattr(capi, mode))
+        torch.cuda.synchronize()
+        assert bool((og[hole] == SENT).all()), mode
+        for j in range(len(insts)):
+            assert torch.equal(bg.view(og, j), b0.view(o0, j)), (mode, j)
+    s0, sg = x0.clone(), x_g.clone()
+    capi.cbs_steps(c, b0, V_0, f_0, s0, s0, capi.CBS_STEP, 7)
+    capi.cbs_steps(c, bg, V_g, f_g, sg, sg, capi.CBS_STEP, 7)
+    torch.cuda.synchronize()
+    assert bool((sg[hole] == SENT).all())
+    for j in range(len(insts)):
+        assert torch.equal(bg.view(sg, j), b0.view(s0, j)), j
+    u0 = torch.zeros(b0.extent, dtype=torch.complex128, device="cuda")
+    ug = torch.full((bg.extent,), SENT, dtype=torch.complex128, device="cuda")
+    for j in range(len(insts)):
+        bg.view(ug, j).zero_()
+    st0, r0 = capi.cbs_solve(c, b0, k2_0, f_0, u0, rtol=1e-5, max_iter=5000, check_every=16)
+    stg, rg = capi.cbs_solve(c, bg, k2_g, f_g, ug, rtol=1e-5, max_iter=5000, check_every=16)
+    assert st0 == stg == capi.OK and r0["iters"] == rg["iters"]
+    assert bool((ug[hole] == SENT).all())
+    for j in range(len(insts)):
+        assert torch.equal(bg.view(ug, j), b0.view(u0, j)), j
