@@ -36,6 +36,10 @@
  *
  * Streams.  Calls taking a stream are asynchronous on it except where noted
  * ("synchronises"): the solvers synchronise before filling their report.
+ * cbs_apply and cbs_steps may be captured into a CUDA graph on the caller's
+ * stream once a call with the same batch has run outside capture (that call
+ * builds the batch plan and workspace; later calls only enqueue work, forking
+ * side streams by events for concurrent grid sides).
  */
 #ifndef NPBS_H
 #define NPBS_H

@@ -348,3 +348,36 @@ def test_custom_offsets_with_gaps_leave_gaps_untouched():
     assert bool((ug[hole] == SENT).all())
     for j in range(len(insts)):
         assert torch.equal(bg.view(ug, j), b0.view(u0, j)), j
+
+
+def test_apply_and_fused_steps_capture_into_a_cuda_graph():
+    """After a first call with the batch (which builds its plan and workspace),
+    cbs_apply and cbs_steps issue only stream work, so a caller can capture
+    them into a CUDA graph (here torch's) and replay it: identical results,
+    grid sides on the forked side streams included."""
+    capi, c = ctx()
+    insts = [synth.small_instance(128, 128, seed=50, layer=8), synth.small_instance(256, 256, seed=51, layer=16),
+             synth.small_instance(96, 48, seed=52, layer=6)]
+    b, k2, f, n, V = setup_batch(capi, c, insts)
+    x0 = b.pack([random_field((i.ny, i.nx), 53 + j) for j, i in enumerate(insts)])
+    ref = x0.clone()
+    nref = torch.zeros(b.count, dtype=torch.float64, device="cuda")
+    capi.cbs_apply(c, b, V, f, ref, ref, capi.CBS_STEP, nref)
+    capi.cbs_steps(c, b, V, f, ref, ref, capi.CBS_STEP, 4, nref)
+    torch.cuda.synchronize()
+    x = x0.clone()
+    nrm = torch.zeros(b.count, dtype=torch.float64, device="cuda")
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):  # warm-up outside capture on the capture stream
+        capi.cbs_apply(c, b, V, f, x, x, capi.CBS_STEP, nrm)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        capi.cbs_apply(c, b, V, f, x, x, capi.CBS_STEP, nrm)
+        capi.cbs_steps(c, b, V, f, x, x, capi.CBS_STEP, 4, nrm)
+    x.copy_(x0)
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(x, ref)
+    assert torch.allclose(nrm, nref, rtol=1e-12, atol=0)
