@@ -118,6 +118,18 @@ typedef struct {
 
 /* ---- context ------------------------------------------------------------ */
 
+/* Device-side failures.  Every wait inside the library's kernels (TMA and
+ * tensor-core pipeline barriers) is bounded (about 2 s); a wait that gives up
+ * records it in a device flag, and the kernel cleans up and returns, leaving
+ * its outputs invalid.  npbs_device_status synchronises the device and
+ * returns NPBS_ERR_DEVICE_TIMEOUT (clearing the flag) if that happened since
+ * the last call, else NPBS_OK. */
+npbs_status npbs_device_status(npbs_ctx* ctx);
+/* Exercises that path without harm: one thread waits `seconds` (0 < s <= 2)
+ * on a barrier that nothing completes, gives up and sets the flag; the next
+ * npbs_device_status returns NPBS_ERR_DEVICE_TIMEOUT.  Asynchronous. */
+npbs_status npbs_test_device_timeout(npbs_ctx* ctx, double seconds, npbs_stream stream);
+
 /* Create a context on CUDA device `device` (made current for the call). */
 npbs_status npbs_create(npbs_ctx** out, int device);
 npbs_status npbs_destroy(npbs_ctx* ctx);

@@ -63,6 +63,8 @@ _SIGS = {
                                        C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_void_p]),
     "cbs_apply": (C.c_int, [C.c_void_p, C.POINTER(npbs_batch), C.c_void_p, C.c_void_p, C.c_void_p,
                             C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
+    "npbs_device_status": (C.c_int, [C.c_void_p]),
+    "npbs_test_device_timeout": (C.c_int, [C.c_void_p, C.c_double, C.c_void_p]),
     "cbs_steps": (C.c_int, [C.c_void_p, C.POINTER(npbs_batch), C.c_void_p, C.c_void_p, C.c_void_p,
                             C.c_void_p, C.c_int, C.c_int32, C.c_void_p, C.c_void_p]),
     "cbs_solve": (C.c_int, [C.c_void_p, C.POINTER(npbs_batch), C.c_void_p, C.c_void_p, C.c_void_p,
@@ -258,6 +260,16 @@ def cbs_apply(ctx: Context, batch: Batch, V, f, x, out, mode: int, norm2: Option
         raise ValueError("norm2 must be float64")
     ctx.check(lib().cbs_apply(ctx.handle, C.byref(batch.c_batch()), _ptr(V), _ptr(f), _ptr(x), _ptr(out),
                               int(mode), _ptr(norm2), _stream(stream)))
+
+
+def npbs_device_status(ctx: Context) -> int:
+    """Synchronise; ERR_DEVICE_TIMEOUT (once) if a bounded device wait gave up, else OK."""
+    return int(lib().npbs_device_status(ctx.handle))
+
+
+def npbs_test_device_timeout(ctx: Context, seconds: float = 0.05, stream=None):
+    """Make one bounded device wait give up after `seconds` (tests the error path)."""
+    ctx.check(lib().npbs_test_device_timeout(ctx.handle, float(seconds), _stream(stream)))
 
 
 def cbs_steps(ctx: Context, batch: Batch, V, f, x, out, mode: int, steps: int,

@@ -561,6 +561,28 @@ npbs_status cbs_apply(npbs_ctx* ctx, const npbs_batch* batch, const void* V, con
     return run_apply(ctx, *pl, (int)mode, a, nullptr, reinterpret_cast<cudaStream_t>(stream));
 }
 
+npbs_status npbs_device_status(npbs_ctx* ctx) {
+    if (!ctx) return NPBS_ERR_INVALID_ARG;
+    NPBS_CK(ctx, cudaSetDevice(ctx->device));
+    NPBS_CK(ctx, cudaDeviceSynchronize());
+    if (conv_tc_timeout_flag()) {
+        conv_tc_clear_timeout();
+        return set_err(ctx, NPBS_ERR_DEVICE_TIMEOUT,
+                       "a bounded device wait gave up (a TMA or tensor-core stage never completed); the kernel "
+                       "returned early and its results are invalid");
+    }
+    return NPBS_OK;
+}
+
+npbs_status npbs_test_device_timeout(npbs_ctx* ctx, double seconds, npbs_stream stream) {
+    if (!ctx) return NPBS_ERR_INVALID_ARG;
+    if (!(seconds > 0.0 && seconds <= 2.0))
+        return set_err(ctx, NPBS_ERR_INVALID_ARG, "npbs_test_device_timeout: need 0 < seconds <= 2");
+    NPBS_CK(ctx, wait_selftest(seconds, reinterpret_cast<cudaStream_t>(stream)));
+    ctx->count(reinterpret_cast<cudaStream_t>(stream), 1);
+    return NPBS_OK;
+}
+
 npbs_status cbs_steps(npbs_ctx* ctx, const npbs_batch* batch, const void* V, const void* f, const void* x,
                       void* out, npbs_mode mode, int32_t steps, double* norm2, npbs_stream stream) {
     if (!ctx) return NPBS_ERR_INVALID_ARG;

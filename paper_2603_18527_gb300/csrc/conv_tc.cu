@@ -53,16 +53,28 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
     return ok != 0;
 }
 // Bounded wait: false (and the global flag set) after about two seconds.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long long limit = kWaitCycles) {
     if (mbar_try(bar, parity)) return true;
     const long long t0 = clock64();
     while (!mbar_try(bar, parity)) {
-        if (clock64() - t0 > kWaitCycles) {
+        if (clock64() - t0 > limit) {
             atomicExch(&g_conv_tc_timeout, 1);
             return false;
         }
     }
     return true;
+}
+
+// Exercises the bounded-wait path: thread 0 waits on an mbarrier that nothing
+// arrives at, gives up after `limit` cycles and sets the timeout flag; the
+// kernel then returns normally.
+__global__ void k_wait_selftest(long long limit) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(su32(&bar), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        (void)mbar_wait(su32(&bar), 0, limit);
+    }
 }
 
 __device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map, uint32_t bar, int c0, int c1, int c2,
@@ -946,6 +958,20 @@ int conv_tc_timeout_flag() {
     int v = 0;
     cudaMemcpyFromSymbol(&v, g_conv_tc_timeout, sizeof(int));
     return v;
+}
+
+void conv_tc_clear_timeout() {
+    const int z = 0;
+    cudaMemcpyToSymbol(g_conv_tc_timeout, &z, sizeof(int));
+}
+
+cudaError_t wait_selftest(double seconds, cudaStream_t st) {
+    int dev = 0, khz = 2000000;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev);
+    const long long limit = (long long)(seconds * (double)khz * 1e3);
+    k_wait_selftest<<<1, 32, 0, st>>>(limit > 0 ? limit : 1);
+    return cudaGetLastError();
 }
 
 }  // namespace npbs

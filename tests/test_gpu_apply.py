@@ -381,3 +381,25 @@ def test_apply_and_fused_steps_capture_into_a_cuda_graph():
     torch.cuda.synchronize()
     assert torch.equal(x, ref)
     assert torch.allclose(nrm, nref, rtol=1e-12, atol=0)
+
+
+def test_bounded_device_wait_reports_timeout_and_context_stays_usable(env):
+    """Failure detection without a fault: a kernel thread waits 50 ms on a
+    barrier that nothing completes, gives up and sets the device flag; the
+    host reads NPBS_ERR_DEVICE_TIMEOUT once, and the context and device keep
+    working (the next apply matches the oracle)."""
+    capi, c, insts, probs, b, k2, f, V, xs, x = env
+    assert capi.npbs_device_status(c) == capi.OK
+    capi.npbs_test_device_timeout(c, 0.05)
+    assert capi.npbs_device_status(c) == capi.ERR_DEVICE_TIMEOUT
+    assert "bounded device wait" in c.last_error()
+    assert capi.npbs_device_status(c) == capi.OK
+    out = torch.zeros_like(x)
+    capi.cbs_apply(c, b, V, f, x, out, capi.CBS_STEP)
+    torch.cuda.synchronize()
+    got = b.unpack(out)
+    for j in (0, 7):
+        ref, _ = _oracle("CBS_STEP", probs[j], xs[j])
+        assert rel_l2(got[j], ref.numpy()) <= TOL
+    with pytest.raises(capi.NpbsError):
+        capi.npbs_test_device_timeout(c, 5.0)
