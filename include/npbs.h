@@ -36,6 +36,9 @@
  *
  * Streams.  Calls taking a stream are asynchronous on it except where noted
  * ("synchronises"): the solvers synchronise before filling their report.
+ * Threads.  A context (and a network) is used by one host thread at a time:
+ * its plan cache, workspaces, autotuned choices and side streams are not
+ * locked.  Separate contexts may be used from separate threads.
  * cbs_apply and cbs_steps may be captured into a CUDA graph on the caller's
  * stream once a call with the same batch has run outside capture (that call
  * builds the batch plan and workspace; later calls only enqueue work, forking
