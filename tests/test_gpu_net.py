@@ -291,3 +291,27 @@ def test_direct_solve_short_trajectory_parity():
         M = lambda r: U.correction(r[None], p.n[None], P)[0]
         ref = H.direct_solve(p, M, tol=0, max_iter=2)
         assert rel_l2(got[j], ref.u.numpy()) <= 5e-2
+
+
+def test_train_step_at_256_matches_oracle():
+    """The training step at full resolution (256^2: halo-row convolutions at
+    levels 0-1, 128-pixel row tiles, tcgen05 weight gradients at every level):
+    loss and gradient against the float64 oracle (2 instances, 2 unrolls)."""
+    capi, c = ctx()
+    insts = [synth.small_instance(256, 256, seed=410 + i, layer=16, ppw=10.0) for i in range(2)]
+    probs = [H.problem_from_instance(i) for i in insts]
+    snaps = [H.cbs_solve(p, tol=0, max_iter=2 + 5 * i).u.numpy() for i, p in enumerate(probs)]
+    b, k2, f, n, V = setup_batch(capi, c, insts)
+    u0 = b.pack(snaps)
+    net = _net(capi, 13)
+    loss = capi.npbs_train_step(c, net, b, V, f, n, u0, unroll=2, lr=0.0, weight_decay=0.0)
+    flat = torch.from_numpy(_weights(13)).double().requires_grad_(True)
+    Vb, lam, fb, nb = U.problems_to_batch(probs)
+    L = U.unrolled_loss(U.unflatten(flat), Vb, lam, fb, nb, torch.from_numpy(np.stack(snaps)), unroll=2)
+    (g,) = torch.autograd.grad(L, flat)
+    assert loss == pytest.approx(float(L), rel=2e-2)
+    gw = net.get_grads()
+    ref = g.numpy()
+    assert rel_l2(gw, ref) <= 8e-2, rel_l2(gw, ref)
+    cos = float(np.dot(gw, ref) / (np.linalg.norm(gw) * np.linalg.norm(ref)))
+    assert cos >= 0.995
