@@ -172,18 +172,17 @@ def bench_learned(capi, ctx, args, stream):
                          "frac_of_bf16_peak_sustained": flt / (ms_t * 1e-3) / 1e12 / peak_s}
     # NPBS vs CBS to 1e-5 on the same batch (amortised: batch time / count) and
     # on its first instance alone (batch 1, median of 3)
-    def solve(name, p, reps=1):
+    def solve(name, p, reps=1, max_iter=None):
         ts = []
+        cap = max_iter or args.npbs_max_iter
         for _ in range(reps):
             u = torch.zeros(p.b.extent, dtype=torch.complex128, device="cuda")
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             if name == "cbs":
-                st, rep = capi.cbs_solve(ctx, p.b, p.k2, p.f, u, rtol=TOL, max_iter=args.npbs_max_iter,
-                                         check_every=16)
+                st, rep = capi.cbs_solve(ctx, p.b, p.k2, p.f, u, rtol=TOL, max_iter=cap, check_every=16)
             else:
-                st, rep = capi.npbs_solve(ctx, net, p.b, p.k2, p.f, p.n, u, rtol=TOL,
-                                          max_iter=args.npbs_max_iter, check_every=4)
+                st, rep = capi.npbs_solve(ctx, net, p.b, p.k2, p.f, p.n, u, rtol=TOL, max_iter=cap, check_every=4)
             torch.cuda.synchronize()
             ts.append(time.perf_counter() - t0)
         return {"ms_per_solve": float(np.median(ts)) * 1e3 / p.b.count, "iters_mean": float(np.mean(rep["iters"])),
@@ -193,7 +192,9 @@ def bench_learned(capi, ctx, args, stream):
     out["npbs_vs_cbs"] = {"workload": f"contrast media law, {len(insts)} x 256^2, tol {TOL}, "
                                       f"cap {args.npbs_max_iter} iterations",
                           "batch": {name: solve(name, pool) for name in ("cbs", "npbs")},
-                          "batch_1": {name: solve(name, one, 3) for name in ("cbs", "npbs")}}
+                          "batch_1": {name: solve(name, one, 3) for name in ("cbs", "npbs")},
+                          # time to solution of plain CBS on the same batch without the paper's cap
+                          "cbs_cap_20000": solve("cbs", pool, max_iter=20000)}
     return out
 
 
