@@ -264,10 +264,16 @@ __global__ void k_head_bwd(const SlotDev sd, const bf16* e, const bf16* ze, cons
 }
 
 // dZ = dY * gelu'(Z): dY float32 (pixel stride ds, offset do), Z bf16 (stride zs,
-// offset zo) -> dZ bf16 [P][C]
-__global__ void k_gelu_bwd(long long P, int C, const float* dy, int ds, int dof, const bf16* z, int zs, int zo, bf16* dz) {
+// offset zo) -> dZ bf16 [P][C]; with db, also db[c] += sum_p dZ[p][c] (the bias
+// gradient of the convolution that produced Z, from the bf16 dZ it consumes).
+// Launched with 256 threads and C / 8 dividing 256, so every thread keeps one
+// group of 8 channels across the grid-stride loop.
+__global__ void k_gelu_bwd(long long P, int C, const float* dy, int ds, int dof, const bf16* z, int zs, int zo, bf16* dz,
+                           float* db) {
+    __shared__ float red[256 * 8];
     const int cc = C / 8;
     const long long total = P * cc;
+    float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
         const long long p = i / cc;
         const int c8 = (int)(i % cc);
@@ -278,8 +284,22 @@ __global__ void k_gelu_bwd(long long P, int C, const float* dy, int ds, int dof,
         const float d[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
         __align__(16) bf16 o[8];
 #pragma unroll
-        for (int k = 0; k < 8; ++k) o[k] = __float2bfloat16_rn(d[k] * gelu_grad(__bfloat162float(zz[k])));
+        for (int k = 0; k < 8; ++k) {
+            o[k] = __float2bfloat16_rn(d[k] * gelu_grad(__bfloat162float(zz[k])));
+            acc[k] += __bfloat162float(o[k]);
+        }
         *reinterpret_cast<uint4*>(dz + p * C + c8 * 8) = *reinterpret_cast<uint4*>(o);
+    }
+    if (!db) return;  // uniform over the launch
+    const int g = threadIdx.x % cc, l = threadIdx.x / cc;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) red[l * C + g * 8 + k] = acc[k];
+    __syncthreads();
+    const int lanes = blockDim.x / cc;
+    for (int c = threadIdx.x; c < C; c += blockDim.x) {
+        float t = 0.f;
+        for (int j = 0; j < lanes; ++j) t += red[j * C + c];
+        atomicAdd(db + c, t);
     }
 }
 
@@ -784,7 +804,7 @@ npbs_status net_run_backward(npbs_ctx* ctx, Net& net, const NetRun& run, const f
             ++k;
         }
         // helpers for one conv's backward given dZ (bf16, contiguous [P][Cout]) in A.dz
-        auto wgrad = [&](int li, const bf16* x, int xs, int xo, int R, int Rw) -> cudaError_t {
+        auto wgrad = [&](int li, const bf16* x, int xs, int xo, int R, int Rw, bool bias_in_gelu = true) -> cudaError_t {
             const LayerDef& L = defs[li];
             ConvWgrad w{};
             w.x = x;
@@ -822,10 +842,13 @@ npbs_status net_run_backward(npbs_ctx* ctx, Net& net, const NetRun& run, const f
             w.pix_per_cta = (int)std::min<long long>(ppc, 1 << 20);
             cudaError_t e = conv_wgrad(w, st);
             if (e != cudaSuccess) return e;
-            const int lanes = 256 / (L.cout / 8);
-            const long long nblk = std::min<long long>((P + lanes - 1) / lanes, 152LL * 8);
-            k_bias_grad<<<(unsigned)nblk, 256, 0, st>>>(P, L.cout, A.dz, net.grads + L.b_off);
-            k += 2;
+            ++k;
+            if (!bias_in_gelu) {
+                const int lanes = 256 / (L.cout / 8);
+                const long long nblk = std::min<long long>((P + lanes - 1) / lanes, 152LL * 8);
+                k_bias_grad<<<(unsigned)nblk, 256, 0, st>>>(P, L.cout, A.dz, net.grads + L.b_off);
+                ++k;
+            }
             return cudaGetLastError();
         };
         auto dgrad = [&](int li, int R, int Rw, float* dst, int ds, int dof) -> cudaError_t {
@@ -848,8 +871,10 @@ npbs_status net_run_backward(npbs_ctx* ctx, Net& net, const NetRun& run, const f
             ++k;
             return conv_fwd(a, st);
         };
-        auto gelu_b = [&](long long P, int C, const float* dy, int ds, int dof, const bf16* z, int zs, int zo) {
-            k_gelu_bwd<<<grid_for(P * C / 8), 256, 0, st>>>(P, C, dy, ds, dof, z, zs, zo, A.dz);
+        // dZ of layer li's output; accumulates that layer's bias gradient too
+        auto gelu_b = [&](int li, long long P, int C, const float* dy, int ds, int dof, const bf16* z, int zs, int zo) {
+            k_gelu_bwd<<<grid_for(P * C / 8), 256, 0, st>>>(P, C, dy, ds, dof, z, zs, zo, A.dz,
+                                                             net.grads + defs[li].b_off);
             ++k;
         };
         cudaError_t e = cudaSuccess;
@@ -858,16 +883,16 @@ npbs_status net_run_backward(npbs_ctx* ctx, Net& net, const NetRun& run, const f
             const int R = H >> l, Rw = W >> l, C = ch[l];
             const long long P = (long long)nb * R * Rw;
             const int ib = up_i(l) + 2, ia = up_i(l) + 1, iu = up_i(l);
-            if (l > 0) gelu_b(P, C, A.de[l], C, 0, A.ze[l], C, 0);  // level 0: dz of dec_b from the head
-            e = wgrad(ib, A.d[l], C, 0, R, Rw);
+            if (l > 0) gelu_b(ib, P, C, A.de[l], C, 0, A.ze[l], C, 0);  // level 0: dz of dec_b from the head
+            e = wgrad(ib, A.d[l], C, 0, R, Rw, l > 0);
             if (e == cudaSuccess) e = dgrad(ib, R, Rw, A.dd[l], C, 0);
             if (e != cudaSuccess) break;
-            gelu_b(P, C, A.dd[l], C, 0, A.zd[l], C, 0);
+            gelu_b(ia, P, C, A.dd[l], C, 0, A.zd[l], C, 0);
             e = wgrad(ia, A.cat[l], 2 * C, 0, R, Rw);
             if (e == cudaSuccess) e = dgrad(ia, R, Rw, A.dcat[l], 2 * C, 0);
             if (e != cudaSuccess) break;
             // up conv: output channels [C, 2C) of cat
-            gelu_b(P, C, A.dcat[l], 2 * C, C, A.zcat[l], 2 * C, C);
+            gelu_b(iu, P, C, A.dcat[l], 2 * C, C, A.zcat[l], 2 * C, C);
             const bf16* usrc = l == 2 ? A.cat[3] : A.e[l + 1];
             const int uss = l == 2 ? ch[3] : ch[l + 1];
             e = wgrad(iu, usrc, uss, 0, R, Rw);
@@ -883,11 +908,11 @@ npbs_status net_run_backward(npbs_ctx* ctx, Net& net, const NetRun& run, const f
             const int CC = l < 3 ? 2 * C : C;
             const long long P = (long long)nb * R * Rw;
             // enc b: output = cat channels [0, C); dY in dcat (already has the pool adjoint for l < 3)
-            gelu_b(P, C, A.dcat[l], CC, 0, A.zcat[l], CC, 0);
+            gelu_b(enc_b(l), P, C, A.dcat[l], CC, 0, A.zcat[l], CC, 0);
             e = wgrad(enc_b(l), A.a[l], C, 0, R, Rw);
             if (e == cudaSuccess) e = dgrad(enc_b(l), R, Rw, A.da[l], C, 0);
             if (e != cudaSuccess) break;
-            gelu_b(P, C, A.da[l], C, 0, A.za[l], C, 0);
+            gelu_b(enc_a(l), P, C, A.da[l], C, 0, A.za[l], C, 0);
             const bf16* x = l == 0 ? A.netin : A.in[l];
             const int xs = l == 0 ? 16 : ch[l - 1];
             e = wgrad(enc_a(l), x, xs, 0, R, Rw);

@@ -91,7 +91,7 @@ def test_npbs_solve_with_shipped_network_256():
     w = np.load(os.path.join(ROOT, "paper_2603_18527_gb300", "weights", "unet_contrast256.npz"))["params"]
     net = capi.Net(0, seed=0)
     net.set_params(w.astype(np.float32))
-    insts = T.media(256, 4, 9100)
+    insts = T.media(256, 4, 30000)  # seeds outside every training pool
     pool = T.Pool(c, insts)
     u = torch.zeros(pool.b.extent, dtype=torch.complex128, device="cuda")
     st, rep = capi.npbs_solve(c, net, pool.b, pool.k2, pool.f, pool.n, u, rtol=1e-5, max_iter=20000, check_every=4)
