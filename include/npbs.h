@@ -144,10 +144,11 @@ const char* npbs_version(void);
  * kernels they contain); -1 for a NULL ctx.  For benchmarks. */
 int64_t npbs_launch_count(const npbs_ctx* ctx);
 
-/* Process-wide counts of network convolution launches by engine: the tcgen05
- * tensor-core kernel (TMA-fed, TMEM accumulator) and the warp-level MMA kernel
- * used where TMA cannot tile the geometry (upsampling convolutions, grids
- * whose sides do not divide or are not multiples of 128).  For benchmarks. */
+/* Process-wide counts of network convolution calls (forward, input gradient
+ * and weight gradient) by engine: the tcgen05 tensor-core kernels (TMA-fed,
+ * TMEM accumulators) and the warp-level MMA kernels used where TMA cannot
+ * tile the geometry (grids whose 128- or 64-pixel runs do not tile the image)
+ * or when NPBS_CONV=mma / NPBS_WGRAD=mma force them.  For benchmarks. */
 void npbs_conv_stats(int64_t* tensor_core_launches, int64_t* warp_mma_launches);
 
 /* ---- problem set-up ----------------------------------------------------- */
