@@ -30,7 +30,7 @@ def _worker(rank, world, port, out):
 
 
 def test_replica_aggregation_two_ranks():
-    mgr = mp.Manager()
+    mgr = mp.get_context("spawn").Manager()
     out = mgr.dict()
     mp.start_processes(_worker, args=(2, _free_port(), out), nprocs=2, join=True, start_method="spawn")
     assert out[0] == (15.0, 6.0) and out[1] == (15.0, 6.0)
