@@ -298,6 +298,8 @@ def make_workload(args):
         return synth.workload_mixed(args.n256, args.nother), "cbs_mixed_256x256^2+64x{128,192,384,512}^2"
     if args.workload == "small":
         return synth.workload_96(), "cbs_96^2"
+    if args.workload == "layered1024":
+        return synth.workload_layered(args.fgmres_count, 1024), f"layered_{args.fgmres_count}x1024^2"
     raise ValueError(args.workload)
 
 
@@ -352,7 +354,8 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="mixed", choices=["mixed", "small"])
+    ap.add_argument("--workload", default="mixed", choices=["mixed", "small", "layered1024"],
+                    help="layered1024: the FGMRES media at 1024^2 (--fgmres-count of them), with --apply-only")
     ap.add_argument("--n256", type=int, default=256)
     ap.add_argument("--nother", type=int, default=64)
     ap.add_argument("--check-every", type=int, default=16)
@@ -376,6 +379,8 @@ def main():
     ap.add_argument("--net-forward-only", action="store_true",
                     help="time only the network forward on --npbs-count 256^2 instances (for profiler captures)")
     args = ap.parse_args()
+    if args.workload == "layered1024" and not args.apply_only:
+        ap.error("--workload layered1024 is an apply-only workload")
     if args.impl == "reference":
         return run_reference(args)
     if args.train_step_only:

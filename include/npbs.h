@@ -181,7 +181,7 @@ npbs_status cbs_apply(npbs_ctx* ctx, const npbs_batch* batch, const void* V, con
  * autotuned count, 8 before npbs_autotune_apply) runs all steps in one
  * cluster launch, so that after the first step the operands come from L2 and
  * no launch gaps remain; larger groups, which fill the GPU, run one launch
- * per step.
+ * per step.  Side 1024 and the other grids run three launches per step.
  * Step 0 reads x, later steps read out; x may alias out.  mode: CBS_STEP or
  * PREC_SWEEP (anything else: NPBS_ERR_INVALID_ARG); steps >= 0 (0: nothing).
  * norm2 (nullable, DEVICE float64 [count], zeroed by the call) receives the
@@ -191,11 +191,13 @@ npbs_status cbs_steps(npbs_ctx* ctx, const npbs_batch* batch, const void* V, con
                       const void* x, void* out, npbs_mode mode, int32_t steps, double* norm2,
                       npbs_stream stream);
 
-/* Autotuner for the single-launch cluster apply: for every square grid side
- * of the batch that has a cluster kernel (128, 192, 256, 384, 512), time each
+/* Autotuner for the square-grid apply: for every square grid side of the
+ * batch that has a cluster kernel (128, 192, 256, 384, 512), time each
  * compiled (N1 x N2 factorisation, cluster size, threads, with or without the
  * L2 prefetch of the next instance) variant over `reps` CBS_STEP applies on
- * the caller's data and keep the fastest for later calls on ctx.  It also
+ * the caller's data and keep the fastest for later calls on ctx; side 1024
+ * (three-launch band kernels) likewise over its compiled band shapes (rows
+ * and columns per block).  It also
  * times one instance per variant and keeps the lowest-latency variant for
  * launches of at most the largest power-of-two count of instances for which
  * it stays faster (the few unconverged instances late in a solve), and the

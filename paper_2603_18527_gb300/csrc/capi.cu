@@ -224,7 +224,8 @@ npbs_status run_apply(npbs_ctx* ctx, const Plan& pl, int mode, const ApplyArgs& 
         return NPBS_OK;
     }
     const bool compact = active && active == pl.alist_mask;
-    // grid sides with work, largest first: each side is one cluster launch;
+    // grid sides with work, largest first: each side is one cluster launch
+    // (three band launches for 1024);
     // with several sides the larger ones go to side streams so that the
     // few-wave launches of the large grids overlap the others
     std::vector<std::pair<int, FastDev>> todo;
@@ -256,10 +257,10 @@ npbs_status run_apply(npbs_ctx* ctx, const Plan& pl, int mode, const ApplyArgs& 
                 if (k < a.steps - 1) ak.norm2 = nullptr;
                 NPBS_CK(ctx, launch_apply_fast(n, var, mode, todo[i].second, bd, ak, s));
             }
-            ctx->count(st, a.steps);
+            ctx->count(st, (long long)a.steps * fast_kernel_launches(n, mode, 1));
         } else {
             NPBS_CK(ctx, launch_apply_fast(n, var, mode, todo[i].second, bd, a, s));
-            ctx->count(st, 1);
+            ctx->count(st, fast_kernel_launches(n, mode, a.steps));
         }
         if (i < nside) NPBS_CK(ctx, cudaEventRecord(ctx->join_ev[i], s));
     }
@@ -477,7 +478,7 @@ npbs_status npbs_autotune_apply(npbs_ctx* ctx, const npbs_batch* batch, const vo
         if (e == cudaSuccess) e = cudaEventRecord(e1, s);
         if (e == cudaSuccess) e = cudaEventSynchronize(e1);
         if (e == cudaSuccess) e = cudaEventElapsedTime(ms, e0, e1);
-        ctx->count(s, nrep + 1);
+        ctx->count(s, (long long)(nrep + 1) * fast_kernel_launches(g.n, NPBS_CBS_STEP, steps));
         *ms /= (float)nrep;
         return e;
     };

@@ -30,8 +30,9 @@ struct Plan {
     int nrow32 = 0, ncol32 = 0, nrow64 = 0, ncol64 = 0;
     VecItem* vitems = nullptr;
     int nvec = 0;
-    // float32 modes: square instances of a cluster-kernel size go to one
-    // launch per size; the rest use the three-launch path (rows32s / cols32s)
+    // float32 modes: square instances of a cluster-kernel size (or 1024) go
+    // to one group per size; the rest use the generic three-launch path
+    // (rows32s / cols32s)
     struct FastGroup {
         int n = 0;
         int* list = nullptr;
@@ -80,7 +81,8 @@ struct npbs_ctx {
     npbs::DevBuf scratch;   // spectrum between apply passes
     npbs::DevBuf work[12];  // solver workspaces
     npbs::DevBuf net_ws;    // network activations
-    bool use_fast = true;  // cluster apply for square 128..512 grids (NPBS_APPLY_PATH=three_pass disables)
+    bool use_fast = true;  // cluster apply for square 128..512 grids, band kernels for 1024
+                           // (NPBS_APPLY_PATH=three_pass disables both)
     std::map<int, int> fast_variant;  // grid side -> chosen cluster-kernel variant (autotuned; default 0)
     // grid side -> (variant, max count): the lowest-latency variant, used
     // instead when at most `max count` instances of that side are launched

@@ -139,9 +139,10 @@ def test_invalid_arguments_are_rejected():
 
 
 def test_cluster_path_matches_three_pass_path(env, monkeypatch):
-    """Square 128..512 grids run on the single-launch cluster kernel; a context
-    created with NPBS_APPLY_PATH=three_pass runs the three-launch kernels.  Both
-    must agree to float32 round-off for every mode."""
+    """Square 128..512 grids run on the single-launch cluster kernel and 1024
+    on the band kernels; a context created with NPBS_APPLY_PATH=three_pass runs
+    the generic three-launch kernels.  Both must agree to float32 round-off for
+    every mode."""
     capi, c, insts, probs, b, k2, f, V, xs, x = env
     monkeypatch.setenv("NPBS_APPLY_PATH", "three_pass")
     c3 = capi.Context(0)
@@ -161,6 +162,15 @@ def test_cluster_path_matches_three_pass_path(env, monkeypatch):
 # compiled (N1, N2, cluster, threads, min CTAs) configurations per side; each
 # also exists with the L2 prefetch of the next instance (variant + count)
 KERNEL_VARIANTS = {128: 3, 192: 3, 256: 4, 384: 4, 512: 2}
+# compiled band configurations (rows / columns per block) of the 1024 kernels
+BAND_VARIANTS = {1024: 2}
+
+
+def selectable_variants(side):
+    """Variants NPBS_FAST_VARIANT may pin for a square side (0: none)."""
+    if side in KERNEL_VARIANTS:
+        return 2 * KERNEL_VARIANTS[side]
+    return BAND_VARIANTS.get(side, 0)
 
 
 @pytest.mark.parametrize("side,variants", [(s, 2 * v) for s, v in KERNEL_VARIANTS.items()])
@@ -186,6 +196,44 @@ def test_every_cluster_variant_matches_three_pass(side, variants, monkeypatch):
             A, B = b.unpack(o1), b.unpack(o2)
             for j in range(2):
                 assert rel_l2(A[j], B[j]) <= 2e-6, (side, v, mode)
+
+
+@pytest.mark.parametrize("side,variants", list(BAND_VARIANTS.items()))
+def test_every_band_variant_matches_three_pass(side, variants, monkeypatch):
+    """The 1024 band kernels (rows forward, columns with the symbol, rows
+    inverse with the epilogue; spectrum kept in digit order) give the generic
+    three-launch result for every mode and every compiled band shape, norms
+    included."""
+    capi, c0 = ctx()
+    insts = [synth.small_instance(side, side, seed=250 + j, layer=side // 16) for j in range(2)]
+    b, k2, f, n, V = setup_batch(capi, c0, insts)
+    x = b.pack([random_field((side, side), 260 + j) for j in range(2)])
+    monkeypatch.setenv("NPBS_APPLY_PATH", "three_pass")
+    c3 = capi.Context(0)
+    monkeypatch.delenv("NPBS_APPLY_PATH")
+    for v in range(variants):
+        monkeypatch.setenv("NPBS_FAST_VARIANT", f"{side}:{v}")
+        cv = capi.Context(0)
+        for mode in ["RESIDUAL", "CBS_STEP", "OP_B", "ADJ_B", "TRUE_RESIDUAL", "PREC_SWEEP"]:
+            o1, o2 = torch.zeros_like(x), torch.zeros_like(x)
+            n1 = torch.zeros(b.count, dtype=torch.float64, device="cuda")
+            n2 = torch.zeros(b.count, dtype=torch.float64, device="cuda")
+            capi.cbs_apply(cv, b, V, f, x, o1, getattr(capi, mode), n1)
+            capi.cbs_apply(c3, b, V, f, x, o2, getattr(capi, mode), n2)
+            torch.cuda.synchronize()
+            A, B = b.unpack(o1), b.unpack(o2)
+            for j in range(2):
+                assert rel_l2(A[j], B[j]) <= 2e-6, (side, v, mode)
+            assert np.allclose(n1.cpu().numpy(), n2.cpu().numpy(), rtol=1e-5), (side, v, mode)
+
+
+def test_autotuner_picks_a_valid_band_variant():
+    capi, c = ctx()
+    insts = [synth.small_instance(1024, 1024, seed=270 + j, layer=64) for j in range(2)]
+    b, k2, f, n, V = setup_batch(capi, c, insts)
+    x = torch.zeros(b.extent, dtype=torch.complex64, device="cuda")
+    tuned = capi.npbs_autotune_apply(c, b, V, f, x, reps=2)
+    assert set(tuned) == {1024} and 0 <= tuned[1024] < BAND_VARIANTS[1024]
 
 
 def test_autotuner_picks_a_valid_variant():
@@ -227,20 +275,21 @@ def test_prefetch_variants_identical_on_batches_beyond_residency(side, monkeypat
             assert torch.allclose(n1, n2, rtol=1e-12, atol=0), (side, v)
 
 
-@pytest.mark.parametrize("side,count", [(96, 3), (128, 3), (128, 10), (192, 3), (256, 3), (384, 3), (512, 3)])
+@pytest.mark.parametrize("side,count", [(96, 3), (128, 3), (128, 10), (192, 3), (256, 3), (384, 3), (512, 3),
+                                        (1024, 2)])
 def test_fused_steps_bit_identical_to_repeated_applies(side, count, monkeypatch):
     """cbs_steps(K) is K in-place CBS_STEP (or PREC_SWEEP) applies, fused into
     one launch per grid side for small groups (3 instances) and one launch per
     step for groups above the fused count (10 > 8): every compiled variant
     gives exactly the output of K separate cbs_apply calls (96^2 takes the
-    three-launch path)."""
+    generic three-launch path, 1024^2 the band kernels, three launches a step)."""
     capi, c0 = ctx()
     insts = [synth.small_instance(side, side, seed=600 + j, layer=side // 16) for j in range(count)]
     b, k2, f, n, V = setup_batch(capi, c0, insts)
     x0 = b.pack([random_field((side, side), 610 + j) for j in range(count)])
     K = 5
-    for v in range(2 * KERNEL_VARIANTS.get(side, 0) or 1):
-        if side in KERNEL_VARIANTS:
+    for v in range(selectable_variants(side) or 1):
+        if selectable_variants(side):
             monkeypatch.setenv("NPBS_FAST_VARIANT", f"{side}:{v}")
         cv = capi.Context(0)
         for mode in ("CBS_STEP", "PREC_SWEEP"):
@@ -270,13 +319,14 @@ def test_zero_fused_steps_is_a_noop(env):
 @pytest.mark.parametrize("mode", ["RESIDUAL", "CBS_STEP", "ADJ_B", "TRUE_RESIDUAL"])
 def test_apply_parity_with_grid_spacing(mode):
     """h != 1 (xi = 2 pi n / (N h), App. Pseudospectral): every instance of a
-    batch carries its own h, on cluster (128^2, 192^2) and three-launch
-    (96 x 48) grids; a dropped or misplaced 1/h fails this."""
+    batch carries its own h, on cluster (128^2, 192^2), band (1024^2) and
+    three-launch (96 x 48) grids; a dropped or misplaced 1/h fails this."""
     import dataclasses
     capi, c = ctx()
     base = [synth.small_instance(128, 128, seed=60, layer=8), synth.small_instance(192, 192, seed=61, layer=12),
-            synth.small_instance(96, 48, seed=62, layer=6), synth.small_instance(128, 128, seed=63, layer=8)]
-    hs = [0.5, 2.5, 0.5, 1.7]
+            synth.small_instance(96, 48, seed=62, layer=6), synth.small_instance(128, 128, seed=63, layer=8),
+            synth.small_instance(1024, 1024, seed=64, layer=64)]
+    hs = [0.5, 2.5, 0.5, 1.7, 0.8]
     insts = [dataclasses.replace(i, h=h) for i, h in zip(base, hs)]
     b, k2, f, n, V = setup_batch(capi, c, insts)
     xs = [random_field((i.ny, i.nx), 70 + j) for j, i in enumerate(insts)]
