@@ -37,9 +37,10 @@ UNIT = "ms/solve"
 TOL = 1e-5
 B_PER_PT = 32  # algorithmic bytes per point of one CBS apply: read u, f, V, write u (complex64)
 # DRAM bytes per point of the cluster apply (dram__bytes_read + dram__bytes_write) from one ncu
-# capture of a 64 x 256^2 CBS_STEP launch: 106.18 MB + 17.81 MB over 4,194,304 points.  Scaled
-# to the bench batch by its point count; set to None whenever the apply kernel changes.
-TRAFFIC_B_PER_PT = (106.18e6 + 17.81e6) / 4194304
+# capture of a 64 x 256^2 CBS_STEP launch, scaled to the bench batch by its point count; None
+# whenever the apply kernel has changed since the capture.  The last capture (106.18 MB + 17.81 MB
+# over 4,194,304 points) predates the float32 per-thread norm accumulator, so none is reported.
+TRAFFIC_B_PER_PT = None
 
 
 def peaks():
@@ -373,6 +374,8 @@ def main():
     ap.add_argument("--fgmres-count", type=int, default=8)
     ap.add_argument("--fgmres-max-iter", type=int, default=400)
     ap.add_argument("--no-learned", action="store_true", help="skip the network / NPBS / FGMRES sections")
+    ap.add_argument("--fgmres-only", action="store_true",
+                    help="only FGMRES(20) with 16 CBS sweeps on the layered 1024^2 media (--fgmres-count, --fgmres-max-iter)")
     ap.add_argument("--train-step-only", action="store_true",
                     help="time only npbs_train_step (batch --train-batch at 256^2, 4 unrolls) for profiler captures")
     ap.add_argument("--train-batch", type=int, default=32)
@@ -398,6 +401,21 @@ def main():
         fl = 4 * 4 * unet_forward_flops(256, 256) * args.train_batch
         print(json.dumps({"train_step_only": args.train_batch, "ms": ms, "tflops": fl / (ms * 1e-3) / 1e12,
                           "conv_launches": capi.npbs_conv_stats()}), flush=True)
+        return 0
+    if args.fgmres_only:
+        from paper_2603_18527_gb300 import build, capi
+        build.build()
+        ctx = capi.Context(0)
+        insts = synth.workload_layered(args.fgmres_count, 1024)
+        b = capi.Batch([(i.ny, i.nx) for i in insts], h=[i.h for i in insts])
+        k2 = b.pack([i.k2 for i in insts])
+        f = b.pack([i.f for i in insts])
+        n = torch.zeros(b.extent, dtype=torch.float32, device="cuda")  # unused by the CBS preconditioner
+        V = torch.zeros_like(k2)
+        capi.npbs_build_potential(ctx, b, k2, V)
+        res = fgmres_case(capi, ctx, None, b, k2, f, n, [("cbs16", 1)], args.fgmres_max_iter)
+        print(json.dumps({"fgmres_only": f"layered media, {len(insts)} x 1024^2, restart 20, 16 CBS sweeps, "
+                                         f"tol {TOL}, cap {args.fgmres_max_iter}", **res}), flush=True)
         return 0
     if args.net_forward_only:
         from paper_2603_18527_gb300 import build, capi
@@ -548,7 +566,8 @@ def main():
                 "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
                              "traffic": None if TRAFFIC_B_PER_PT is None else TRAFFIC_B_PER_PT * pts,
                              "traffic_note": "bytes per apply, ncu dram read+write of a 64x256^2 launch scaled "
-                                             "by points", "kernel": "cbs_apply CBS_STEP (one cluster launch per grid side)",
+                                             "by points; null when the kernel changed since the capture",
+                             "kernel": "cbs_apply CBS_STEP (one cluster launch per grid side)",
                              "apply_ms": apply_ms, "peak_kind": kind, "autotuned_variants": tuned,
                              "cufft_same_step_ms": lib_ms},
                 "cpu_baseline": cpu,

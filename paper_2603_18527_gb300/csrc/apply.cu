@@ -160,6 +160,7 @@ __global__ void __launch_bounds__(kThreads) k_rows_inverse(BatchDev bd, ApplyArg
     const R scale = R(1) / (R(in.nx) * R(in.ny));
     const R ie = R(1) / R(in.eps);
     double acc = 0.0, acc2 = 0.0;
+    float accf = 0.f;  // float32 modes: this thread's share in float32, float64 across threads
     for (int e = threadIdx.x; e < n; e += blockDim.x) {
         const long long g = base + e;
         const C zz = z[e];
@@ -222,9 +223,10 @@ __global__ void __launch_bounds__(kThreads) k_rows_inverse(BatchDev bd, ApplyArg
                 o = make_float2(x.x + gr * rr - gi * ri, x.y + gr * ri + gi * rr);
             }
             a.out[g] = o;
-            acc += (double)(rr * rr + ri * ri);
+            accf = fmaf(rr, rr, fmaf(ri, ri, accf));
         }
     }
+    acc += (double)accf;
     if (a.norm2 || a.norm2b) {
         const double s = block_sum(acc, red);
         double s2 = 0.0;

@@ -240,7 +240,7 @@ __global__ void __launch_bounds__(T, MINB) k_band_rows_inv(FastDev fd, BatchDev 
     static_assert(N1 % EC == 0, "whole chunks");
     const float scale = 1.f / ((float)N * (float)N);
     const float ie = (float)(1.0 / in.eps);
-    double acc = 0.0;
+    float acc = 0.f;  // this thread's share of the norm (float64 across threads)
     for (int j = tid; j < RB * N2; j += T) {
         const int n2 = j % N2, r = j / N2;
         float2 v[N1];
@@ -299,13 +299,14 @@ __global__ void __launch_bounds__(T, MINB) k_band_rows_inv(FastDev fd, BatchDev 
                     o = make_float2(x.x + gr * rr - gi * ri, x.y + gr * ri + gi * rr);
                 }
                 a.out[g] = o;
-                acc += (double)(rr * rr + ri * ri);
+                acc = fmaf(rr, rr, fmaf(ri, ri, acc));
             }
         }
     }
     if (a.norm2) {
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if ((tid & 31) == 0) red[tid >> 5] = acc;
+        double accd = acc;
+        for (int o = 16; o > 0; o >>= 1) accd += __shfl_xor_sync(0xffffffffu, accd, o);
+        if ((tid & 31) == 0) red[tid >> 5] = accd;
         __syncthreads();
         if (tid == 0) {
             double t = 0.0;

@@ -284,7 +284,10 @@ __device__ __forceinline__ double cluster_step(const InstDev& in, const BatchDev
     // ---------------- P7: row inverse pass B and the epilogue
     const float scale = 1.f / ((float)N * (float)N);
     const float ie = (float)(1.0 / in.eps);
-    double acc = 0.0;
+    // this thread's share of the norm in float32 (a few dozen points); the
+    // block and instance sums are float64 (per-point float64 work would load
+    // the FP64 pipe, a small fraction of the FP32 rate on GB300)
+    float acc = 0.f;
 #pragma unroll
     for (int s = 0; s < J1; ++s) {
         const int j = tid + s * T;
@@ -345,12 +348,12 @@ __device__ __forceinline__ double cluster_step(const InstDev& in, const BatchDev
                     o = make_float2(x.x + gr * rr - gi * ri, x.y + gr * ri + gi * rr);
                 }
                 a.out[g] = o;
-                if (last) acc += (double)(rr * rr + ri * ri);
+                if (last) acc = fmaf(rr, rr, fmaf(ri, ri, acc));
             }
         }
     }
     NPBS_PHASE_MARK(7);
-    return acc;
+    return (double)acc;
 }
 
 // The same step compiled as a separate function: the fused multi-step loop

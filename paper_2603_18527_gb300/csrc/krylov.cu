@@ -31,6 +31,10 @@ __device__ __forceinline__ double warp_sum(double v) {
 }
 
 // h[inst][i] += <V_i, w> for i < nv (V_i rows of length `stride` elements).
+// Each thread sums its (at most kVecChunk / blockDim) products in float32 and
+// the block and instance sums are float64: float64 arithmetic per element would
+// bound the kernel by the FP64 pipe, whose rate on GB300 is a small fraction
+// of the FP32 rate (the vectors themselves are float32).
 __global__ void k_dots(const VecItem* items, const InstDev* inst, const int* active, const float2* __restrict__ Vb,
                        long long stride, int nv, const float2* __restrict__ w, double2* h, int ldh) {
     const VecItem it = items[blockIdx.x];
@@ -39,14 +43,14 @@ __global__ void k_dots(const VecItem* items, const InstDev* inst, const int* act
     __shared__ double red[2][kVecThreads / 32];
     for (int i = 0; i < nv; ++i) {
         const float2* v = Vb + (long long)i * stride + base;
-        double sr = 0.0, si = 0.0;
+        float pr = 0.f, pi = 0.f;
         for (int e = threadIdx.x; e < it.len; e += blockDim.x) {
             const float2 a = v[e], b = w[base + e];
-            sr += (double)a.x * b.x + (double)a.y * b.y;   // conj(a) b
-            si += (double)a.x * b.y - (double)a.y * b.x;
+            pr = fmaf(a.x, b.x, fmaf(a.y, b.y, pr));   // conj(a) b
+            pi = fmaf(a.x, b.y, fmaf(-a.y, b.x, pi));
         }
-        sr = warp_sum(sr);
-        si = warp_sum(si);
+        const double sr = warp_sum((double)pr);
+        const double si = warp_sum((double)pi);
         const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
         if (lane == 0) { red[0][wp] = sr; red[1][wp] = si; }
         __syncthreads();
@@ -60,7 +64,8 @@ __global__ void k_dots(const VecItem* items, const InstDev* inst, const int* act
     }
 }
 
-// w -= sum_i c[inst][i] V_i; optionally norm2[inst] += ||w||^2 of the result.
+// w -= sum_i c[inst][i] V_i; optionally norm2[inst] += ||w||^2 of the result
+// (per-thread float32 partial sums, float64 across threads, as in k_dots).
 __global__ void k_update(const VecItem* items, const InstDev* inst, const int* active, const float2* __restrict__ Vb,
                          long long stride, int nv, float2* w, const double2* c, int ldc, double* norm2,
                          const int* nv_inst) {
@@ -74,7 +79,7 @@ __global__ void k_update(const VecItem* items, const InstDev* inst, const int* a
         cs[i] = make_float2((float)t.x, (float)t.y);
     }
     __syncthreads();
-    double acc = 0.0;
+    float accf = 0.f;
     for (int e = threadIdx.x; e < it.len; e += blockDim.x) {
         float2 x = w[base + e];
         for (int i = 0; i < nv; ++i) {
@@ -84,11 +89,11 @@ __global__ void k_update(const VecItem* items, const InstDev* inst, const int* a
             x.y -= a.x * v.y + a.y * v.x;
         }
         w[base + e] = x;
-        acc += (double)x.x * x.x + (double)x.y * x.y;
+        accf = fmaf(x.x, x.x, fmaf(x.y, x.y, accf));
     }
     if (norm2) {
         __shared__ double red[kVecThreads / 32];
-        acc = warp_sum(acc);
+        const double acc = warp_sum((double)accf);
         if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
         __syncthreads();
         if (threadIdx.x == 0) {
