@@ -265,6 +265,29 @@ def test_fgmres_full_restart_is_exact_in_n_steps():
     assert _rel(_vec(res.u), ustar) < 1e-9
 
 
+@pytest.mark.parametrize("k", [1, 3, 6])
+def test_fgmres_iterate_minimises_the_residual_over_the_krylov_space(tiny, k):
+    """k unpreconditioned FGMRES steps from u = 0 inside one cycle give the
+    element of K_k(B, b) = span{b, B b, ..., B^(k-1) b}, b = G f, with the least
+    ||b - B u||_2 (the defining property of GMRES, Saad 1993), found here by
+    least squares with the dense B: a dropped Givens term, a wrong conjugate or
+    a misplaced Hessenberg entry moves the iterate off the minimiser."""
+    inst, p, ops = tiny
+    B = ops["B"]
+    b = ops["G"] @ inst.f.reshape(-1)
+    cols = [b]
+    for _ in range(k - 1):
+        cols.append(B @ cols[-1])
+    Q, _ = np.linalg.qr(np.stack(cols, axis=1))  # orthonormal basis of the same space
+    c, *_ = np.linalg.lstsq(B @ Q, b, rcond=None)
+    u_ls = Q @ c
+    res = FG.fgmres_solve(p, None, restart=20, tol=1e-14, max_iter=k)
+    assert res.iters == k
+    assert _rel(_vec(res.u), u_ls) < 1e-8
+    # and the residual can only fall from one k to the next
+    assert np.linalg.norm(b - B @ _vec(res.u)) <= np.linalg.norm(b) * (1 + 1e-12)
+
+
 def test_free_space_green_function_trend():
     """Physics sanity, not parity: with an absorbing layer the field of a point
     source in a homogeneous medium approaches (i/4) H0^(1)(k r) in an annulus,
