@@ -34,18 +34,25 @@ def tiny():
     return inst, p, ops
 
 
-def test_plane_wave_symbols():
+def _modes(N):
+    """-N/2 .. N/2 - 1 for even N (App. Pseudospectral); for odd N (sides 3^b)
+    the symmetric -(N-1)/2 .. (N-1)/2, the one band-limited choice."""
+    return range(-N // 2, N // 2) if N % 2 == 0 else range(-(N - 1) // 2, (N + 1) // 2)
+
+
+@pytest.mark.parametrize("ny,nx,h", [(6, 10, 0.7), (9, 6, 1.3)])
+def test_plane_wave_symbols(ny, nx, h):
     """G and A act on e^{i xi.x} as 1/lambda and |xi|^2 - k^2 (App. Transform-
     diagonalizable, Helmholtz case), with xi = 2 pi n/(N h) and n taken in
     -N/2..N/2-1, for every mode including the Nyquist ones; h != 1 and
-    nx != ny exercise the scaling and orientation."""
-    ny, nx, h = 6, 10, 0.7
+    nx != ny exercise the scaling and orientation, an odd side (9) the
+    symmetric mode range of odd lengths."""
     k0sq, eps, k2c = 1.3, 0.45, 1.1 + 0.2j
     lam = H.symbol(ny, nx, h, k0sq, eps)
     y = torch.arange(ny, dtype=torch.float64)[:, None] * h
     x = torch.arange(nx, dtype=torch.float64)[None, :] * h
-    for my in range(-ny // 2, ny // 2):
-        for mx in range(-nx // 2, nx // 2):
+    for my in _modes(ny):
+        for mx in _modes(nx):
             xy = 2 * math.pi * my / (ny * h)
             xx = 2 * math.pi * mx / (nx * h)
             u = torch.exp(1j * (xy * y + xx * x))
@@ -263,6 +270,21 @@ def test_fgmres_full_restart_is_exact_in_n_steps():
     A = D.neg_laplacian(4, 6) - np.diag(inst.k2.reshape(-1))
     ustar = np.linalg.solve(A, inst.f.reshape(-1))
     assert _rel(_vec(res.u), ustar) < 1e-9
+
+
+def test_prec_sweep_is_richardson_on_B_and_the_cbs_step_for_v_equal_G_f(tiny):
+    """The FGMRES CBS preconditioner sweep z + gamma (v - B z) against the dense
+    B and gamma, and for v = G f it is Eq. (CBS) itself (G(V z + f) - z =
+    G f - B z), through a different code path (the Born residual)."""
+    inst, p, ops = tiny
+    rng = np.random.default_rng(11)
+    shape = inst.k2.shape
+    z = torch.from_numpy(rng.standard_normal(shape) + 1j * rng.standard_normal(shape))
+    v = torch.from_numpy(rng.standard_normal(shape) + 1j * rng.standard_normal(shape))
+    ref = _vec(z) + ops["gamma"] @ (_vec(v) - ops["B"] @ _vec(z))
+    assert _rel(_vec(H.prec_cbs_sweep(p, z, v)), ref) < 1e-12
+    Gf = H.green(p.f, p.lam)
+    assert _rel(_vec(H.prec_cbs_sweep(p, z, Gf)), _vec(H.cbs_step(p, z))) < 1e-12
 
 
 @pytest.mark.parametrize("k", [1, 3, 6])

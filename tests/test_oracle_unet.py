@@ -60,6 +60,55 @@ def test_pool_up_and_gelu_definitions():
     assert torch.allclose(Fnn.gelu(t), ref, atol=1e-15)
 
 
+def test_oracle_conv_applies_the_erf_gelu():
+    """The oracle's conv + activation with a centre-tap identity kernel is the
+    erf-form GELU x Phi(x) (the tanh approximation differs by up to ~1e-3)."""
+    t = torch.linspace(-3.0, 3.0, 25, dtype=torch.float64).reshape(1, 1, 5, 5)
+    w = torch.zeros(1, 1, 3, 3, dtype=torch.float64)
+    w[0, 0, 1, 1] = 1.0
+    got = U._conv_gelu(t, {"c.w": w, "c.b": torch.zeros(1, dtype=torch.float64)}, "c")
+    ref = torch.tensor([v * 0.5 * (1 + math.erf(v / math.sqrt(2))) for v in t.reshape(-1).tolist()],
+                       dtype=torch.float64).reshape(t.shape)
+    assert torch.allclose(got, ref, atol=1e-15, rtol=0)
+
+
+def test_decoder_concatenates_skip_then_up():
+    """Channel order of the decoder input (the reading: [skip, up]): with the
+    up-branch convolution zeroed its GELU output is exactly 0, so the weights
+    that dec<l>a applies to channels [C, 2C) cannot change the output, while
+    those on [0, C) (the skip) do."""
+    _, P = _params(7)
+    rng = np.random.default_rng(4)
+    x = torch.from_numpy(rng.standard_normal((1, 3, 16, 16)))
+    for lvl, C in [(2, 128), (0, 32)]:
+        Q = {k: v.clone() for k, v in P.items()}
+        Q[f"up{lvl}.w"].zero_()
+        Q[f"up{lvl}.b"].zero_()
+        y0 = U.network(x, Q)
+        Q1 = {k: v.clone() for k, v in Q.items()}
+        Q1[f"dec{lvl}a.w"][:, C:] += 0.5
+        assert torch.equal(U.network(x, Q1), y0), lvl
+        Q2 = {k: v.clone() for k, v in Q.items()}
+        Q2[f"dec{lvl}a.w"][:, :C] += 0.5
+        assert not torch.allclose(U.network(x, Q2), y0), lvl
+
+
+def test_output_channels_are_real_then_imaginary():
+    """Head channel 0 is Re c and channel 1 is Im c: zeroing one head row
+    makes the correction purely imaginary or purely real."""
+    _, P = _params(8)
+    rng = np.random.default_rng(6)
+    r = torch.from_numpy(rng.standard_normal((1, 16, 16)) + 1j * rng.standard_normal((1, 16, 16)))
+    n = torch.from_numpy(1 + 0.1 * rng.standard_normal((1, 16, 16)))
+    for row, part in [(1, "imag"), (0, "real")]:
+        Q = {k: v.clone() for k, v in P.items()}
+        Q["out.w"][row].zero_()
+        c = U.correction(r, n, Q)
+        assert float(getattr(c, part).abs().max()) == 0.0
+        other = "real" if part == "imag" else "imag"
+        assert float(getattr(c, other).abs().max()) > 0.0
+
+
 def test_scale_wrapper_positive_homogeneity():
     _, P = _params(1)
     rng = np.random.default_rng(3)
@@ -155,6 +204,37 @@ def test_loss_kinds_vanish_for_the_exact_inverse_of_their_format():
                 Mo = inv[other]
                 Mx = lambda x, Mo=Mo: torch.from_numpy((Mo @ x[0].numpy().reshape(-1)).reshape(1, 8, 12))
                 assert float(U.unrolled_loss_kind(Mx, kind, V, lam, k2, xi2, f, u0, unroll=2)) > 1e-6
+
+
+@pytest.mark.parametrize("kind", U.LOSS_KINDS)
+def test_loss_kinds_match_dense_one_and_two_step_formulas(kind):
+    """Each objective of Sec. 4 for the network M = alpha I, from dense A and G
+    (DFT definition): t_{k+1} = t_k - A alpha P_in t_k, loss = mean over k of
+    ||P_out t_{k+1}||^2 / ||P_out t_0||^2 with (P_in, P_out) = (I, I) for
+    Eq. L_dir, (G, I) for Eq. L_bs_l2 and (G, G) for Eq. L_bs_Reta_integral;
+    a swapped projection fails it."""
+    from oracle import dense as D
+    inst = synth.small_instance(8, 12, seed=3, layer=2, ppw=5.0)
+    p = H.problem_from_instance(inst)
+    ops = D.operators(inst.k2, 1.0, p.k0sq, p.eps)
+    V, lam, f, n = U.problems_to_batch([p])
+    k2 = p.k2[None]
+    xi2 = H.xi_squared(8, 12, 1.0).to(torch.complex128)
+    u0 = H.cbs_solve(p, tol=0, max_iter=3).u[None]
+    A, G = ops["A"], ops["G"]
+    I = np.eye(A.shape[0])
+    Pin = I if kind == "dir" else G
+    Pout = G if kind == "bs_reta" else I
+    alpha = 0.37 - 0.21j
+    t = inst.f.reshape(-1) - A @ u0[0].numpy().reshape(-1)
+    t0n = np.linalg.norm(Pout @ t) ** 2
+    for unroll in (1, 2):
+        tk, acc = t.copy(), 0.0
+        for _ in range(unroll):
+            tk = tk - A @ (alpha * (Pin @ tk))
+            acc += np.linalg.norm(Pout @ tk) ** 2 / t0n
+        L = float(U.unrolled_loss_kind(lambda x: alpha * x, kind, V, lam, k2, xi2, f, u0, unroll=unroll))
+        assert L == pytest.approx(acc / unroll, rel=1e-10), (kind, unroll)
 
 
 def test_reta_kind_in_true_residual_coordinates_equals_born_state_loss():
