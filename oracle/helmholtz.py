@@ -92,11 +92,6 @@ def apply_A(u: torch.Tensor, k2: torch.Tensor, h: float = 1.0) -> torch.Tensor:
     return laplacian_neg(u, h) - k2 * u
 
 
-def apply_L_eta(u: torch.Tensor, lam: torch.Tensor) -> torch.Tensor:
-    """L_eta u = F^{-1}(lambda F u)."""
-    return torch.fft.ifft2(lam * torch.fft.fft2(u))
-
-
 @dataclasses.dataclass
 class Problem:
     """A discretised Helmholtz instance with the method's derived quantities."""

@@ -57,6 +57,9 @@ M = [
  ("unet.py", "batched B order", "return x - torch.fft.ifft2(torch.fft.fft2(V * x) / lam)", "return x - V * torch.fft.ifft2(torch.fft.fft2(x) / lam)"),
  ("unet.py", "unrolled loss r update sign", "r = r - batched_op_B(V, lam, c)", "r = r + batched_op_B(V, lam, c)"),
  ("unet.py", "dir P_in G", 'proj_in = (lambda v: v) if kind == "dir" else (lambda v: batched_green(lam, v))', 'proj_in = (lambda v: batched_green(lam, v))'),
+ ("helmholtz.py", "true residual sign", "return p.f - apply_A(u, p.k2, p.h)", "return apply_A(u, p.k2, p.h) - p.f"),
+ ("unet.py", "adam eps inside sqrt", "theta = theta - lr * mhat / (torch.sqrt(vhat) + eps)", "theta = theta - lr * mhat / torch.sqrt(vhat + eps)"),
+ ("unet.py", "pool after the level's convs", "        if lvl > 0:\n            h = _pool(h)\n        h = _conv_gelu(h, P, f\"enc{lvl}a\")", "        h = _conv_gelu(h, P, f\"enc{lvl}a\")\n        if lvl > 0:\n            h = _pool(h)"),
  ("fgmres.py", "rotation without conj", "Hm[i, j] = cs[i].conj() * a + sn[i].conj() * c", "Hm[i, j] = cs[i] * a + sn[i].conj() * c"),
  ("fgmres.py", "sign of g", "g[j + 1] = -sn[j] * gj", "g[j + 1] = sn[j] * gj"),
  ("fgmres.py", "dot operands swapped", "hij = _dot(Vb[i], w)", "hij = _dot(w, Vb[i])"),

@@ -60,6 +60,27 @@ def test_pool_up_and_gelu_definitions():
     assert torch.allclose(Fnn.gelu(t), ref, atol=1e-15)
 
 
+def test_each_convolution_runs_at_its_level_resolution(monkeypatch):
+    """U-Net layout (pool, then the level's two convolutions; upsample, then
+    the up convolution): every convolution named for level l sees an input of
+    (H / 2^l) x (W / 2^l), recorded at the library conv2d call itself."""
+    _, P = _params(9)
+    seen = {}
+    conv = U.Fnn.conv2d
+
+    def spy(x, w, *a, **k):
+        seen[id(w)] = tuple(x.shape[-2:])
+        return conv(x, w, *a, **k)
+
+    monkeypatch.setattr(U.Fnn, "conv2d", spy)
+    H_, W_ = 32, 48
+    U.network(torch.zeros(1, 3, H_, W_, dtype=torch.float64), P)
+    for name, _, _ in U.CONVS:
+        lvl = int(name[-2] if name[-1] in "ab" else name[-1])
+        assert seen[id(P[name + ".w"])] == (H_ >> lvl, W_ >> lvl), name
+    assert seen[id(P["out.w"])] == (H_, W_)
+
+
 def test_oracle_conv_applies_the_erf_gelu():
     """The oracle's conv + activation with a centre-tap identity kernel is the
     erf-form GELU x Phi(x) (the tanh approximation differs by up to ~1e-3)."""
@@ -274,11 +295,13 @@ def test_loss_kind_gradient_matches_central_fd(kind):
 def test_adamw_first_step_closed_form():
     """At step 1, mhat = g and vhat = g^2, so the update is
     -lr * g / (|g| + eps) after decay by (1 - lr wd)."""
-    th = torch.tensor([1.0, -2.0, 0.5], dtype=torch.float64)
-    g = torch.tensor([0.3, -0.01, 0.0], dtype=torch.float64)
+    # the last gradient is tiny against sqrt(eps): eps added outside the root
+    # (Adam's form) and inside it differ by a factor of ~10 there
+    th = torch.tensor([1.0, -2.0, 0.5, 0.25], dtype=torch.float64)
+    g = torch.tensor([0.3, -0.01, 0.0, 1e-6], dtype=torch.float64)
     lr, wd, eps = 1e-3, 1e-2, 1e-8
-    new, m, v = U.adamw_step(th, g, torch.zeros(3, dtype=torch.float64), torch.zeros(3, dtype=torch.float64),
-                             1, lr=lr, weight_decay=wd, eps=eps)
+    z = torch.zeros(4, dtype=torch.float64)
+    new, m, v = U.adamw_step(th, g, z, z.clone(), 1, lr=lr, weight_decay=wd, eps=eps)
     expect = th * (1 - lr * wd) - lr * g / (g.abs() + eps)
-    assert torch.allclose(new, expect, atol=1e-15)
+    assert torch.allclose(new, expect, atol=1e-15, rtol=0)
     assert torch.allclose(m, 0.1 * g) and torch.allclose(v, 0.001 * g * g)
