@@ -79,3 +79,21 @@ def test_bench_rejects_the_layered_workload_outside_apply_only():
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--workload", "layered1024"],
                        capture_output=True, text=True, timeout=300)
     assert r.returncode == 2 and "apply-only" in r.stderr
+
+
+def test_reference_arm_prints_one_contract_line():
+    """`bench.py --impl reference` times the CPU oracle on a bounded sample of
+    the bench workload and prints one JSON line with the contract's keys."""
+    import json
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                        "--warmup", "1"], capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for k in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+              "config", "cpu_baseline", "e2e"):
+        assert k in d, k
+    assert d["impl"] == "reference" and d["higher_is_better"] is False and d["value"] > 0
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
