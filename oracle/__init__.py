@@ -23,6 +23,12 @@ each function can be read against the paper's equations:
 * ``dense``: explicit dense matrices of the same operators for tiny grids,
   built from the DFT definition (no FFT), used only to pin the above.
 
+Pins (``tests/test_oracle_pins.py``, ``tests/test_oracle_unet.py``) tie each
+function to something other than itself: dense matrices from the DFT
+definition, closed forms, algebraic identities, brute force and central finite
+differences.  ``tests/oracle_mutation_check.py`` plants plausible mistakes in a
+copy of this package one at a time and requires each to fail a pin.
+
 Parity unpinned: nothing here depends on the paper's trained weights or on
 OpenFWI; the trained network's iteration counts are reported, not pinned.
 """
