@@ -8,8 +8,17 @@
 // the pool), and latency-sensitive code that must not pay for cudaMalloc /
 // cudaFree, which can synchronise the whole device.  This entry point runs the
 // same kernels with the scratch and the plan in file-scope static device
-// arrays of fixed size that the library reserves when it is loaded; every GPU
-// that loads the library holds them (about 8.3 MiB) until the process exits.
+// arrays of fixed size (about 8.3 MiB).  The CUDA runtime places them on a
+// device when the library's module is loaded there: under lazy module loading
+// (the default) that happens in the first call on the device, which therefore
+// must come before the caller's own pool takes the device's memory (or the
+// process runs with CUDA_MODULE_LOADING=EAGER).  From then on the device holds
+// them until the process exits.
+//
+// The plan (instance table, radix plans, twiddles, row / column work items)
+// is written on the device by a small set-up kernel from its launch
+// parameters, in stream order before the apply kernels; no host buffer is
+// read after the call returns.
 //
 // Limits: at most kStaticMaxPoints elements of batch extent (max offset + nx*ny),
 // kStaticMaxInstances instances, kStaticMaxSizes distinct transform lengths
@@ -64,13 +73,18 @@ npbs_status setup_current_device(int dev, char* err, int errlen) {
     void* p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
     if (e != cudaSuccess) {
-        if (err && errlen > 0) snprintf(err, errlen, "cudaGetSymbolAddress(scratch): %s", cudaGetErrorString(e));
+        if (err && errlen > 0)
+            snprintf(err, errlen,
+                     "loading the static scratch on device %d failed (%s): the first call on a device must come "
+                     "before other allocators take its memory",
+                     dev, cudaGetErrorString(e));
         return NPBS_ERR_CUDA;
     }
     s.scratch = static_cast<float2*>(p);
     e = cudaGetSymbolAddress(&p, g_static_plan);
     if (e != cudaSuccess) {
-        if (err && errlen > 0) snprintf(err, errlen, "cudaGetSymbolAddress(plan): %s", cudaGetErrorString(e));
+        if (err && errlen > 0)
+            snprintf(err, errlen, "loading the static plan on device %d failed (%s)", dev, cudaGetErrorString(e));
         return NPBS_ERR_CUDA;
     }
     s.plan = static_cast<StaticPlan*>(p);
@@ -88,7 +102,19 @@ npbs_status fail(char* err, int errlen, npbs_status st, const char* msg) {
     return st;
 }
 
-bool radix_plan_of(int n, RadixPlan* p) {
+// Everything the set-up kernel needs, passed by value as its launch parameter
+// (about 4.5 KB): the instance table with each instance's first row and
+// column work item, and the distinct transform lengths.
+struct StaticParams {
+    InstDev inst[kStaticMaxInstances];
+    int row0[kStaticMaxInstances + 1];  // first row item of instance j; row0[count] = number of row items
+    int col0[kStaticMaxInstances + 1];
+    int sizes[kStaticMaxSizes];
+    int count, nsizes;
+};
+
+// Radix schedule 8, 4, 2 then 3 (the same rule as the context's plans).
+__host__ __device__ inline bool radix_plan_of(int n, RadixPlan* p) {
     if (n < 2 || n > kMaxN) return false;
     p->n = n;
     p->npass = 0;
@@ -100,10 +126,49 @@ bool radix_plan_of(int n, RadixPlan* p) {
     return m == 1 && p->npass <= kMaxPass;
 }
 
-// Host-side staging of the plan (static storage, guarded by g_mutex; the
-// pageable copies below are staged by the driver before they return, so the
-// buffer may be reused by the next call at once).
-StaticPlan g_host_plan;
+// Rows per row item and columns per column item of an nx x ny instance (the
+// tiling of the three-launch apply).
+__host__ __device__ inline int rows_per_item(int nx, int ny) {
+    const int t = kTileElems<float>() / nx;
+    return t < 1 ? 1 : (t < ny ? t : ny);
+}
+__host__ __device__ inline int cols_per_item(int ny) {
+    const int t = kTileElems<float>() / ny;
+    return t < 1 ? 1 : (t < 16 ? t : 16);
+}
+
+// Writes the plan of one call into the static plan array.  Grid-stride over
+// the instance table, the twiddle tables and the work items.
+__global__ void k_static_plan(const __grid_constant__ StaticParams p, StaticPlan* dp) {
+    const int t0 = blockIdx.x * blockDim.x + threadIdx.x, nt = gridDim.x * blockDim.x;
+    for (int j = t0; j < p.count; j += nt) dp->inst[j] = p.inst[j];
+    for (int k = t0; k < p.nsizes; k += nt) radix_plan_of(p.sizes[k], &dp->plans[k]);
+    for (int e = t0; e < p.nsizes * kMaxN; e += nt) {
+        const int k = e / kMaxN, q = e - k * kMaxN, n = p.sizes[k];
+        if (q < n) {
+            double sn, cs;
+            sincospi(-2.0 * (double)q / (double)n, &sn, &cs);
+            dp->tw32[e] = make_float2((float)cs, (float)sn);
+        }
+    }
+    for (int i = t0; i < p.row0[p.count]; i += nt) {
+        int j = 0;
+        while (p.row0[j + 1] <= i) ++j;
+        const InstDev& d = p.inst[j];
+        const int rp = rows_per_item(d.nx, d.ny), r0 = (i - p.row0[j]) * rp;
+        dp->rows[i] = RowItem{j, r0, rp < d.ny - r0 ? rp : d.ny - r0, 0};
+    }
+    for (int i = t0; i < p.col0[p.count]; i += nt) {
+        int j = 0;
+        while (p.col0[j + 1] <= i) ++j;
+        const InstDev& d = p.inst[j];
+        const int cp = cols_per_item(d.ny), c0 = (i - p.col0[j]) * cp;
+        dp->cols[i] = ColItem{j, c0, cp < d.nx - c0 ? cp : d.nx - c0, 0};
+    }
+}
+
+// Parameter block of the call in progress (guarded by g_mutex).
+StaticParams g_params;
 
 }  // namespace
 }  // namespace npbs
@@ -129,13 +194,12 @@ extern "C" npbs_status cbs_apply_static(const npbs_batch* batch, const void* V, 
         return fail(err, errlen, NPBS_ERR_UNSUPPORTED_SIZE, m);
     }
 
-    // Plan on the host, in the staging copy (one call at a time on the host).
+    // Plan on the host into the parameter block (one call at a time on the host).
     std::lock_guard<std::mutex> lock(g_mutex);
-    StaticPlan& hp = g_host_plan;
-    int nsizes = 0, sizes[kStaticMaxSizes];
+    StaticParams& hp = g_params;
+    int nsizes = 0;
     int nrows = 0, ncols = 0;
     long long extent = 0;
-    constexpr int tile = kTileElems<float>();
     for (int j = 0; j < count; ++j) {
         const npbs_instance& s = batch->inst[j];
         if (!(s.h > 0.0) || !std::isfinite(s.h) || !std::isfinite(s.k0sq) || !(s.eps > 0.0) || !std::isfinite(s.eps) ||
@@ -146,18 +210,15 @@ extern "C" npbs_status cbs_apply_static(const npbs_batch* batch, const void* V, 
         const int dims[2] = {s.nx, s.ny};
         for (int d = 0; d < 2; ++d) {
             int k = 0;
-            while (k < nsizes && sizes[k] != dims[d]) ++k;
+            while (k < nsizes && hp.sizes[k] != dims[d]) ++k;
             if (k == nsizes) {
                 if (nsizes == kStaticMaxSizes)
                     return fail(err, errlen, NPBS_ERR_UNSUPPORTED_SIZE,
                                 "cbs_apply_static: more distinct grid sizes than the static limit of 8");
-                if (!radix_plan_of(dims[d], &hp.plans[k]))
+                RadixPlan rp;
+                if (!radix_plan_of(dims[d], &rp))
                     return fail(err, errlen, NPBS_ERR_UNSUPPORTED_SIZE, "grid side is not 2^a 3^b in [2, 1024]");
-                for (int q = 0; q < dims[d]; ++q) {
-                    const double a = -2.0 * M_PI * (double)q / (double)dims[d];
-                    hp.tw32[k * kMaxN + q] = make_float2((float)std::cos(a), (float)std::sin(a));
-                }
-                sizes[nsizes++] = dims[d];
+                hp.sizes[nsizes++] = dims[d];
             }
             idx[d] = k;
         }
@@ -180,19 +241,20 @@ extern "C" npbs_status cbs_apply_static(const npbs_batch* batch, const void* V, 
                      extent, kStaticMaxPoints);
             return fail(err, errlen, NPBS_ERR_UNSUPPORTED_SIZE, m);
         }
-        const int rp = std::max(1, std::min(s.ny, tile / s.nx));
-        for (int r0 = 0; r0 < s.ny; r0 += rp) {
-            if (nrows == kStaticMaxItems)
-                return fail(err, errlen, NPBS_ERR_UNSUPPORTED_SIZE, "cbs_apply_static: too many row work items");
-            hp.rows[nrows++] = RowItem{j, r0, std::min(rp, s.ny - r0), 0};
-        }
-        const int cp = std::max(1, std::min(16, tile / s.ny));
-        for (int c0 = 0; c0 < s.nx; c0 += cp) {
-            if (ncols == kStaticMaxItems)
-                return fail(err, errlen, NPBS_ERR_UNSUPPORTED_SIZE, "cbs_apply_static: too many column work items");
-            hp.cols[ncols++] = ColItem{j, c0, std::min(cp, s.nx - c0), 0};
-        }
+        const int rp = rows_per_item(s.nx, s.ny), cp = cols_per_item(s.ny);
+        hp.row0[j] = nrows;
+        hp.col0[j] = ncols;
+        nrows += (s.ny + rp - 1) / rp;
+        ncols += (s.nx + cp - 1) / cp;
+        if (nrows > kStaticMaxItems)
+            return fail(err, errlen, NPBS_ERR_UNSUPPORTED_SIZE, "cbs_apply_static: too many row work items");
+        if (ncols > kStaticMaxItems)
+            return fail(err, errlen, NPBS_ERR_UNSUPPORTED_SIZE, "cbs_apply_static: too many column work items");
     }
+    hp.row0[count] = nrows;
+    hp.col0[count] = ncols;
+    hp.count = count;
+    hp.nsizes = nsizes;
 
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
@@ -202,18 +264,14 @@ extern "C" npbs_status cbs_apply_static(const npbs_batch* batch, const void* V, 
     StaticPlan* dp = g_state[dev].plan;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
 
-    // Upload the used parts of the plan (pageable source: staged before return).
-    cudaError_t e = cudaMemcpyAsync(dp->inst, hp.inst, sizeof(InstDev) * count, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(dp->plans, hp.plans, sizeof(RadixPlan) * nsizes, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(dp->tw32, hp.tw32, sizeof(float2) * kMaxN * nsizes, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(dp->rows, hp.rows, sizeof(RowItem) * nrows, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(dp->cols, hp.cols, sizeof(ColItem) * ncols, cudaMemcpyHostToDevice, s);
+    // The plan is written on the device, in stream order, from the launch
+    // parameters (captured by value at launch).
+    k_static_plan<<<32, 256, 0, s>>>(hp, dp);
+    cudaError_t e = cudaGetLastError();
     // the reductions accumulate: norm2 must start at zero
     if (e == cudaSuccess && norm2) e = cudaMemsetAsync(norm2, 0, sizeof(double) * count, s);
     if (e != cudaSuccess) {
-        if (err && errlen > 0) snprintf(err, errlen, "plan upload: %s", cudaGetErrorString(e));
+        if (err && errlen > 0) snprintf(err, errlen, "plan set-up: %s", cudaGetErrorString(e));
         return NPBS_ERR_CUDA;
     }
     BatchDev bd;

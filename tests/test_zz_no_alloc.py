@@ -51,3 +51,27 @@ def test_static_apply_rejects_batches_beyond_its_scratch():
         capi.cbs_apply_static(b, t, t, t, t, capi.RESIDUAL)
     assert e.value.status == capi.ERR_UNSUPPORTED_SIZE
     assert "static scratch" in str(e.value)
+
+
+def test_static_apply_rejects_more_instances_than_its_plan_holds():
+    capi, c = ctx()
+    b = capi.Batch([(8, 8)] * 65, k0sq=[1.0] * 65, eps=[1.0] * 65)
+    t = torch.zeros(b.extent, dtype=torch.complex64, device="cuda")
+    with pytest.raises(capi.NpbsError) as e:
+        capi.cbs_apply_static(b, t, t, t, t, capi.RESIDUAL)
+    assert e.value.status == capi.ERR_UNSUPPORTED_SIZE
+    assert "65 instances exceed the static limit of 64" in str(e.value)
+
+
+def test_static_apply_rejects_more_distinct_grid_sides_than_its_plan_holds():
+    capi, c = ctx()
+    # nine distinct sides, each 2^a 3^b: the ninth exceeds the eight plan slots
+    shapes = [(2, 3), (4, 6), (8, 9), (12, 16), (18, 24), (27, 32)]
+    sides = {s for sh in shapes for s in sh}
+    assert len(sides) == 12
+    b = capi.Batch(shapes, k0sq=[1.0] * len(shapes), eps=[1.0] * len(shapes))
+    t = torch.zeros(b.extent, dtype=torch.complex64, device="cuda")
+    with pytest.raises(capi.NpbsError) as e:
+        capi.cbs_apply_static(b, t, t, t, t, capi.RESIDUAL)
+    assert e.value.status == capi.ERR_UNSUPPORTED_SIZE
+    assert "distinct grid sizes" in str(e.value)
