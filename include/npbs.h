@@ -153,16 +153,39 @@ void npbs_conv_stats(int64_t* tensor_core_launches, int64_t* warp_mma_launches);
 
 /* ---- problem set-up ----------------------------------------------------- */
 
-/* Reference constants and potential (Sec. 3.1; the paper leaves k0 and eta
- * free, this library takes k0^2 = (min Re k^2 + max Re k^2)/2 and
- * eps = max |k^2 - k0^2| over each instance's full grid).
+/* The medium, its absorbing layer and the potential (Sec. 3.1: the Helmholtz
+ * problem with k = omega n(x), truncated by an absorbing layer folded into the
+ * operator; App. Dataset Illustration: a padded grid around the interior).
+ * For every instance j:
+ *   k^2(x) = omega_j^2 n(x)^2 + i a omega_j^2 rho(x)^2,  a = ramp_amp_over_omega2,
+ *   rho = max(d_x, d_y) / W, W = layer_cells, d = depth in cells into the W-cell
+ *   layer along each side (1 .. W at the outermost cell, 0 inside; the larger
+ *   of the two in the corners),
+ * computed in float64 and stored as complex64 in k2_out; then the reference
+ * constants and potential as npbs_potential_from_k2.  The paper describes the
+ * layer only as a sponge / PML; this quadratic ramp up to a omega^2 is the
+ * library's reading.
+ * n: DEVICE float32 refractive index with the batch layout.  omega: HOST
+ * double[count], > 0.  layer_cells >= 0 (0: no layer), the same for every
+ * instance of the call (call once per layer width).  ramp_amp_over_omega2 >= 0.
+ * k2_out: DEVICE complex64 (nullable: then a context buffer holds k^2 for the
+ * call only); V_out: DEVICE complex64 (nullable); k0sq_out, eps_out: HOST
+ * double[count].  At most 65535 instances.  Synchronises the stream. */
+npbs_status npbs_build_potential(npbs_ctx* ctx, const npbs_batch* batch, const float* n,
+                                 const double* omega, int32_t layer_cells,
+                                 double ramp_amp_over_omega2, void* k2_out, void* V_out,
+                                 double* k0sq_out, double* eps_out, npbs_stream stream);
+
+/* Reference constants and potential from a given k^2 (Sec. 3.1; the paper
+ * leaves k0 and eta free, this library takes k0^2 = (min Re k^2 + max Re k^2)/2
+ * and eps = max |k^2 - k0^2| over each instance's full grid).
  * k2: DEVICE complex64 k(x)^2 (Im k^2 >= 0 carries the absorbing layer).
  * V_out: DEVICE complex64, receives V = k^2 - k0^2 - i eps (may be NULL).
  * k0sq_out, eps_out: HOST double[count].  The k0sq / eps fields of `batch`
  * are ignored.  Synchronises the stream. */
-npbs_status npbs_build_potential(npbs_ctx* ctx, const npbs_batch* batch, const void* k2,
-                                 void* V_out, double* k0sq_out, double* eps_out,
-                                 npbs_stream stream);
+npbs_status npbs_potential_from_k2(npbs_ctx* ctx, const npbs_batch* batch, const void* k2,
+                                   void* V_out, double* k0sq_out, double* eps_out,
+                                   npbs_stream stream);
 
 /* ---- the apply (Eq. CBS / Eq. npbs_integral / Eq. LS_discrete) ------------ */
 
@@ -216,14 +239,20 @@ npbs_status npbs_autotune_apply(npbs_ctx* ctx, const npbs_batch* batch, const vo
  * its own pool, or latency-critical code that must not pay for (possibly
  * device-synchronising) cudaMalloc / cudaFree, cannot allow that.  This entry
  * point takes no context and allocates nothing: the scratch (2^20 complex64
- * elements, 8 MiB) and the plan live in static device arrays that the library
- * reserves on every GPU that loads it, until the process exits.  The caller
- * still passes inputs and outputs (same meaning and layout as cbs_apply) on the
- * current device.  Limits: batch extent (max offset + nx*ny) <= 2^20 elements,
- * <= 64 instances, <= 8 distinct grid sides; larger batches return
- * NPBS_ERR_UNSUPPORTED_SIZE.  The first call on a device resolves the static
- * arrays' device addresses and sets kernel attributes; make that first call
- * before any stream capture.  All calls share the static arrays: calls that
+ * elements, 8 MiB) and the plan live in static device arrays of the library.
+ * The CUDA runtime places them on a device when it loads the library's module
+ * there; under lazy module loading (the default) that is the first call on the
+ * device, so make that call before the caller's own pool takes the device's
+ * memory (or run with CUDA_MODULE_LOADING=EAGER); if they cannot be placed the
+ * call returns NPBS_ERR_CUDA with a message.  The device then holds them until
+ * the process exits.  Each call writes its plan on the device with a small
+ * set-up kernel from its launch parameters, in stream order before the apply.
+ * The caller still passes inputs and outputs (same meaning and layout as
+ * cbs_apply) on the current device.  Limits: batch extent (max offset + nx*ny)
+ * <= 2^20 elements, <= 64 instances, <= 8 distinct grid sides; larger batches
+ * return NPBS_ERR_UNSUPPORTED_SIZE.  The first call on a device resolves the
+ * static arrays' device addresses and sets kernel attributes; make that first
+ * call before any stream capture.  All calls share the static arrays: calls that
  * overlap on the GPU (different streams or host threads) race; calls on one
  * stream are ordered.  err (nullable, errlen bytes) receives a one-line
  * message on failure.  Asynchronous on `stream`. */

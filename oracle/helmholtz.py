@@ -53,6 +53,37 @@ def reference_constants(k2: torch.Tensor) -> tuple[float, float]:
     return k0sq, eps
 
 
+def absorbing_medium(n, omega: float, layer_cells: int, ramp_amp_over_omega2: float = 0.5) -> torch.Tensor:
+    """k^2(x) = omega^2 n(x)^2 + i a omega^2 rho(x)^2 on the padded grid.
+
+    Sec. 3.1 truncates the domain with an absorbing layer folded into the
+    operator; the paper names only "sponge or PML".  The reading used here: a
+    W-cell layer (W = layer_cells) along every side whose imaginary part rises
+    quadratically with the depth, a = ramp_amp_over_omega2.  Per cell, the depth
+    into the layer along one axis counts 1 at the innermost layer cell up to W
+    at the outermost one (0 in the interior); rho is the larger of the two axis
+    depths divided by W.  Written cell by cell.
+    """
+    n = np.asarray(n, dtype=np.float64)
+    ny, nx = n.shape
+    W = int(layer_cells)
+    k2 = np.zeros((ny, nx), dtype=np.complex128)
+    for y in range(ny):
+        for x in range(nx):
+            depths = []
+            for j, N in ((y, ny), (x, nx)):
+                d = 0
+                if j < W:
+                    d = W - j
+                if j >= N - W:
+                    d = j - (N - W) + 1
+                depths.append(d)
+            rho = max(depths) / W if W > 0 else 0.0
+            k2[y, x] = complex((omega * omega) * (n[y, x] * n[y, x]),
+                               ramp_amp_over_omega2 * omega * omega * (rho * rho))
+    return torch.from_numpy(k2)
+
+
 def symbol(ny: int, nx: int, h: float, k0sq: float, eps: float) -> torch.Tensor:
     """lambda_n = |xi_n|^2 - (k0^2 + i eta): symbol of L_eta (App. Pseudospectral)."""
     return xi_squared(ny, nx, h).to(C128) - complex(k0sq, eps)

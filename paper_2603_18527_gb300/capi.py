@@ -59,7 +59,10 @@ _SIGS = {
     "npbs_last_error": (C.c_char_p, [C.c_void_p]),
     "npbs_launch_count": (C.c_int64, [C.c_void_p]),
     "npbs_conv_stats": (None, [C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
-    "npbs_build_potential": (C.c_int, [C.c_void_p, C.POINTER(npbs_batch), C.c_void_p, C.c_void_p,
+    "npbs_potential_from_k2": (C.c_int, [C.c_void_p, C.POINTER(npbs_batch), C.c_void_p, C.c_void_p,
+                                         C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_void_p]),
+    "npbs_build_potential": (C.c_int, [C.c_void_p, C.POINTER(npbs_batch), C.c_void_p, C.POINTER(C.c_double),
+                                       C.c_int32, C.c_double, C.c_void_p, C.c_void_p,
                                        C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_void_p]),
     "cbs_apply": (C.c_int, [C.c_void_p, C.POINTER(npbs_batch), C.c_void_p, C.c_void_p, C.c_void_p,
                             C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
@@ -241,16 +244,35 @@ def launch_count(ctx: Context) -> int:
     return int(lib().npbs_launch_count(ctx.handle))
 
 
-def npbs_build_potential(ctx: Context, batch: Batch, k2: torch.Tensor, V_out: Optional[torch.Tensor],
-                         stream=None):
-    """Fill V_out and return (k0sq, eps) lists; also stores them in ``batch``."""
+def npbs_potential_from_k2(ctx: Context, batch: Batch, k2: torch.Tensor, V_out: Optional[torch.Tensor],
+                           stream=None):
+    """Fill V_out from k^2 and return (k0sq, eps) lists; also stores them in ``batch``."""
     n = batch.count
     k0 = (C.c_double * max(1, n))()
     ep = (C.c_double * max(1, n))()
-    ctx.check(lib().npbs_build_potential(ctx.handle, C.byref(batch.c_batch()), _ptr(k2), _ptr(V_out), k0, ep,
-                                         _stream(stream)))
+    ctx.check(lib().npbs_potential_from_k2(ctx.handle, C.byref(batch.c_batch()), _ptr(k2), _ptr(V_out), k0, ep,
+                                           _stream(stream)))
     batch.k0sq = [k0[j] for j in range(n)]
     batch.eps = [ep[j] for j in range(n)]
+    return batch.k0sq, batch.eps
+
+
+def npbs_build_potential(ctx: Context, batch: Batch, n: torch.Tensor, omega: Sequence[float], layer_cells: int,
+                         ramp_amp_over_omega2: float, k2_out: Optional[torch.Tensor], V_out: Optional[torch.Tensor],
+                         stream=None):
+    """Build k^2 (absorbing layer included) and V from n and omega on the GPU;
+    return (k0sq, eps) lists and store them in ``batch``."""
+    if n.dtype != torch.float32:
+        raise ValueError("n must be float32")
+    cnt = batch.count
+    om = (C.c_double * max(1, cnt))(*[float(w) for w in omega])
+    k0 = (C.c_double * max(1, cnt))()
+    ep = (C.c_double * max(1, cnt))()
+    ctx.check(lib().npbs_build_potential(ctx.handle, C.byref(batch.c_batch()), _ptr(n), om, int(layer_cells),
+                                         float(ramp_amp_over_omega2), _ptr(k2_out), _ptr(V_out), k0, ep,
+                                         _stream(stream)))
+    batch.k0sq = [k0[j] for j in range(cnt)]
+    batch.eps = [ep[j] for j in range(cnt)]
     return batch.k0sq, batch.eps
 
 

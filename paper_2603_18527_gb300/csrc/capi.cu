@@ -346,6 +346,37 @@ __global__ void k_potential(const InstDev* inst, const float2* k2, float2* V, do
     }
 }
 
+// Depth (cells, 1..w) of index j into a w-cell absorbing layer at both ends
+// of a line of n cells; 0 in the interior.  The upper end wins where the two
+// layers overlap (w > n / 2).
+__device__ __forceinline__ int layer_depth(int j, int n, int w) {
+    int d = j < w ? w - j : 0;
+    if (j >= n - w) d = j - (n - w) + 1;
+    return d;
+}
+
+// k^2 = omega^2 n^2 + i a omega^2 rho^2 with rho = max(depth_x, depth_y) / w
+// (quadratic imaginary ramp, the larger depth in the corners), in float64,
+// stored as complex64.  One block row of the grid per instance.
+__global__ void k_medium(const InstDev* inst, const float* n, const double* omega, int w, double amp,
+                         float2* k2) {
+    const InstDev in = inst[blockIdx.y];
+    const double om = omega[blockIdx.y];
+    const long long np = (long long)in.nx * in.ny;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < np; e += (long long)gridDim.x * blockDim.x) {
+        const int y = (int)(e / in.nx), x = (int)(e - (long long)y * in.nx);
+        double rho = 0.0;
+        if (w > 0) {
+            const int d = max(layer_depth(y, in.ny, w), layer_depth(x, in.nx, w));
+            rho = (double)d / (double)w;
+        }
+        const double nn = (double)n[in.offset + e];
+        const double re = (om * om) * (nn * nn);
+        const double im = amp * om * om * (rho * rho);
+        k2[in.offset + e] = make_float2((float)re, (float)im);
+    }
+}
+
 }  // namespace npbs
 
 using namespace npbs;
@@ -416,11 +447,11 @@ const char* npbs_last_error(const npbs_ctx* ctx) { return ctx ? ctx->err.c_str()
 
 int64_t npbs_launch_count(const npbs_ctx* ctx) { return ctx ? (int64_t)ctx->launches : -1; }
 
-npbs_status npbs_build_potential(npbs_ctx* ctx, const npbs_batch* batch, const void* k2, void* V_out,
-                                 double* k0sq_out, double* eps_out, npbs_stream stream) {
+npbs_status npbs_potential_from_k2(npbs_ctx* ctx, const npbs_batch* batch, const void* k2, void* V_out,
+                                   double* k0sq_out, double* eps_out, npbs_stream stream) {
     if (!ctx) return NPBS_ERR_INVALID_ARG;
     if (!batch || batch->count < 0 || (batch->count > 0 && (!batch->inst || !k2 || !k0sq_out || !eps_out)))
-        return set_err(ctx, NPBS_ERR_INVALID_ARG, "npbs_build_potential: NULL argument");
+        return set_err(ctx, NPBS_ERR_INVALID_ARG, "npbs_potential_from_k2: NULL argument");
     if (batch->count == 0) return NPBS_OK;
     // the constants are outputs here: plan with placeholders that pass validation
     std::vector<npbs_instance> tmp(batch->inst, batch->inst + batch->count);
@@ -443,6 +474,44 @@ npbs_status npbs_build_potential(npbs_ctx* ctx, const npbs_batch* batch, const v
         eps_out[j] = hc[2 * j + 1];
     }
     return NPBS_OK;
+}
+
+npbs_status npbs_build_potential(npbs_ctx* ctx, const npbs_batch* batch, const float* n, const double* omega,
+                                 int32_t layer_cells, double ramp_amp_over_omega2, void* k2_out, void* V_out,
+                                 double* k0sq_out, double* eps_out, npbs_stream stream) {
+    if (!ctx) return NPBS_ERR_INVALID_ARG;
+    if (!batch || batch->count < 0 || (batch->count > 0 && (!batch->inst || !n || !omega || !k0sq_out || !eps_out)))
+        return set_err(ctx, NPBS_ERR_INVALID_ARG, "npbs_build_potential: NULL argument");
+    if (layer_cells < 0 || !(ramp_amp_over_omega2 >= 0.0) || !std::isfinite(ramp_amp_over_omega2))
+        return set_err(ctx, NPBS_ERR_INVALID_ARG, "npbs_build_potential: need layer_cells >= 0 and a finite ramp >= 0");
+    if (batch->count == 0) return NPBS_OK;
+    if (batch->count > 65535) return set_err(ctx, NPBS_ERR_INVALID_ARG, "npbs_build_potential: more than 65535 instances");
+    for (int j = 0; j < batch->count; ++j)
+        if (!(omega[j] > 0.0) || !std::isfinite(omega[j])) {
+            char buf[128];
+            snprintf(buf, sizeof buf, "npbs_build_potential: instance %d: need a finite omega > 0", j);
+            return set_err(ctx, NPBS_ERR_INVALID_ARG, buf);
+        }
+    std::vector<npbs_instance> tmp(batch->inst, batch->inst + batch->count);
+    for (auto& t : tmp) { t.k0sq = 0.0; t.eps = 1.0; }
+    npbs_batch b2{batch->count, tmp.data()};
+    npbs_status st;
+    const Plan* pl = get_plan(ctx, &b2, &st);
+    if (!pl) return st;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    float2* k2 = static_cast<float2*>(k2_out);
+    if (!k2) {
+        NPBS_CK(ctx, ctx->work[10].ensure(sizeof(float2) * (size_t)std::max<long long>(pl->extent, 1)));
+        k2 = static_cast<float2*>(ctx->work[10].p);
+    }
+    NPBS_CK(ctx, ctx->work[11].ensure(sizeof(double) * batch->count));
+    double* dom = static_cast<double*>(ctx->work[11].p);
+    NPBS_CK(ctx, cudaMemcpyAsync(dom, omega, sizeof(double) * batch->count, cudaMemcpyHostToDevice, s));
+    dim3 grid(64, (unsigned)batch->count);
+    k_medium<<<grid, 256, 0, s>>>(pl->inst, n, dom, layer_cells, ramp_amp_over_omega2, k2);
+    NPBS_CK(ctx, cudaGetLastError());
+    ctx->count(s, 1);
+    return npbs_potential_from_k2(ctx, batch, k2, V_out, k0sq_out, eps_out, stream);
 }
 
 npbs_status npbs_autotune_apply(npbs_ctx* ctx, const npbs_batch* batch, const void* V, const void* f, void* x,

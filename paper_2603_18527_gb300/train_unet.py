@@ -49,7 +49,7 @@ class Pool:
         self.f = self.b.pack([i.f for i in insts])
         self.n = self.b.pack([coefficient_channel(i, scale_by_omega) for i in insts], dtype=torch.float32)
         self.V = torch.zeros_like(self.k2)
-        capi.npbs_build_potential(ctx, self.b, self.k2, self.V)
+        capi.npbs_potential_from_k2(ctx, self.b, self.k2, self.V)
 
 
 def snapshot_bank(ctx, pool: Pool, max_snap: int = 2048) -> tuple[list[int], torch.Tensor]:

@@ -21,7 +21,7 @@ def setup_batch(capi, c, insts):
     f = b.pack([i.f for i in insts])
     n = b.pack([i.n for i in insts], dtype=torch.float32)
     V = torch.zeros_like(k2)
-    capi.npbs_build_potential(c, b, k2, V)
+    capi.npbs_potential_from_k2(c, b, k2, V)
     return b, k2, f, n, V
 
 

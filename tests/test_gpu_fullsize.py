@@ -29,7 +29,7 @@ def mixed():
     k2 = b.pack([i.k2 for i in insts])
     f = b.pack([i.f for i in insts])
     V = torch.zeros_like(k2)
-    capi.npbs_build_potential(c, b, k2, V)
+    capi.npbs_potential_from_k2(c, b, k2, V)
     x = torch.zeros_like(k2)
     capi.npbs_autotune_apply(c, b, V, f, x, reps=2)
     return capi, c, insts, b, k2, f, V
@@ -76,7 +76,7 @@ def test_layered_1024_fgmres_cbs_preconditioned():
     k2, f = b.pack([i.k2 for i in insts]), b.pack([i.f for i in insts])
     n = b.pack([i.n for i in insts], dtype=torch.float32)
     V = torch.zeros_like(k2)
-    capi.npbs_build_potential(c, b, k2, V)
+    capi.npbs_potential_from_k2(c, b, k2, V)
     u = torch.zeros(b.extent, dtype=torch.complex128, device="cuda")
     st, rep = capi.fgmres_solve(c, None, b, k2, f, n, u, restart=20, precond=1, cbs_sweeps=16, rtol=1e-5,
                                 max_iter=1000)

@@ -334,3 +334,31 @@ def test_free_space_green_function_trend():
         errs.append(np.linalg.norm(num - ex) / np.linalg.norm(ex))
     assert errs[1] < errs[0]
     assert errs[1] < 0.15
+
+
+def test_absorbing_medium_special_cells():
+    """The layer reading of Sec. 3.1 on a 7 x 9 grid with a 2-cell layer:
+    interior cells carry no absorption, the outermost ring the full a omega^2,
+    one cell in a quarter of it (rho = 1/2, quadratic ramp), corners take the
+    larger depth, and the real part is omega^2 n^2."""
+    rng = np.random.default_rng(5)
+    n = 1.0 + 0.3 * rng.standard_normal((7, 9))
+    om, a, W = 0.7, 0.5, 2
+    k2 = H.absorbing_medium(n, om, W, a).numpy()
+    full = a * om * om
+    assert np.array_equal(k2.real, (om * om) * (n * n))
+    assert k2[3, 4].imag == 0.0 and k2[2, 2].imag == 0.0 and k2[4, 6].imag == 0.0
+    for y, x in [(0, 4), (6, 4), (3, 0), (3, 8), (0, 0), (6, 8)]:
+        assert k2[y, x].imag == pytest.approx(full, rel=1e-15)
+    for y, x in [(1, 4), (5, 4), (3, 1), (3, 7), (1, 1), (5, 7)]:
+        assert k2[y, x].imag == pytest.approx(full / 4, rel=1e-15)
+    assert k2[1, 0].imag == pytest.approx(full, rel=1e-15)  # corner: the deeper axis wins
+    assert np.allclose(k2.imag, k2.imag[::-1, ::-1], rtol=0, atol=0)
+    assert not np.any(H.absorbing_medium(n, om, 0, a).numpy().imag)
+
+
+def test_absorbing_medium_is_the_workload_recipe():
+    """The synthetic workloads assemble k^2 with the same layer (96^2 law)."""
+    inst = synth.workload_96()[0]
+    k2 = H.absorbing_medium(inst.n, inst.omega, inst.layer, 0.5).numpy()
+    assert np.allclose(k2, inst.k2, rtol=1e-15, atol=0)
