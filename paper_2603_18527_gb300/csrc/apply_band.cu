@@ -170,7 +170,8 @@ __global__ void __launch_bounds__(T, MINB) k_band_cols(FastDev fd, BatchDev bd, 
                     // lambda = xi2 - k0^2 - i eps; 1/lambda = conj(lambda) / |lambda|^2
                     const float lr = xi2 - k0sq;
                     const float lim = (MODE == NPBS_ADJ_B) ? eps : -eps;  // conj for the adjoint
-                    const float inv = 1.f / (lr * lr + lim * lim);
+                    float inv;  // hardware reciprocal (rcp.approx, ~1 ulp)
+                    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(inv) : "f"(fmaf(lr, lr, lim * lim)));
                     v[k2] = make_float2((t.x * lr + t.y * lim) * inv, (t.y * lr - t.x * lim) * inv);
                 }
             }

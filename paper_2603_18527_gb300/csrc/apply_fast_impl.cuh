@@ -15,6 +15,16 @@
 // distributed shared memory: each thread stores its register results directly
 // into the owning CTA's slab between two cluster barriers.
 //
+// The row -> column exchange has a second form (template parameter XP = 1):
+// each thread writes its row-pass results straight to the instance's region
+// of the spectrum scratch in column-major order (coalesced 256-byte stores),
+// one cluster barrier, and the column pass loads its columns from L2; the
+// CTA then discards its columns' lines from L2 (discard.global.L2) so that
+// the dirty scratch is never written back to DRAM.  On GB300 the L2 route
+// moves the exchange faster than distributed shared memory (measured
+// GPU-wide: about 3.8 TB/s through L2 against 2.5 TB/s through DSMEM); the
+// autotuner chooses per grid side.
+//
 // DRAM traffic is the algorithmic minimum: the prologue reads x, V, f once
 // (Eq. CBS: q = V x + f), the epilogue re-reads x and V (they are still in L2)
 // and writes out once.  Phases per apply:
@@ -83,7 +93,7 @@ __device__ __forceinline__ void prefetch_rows(const int next, const int rank, co
 // out (each thread reads back exactly the points it wrote in the previous
 // step, so the thread's own program order suffices; coherent loads, never the
 // read-only path, since out changes during the kernel).
-template <int N1, int N2, int CS, int T, int MODE, bool first, bool last>
+template <int N1, int N2, int CS, int T, int MODE, bool first, bool last, int XP>
 __device__ __forceinline__ double cluster_step(const InstDev& in, const BatchDev& bd, const ApplyArgs& a, float2* S,
                                                const float2* tw, const int rank, const int tid, const int next) {
     constexpr int N = N1 * N2;
@@ -147,21 +157,37 @@ __device__ __forceinline__ double cluster_step(const InstDev& in, const BatchDev
             DftR<N2, -1>::run(h2[s]);
         }
     }
-    cluster.sync();
+    if constexpr (XP == 1) {
+        // exchange through L2: column-major [position][row] in the scratch
+        float2* regA = static_cast<float2*>(a.scratch) + base;
 #pragma unroll
-    for (int s = 0; s < J2; ++s) {
-        const int j = tid + s * T;
-        if (j < ROWS * N1) {
-            const int r = j % ROWS, k1 = j / ROWS;
-            const int p0 = N2 * k1;
-            const int d = p0 / ROWS, pl = p0 - d * ROWS;
-            float2* dst = cluster.map_shared_rank(S, d);
-            const int R = rank * ROWS + r;
+        for (int s = 0; s < J2; ++s) {
+            const int j = tid + s * T;
+            if (j < ROWS * N1) {
+                const int r = j % ROWS, k1 = j / ROWS;
+                const int R = rank * ROWS + r;
 #pragma unroll
-            for (int i = 0; i < N2; ++i) dst[(pl + i) * LD + pad<N2>(R)] = h2[s][i];
+                for (int i = 0; i < N2; ++i) __stcg(regA + (long long)(N2 * k1 + i) * N + R, h2[s][i]);
+            }
         }
+        cluster.sync();
+    } else {
+        cluster.sync();
+#pragma unroll
+        for (int s = 0; s < J2; ++s) {
+            const int j = tid + s * T;
+            if (j < ROWS * N1) {
+                const int r = j % ROWS, k1 = j / ROWS;
+                const int p0 = N2 * k1;
+                const int d = p0 / ROWS, pl = p0 - d * ROWS;
+                float2* dst = cluster.map_shared_rank(S, d);
+                const int R = rank * ROWS + r;
+#pragma unroll
+                for (int i = 0; i < N2; ++i) dst[(pl + i) * LD + pad<N2>(R)] = h2[s][i];
+            }
+        }
+        cluster.sync();
     }
-    cluster.sync();
 
     NPBS_PHASE_MARK(2);
     // ---------------- P3: column pass 1 (slab now [ROWS columns][N rows])
@@ -171,8 +197,14 @@ __device__ __forceinline__ double cluster_step(const InstDev& in, const BatchDev
         if (j < ROWS * N2) {
             const int n2 = j % N2, c = j / N2;
             float2 v[N1];
+            if constexpr (XP == 1) {
+                const float2* col = static_cast<const float2*>(a.scratch) + base + (long long)(rank * ROWS + c) * N;
 #pragma unroll
-            for (int m = 0; m < N1; ++m) v[m] = S[c * LD + pad<N2>(n2 + N2 * m)];
+                for (int m = 0; m < N1; ++m) v[m] = __ldcg(col + n2 + N2 * m);
+            } else {
+#pragma unroll
+                for (int m = 0; m < N1; ++m) v[m] = S[c * LD + pad<N2>(n2 + N2 * m)];
+            }
             DftR<N1, -1>::run(v);
 #pragma unroll
             for (int k1 = 0; k1 < N1; ++k1) {
@@ -183,6 +215,14 @@ __device__ __forceinline__ double cluster_step(const InstDev& in, const BatchDev
         }
     }
     __syncthreads();
+    if constexpr (XP == 1) {
+        // this CTA's columns of the scratch are consumed: drop them from L2
+        // without a write-back (their contents become undefined)
+        const char* col0 = reinterpret_cast<const char*>(static_cast<const float2*>(a.scratch) + base +
+                                                         (long long)rank * ROWS * N);
+        for (int l = tid; l < ROWS * N * 8 / 128; l += T)
+            asm volatile("discard.global.L2 [%0], 128;" ::"l"(__cvta_generic_to_global(col0 + 128 * l)) : "memory");
+    }
 
     NPBS_PHASE_MARK(3);
     // ---------------- P4: column pass 2, Green symbol, inverse pass A
@@ -212,7 +252,10 @@ __device__ __forceinline__ double cluster_step(const InstDev& in, const BatchDev
                     } else {
                         const float lr = xi2 - k0sq;
                         const float li = (MODE == NPBS_ADJ_B) ? eps : -eps;
-                        const float inv = 1.f / (lr * lr + li * li);
+                        // hardware reciprocal (rcp.approx, ~1 ulp): the symbol
+                        // needs far less than float32 round-to-nearest division
+                        float inv;
+                        asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(inv) : "f"(fmaf(lr, lr, li * li)));
                         v[k2] = make_float2((t.x * lr + t.y * li) * inv, (t.y * lr - t.x * li) * inv);
                     }
                 }
@@ -359,13 +402,13 @@ __device__ __forceinline__ double cluster_step(const InstDev& in, const BatchDev
 // The same step compiled as a separate function: the fused multi-step loop
 // calls it, so nothing loop-invariant (addresses, the symbol 1/lambda,
 // twiddles) is hoisted out of the loop and kept live across the phases.
-template <int N1, int N2, int CS, int T, int MODE, bool first, bool last>
+template <int N1, int N2, int CS, int T, int MODE, bool first, bool last, int XP>
 __device__ __noinline__ double cluster_step_call(const InstDev& in, const BatchDev& bd, const ApplyArgs& a, float2* S,
                                                  const float2* tw, const int rank, const int tid) {
-    return cluster_step<N1, N2, CS, T, MODE, first, last>(in, bd, a, S, tw, rank, tid, -1);
+    return cluster_step<N1, N2, CS, T, MODE, first, last, XP>(in, bd, a, S, tw, rank, tid, -1);
 }
 
-template <int N1, int N2, int CS, int T, int MODE>
+template <int N1, int N2, int CS, int T, int MODE, int XP>
 __device__ __forceinline__ void cluster_apply_one(const int instx, const BatchDev& bd, const ApplyArgs& a,
                                                   float2* smem, double* red, const int next = -1) {
     constexpr int N = N1 * N2;
@@ -386,16 +429,16 @@ __device__ __forceinline__ void cluster_apply_one(const int instx, const BatchDe
     double acc;
     constexpr bool ITER = MODE == NPBS_CBS_STEP || MODE == NPBS_PREC_SWEEP;
     if (!ITER || a.steps <= 1) {
-        acc = cluster_step<N1, N2, CS, T, MODE, true, true>(in, bd, a, S, tw, rank, tid, next);
+        acc = cluster_step<N1, N2, CS, T, MODE, true, true, XP>(in, bd, a, S, tw, rank, tid, next);
     } else if constexpr (ITER) {
         // fused steps: after the first, u, V and f of the instance come from L2
-        cluster_step_call<N1, N2, CS, T, MODE, true, false>(in, bd, a, S, tw, rank, tid);
+        cluster_step_call<N1, N2, CS, T, MODE, true, false, XP>(in, bd, a, S, tw, rank, tid);
         __syncthreads();  // the next step rewrites the slab
         for (int it = 1; it < a.steps - 1; ++it) {
-            cluster_step_call<N1, N2, CS, T, MODE, false, false>(in, bd, a, S, tw, rank, tid);
+            cluster_step_call<N1, N2, CS, T, MODE, false, false, XP>(in, bd, a, S, tw, rank, tid);
             __syncthreads();
         }
-        acc = cluster_step_call<N1, N2, CS, T, MODE, false, true>(in, bd, a, S, tw, rank, tid);
+        acc = cluster_step_call<N1, N2, CS, T, MODE, false, true, XP>(in, bd, a, S, tw, rank, tid);
     }
     if (a.norm2) {
         acc = warp_sum_d(acc);
@@ -411,7 +454,7 @@ __device__ __forceinline__ void cluster_apply_one(const int instx, const BatchDe
 }
 
 // One cluster per instance.
-template <int N1, int N2, int CS, int T, int MODE, int MINB = 1>
+template <int N1, int N2, int CS, int T, int MODE, int MINB = 1, int XP = 0>
 __global__ void __launch_bounds__(T, MINB) k_apply_cluster(FastDev fd, BatchDev bd, ApplyArgs a) {
     extern __shared__ __align__(16) float2 smem[];
     __shared__ double red[T / 32];
@@ -423,7 +466,7 @@ __global__ void __launch_bounds__(T, MINB) k_apply_cluster(FastDev fd, BatchDev 
         next = fd.list[cl + fd.ahead];
         if (bd.active && !bd.active[next]) next = -1;
     }
-    cluster_apply_one<N1, N2, CS, T, MODE>(instx, bd, a, smem, red, next);
+    cluster_apply_one<N1, N2, CS, T, MODE, XP>(instx, bd, a, smem, red, next);
 }
 
 // Prefetch distance in clusters: a third of the resident count (measured on
@@ -440,7 +483,7 @@ inline int prefetch_ahead(int resident) {
 
 // Clusters of one variant resident on the device at once (set when the
 // attributes are; 0 when unknown, which disables the prefetch).
-template <int N1, int N2, int CS, int T, int MODE, int MINB>
+template <int N1, int N2, int CS, int T, int MODE, int MINB, int XP>
 int& resident_clusters() {
     static int v = 0;
     return v;
@@ -450,9 +493,9 @@ template <int N1, int N2, int CS, int T> constexpr size_t fast_smem() {
     return sizeof(float2) * ((size_t)(N1 * N2 / CS) * (N1 * N2 + N1 + 1) + (size_t)N1 * (N2 + 1));
 }
 
-template <int N1, int N2, int CS, int T, int MODE, int MINB = 1>
+template <int N1, int N2, int CS, int T, int MODE, int MINB = 1, int XP = 0>
 cudaError_t set_attr_one() {
-    auto k = k_apply_cluster<N1, N2, CS, T, MODE, MINB>;
+    auto k = k_apply_cluster<N1, N2, CS, T, MODE, MINB, XP>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fast_smem<N1, N2, CS, T>());
     if (e == cudaSuccess && CS > 8) e = cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e == cudaSuccess) {
@@ -468,25 +511,25 @@ cudaError_t set_attr_one() {
         cfg.attrs = attr;
         cfg.numAttrs = 1;
         int n = 0;
-        if (cudaOccupancyMaxActiveClusters(&n, k, &cfg) == cudaSuccess) resident_clusters<N1, N2, CS, T, MODE, MINB>() = n;
+        if (cudaOccupancyMaxActiveClusters(&n, k, &cfg) == cudaSuccess) resident_clusters<N1, N2, CS, T, MODE, MINB, XP>() = n;
         else (void)cudaGetLastError();
     }
     return e;
 }
 
-template <int N1, int N2, int CS, int T, int MINB>
+template <int N1, int N2, int CS, int T, int MINB, int XP = 0>
 cudaError_t set_attr_size() {
     cudaError_t e = cudaSuccess;
-    if (e == cudaSuccess) e = set_attr_one<N1, N2, CS, T, NPBS_RESIDUAL, MINB>();
-    if (e == cudaSuccess) e = set_attr_one<N1, N2, CS, T, NPBS_CBS_STEP, MINB>();
-    if (e == cudaSuccess) e = set_attr_one<N1, N2, CS, T, NPBS_OP_B, MINB>();
-    if (e == cudaSuccess) e = set_attr_one<N1, N2, CS, T, NPBS_ADJ_B, MINB>();
-    if (e == cudaSuccess) e = set_attr_one<N1, N2, CS, T, NPBS_TRUE_RESIDUAL, MINB>();
-    if (e == cudaSuccess) e = set_attr_one<N1, N2, CS, T, NPBS_PREC_SWEEP, MINB>();
+    if (e == cudaSuccess) e = set_attr_one<N1, N2, CS, T, NPBS_RESIDUAL, MINB, XP>();
+    if (e == cudaSuccess) e = set_attr_one<N1, N2, CS, T, NPBS_CBS_STEP, MINB, XP>();
+    if (e == cudaSuccess) e = set_attr_one<N1, N2, CS, T, NPBS_OP_B, MINB, XP>();
+    if (e == cudaSuccess) e = set_attr_one<N1, N2, CS, T, NPBS_ADJ_B, MINB, XP>();
+    if (e == cudaSuccess) e = set_attr_one<N1, N2, CS, T, NPBS_TRUE_RESIDUAL, MINB, XP>();
+    if (e == cudaSuccess) e = set_attr_one<N1, N2, CS, T, NPBS_PREC_SWEEP, MINB, XP>();
     return e;
 }
 
-template <int N1, int N2, int CS, int T, int MODE, int MINB = 1>
+template <int N1, int N2, int CS, int T, int MODE, int MINB = 1, int XP = 0>
 cudaError_t launch_one(const FastDev& fd, const BatchDev& bd, const ApplyArgs& a, cudaStream_t st) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(fd.count * CS), 1, 1);
@@ -501,19 +544,19 @@ cudaError_t launch_one(const FastDev& fd, const BatchDev& bd, const ApplyArgs& a
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     FastDev f2 = fd;
-    f2.ahead = fd.ahead > 0 ? prefetch_ahead(resident_clusters<N1, N2, CS, T, MODE, MINB>()) : 0;
-    return cudaLaunchKernelEx(&cfg, k_apply_cluster<N1, N2, CS, T, MODE, MINB>, f2, bd, a);
+    f2.ahead = fd.ahead > 0 ? prefetch_ahead(resident_clusters<N1, N2, CS, T, MODE, MINB, XP>()) : 0;
+    return cudaLaunchKernelEx(&cfg, k_apply_cluster<N1, N2, CS, T, MODE, MINB, XP>, f2, bd, a);
 }
 
-template <int N1, int N2, int CS, int T, int MINB>
+template <int N1, int N2, int CS, int T, int MINB, int XP = 0>
 cudaError_t launch_size(int mode, const FastDev& fd, const BatchDev& bd, const ApplyArgs& a, cudaStream_t st) {
     switch (mode) {
-        case NPBS_RESIDUAL: return launch_one<N1, N2, CS, T, NPBS_RESIDUAL, MINB>(fd, bd, a, st);
-        case NPBS_CBS_STEP: return launch_one<N1, N2, CS, T, NPBS_CBS_STEP, MINB>(fd, bd, a, st);
-        case NPBS_OP_B: return launch_one<N1, N2, CS, T, NPBS_OP_B, MINB>(fd, bd, a, st);
-        case NPBS_ADJ_B: return launch_one<N1, N2, CS, T, NPBS_ADJ_B, MINB>(fd, bd, a, st);
-        case NPBS_TRUE_RESIDUAL: return launch_one<N1, N2, CS, T, NPBS_TRUE_RESIDUAL, MINB>(fd, bd, a, st);
-        case NPBS_PREC_SWEEP: return launch_one<N1, N2, CS, T, NPBS_PREC_SWEEP, MINB>(fd, bd, a, st);
+        case NPBS_RESIDUAL: return launch_one<N1, N2, CS, T, NPBS_RESIDUAL, MINB, XP>(fd, bd, a, st);
+        case NPBS_CBS_STEP: return launch_one<N1, N2, CS, T, NPBS_CBS_STEP, MINB, XP>(fd, bd, a, st);
+        case NPBS_OP_B: return launch_one<N1, N2, CS, T, NPBS_OP_B, MINB, XP>(fd, bd, a, st);
+        case NPBS_ADJ_B: return launch_one<N1, N2, CS, T, NPBS_ADJ_B, MINB, XP>(fd, bd, a, st);
+        case NPBS_TRUE_RESIDUAL: return launch_one<N1, N2, CS, T, NPBS_TRUE_RESIDUAL, MINB, XP>(fd, bd, a, st);
+        case NPBS_PREC_SWEEP: return launch_one<N1, N2, CS, T, NPBS_PREC_SWEEP, MINB, XP>(fd, bd, a, st);
         default: return cudaErrorInvalidValue;
     }
 }
