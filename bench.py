@@ -171,8 +171,10 @@ def bench_learned(capi, ctx, args, stream):
     flt = 4 * 4 * unet_forward_flops(256, 256) * 32
     out["train_step"] = {"batch": 32, "grid": 256, "unroll": 4, "ms": ms_t, "tflops": flt / (ms_t * 1e-3) / 1e12,
                          "frac_of_bf16_peak_sustained": flt / (ms_t * 1e-3) / 1e12 / peak_s}
-    # NPBS vs CBS to 1e-5 on the same batch (amortised: batch time / count) and
-    # on its first instance alone (batch 1, median of 3)
+    # NPBS vs CBS to 1e-5 on the same media: time to solution with a cap large
+    # enough that (nearly) every instance converges, on the whole batch
+    # (amortised: batch time / count), on the subset both solvers converge, and
+    # instance by instance (batch 1)
     def solve(name, p, reps=1, max_iter=None):
         ts = []
         cap = max_iter or args.npbs_max_iter
@@ -186,16 +188,36 @@ def bench_learned(capi, ctx, args, stream):
                 st, rep = capi.npbs_solve(ctx, net, p.b, p.k2, p.f, p.n, u, rtol=TOL, max_iter=cap, check_every=4)
             torch.cuda.synchronize()
             ts.append(time.perf_counter() - t0)
-        return {"ms_per_solve": float(np.median(ts)) * 1e3 / p.b.count, "iters_mean": float(np.mean(rep["iters"])),
-                "converged": int(sum(1 for x in rep["status"] if x == capi.OK)),
-                "fallback_to_cbs": int(sum(rep.get("fallback") or [0]))}
-    one = T.Pool(ctx, insts[:1])
-    out["npbs_vs_cbs"] = {"workload": f"contrast media law, {len(insts)} x 256^2, tol {TOL}, "
-                                      f"cap {args.npbs_max_iter} iterations",
-                          "batch": {name: solve(name, pool) for name in ("cbs", "npbs")},
-                          "batch_1": {name: solve(name, one, 3) for name in ("cbs", "npbs")},
-                          # time to solution of plain CBS on the same batch without the paper's cap
-                          "cbs_cap_20000": solve("cbs", pool, max_iter=20000)}
+        ok = [j for j, x in enumerate(rep["status"]) if x == capi.OK]
+        its = [rep["iters"][j] for j in ok]
+        return {"ms_per_solve": float(np.median(ts)) * 1e3 / p.b.count, "converged": len(ok),
+                "iters_mean": float(np.mean(rep["iters"])),
+                "iters_median_converged": float(np.median(its)) if its else None,
+                "fallback_to_cbs": int(sum(rep.get("fallback") or [0])), "cap": cap}, set(ok)
+    big = args.solution_cap
+    out_v = {"workload": f"contrast media law, {len(insts)} x 256^2, tol {TOL}"}
+    res = {}
+    for name in ("cbs", "npbs"):
+        r, ok = solve(name, pool, max_iter=big)
+        res[name] = ok
+        out_v[f"{name}_to_solution"] = r
+    both = sorted(res["cbs"] & res["npbs"])
+    if both:
+        sub = T.Pool(ctx, [insts[j] for j in both])
+        out_v["common_subset"] = {"instances": len(both),
+                                  **{name: solve(name, sub, max_iter=big)[0] for name in ("cbs", "npbs")}}
+    # the paper's cap (App. Experimental Setup: 2500 iterations)
+    out_v["cap_2500"] = {name: solve(name, pool, max_iter=2500)[0] for name in ("cbs", "npbs")}
+    # batch 1: the first instances one at a time
+    singles = {"cbs": [], "npbs": []}
+    for j in range(min(args.batch1_count, len(insts))):
+        one = T.Pool(ctx, insts[j:j + 1])
+        for name in ("cbs", "npbs"):
+            r, ok = solve(name, one, max_iter=big)
+            singles[name].append({"ms": r["ms_per_solve"], "iters": r["iters_mean"], "converged": bool(ok)})
+    out_v["batch_1"] = {name: {"ms_median": float(np.median([x["ms"] for x in v])), "solves": v}
+                        for name, v in singles.items()}
+    out["npbs_vs_cbs"] = out_v
     return out
 
 
@@ -243,7 +265,7 @@ def bench_fgmres(capi, ctx, args):
     # third network channel as in training: the local wavenumber omega * n
     n = b.pack([T.coefficient_channel(i, True) for i in insts], dtype=torch.float32)
     V = torch.zeros_like(k2)
-    capi.npbs_build_potential(ctx, b, k2, V)
+    capi.npbs_potential_from_k2(ctx, b, k2, V)
     out["layered"] = {"workload": f"layered media, {len(insts)} x 1024^2, restart 20, tol {TOL}, network {name}",
                       **fgmres_case(capi, ctx, net, b, k2, f, n, [("none", 0), ("cbs16", 1), ("npbs", 2)],
                                     args.fgmres_max_iter)}
@@ -318,6 +340,49 @@ def cpu_oracle_solve(inst, budget_s=25.0):
     return dt, res
 
 
+def cpu_oracle_breadth(npbs_iters=None):
+    """The oracle's cost per CBS apply at 96^2, 256^2 and 1024^2 on one host
+    core and on all of them, and its cost per NPBS iteration at 256^2 (apply +
+    the float64 network) on all cores.  Bounded: a few seconds of CPU work."""
+    from oracle import helmholtz as H
+    from oracle import unet as OU
+    allc = torch.get_num_threads()
+    out = {"cores_all": allc, "per_apply_ms": {}}
+    for n, reps in ((96, 40), (256, 8), (1024, 2)):
+        inst = synth.small_instance(n, seed=7, layer=max(1, n // 16))
+        p = H.problem_from_instance(inst)
+        u = torch.zeros(n, n, dtype=torch.complex128)
+        row = {}
+        for cores in (1, allc):
+            torch.set_num_threads(cores)
+            H.cbs_step(p, u)
+            t0 = time.perf_counter()
+            for _ in range(reps):
+                H.cbs_step(p, u)
+            row[f"cores_{cores}"] = (time.perf_counter() - t0) * 1e3 / reps
+        out["per_apply_ms"][f"{n}x{n}"] = row
+    torch.set_num_threads(allc)
+    # one NPBS iteration at 256^2: Born residual + the float64 network correction
+    from paper_2603_18527_gb300 import train_unet as T
+    inst = T.media(256, 1, 2000)[0]
+    p = H.problem_from_instance(inst)
+    params = OU.unflatten(torch.from_numpy(
+        np.load(os.path.join(ROOT, "paper_2603_18527_gb300", "weights", "unet_contrast256.npz"))["params"]
+        .astype(np.float64)))
+    nch = torch.from_numpy(T.coefficient_channel(inst, True).astype(np.float64))
+    u = torch.zeros(256, 256, dtype=torch.complex128)
+    t0 = time.perf_counter()
+    r = H.born_residual(p, u)
+    u = u + OU.correction(r[None], nch[None], params)[0]
+    it_ms = (time.perf_counter() - t0) * 1e3
+    out["npbs_iteration_ms_256"] = it_ms
+    if npbs_iters:
+        out["npbs_solve_ms_256_extrapolated"] = it_ms * npbs_iters
+        out["npbs_extrapolation"] = (f"oracle ms per NPBS iteration x the library's mean NPBS iteration count "
+                                     f"({npbs_iters:.0f}) on the contrast media")
+    return out
+
+
 def run_reference(args):
     """The CPU oracle as the reference arm, on a bounded sample of the workload."""
     rank = int(os.environ.get("RANK", "0"))
@@ -371,6 +436,9 @@ def main():
                     help="trained network (.npz canonical parameters or an npbs_net_save checkpoint)")
     ap.add_argument("--npbs-count", type=int, default=64)
     ap.add_argument("--npbs-max-iter", type=int, default=2500)
+    ap.add_argument("--solution-cap", type=int, default=100000,
+                    help="iteration cap of the time-to-solution comparison of NPBS and CBS")
+    ap.add_argument("--batch1-count", type=int, default=4, help="instances solved one at a time")
     ap.add_argument("--fgmres-count", type=int, default=8)
     ap.add_argument("--fgmres-max-iter", type=int, default=400)
     ap.add_argument("--no-learned", action="store_true", help="skip the network / NPBS / FGMRES sections")
@@ -412,7 +480,7 @@ def main():
         f = b.pack([i.f for i in insts])
         n = torch.zeros(b.extent, dtype=torch.float32, device="cuda")  # unused by the CBS preconditioner
         V = torch.zeros_like(k2)
-        capi.npbs_build_potential(ctx, b, k2, V)
+        capi.npbs_potential_from_k2(ctx, b, k2, V)
         res = fgmres_case(capi, ctx, None, b, k2, f, n, [("cbs16", 1)], args.fgmres_max_iter)
         print(json.dumps({"fgmres_only": f"layered media, {len(insts)} x 1024^2, restart 20, 16 CBS sweeps, "
                                          f"tol {TOL}, cap {args.fgmres_max_iter}", **res}), flush=True)
@@ -454,7 +522,7 @@ def main():
     k2 = k2_h.cuda()
     f = f_h.cuda()
     V = torch.zeros_like(k2)
-    capi.npbs_build_potential(ctx, b, k2, V)
+    capi.npbs_potential_from_k2(ctx, b, k2, V)
     u = torch.zeros(b.extent, dtype=torch.complex128, device="cuda")
     stream = torch.cuda.current_stream()
     # autotune the cluster-kernel variant per grid side on this workload (set-up, untimed)
@@ -534,7 +602,7 @@ def main():
     for _ in range(e2e_steps):
         k2.copy_(k2_h, non_blocking=True)
         f.copy_(f_h, non_blocking=True)
-        capi.npbs_build_potential(ctx, b, k2, V)
+        capi.npbs_potential_from_k2(ctx, b, k2, V)
         step()
         u_h.copy_(u, non_blocking=True)
     e1.record(stream)
@@ -556,6 +624,13 @@ def main():
                    "cores": torch.get_num_threads(), "kind": "oracle",
                    "sample": f"oracle CBS solve of one {sample[0].ny}x{sample[0].nx} instance of the workload "
                              f"to {TOL} ({res.iters} iterations, rTol checked every iteration)"}
+            try:
+                nits = None
+                if learned:
+                    nits = learned["npbs_vs_cbs"]["npbs_to_solution"]["iters_mean"]
+                cpu["breadth"] = cpu_oracle_breadth(nits)
+            except Exception as e:  # the headline baseline stands without the breadth figures
+                cpu["breadth"] = {"error": repr(e)}
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
                 "vs_baseline": None, "dtype": "c64 (f64 refinement)", "data": "synthetic",
