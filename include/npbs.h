@@ -316,8 +316,32 @@ npbs_status fgmres_solve(npbs_ctx* ctx, const npbs_net* net, const npbs_batch* b
  * up2, dec2a, dec2b, up1, dec1a, dec1b, up0, dec0a, dec0b) a float32 weight
  * [Cout][Cin][3][3] then a bias [Cout]; then the head weight [2][32]. */
 
-/* Total number of parameters in the canonical order. */
+/* Total number of parameters of the U-Net in the canonical order. */
 int64_t npbs_net_num_params(void);
+/* Parameters of a network of either kind (U-Net or FNO); -1 for NULL. */
+int64_t npbs_net_param_count(const npbs_net* net);
+
+/* The FNO map (App. Architectural Instantiations, Eqs. fno_impl, fno_lift,
+ * fno_proj, lfl, nlfl), the paper's primary backbone, as a network of the
+ * same object type: every entry taking an npbs_net (forward, backward, AdamW,
+ * save / load, npbs_solve, fgmres_solve, the training steps) accepts it.
+ *   M(r; a) = P( LFL_f[ NLFL_L(...NLFL_1(Phi(a))) * LFL_r(Psi(r)) ] ),
+ *   Phi(a) = W_a LayerNorm(a) + b_a, Psi(r) = W_r [Re r, Im r], P(z) = W_p z,
+ *   LFL(x) = irfft2(W^F * R(rfft2(x))) + W^loc x (+ b), NLFL = GELU(LFL);
+ * a is the network's coefficient channel (the `n` argument of the entries).
+ * M is linear in r (no bias on the residual path, no scale wrapper).  The
+ * NLFL and fusion layers keep the modes with min(ky, N - ky) < modes and
+ * kx < modes of the half plane, the residual layer all of them (N/2 + 1
+ * columns).  The paper's configuration is width 25, modes 45, layers 3.  The
+ * network is tied to one grid: every instance must be n x n.  n: even,
+ * 2^a 3^b, 4..1024; width 1..32; modes 1..n/2+1; layers 0..8.  Float32
+ * throughout.  Canonical parameter order: lift_a.w [C], lift_a.b [C]; per
+ * layer spec [C][C][Ky][Kx][2 = re, im], loc.w [C out][C in], loc.b [C];
+ * lift_r.w [C][2]; spec_r [C][C][n][n/2+1][2]; loc_r.w [C][C];
+ * spec_f [C][C][Ky][Kx][2]; loc_f.w [C][C]; proj.w [2][C].  Seeded initial
+ * weights. */
+npbs_status npbs_net_create_fno(npbs_net** out, int device, int n, int width, int modes, int layers,
+                                uint64_t seed);
 /* Create a network on `device` with seeded He-normal weights. */
 npbs_status npbs_net_create(npbs_net** out, int device, uint64_t seed);
 npbs_status npbs_net_destroy(npbs_net* net);

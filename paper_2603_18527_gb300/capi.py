@@ -86,6 +86,9 @@ _SIGS = {
     "cbs_apply_static": (C.c_int, [C.POINTER(npbs_batch), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
                                    C.c_void_p, C.c_void_p, C.c_char_p, C.c_int32]),
     "npbs_net_num_params": (C.c_int64, []),
+    "npbs_net_param_count": (C.c_int64, [C.c_void_p]),
+    "npbs_net_create_fno": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
+                                      C.c_uint64]),
     "npbs_net_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_uint64]),
     "npbs_net_destroy": (C.c_int, [C.c_void_p]),
     "npbs_net_set_params": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64]),
@@ -158,6 +161,20 @@ class Context:
     @property
     def handle(self):
         return self._h
+
+    @classmethod
+    def fno(cls, n: int, width: int = 25, modes: int = 45, layers: int = 3, device: int = 0,
+            seed: int = 0) -> "Net":
+        """An FNO network (App. Architectural Instantiations) for n x n grids."""
+        h = C.c_void_p()
+        st = lib().npbs_net_create_fno(C.byref(h), int(device), int(n), int(width), int(modes), int(layers),
+                                       C.c_uint64(seed))
+        if st != OK:
+            raise NpbsError(st, "npbs_net_create_fno failed")
+        return cls(device, handle=h)
+
+    def num_params(self) -> int:
+        return int(lib().npbs_net_param_count(self._h))
 
     def last_error(self) -> str:
         return lib().npbs_last_error(self._h).decode()
@@ -401,7 +418,7 @@ def npbs_net_num_params() -> int:
 
 
 class Net:
-    """An npbs_net (U-Net weights, gradients, AdamW moments) on one device."""
+    """An npbs_net (U-Net or FNO weights, gradients, AdamW moments) on one device."""
 
     def __init__(self, device: int = 0, seed: int = 0, handle=None):
         if handle is not None:
@@ -416,6 +433,20 @@ class Net:
     @property
     def handle(self):
         return self._h
+
+    @classmethod
+    def fno(cls, n: int, width: int = 25, modes: int = 45, layers: int = 3, device: int = 0,
+            seed: int = 0) -> "Net":
+        """An FNO network (App. Architectural Instantiations) for n x n grids."""
+        h = C.c_void_p()
+        st = lib().npbs_net_create_fno(C.byref(h), int(device), int(n), int(width), int(modes), int(layers),
+                                       C.c_uint64(seed))
+        if st != OK:
+            raise NpbsError(st, "npbs_net_create_fno failed")
+        return cls(device, handle=h)
+
+    def num_params(self) -> int:
+        return int(lib().npbs_net_param_count(self._h))
 
     @classmethod
     def load(cls, path: str, device: int = 0) -> "Net":
@@ -437,14 +468,14 @@ class Net:
             raise NpbsError(st, "npbs_net_set_params failed")
 
     def get_params(self) -> np.ndarray:
-        a = np.zeros(npbs_net_num_params(), np.float32)
+        a = np.zeros(self.num_params(), np.float32)
         st = lib().npbs_net_get_params(self._h, a.ctypes.data_as(C.c_void_p), a.size)
         if st != OK:
             raise NpbsError(st, "npbs_net_get_params failed")
         return a
 
     def get_grads(self) -> np.ndarray:
-        a = np.zeros(npbs_net_num_params(), np.float32)
+        a = np.zeros(self.num_params(), np.float32)
         st = lib().npbs_net_get_grads(self._h, a.ctypes.data_as(C.c_void_p), a.size)
         if st != OK:
             raise NpbsError(st, "npbs_net_get_grads failed")

@@ -1,0 +1,871 @@
+// The FNO residual-to-correction map (App. Architectural Instantiations, Eqs.
+// fno_impl, fno_lift, fno_proj, lfl, nlfl) on the GPU: forward, hand-written
+// adjoint and weight gradients, as a second kind of npbs_net.
+//
+//   M(r; a) = P( LFL_f[ NLFL_L(...NLFL_1(Phi(a))) * LFL_r(Psi(r)) ] )
+//   Phi(a) = W_a LayerNorm(a) + b_a,  Psi(r) = W_r [Re r, Im r],  P(z) = W_p z
+//   LFL(x) = irfft2(W^F * R(rfft2(x))) + W^loc x (+ b),  NLFL = GELU(LFL)
+//
+// Hyper-parameters of the paper's backbone: 25 channels, three NLFL layers,
+// 45 retained modes (rows with min(ky, N - ky) < 45, columns kx < 45 of the
+// half plane), the residual layer at full bandwidth (every row, kx = 0..N/2).
+//
+// Layout, per group of nb instances of one N x N grid: channel planes
+// [nb][C][N*N] float32; spectra of channel pairs [nb][P][N*N] complex64
+// (channel 2j in the real part and 2j + 1 in the imaginary part, so that one
+// complex FFT transforms two real channels); retained modes compact
+// [nb][C][Ky*Kx] complex64 (rows in FFT order, then columns).
+//
+// A spectral block y = irfft2(W * R(rfft2(x))) runs as: pack channel pairs,
+// 2D FFT (row and column kernels of radix-2/3/4/8 Stockham passes in shared
+// memory), extract the retained modes of each real channel
+// (X_a = (Z_k + conj Z_-k) / 2, X_b = (Z_k - conj Z_-k) / 2i), mix channels
+// per mode, complete the half plane to a Hermitian spectrum (on the kx = 0 and
+// N/2 columns the Hermitian part, which is all the real part of irfft2 keeps)
+// packed two channels per complex field, inverse 2D FFT, and an epilogue
+// (1/N^2, the 1x1 convolution, bias, GELU).  Its adjoint is the same pipeline
+// with the conjugate channel-transposed weights; the spectral weight gradient
+// is c_kx / N^2 sum_b G_o conj(X_i), c = 2 except on the kx = 0 and N/2
+// columns (c = 1).  The coefficient branch depends on a only; every call
+// recomputes it (activation checkpointing in the backward).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "fft.cuh"
+#include "net.cuh"
+
+namespace npbs {
+
+namespace {
+
+constexpr int kMaxC = 32;     // channel bound of the register-blocked kernels
+constexpr int kTile = 4096;   // complex elements of one FFT tile buffer (two per block)
+constexpr int kModesPerBlock = 8;
+
+int grid_of(long long n, int per = 256) { return (int)std::min<long long>((n + per - 1) / per, 152LL * 64); }
+
+// rows of the compact mode list for m retained modes: min(ky, n - ky) < m
+__host__ __device__ inline int rows_kept(int n, int m) {
+    int c = 0;
+    for (int k = 0; k < n; ++k) c += (k < n - k ? k : n - k) < m;
+    return c;
+}
+// compact row index of ky (-1 if not retained)
+__device__ __forceinline__ int row_index(int ky, int n, int m) {
+    if (2 * m - 1 >= n) return ky;
+    if (ky < m) return ky;
+    if (ky >= n - m + 1) return ky - (n - 2 * m + 1);
+    return -1;
+}
+// FFT-order row of compact row index ri
+__device__ __forceinline__ int row_of(int ri, int n, int m) {
+    if (2 * m - 1 >= n) return ri;
+    return ri < m ? ri : ri + (n - 2 * m + 1);
+}
+
+__device__ __forceinline__ float gelu_f(float x) { return 0.5f * x * (1.f + erff(x * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu_grad(float x) {
+    return 0.5f * (1.f + erff(x * 0.70710678118654752f)) + x * 0.39894228040143268f * expf(-0.5f * x * x);
+}
+
+// ------------------------------------------------------------- 2D FFT passes
+
+// rb rows of one field per block, the transform along each row
+template <int DIR>
+__global__ void __launch_bounds__(256) k_fft_rows(float2* data, int n, int rb, RadixPlan plan, const float2* tw) {
+    extern __shared__ __align__(16) float2 sm[];
+    const int nb = n / rb;
+    const long long field = blockIdx.x / nb;
+    float2* p = data + field * n * n + (long long)(blockIdx.x % nb) * rb * n;
+    const int cnt = rb * n;
+    for (int e = threadIdx.x; e < cnt; e += blockDim.x) sm[e] = p[e];
+    __syncthreads();
+    float2* res = fft_tile<float2, DIR, false>(sm, sm + kTile, plan, rb, 1, n, tw, threadIdx.x, blockDim.x);
+    for (int e = threadIdx.x; e < cnt; e += blockDim.x) p[e] = res[e];
+}
+
+// cb columns of one field per block, the transform along each column
+template <int DIR>
+__global__ void __launch_bounds__(256) k_fft_cols(float2* data, int n, int cb, RadixPlan plan, const float2* tw) {
+    extern __shared__ __align__(16) float2 sm[];
+    const int nb = n / cb;
+    const long long field = blockIdx.x / nb;
+    float2* p = data + field * n * n + (long long)(blockIdx.x % nb) * cb;
+    const int cnt = cb * n;
+    for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+        const int i = e / cb, b = e - i * cb;
+        sm[e] = p[(long long)i * n + b];
+    }
+    __syncthreads();
+    float2* res = fft_tile<float2, DIR, true>(sm, sm + kTile, plan, cb, cb, 1, tw, threadIdx.x, blockDim.x);
+    for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+        const int i = e / cb, b = e - i * cb;
+        p[(long long)i * n + b] = res[e];
+    }
+}
+
+int largest_divisor_at_most(int n, int lim) {
+    for (int d = std::min(n, lim); d >= 1; --d)
+        if (n % d == 0) return d;
+    return 1;
+}
+
+}  // namespace
+
+namespace {
+
+// ------------------------------------------------------------- pointwise kernels
+
+// LayerNorm statistics of each instance's coefficient field: mean and 1/sqrt(var + 1e-5)
+__global__ void k_ln_stats(SlotDev sd, const float* a, float* stats) {
+    __shared__ double s1[32], s2[32];
+    const float* p = a + sd.off[blockIdx.x];
+    double m = 0.0, q = 0.0;
+    for (long long e = threadIdx.x; e < sd.np; e += blockDim.x) {
+        const double v = p[e];
+        m += v;
+        q += v * v;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        m += __shfl_xor_sync(0xffffffffu, m, o);
+        q += __shfl_xor_sync(0xffffffffu, q, o);
+    }
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) { s1[w] = m; s2[w] = q; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a1 = 0.0, a2 = 0.0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) { a1 += s1[i]; a2 += s2[i]; }
+        const double mu = a1 / (double)sd.np;
+        const double var = fmax(a2 / (double)sd.np - mu * mu, 0.0);
+        stats[2 * blockIdx.x] = (float)mu;
+        stats[2 * blockIdx.x + 1] = (float)(1.0 / sqrt(var + 1e-5));
+    }
+}
+
+// z = LayerNorm(a) as a one-channel plane [nb][1][np]
+__global__ void k_ln_plane(SlotDev sd, const float* a, const float* stats, float* z) {
+    const long long tot = (long long)sd.nb * sd.np;
+    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < tot; g += (long long)gridDim.x * blockDim.x) {
+        const int b = (int)(g / sd.np);
+        const long long p = g - (long long)b * sd.np;
+        z[g] = (a[sd.off[b] + p] - stats[2 * b]) * stats[2 * b + 1];
+    }
+}
+
+// [Re r, Im r] (or [Re, Im] of any complex field at the batch offsets) as a two-channel plane
+__global__ void k_complex_planes(SlotDev sd, const float2* r, float* z) {
+    const long long tot = (long long)sd.nb * sd.np;
+    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < tot; g += (long long)gridDim.x * blockDim.x) {
+        const int b = (int)(g / sd.np);
+        const long long p = g - (long long)b * sd.np;
+        const float2 v = r[sd.off[b] + p];
+        z[((long long)b * 2) * sd.np + p] = v.x;
+        z[((long long)b * 2 + 1) * sd.np + p] = v.y;
+    }
+}
+
+// out[b][o][p] = sum_i M(o, i) x[b][i][p] + bias[o] (+ part of a spectral
+// result Z / N^2), pre-activation optionally kept, GELU optionally applied.
+// M(o, i) = w[o * so + i * si] (si = 1, so = Ci for the forward 1x1; swapped
+// strides give the transpose).  Z (nullable): channel o is the real (o even)
+// or imaginary (o odd) part of field o / 2 of [nb][ceil(Co/2)][np].
+__global__ void k_mix_points(int nb, long long np, const float* x, int Ci, const float* w, int so, int si,
+                             const float* bias, const float2* Z, float zscale, int Co, int act, float* pre,
+                             float* out, int add) {
+    const long long tot = (long long)nb * np;
+    const int Q = (Co + 1) / 2;
+    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < tot; g += (long long)gridDim.x * blockDim.x) {
+        const int b = (int)(g / np);
+        const long long p = g - (long long)b * np;
+        float xv[kMaxC];
+#pragma unroll
+        for (int i = 0; i < kMaxC; ++i)
+            if (i < Ci) xv[i] = x[((long long)b * Ci + i) * np + p];
+        for (int o = 0; o < Co; ++o) {
+            float s = bias ? bias[o] : 0.f;
+#pragma unroll
+            for (int i = 0; i < kMaxC; ++i)
+                if (i < Ci) s = fmaf(__ldg(w + o * so + i * si), xv[i], s);
+            if (Z) {
+                const float2 z = Z[((long long)b * Q + o / 2) * np + p];
+                s = fmaf((o & 1) ? z.y : z.x, zscale, s);
+            }
+            const long long oi = ((long long)b * Co + o) * np + p;
+            if (pre) pre[oi] = s;
+            const float v = act ? gelu_f(s) : s;
+            out[oi] = add ? out[oi] + v : v;
+        }
+    }
+}
+
+// pack real channel planes [nb][Ci][np] into complex pair fields [nb][P][np]
+__global__ void k_pack(int nb, long long np, const float* x, int Ci, float2* Z) {
+    const int P = (Ci + 1) / 2;
+    const long long tot = (long long)nb * P * np;
+    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < tot; g += (long long)gridDim.x * blockDim.x) {
+        const long long p = g % np;
+        const long long bj = g / np;
+        const int j = (int)(bj % P), b = (int)(bj / P);
+        const float re = x[((long long)b * Ci + 2 * j) * np + p];
+        const float im = 2 * j + 1 < Ci ? x[((long long)b * Ci + 2 * j + 1) * np + p] : 0.f;
+        Z[g] = make_float2(re, im);
+    }
+}
+
+// retained half-plane modes of each real channel from the pair spectra
+__global__ void k_extract(int nb, int n, int m, int Kx, int K, const float2* Z, int Ci, float2* X) {
+    const int P = (Ci + 1) / 2;
+    const long long np = (long long)n * n;
+    const long long tot = (long long)nb * Ci * K;
+    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < tot; g += (long long)gridDim.x * blockDim.x) {
+        const int k = (int)(g % K);
+        const long long bi = g / K;
+        const int i = (int)(bi % Ci), b = (int)(bi / Ci);
+        const int ky = row_of(k / Kx, n, m), kx = k % Kx;
+        const int my = (n - ky) % n, mx = (n - kx) % n;
+        const float2* f = Z + ((long long)b * P + i / 2) * np;
+        const float2 zk = f[(long long)ky * n + kx], zm = f[(long long)my * n + mx];
+        X[g] = (i & 1) ? make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x))
+                       : make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
+    }
+}
+
+// Channel mixing per retained mode: Y[b][o][k] = sum_i W[i][o][k] X[b][i][k]
+// (adj = 0, A = Ci inputs, Co outputs) or Y[b][i][k] = sum_o conj(W[i][o][k]) X[b][o][k]
+// (adj = 1, A = Co inputs, Ci outputs).  W is the canonical [Ci][Co][K] complex
+// block as (re, im) float pairs: its offset in the parameter vector may be odd,
+// so it is read as floats, never as float2.
+__global__ void k_mix_modes(int nb, int K, const float2* X, const float* W, int Ci, int Co, int adj, float2* Y) {
+    const int b = blockIdx.x % nb;
+    const int k = (blockIdx.x / nb) * blockDim.x + threadIdx.x;
+    if (k >= K) return;
+    const int A = adj ? Co : Ci, O = adj ? Ci : Co;
+    float2 acc[kMaxC];
+#pragma unroll
+    for (int o = 0; o < kMaxC; ++o) acc[o] = make_float2(0.f, 0.f);
+    for (int a = 0; a < A; ++a) {
+        const float2 x = X[((long long)b * A + a) * K + k];
+#pragma unroll
+        for (int o = 0; o < kMaxC; ++o) {
+            if (o < O) {
+                const long long wi = adj ? ((long long)o * Co + a) * K + k : ((long long)a * Co + o) * K + k;
+                float2 w = make_float2(__ldg(W + 2 * wi), __ldg(W + 2 * wi + 1));
+                if (adj) w.y = -w.y;
+                acc[o].x = fmaf(w.x, x.x, fmaf(-w.y, x.y, acc[o].x));
+                acc[o].y = fmaf(w.x, x.y, fmaf(w.y, x.x, acc[o].y));
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 0; o < kMaxC; ++o)
+        if (o < O) Y[((long long)b * O + o) * K + k] = acc[o];
+}
+
+// Hermitian completion of the retained half-plane spectra, two channels per
+// complex field: Z[b][q] = H(Y[b][2q]) + i H(Y[b][2q + 1]).
+__global__ void k_hermite(int nb, int n, int m, int Kx, int K, const float2* Y, int Co, float2* Z) {
+    const int Q = (Co + 1) / 2;
+    const long long np = (long long)n * n;
+    const long long tot = (long long)nb * Q * np;
+    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < tot; g += (long long)gridDim.x * blockDim.x) {
+        const long long p = g % np;
+        const long long bq = g / np;
+        const int q = (int)(bq % Q), b = (int)(bq / Q);
+        const int ky = (int)(p / n), kx = (int)(p % n);
+        const int mky = (n - ky) % n;
+        float2 h[2];
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+            const int c = 2 * q + t;
+            h[t] = make_float2(0.f, 0.f);
+            if (c >= Co) continue;
+            const float2* y = Y + ((long long)b * Co + c) * K;
+            auto at = [&](int yy, int xx) -> float2 {
+                const int ri = row_index(yy, n, m);
+                if (ri < 0 || xx >= Kx) return make_float2(0.f, 0.f);
+                return y[(long long)ri * Kx + xx];
+            };
+            if (kx == 0 || 2 * kx == n) {
+                const float2 u = at(ky, kx), v = at(mky, kx);
+                h[t] = make_float2(0.5f * (u.x + v.x), 0.5f * (u.y - v.y));
+            } else if (2 * kx < n) {
+                h[t] = at(ky, kx);
+            } else {
+                const float2 v = at(mky, n - kx);
+                h[t] = make_float2(v.x, -v.y);
+            }
+        }
+        Z[g] = make_float2(h[0].x - h[1].y, h[0].y + h[1].x);
+    }
+}
+
+// ------------------------------------------------------------- gradients
+
+// dW[i][o][k] += c_kx / n^2 sum_b G[b][o][k] conj(X[b][i][k]) for kModesPerBlock
+// modes per block, one thread per channel pair.
+__global__ void k_wgrad_modes(int nb, int n, int Kx, int K, const float2* G, const float2* X, int Ci, int Co,
+                              float* dW) {
+    __shared__ float2 xs[kMaxC][kModesPerBlock], gs[kMaxC][kModesPerBlock];
+    const int k0 = blockIdx.x * kModesPerBlock;
+    const int t = threadIdx.x;
+    const int i = t / Co, o = t - (t / Co) * Co;
+    const bool mine = t < Ci * Co;
+    float2 acc[kModesPerBlock];
+#pragma unroll
+    for (int q = 0; q < kModesPerBlock; ++q) acc[q] = make_float2(0.f, 0.f);
+    for (int b = 0; b < nb; ++b) {
+        for (int e = t; e < (Ci + Co) * kModesPerBlock; e += blockDim.x) {
+            const int c = e / kModesPerBlock, q = e - c * kModesPerBlock;
+            const int k = k0 + q;
+            if (c < Ci) xs[c][q] = k < K ? X[((long long)b * Ci + c) * K + k] : make_float2(0.f, 0.f);
+            else gs[c - Ci][q] = k < K ? G[((long long)b * Co + (c - Ci)) * K + k] : make_float2(0.f, 0.f);
+        }
+        __syncthreads();
+        if (mine) {
+#pragma unroll
+            for (int q = 0; q < kModesPerBlock; ++q) {
+                const float2 g = gs[o][q], x = xs[i][q];
+                acc[q].x = fmaf(g.x, x.x, fmaf(g.y, x.y, acc[q].x));
+                acc[q].y = fmaf(g.y, x.x, fmaf(-g.x, x.y, acc[q].y));
+            }
+        }
+        __syncthreads();
+    }
+    if (!mine) return;
+    const float inv = 1.f / ((float)n * (float)n);
+#pragma unroll
+    for (int q = 0; q < kModesPerBlock; ++q) {
+        const int k = k0 + q;
+        if (k >= K) break;
+        const int kx = k % Kx;
+        const float c = (kx == 0 || 2 * kx == n) ? inv : 2.f * inv;
+        float* w = dW + 2 * (((long long)i * Co + o) * K + k);  // (re, im) pairs, possibly odd offset
+        w[0] += c * acc[q].x;
+        w[1] += c * acc[q].y;
+    }
+}
+
+// 1x1 weight (and bias) gradients: dW[o][i] += sum_{b,p} G[b][o][p] X[b][i][p],
+// db[o] += sum G[b][o][p]; 32-pixel chunks staged in shared memory.
+constexpr int kPairsPerThread = 5;
+__global__ void __launch_bounds__(256) k_wgrad_points(int nb, long long np, const float* G, int Co, const float* X,
+                                                      int Ci, float* dW, float* db) {
+    __shared__ float gs[kMaxC][32], xs[kMaxC][32];
+    const int npair = Co * Ci + (db ? Co : 0);
+    float acc[kPairsPerThread];
+#pragma unroll
+    for (int q = 0; q < kPairsPerThread; ++q) acc[q] = 0.f;
+    const long long chunks = (long long)nb * np / 32;
+    for (long long ch = blockIdx.x; ch < chunks; ch += gridDim.x) {
+        const long long g0 = ch * 32;
+        const int b = (int)(g0 / np);
+        const long long p0 = g0 - (long long)b * np;
+        for (int e = threadIdx.x; e < (Co + Ci) * 32; e += blockDim.x) {
+            const int c = e >> 5, j = e & 31;
+            if (c < Co) gs[c][j] = G[((long long)b * Co + c) * np + p0 + j];
+            else xs[c - Co][j] = X ? X[((long long)b * Ci + (c - Co)) * np + p0 + j] : 0.f;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < kPairsPerThread; ++q) {
+            const int t = threadIdx.x + q * blockDim.x;
+            if (t < npair) {
+                float s = 0.f;
+                if (t < Co * Ci) {
+                    const int o = t / Ci, i = t - (t / Ci) * Ci;
+#pragma unroll 8
+                    for (int j = 0; j < 32; ++j) s = fmaf(gs[o][j], xs[i][j], s);
+                } else {
+                    const int o = t - Co * Ci;
+#pragma unroll 8
+                    for (int j = 0; j < 32; ++j) s += gs[o][j];
+                }
+                acc[q] += s;
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int q = 0; q < kPairsPerThread; ++q) {
+        const int t = threadIdx.x + q * blockDim.x;
+        if (t < npair) {
+            if (t < Co * Ci) atomicAdd(dW + t, acc[q]);
+            else atomicAdd(db + (t - Co * Ci), acc[q]);
+        }
+    }
+}
+
+__global__ void k_gelu_back(long long cnt, const float* dy, const float* pre, float* dx) {
+    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < cnt; g += (long long)gridDim.x * blockDim.x)
+        dx[g] = dy[g] * gelu_grad(pre[g]);
+}
+
+__global__ void k_mul(long long cnt, const float* a, const float* b, float* out) {
+    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < cnt; g += (long long)gridDim.x * blockDim.x)
+        out[g] = a[g] * b[g];
+}
+
+// z = c * x: dx = c * dz, dc = x * dz
+__global__ void k_mul_back(long long cnt, const float* dz, const float* c, const float* x, float* dx, float* dc) {
+    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < cnt; g += (long long)gridDim.x * blockDim.x) {
+        const float d = dz[g];
+        dx[g] = c[g] * d;
+        dc[g] = x[g] * d;
+    }
+}
+
+// out (complex, batch offsets) (+)= (sum_c w[0][c] z[c], sum_c w[1][c] z[c])
+__global__ void k_proj(SlotDev sd, const float* z, int C, const float* w, float2* out, int add) {
+    const long long tot = (long long)sd.nb * sd.np;
+    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < tot; g += (long long)gridDim.x * blockDim.x) {
+        const int b = (int)(g / sd.np);
+        const long long p = g - (long long)b * sd.np;
+        float re = 0.f, im = 0.f;
+        for (int c = 0; c < C; ++c) {
+            const float v = z[((long long)b * C + c) * sd.np + p];
+            re = fmaf(__ldg(w + c), v, re);
+            im = fmaf(__ldg(w + C + c), v, im);
+        }
+        float2* o = out + sd.off[b] + p;
+        *o = add ? make_float2(o->x + re, o->y + im) : make_float2(re, im);
+    }
+}
+
+// dz[b][c][p] = w[0][c] Re g + w[1][c] Im g
+__global__ void k_proj_back(SlotDev sd, const float2* gc, int C, const float* w, float* dz) {
+    const long long tot = (long long)sd.nb * sd.np;
+    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < tot; g += (long long)gridDim.x * blockDim.x) {
+        const int b = (int)(g / sd.np);
+        const long long p = g - (long long)b * sd.np;
+        const float2 v = gc[sd.off[b] + p];
+        for (int c = 0; c < C; ++c) dz[((long long)b * C + c) * sd.np + p] = fmaf(__ldg(w + c), v.x, __ldg(w + C + c) * v.y);
+    }
+}
+
+// gr (complex, batch offsets) (+)= (sum_c w[c][0] dx[c], sum_c w[c][1] dx[c])
+__global__ void k_lift_r_back(SlotDev sd, const float* dx, int C, const float* w, float2* gr, int add) {
+    const long long tot = (long long)sd.nb * sd.np;
+    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < tot; g += (long long)gridDim.x * blockDim.x) {
+        const int b = (int)(g / sd.np);
+        const long long p = g - (long long)b * sd.np;
+        float re = 0.f, im = 0.f;
+        for (int c = 0; c < C; ++c) {
+            const float v = dx[((long long)b * C + c) * sd.np + p];
+            re = fmaf(__ldg(w + 2 * c), v, re);
+            im = fmaf(__ldg(w + 2 * c + 1), v, im);
+        }
+        float2* o = gr + sd.off[b] + p;
+        *o = add ? make_float2(o->x + re, o->y + im) : make_float2(re, im);
+    }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------- host side
+
+static bool fno_radix_plan(int n, RadixPlan* p) {
+    if (n < 2 || n > kMaxN) return false;
+    p->n = n;
+    p->npass = 0;
+    int m = n;
+    while (m % 8 == 0) { p->radix[p->npass++] = 8; m /= 8; }
+    while (m % 4 == 0) { p->radix[p->npass++] = 4; m /= 4; }
+    while (m % 2 == 0) { p->radix[p->npass++] = 2; m /= 2; }
+    while (m % 3 == 0) { p->radix[p->npass++] = 3; m /= 3; }
+    return m == 1 && p->npass <= kMaxPass;
+}
+
+FnoDef fno_def(int n, int C, int m, int L) {
+    FnoDef d;
+    d.n = n;
+    d.C = C;
+    d.m = m;
+    d.L = L;
+    if (n < 2 || C < 1 || m < 1 || L < 0 || L > 8) return d;  // count stays 0: invalid
+    d.ky = rows_kept(n, m);
+    d.kx = std::min(m, n / 2 + 1);
+    d.fy = n;
+    d.fx = n / 2 + 1;
+    const long long spec = 2LL * C * C * d.ky * d.kx, full = 2LL * C * C * d.fy * d.fx;
+    long long o = 0;
+    d.lift_a_w = o; o += C;
+    d.lift_a_b = o; o += C;
+    for (int l = 0; l < L; ++l) {
+        d.spec[l] = o; o += spec;
+        d.loc_w[l] = o; o += (long long)C * C;
+        d.loc_b[l] = o; o += C;
+    }
+    d.lift_r = o; o += 2LL * C;
+    d.spec_r = o; o += full;
+    d.loc_r = o; o += (long long)C * C;
+    d.spec_f = o; o += spec;
+    d.loc_f = o; o += (long long)C * C;
+    d.proj = o; o += 2LL * C;
+    d.count = o;
+    return d;
+}
+
+namespace {
+
+// Workspace of one instance group (nb instances of the FNO's grid).
+struct FnoWS {
+    float* stats = nullptr;
+    float *lnp = nullptr, *rp = nullptr, *gp = nullptr;
+    float* c[9] = {};
+    float* pre[8] = {};
+    float *x0 = nullptr, *x1 = nullptr, *z = nullptr, *z1 = nullptr;
+    float *g1 = nullptr, *g2 = nullptr, *g3 = nullptr, *dc = nullptr;
+    float2 *Zp = nullptr, *Xc = nullptr, *Yc = nullptr, *Gc = nullptr;
+};
+
+size_t ws_layout(const FnoDef& d, int nb, bool train, FnoWS* w, char* base) {
+    const long long np = (long long)d.n * d.n;
+    const long long plane = (long long)nb * np;            // floats per channel-plane set
+    const long long K = std::max((long long)d.ky * d.kx, (long long)d.fy * d.fx);
+    const long long P = (d.C + 1) / 2;
+    size_t o = 0;
+    auto take = [&](size_t bytes) -> char* {
+        char* p = base ? base + o : nullptr;
+        o += (bytes + 255) & ~size_t(255);
+        return p;
+    };
+    auto f = [&](long long n) { return reinterpret_cast<float*>(take(sizeof(float) * n)); };
+    auto c2 = [&](long long n) { return reinterpret_cast<float2*>(take(sizeof(float2) * n)); };
+    FnoWS t;
+    t.stats = f(2LL * nb);
+    t.lnp = f(plane);
+    t.rp = f(2 * plane);
+    const int ncoef = train ? d.L + 1 : 2;
+    for (int l = 0; l < ncoef; ++l) t.c[l] = f(d.C * plane);
+    t.x0 = f(d.C * plane);
+    t.x1 = f(d.C * plane);
+    t.z = f(d.C * plane);
+    t.z1 = f(d.C * plane);
+    t.Zp = c2((long long)nb * P * np);
+    t.Xc = c2((long long)nb * d.C * K);
+    t.Yc = c2((long long)nb * d.C * K);
+    if (train) {
+        t.gp = f(2 * plane);
+        for (int l = 0; l < d.L; ++l) t.pre[l] = f(d.C * plane);
+        t.g1 = f(d.C * plane);
+        t.g2 = f(d.C * plane);
+        t.g3 = f(d.C * plane);
+        t.dc = f(d.C * plane);
+        t.Gc = c2((long long)nb * d.C * K);
+    }
+    if (w) *w = t;
+    return o;
+}
+
+// the coefficient activation after layer l (inference keeps two buffers)
+float* coef(const FnoWS& w, const FnoDef& d, int l, bool train) { return train ? w.c[l] : w.c[l & 1]; }
+
+cudaError_t fft2(const FnoDef& d, float2* Z, long long fields, int dir, cudaStream_t st) {
+    const int n = d.n;
+    const int rb = largest_divisor_at_most(n, kTile / n), cb = largest_divisor_at_most(n, std::min(16, kTile / n));
+    const size_t sm = 2 * kTile * sizeof(float2);
+    if (dir < 0) {
+        k_fft_rows<-1><<<(unsigned)(fields * (n / rb)), 256, sm, st>>>(Z, n, rb, d.plan, d.tw);
+        k_fft_cols<-1><<<(unsigned)(fields * (n / cb)), 256, sm, st>>>(Z, n, cb, d.plan, d.tw);
+    } else {
+        k_fft_rows<1><<<(unsigned)(fields * (n / rb)), 256, sm, st>>>(Z, n, rb, d.plan, d.tw);
+        k_fft_cols<1><<<(unsigned)(fields * (n / cb)), 256, sm, st>>>(Z, n, cb, d.plan, d.tw);
+    }
+    return cudaGetLastError();
+}
+
+// Retained-mode spectra of the real channel planes x [nb][Ci][np] into X [nb][Ci][K].
+cudaError_t spectra(const FnoDef& d, const FnoWS& w, int nb, const float* x, int Ci, int m, float2* X,
+                    cudaStream_t st, long long* kc) {
+    const long long np = (long long)d.n * d.n;
+    const int P = (Ci + 1) / 2;
+    const int Kx = std::min(m, d.n / 2 + 1), K = rows_kept(d.n, m) * Kx;
+    k_pack<<<grid_of((long long)nb * P * np), 256, 0, st>>>(nb, np, x, Ci, w.Zp);
+    cudaError_t e = fft2(d, w.Zp, (long long)nb * P, -1, st);
+    if (e != cudaSuccess) return e;
+    k_extract<<<grid_of((long long)nb * Ci * K), 256, 0, st>>>(nb, d.n, m, Kx, K, w.Zp, Ci, X);
+    *kc += 4;
+    return cudaGetLastError();
+}
+
+// out = act(irfft2(mix(Y)) / ... + M x + bias): Y [nb][Co][K] already mixed;
+// the local matrix M(o, i) = wl[o * so + i * si] acts on x [nb][Ci][np].
+cudaError_t synthesize(const FnoDef& d, const FnoWS& w, int nb, const float2* Y, int Co, int m, const float* x,
+                       int Ci, const float* wl, int so, int si, const float* bias, int act, float* pre, float* out,
+                       int add, cudaStream_t st, long long* kc) {
+    const long long np = (long long)d.n * d.n;
+    const int Q = (Co + 1) / 2;
+    const int Kx = std::min(m, d.n / 2 + 1), K = rows_kept(d.n, m) * Kx;
+    k_hermite<<<grid_of((long long)nb * Q * np), 256, 0, st>>>(nb, d.n, m, Kx, K, Y, Co, w.Zp);
+    cudaError_t e = fft2(d, w.Zp, (long long)nb * Q, 1, st);
+    if (e != cudaSuccess) return e;
+    k_mix_points<<<grid_of((long long)nb * np), 256, 0, st>>>(nb, np, x, Ci, wl, so, si, bias, w.Zp,
+                                                              1.f / (float)np, Co, act, pre, out, add);
+    *kc += 4;
+    return cudaGetLastError();
+}
+
+unsigned mix_grid(int nb, int K) { return (unsigned)(nb * ((K + 127) / 128)); }
+
+// One Fourier layer: out = act(irfft2(W * R(rfft2(x))) + W^loc x + b)
+cudaError_t layer_fwd(const FnoDef& d, const FnoWS& w, int nb, const float* x, const float* Wsp, int m,
+                      const float* wl, const float* bias, int act, float* pre, float* out, cudaStream_t st,
+                      long long* kc) {
+    const int C = d.C;
+    const int K = rows_kept(d.n, m) * std::min(m, d.n / 2 + 1);
+    cudaError_t e = spectra(d, w, nb, x, C, m, w.Xc, st, kc);
+    if (e != cudaSuccess) return e;
+    k_mix_modes<<<mix_grid(nb, K), 128, 0, st>>>(nb, K, w.Xc, Wsp, C, C, 0, w.Yc);
+    *kc += 1;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    return synthesize(d, w, nb, w.Yc, C, m, x, C, wl, C, 1, bias, act, pre, out, 0, st, kc);
+}
+
+// Backward of one Fourier layer from G = dL/d(pre-activation): accumulates the
+// spectral, local and bias gradients; dx = adjoint(G) (nullable).
+cudaError_t layer_bwd(const FnoDef& d, const FnoWS& w, int nb, const float* x, const float* Wsp, float* dWsp, int m,
+                      const float* wl, float* dwl, float* dbias, const float* G, float* dx, cudaStream_t st,
+                      long long* kc) {
+    const int C = d.C;
+    const long long np = (long long)d.n * d.n;
+    const int Kx = std::min(m, d.n / 2 + 1), K = rows_kept(d.n, m) * Kx;
+    cudaError_t e = spectra(d, w, nb, x, C, m, w.Xc, st, kc);
+    if (e == cudaSuccess) e = spectra(d, w, nb, G, C, m, w.Gc, st, kc);
+    if (e != cudaSuccess) return e;
+    const int thr = std::max(32, ((C * C + 31) / 32) * 32);
+    k_wgrad_modes<<<(K + kModesPerBlock - 1) / kModesPerBlock, thr, 0, st>>>(nb, d.n, Kx, K, w.Gc, w.Xc, C, C,
+                                                                             dWsp);
+    k_wgrad_points<<<304, 256, 0, st>>>(nb, np, G, C, x, C, dwl, dbias);
+    *kc += 2;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (!dx) return cudaSuccess;
+    k_mix_modes<<<mix_grid(nb, K), 128, 0, st>>>(nb, K, w.Gc, Wsp, C, C, 1, w.Yc);
+    *kc += 1;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    return synthesize(d, w, nb, w.Yc, C, m, G, C, wl, 1, C, nullptr, 0, nullptr, dx, 0, st, kc);
+}
+
+// The forward of one group, keeping every activation when `train`.
+cudaError_t forward_group(const FnoDef& d, const float* P, const FnoWS& w, const SlotDev& sd, const float2* r,
+                          const float* a, float2* out, int add, bool train, cudaStream_t st, long long* kc) {
+    const int C = d.C, nb = sd.nb;
+    const long long np = sd.np;
+    k_ln_stats<<<nb, 256, 0, st>>>(sd, a, w.stats);
+    k_ln_plane<<<grid_of((long long)nb * np), 256, 0, st>>>(sd, a, w.stats, w.lnp);
+    k_mix_points<<<grid_of((long long)nb * np), 256, 0, st>>>(nb, np, w.lnp, 1, P + d.lift_a_w, 1, 1, P + d.lift_a_b,
+                                                              nullptr, 0.f, C, 0, nullptr, coef(w, d, 0, train), 0);
+    *kc += 3;
+    cudaError_t e = cudaGetLastError();
+    for (int l = 0; l < d.L && e == cudaSuccess; ++l)
+        e = layer_fwd(d, w, nb, coef(w, d, l, train), P + d.spec[l], d.m, P + d.loc_w[l], P + d.loc_b[l], 1,
+                      train ? w.pre[l] : nullptr, coef(w, d, l + 1, train), st, kc);
+    if (e != cudaSuccess) return e;
+    k_complex_planes<<<grid_of((long long)nb * np), 256, 0, st>>>(sd, r, w.rp);
+    k_mix_points<<<grid_of((long long)nb * np), 256, 0, st>>>(nb, np, w.rp, 2, P + d.lift_r, 2, 1, nullptr, nullptr,
+                                                              0.f, C, 0, nullptr, w.x0, 0);
+    *kc += 2;
+    e = layer_fwd(d, w, nb, w.x0, P + d.spec_r, d.fx, P + d.loc_r, nullptr, 0, nullptr, w.x1, st, kc);
+    if (e != cudaSuccess) return e;
+    k_mul<<<grid_of((long long)nb * C * np), 256, 0, st>>>((long long)nb * C * np, coef(w, d, d.L, train), w.x1, w.z);
+    *kc += 1;
+    e = layer_fwd(d, w, nb, w.z, P + d.spec_f, d.m, P + d.loc_f, nullptr, 0, nullptr, w.z1, st, kc);
+    if (e != cudaSuccess) return e;
+    if (!out) return cudaSuccess;  // a recomputation for the backward needs the activations only
+    k_proj<<<grid_of((long long)nb * np), 256, 0, st>>>(sd, w.z1, C, P + d.proj, out, add);
+    *kc += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t set_fft_attrs() {
+    const int sm = (int)(2 * kTile * sizeof(float2));
+    cudaError_t e = cudaFuncSetAttribute(k_fft_rows<-1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_fft_rows<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_fft_cols<-1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_fft_cols<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    return e;
+}
+
+}  // namespace
+
+npbs_status fno_prepare(npbs_ctx* ctx, const FnoDef& d, const Plan& pl, const std::vector<int>& which, bool train,
+                        NetRun* run, cudaStream_t st) {
+    run->groups.clear();
+    run->train = train;
+    std::vector<long long> off;
+    for (int j : which) {
+        const InstDev& in = pl.inst_h[j];
+        if (in.nx != d.n || in.ny != d.n) {
+            char buf[128];
+            snprintf(buf, sizeof buf, "FNO network: instance %d is %d x %d, the network's grid is %d x %d", j, in.ny,
+                     in.nx, d.n, d.n);
+            return set_err(ctx, NPBS_ERR_UNSUPPORTED_SIZE, buf);
+        }
+        off.push_back(in.offset);
+    }
+    if (off.empty()) return NPBS_OK;
+    NPBS_CK(ctx, set_fft_attrs());
+    NPBS_CK(ctx, ctx->net_ws.ensure(ws_layout(d, (int)off.size(), train, nullptr, nullptr)));
+    NPBS_CK(ctx, ctx->work[5].ensure(sizeof(long long) * off.size()));
+    long long* doff = static_cast<long long*>(ctx->work[5].p);
+    NPBS_CK(ctx, cudaMemcpyAsync(doff, off.data(), sizeof(long long) * off.size(), cudaMemcpyHostToDevice, st));
+    NPBS_CK(ctx, cudaStreamSynchronize(st));
+    NetGroup g;
+    g.H = g.W = d.n;
+    g.sd.nb = (int)off.size();
+    g.sd.np = (long long)d.n * d.n;
+    g.sd.off = doff;
+    run->groups.push_back(g);
+    return NPBS_OK;
+}
+
+npbs_status fno_run_forward(npbs_ctx* ctx, const Net& net, const NetRun& run, const float2* r, const float* a,
+                            float2* out, int add, cudaStream_t st) {
+    const FnoDef& d = *net.fno;
+    for (const NetGroup& g : run.groups) {
+        FnoWS w;
+        ws_layout(d, g.sd.nb, run.train, &w, static_cast<char*>(ctx->net_ws.p));
+        long long kc = 0;
+        NPBS_CK(ctx, forward_group(d, net.params, w, g.sd, r, a, out, add, run.train, st, &kc));
+        ctx->count(st, kc);
+    }
+    return NPBS_OK;
+}
+
+// Backward of out = M(r; a): recomputes the forward keeping every activation,
+// accumulates d<gc, M(r; a)>/dtheta into net.grads and writes (or adds) gr.
+npbs_status fno_run_backward(npbs_ctx* ctx, Net& net, const NetRun& run, const float2* r, const float* a,
+                             const float2* gc, float2* gr, int add, cudaStream_t st) {
+    const FnoDef& d = *net.fno;
+    const int C = d.C;
+    const float* P = net.params;
+    float* dP = net.grads;
+    for (const NetGroup& g : run.groups) {
+        FnoWS w;
+        ws_layout(d, g.sd.nb, true, &w, static_cast<char*>(ctx->net_ws.p));
+        const SlotDev sd = g.sd;
+        const int nb = sd.nb;
+        const long long np = sd.np, cnt = (long long)nb * C * np;
+        long long kc = 0;
+        NPBS_CK(ctx, forward_group(d, P, w, sd, r, a, nullptr, 0, true, st, &kc));
+        // projection
+        k_complex_planes<<<grid_of((long long)nb * np), 256, 0, st>>>(sd, gc, w.gp);
+        k_wgrad_points<<<304, 256, 0, st>>>(nb, np, w.gp, 2, w.z1, C, dP + d.proj, nullptr);
+        k_proj_back<<<grid_of((long long)nb * np), 256, 0, st>>>(sd, gc, C, P + d.proj, w.g1);
+        kc += 3;
+        NPBS_CK(ctx, cudaGetLastError());
+        // fusion layer, then the product
+        NPBS_CK(ctx, layer_bwd(d, w, nb, w.z, P + d.spec_f, dP + d.spec_f, d.m, P + d.loc_f, dP + d.loc_f, nullptr,
+                               w.g1, w.g2, st, &kc));
+        k_mul_back<<<grid_of(cnt), 256, 0, st>>>(cnt, w.g2, w.c[d.L], w.x1, w.g1, w.dc);
+        kc += 1;
+        // residual layer and the lifting of r
+        NPBS_CK(ctx, layer_bwd(d, w, nb, w.x0, P + d.spec_r, dP + d.spec_r, d.fx, P + d.loc_r, dP + d.loc_r,
+                               nullptr, w.g1, w.g3, st, &kc));
+        k_wgrad_points<<<304, 256, 0, st>>>(nb, np, w.g3, C, w.rp, 2, dP + d.lift_r, nullptr);
+        k_lift_r_back<<<grid_of((long long)nb * np), 256, 0, st>>>(sd, w.g3, C, P + d.lift_r, gr, add);
+        kc += 2;
+        NPBS_CK(ctx, cudaGetLastError());
+        // coefficient branch, last NLFL first
+        for (int l = d.L - 1; l >= 0; --l) {
+            k_gelu_back<<<grid_of(cnt), 256, 0, st>>>(cnt, w.dc, w.pre[l], w.g1);
+            kc += 1;
+            NPBS_CK(ctx, layer_bwd(d, w, nb, w.c[l], P + d.spec[l], dP + d.spec[l], d.m, P + d.loc_w[l],
+                                   dP + d.loc_w[l], dP + d.loc_b[l], w.g1, w.dc, st, &kc));
+        }
+        k_wgrad_points<<<304, 256, 0, st>>>(nb, np, w.dc, C, w.lnp, 1, dP + d.lift_a_w, dP + d.lift_a_b);
+        kc += 1;
+        NPBS_CK(ctx, cudaGetLastError());
+        ctx->count(st, kc);
+    }
+    return NPBS_OK;
+}
+
+}  // namespace npbs
+
+using namespace npbs;
+
+extern "C" {
+
+npbs_status npbs_net_create_fno(npbs_net** out, int device, int n, int width, int modes, int layers, uint64_t seed) {
+    if (!out) return NPBS_ERR_INVALID_ARG;
+    *out = nullptr;
+    RadixPlan plan;
+    if (n < 4 || n % 2 || !fno_radix_plan(n, &plan) || width < 1 || width > kMaxC || layers < 0 || layers > 8 ||
+        modes < 1 || modes > n / 2 + 1)
+        return NPBS_ERR_INVALID_ARG;
+    if (cudaSetDevice(device) != cudaSuccess) return NPBS_ERR_INVALID_ARG;
+    Net* net = new (std::nothrow) Net();
+    if (!net) return NPBS_ERR_OOM;
+    net->device = device;
+    net->fno = new (std::nothrow) FnoDef(fno_def(n, width, modes, layers));
+    if (!net->fno || net->fno->count <= 0) {
+        delete net;
+        return NPBS_ERR_OOM;
+    }
+    FnoDef& d = *net->fno;
+    d.plan = plan;
+    const long long P = d.count;
+    std::vector<float2> tw(n);
+    for (int k = 0; k < n; ++k) {
+        const double ang = -2.0 * M_PI * (double)k / (double)n;
+        tw[k] = make_float2((float)std::cos(ang), (float)std::sin(ang));
+    }
+    bool ok = cudaMalloc(&net->params, sizeof(float) * P) == cudaSuccess &&
+              cudaMalloc(&net->grads, sizeof(float) * P) == cudaSuccess &&
+              cudaMalloc(&net->m1, sizeof(float) * P) == cudaSuccess &&
+              cudaMalloc(&net->m2, sizeof(float) * P) == cudaSuccess &&
+              cudaMalloc(&d.tw, sizeof(float2) * n) == cudaSuccess;
+    if (!ok) {
+        delete net;
+        return NPBS_ERR_OOM;
+    }
+    // seeded initial parameters: 1x1 weights uniform in +-1/sqrt(fan_in),
+    // spectral weights uniform in [0, 1/C^2) for both parts, biases zero
+    std::vector<float> h(P, 0.f);
+    uint64_t s = seed * 0x9E3779B97F4A7C15ull + 0x632BE59BD9B4E019ull;
+    auto uni = [&]() {
+        s ^= s << 13;
+        s ^= s >> 7;
+        s ^= s << 17;
+        return (double)(s >> 11) * (1.0 / 9007199254740992.0);
+    };
+    auto fill_w = [&](long long o, long long cnt, int fan_in) {
+        const double b = 1.0 / std::sqrt((double)fan_in);
+        for (long long i = 0; i < cnt; ++i) h[o + i] = (float)((2.0 * uni() - 1.0) * b);
+    };
+    auto fill_s = [&](long long o, long long cnt) {
+        for (long long i = 0; i < cnt; ++i) h[o + i] = (float)(uni() / (double)(width * width));
+    };
+    const long long spec = 2LL * width * width * d.ky * d.kx, full = 2LL * width * width * d.fy * d.fx;
+    fill_w(d.lift_a_w, width, 1);
+    for (int l = 0; l < layers; ++l) {
+        fill_s(d.spec[l], spec);
+        fill_w(d.loc_w[l], (long long)width * width, width);
+    }
+    fill_w(d.lift_r, 2LL * width, 2);
+    fill_s(d.spec_r, full);
+    fill_w(d.loc_r, (long long)width * width, width);
+    fill_s(d.spec_f, spec);
+    fill_w(d.loc_f, (long long)width * width, width);
+    fill_w(d.proj, 2LL * width, width);
+    ok = cudaMemcpy(net->params, h.data(), sizeof(float) * P, cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMemset(net->grads, 0, sizeof(float) * P) == cudaSuccess &&
+         cudaMemset(net->m1, 0, sizeof(float) * P) == cudaSuccess &&
+         cudaMemset(net->m2, 0, sizeof(float) * P) == cudaSuccess &&
+         cudaMemcpy(d.tw, tw.data(), sizeof(float2) * n, cudaMemcpyHostToDevice) == cudaSuccess;
+    if (!ok) {
+        delete net;
+        return NPBS_ERR_CUDA;
+    }
+    *out = reinterpret_cast<npbs_net*>(net);
+    return NPBS_OK;
+}
+
+int64_t npbs_net_param_count(const npbs_net* net) {
+    return net ? (int64_t)reinterpret_cast<const Net*>(net)->count() : -1;
+}
+
+}  // extern "C"

@@ -20,11 +20,29 @@ const std::vector<LayerDef>& layer_defs();
 long long dev_param_count();
 long long canon_param_count();
 
-// Weights, gradients and AdamW moments on one device (device layout: per conv
-// [Cout][9][Cin_pad] then bias, then the 2 x 32 head).
+// Shape and canonical parameter offsets of an FNO map (fno.cu): square N x N
+// grids, C hidden channels, m retained modes of the NLFL and fusion layers
+// (Ky x Kx of them), the full-bandwidth residual layer (Fy x Fx modes).
+struct FnoDef {
+    int n = 0, C = 0, m = 0, L = 0;
+    int ky = 0, kx = 0, fy = 0, fx = 0;
+    long long lift_a_w = 0, lift_a_b = 0;
+    long long spec[8] = {}, loc_w[8] = {}, loc_b[8] = {};
+    long long lift_r = 0, spec_r = 0, loc_r = 0, spec_f = 0, loc_f = 0, proj = 0;
+    long long count = 0;
+    float2* tw = nullptr;  // device W_N^k = exp(-2 pi i k / N), k < N
+    RadixPlan plan{};
+};
+FnoDef fno_def(int n, int C, int m, int L);
+
+// Weights, gradients and AdamW moments on one device (U-Net device layout: per
+// conv [Cout][9][Cin_pad] then bias, then the 2 x 32 head; an FNO keeps the
+// canonical order of its parameters).
 struct Net {
     int device = 0;
     long long step = 0;
+    FnoDef* fno = nullptr;  // non-null: this network is the FNO map of fno.cu
+    long long count() const { return fno ? fno->count : dev_param_count(); }
     float* params = nullptr;
     float* grads = nullptr;
     float* m1 = nullptr;
@@ -58,8 +76,16 @@ struct NetRun {
     bool train = false;
 };
 
-npbs_status net_prepare(npbs_ctx* ctx, const Plan& pl, const std::vector<int>& which, bool train, NetRun* run,
-                        cudaStream_t st);
+npbs_status net_prepare(npbs_ctx* ctx, const Net& net, const Plan& pl, const std::vector<int>& which, bool train,
+                        NetRun* run, cudaStream_t st);
+
+// The FNO counterparts (fno.cu), called by the net_* functions for an FNO network.
+npbs_status fno_prepare(npbs_ctx* ctx, const FnoDef& d, const Plan& pl, const std::vector<int>& which, bool train,
+                        NetRun* run, cudaStream_t st);
+npbs_status fno_run_forward(npbs_ctx* ctx, const Net& net, const NetRun& run, const float2* r, const float* a,
+                            float2* out, int add, cudaStream_t st);
+npbs_status fno_run_backward(npbs_ctx* ctx, Net& net, const NetRun& run, const float2* r, const float* a,
+                             const float2* gc, float2* gr, int add, cudaStream_t st);
 // out = M(r) (add = 0) or out += M(r) (add = 1)
 npbs_status net_run_forward(npbs_ctx* ctx, const Net& net, const NetRun& run, const float2* r, const float* n,
                             float2* out, int add, cudaStream_t st);

@@ -135,9 +135,9 @@ extern "C" npbs_status npbs_train_step_loss(npbs_ctx* ctx, npbs_net* net, const 
     std::vector<int> which(cnt);
     for (int j = 0; j < cnt; ++j) which[j] = j;
     NetRun run;
-    st = net_prepare(ctx, *pl, which, true, &run, s);
+    st = net_prepare(ctx, N, *pl, which, true, &run, s);
     if (st != NPBS_OK) return st;
-    NPBS_CK(ctx, cudaMemsetAsync(N.grads, 0, sizeof(float) * dev_param_count(), s));
+    NPBS_CK(ctx, cudaMemsetAsync(N.grads, 0, sizeof(float) * N.count(), s));
     NPBS_CK(ctx, cudaMemsetAsync(nk2, 0, sizeof(double) * cnt * U, s));
 
     // forward: r_0 and the unrolled residuals
@@ -237,9 +237,9 @@ static npbs_status train_step_euclid(npbs_ctx* ctx, Net& N, const Plan* pl, cons
     std::vector<int> which(cnt);
     for (int j = 0; j < cnt; ++j) which[j] = j;
     NetRun run;
-    st = net_prepare(ctx, *pl, which, true, &run, s);
+    st = net_prepare(ctx, N, *pl, which, true, &run, s);
     if (st != NPBS_OK) return st;
-    NPBS_CK(ctx, cudaMemsetAsync(N.grads, 0, sizeof(float) * dev_param_count(), s));
+    NPBS_CK(ctx, cudaMemsetAsync(N.grads, 0, sizeof(float) * N.count(), s));
     NPBS_CK(ctx, cudaMemsetAsync(nk2, 0, sizeof(double) * cnt * U, s));
     NPBS_CK(ctx, cudaMemsetAsync(zero, 0, sizeof(float2) * ext, s));
     // out = f_in - A x (TRUE_RESIDUAL); with f_in = 0 it is -A x

@@ -533,6 +533,10 @@ Net::~Net() {
     cudaFree(wb);
     cudaFree(wt);
     cudaFree(wsub);
+    if (fno) {
+        cudaFree(fno->tw);
+        delete fno;
+    }
 }
 
 cudaError_t Net::refresh_bf16(cudaStream_t st) const {
@@ -722,8 +726,9 @@ static std::map<std::pair<int, int>, std::vector<int>> group(const Plan& pl, con
     return g;
 }
 
-npbs_status net_prepare(npbs_ctx* ctx, const Plan& pl, const std::vector<int>& which, bool train, NetRun* run,
-                        cudaStream_t st) {
+npbs_status net_prepare(npbs_ctx* ctx, const Net& net, const Plan& pl, const std::vector<int>& which, bool train,
+                        NetRun* run, cudaStream_t st) {
+    if (net.fno) return fno_prepare(ctx, *net.fno, pl, which, train, run, st);
     run->groups.clear();
     run->train = train;
     auto gr = group(pl, which);
@@ -763,6 +768,7 @@ static Acts acts_of(npbs_ctx* ctx, const NetGroup& g, bool train) {
 
 npbs_status net_run_forward(npbs_ctx* ctx, const Net& net, const NetRun& run, const float2* r, const float* n,
                             float2* out, int add, cudaStream_t st) {
+    if (net.fno) return fno_run_forward(ctx, net, run, r, n, out, add, st);
     for (const NetGroup& g : run.groups) {
         Acts A = acts_of(ctx, g, false);
         const SlotDev sd = g.sd;
@@ -782,6 +788,7 @@ npbs_status net_run_forward(npbs_ctx* ctx, const Net& net, const NetRun& run, co
 npbs_status net_run_backward(npbs_ctx* ctx, Net& net, const NetRun& run, const float2* r, const float* n,
                              const float2* gc, float2* gr, int add, cudaStream_t st) {
     if (!run.train) return set_err(ctx, NPBS_ERR_INVALID_ARG, "network backward needs a training preparation");
+    if (net.fno) return fno_run_backward(ctx, net, run, r, n, gc, gr, add, st);
     const int ch[4] = {32, 64, 128, 256};
     const auto& defs = layer_defs();
     for (const NetGroup& grp : run.groups) {
@@ -945,9 +952,13 @@ npbs_status net_adamw(npbs_ctx* ctx, Net& net, float lr, float wd, cudaStream_t 
     net.step += 1;
     const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
     const float bc1 = 1.f - std::pow(b1, (float)net.step), bc2 = 1.f - std::pow(b2, (float)net.step);
-    const long long P = dev_param_count();
+    const long long P = net.count();
     k_adamw<<<grid_for(P), 256, 0, st>>>(P, net.params, net.grads, net.m1, net.m2, lr, b1, b2, eps, wd, bc1, bc2);
     NPBS_CK(ctx, cudaGetLastError());
+    if (net.fno) {
+        ctx->count(st, 1);
+        return NPBS_OK;
+    }
     NPBS_CK(ctx, net.refresh_bf16(st));
     ctx->count(st, 1 + (long long)layer_defs().size());
     return NPBS_OK;
@@ -1014,7 +1025,12 @@ npbs_status npbs_net_destroy(npbs_net* net) {
     return NPBS_OK;
 }
 
-static npbs_status copy_out(const float* dev, float* host, int64_t n) {
+static npbs_status copy_out(const Net& N, const float* dev, float* host, int64_t n) {
+    if (N.fno) {
+        if (!dev || !host || n != (int64_t)N.fno->count) return NPBS_ERR_INVALID_ARG;
+        return cudaMemcpy(host, dev, sizeof(float) * n, cudaMemcpyDeviceToHost) == cudaSuccess ? NPBS_OK
+                                                                                               : NPBS_ERR_CUDA;
+    }
     if (!dev || !host || n != (int64_t)canon_param_count()) return NPBS_ERR_INVALID_ARG;
     std::vector<float> dv(dev_param_count());
     if (cudaMemcpy(dv.data(), dev, sizeof(float) * dv.size(), cudaMemcpyDeviceToHost) != cudaSuccess)
@@ -1024,9 +1040,15 @@ static npbs_status copy_out(const float* dev, float* host, int64_t n) {
 }
 
 npbs_status npbs_net_set_params(npbs_net* net, const float* host, int64_t n) {
-    if (!net || !host || n != (int64_t)canon_param_count()) return NPBS_ERR_INVALID_ARG;
+    if (!net || !host) return NPBS_ERR_INVALID_ARG;
     Net* N = reinterpret_cast<Net*>(net);
     cudaSetDevice(N->device);
+    if (N->fno) {
+        if (n != (int64_t)N->fno->count) return NPBS_ERR_INVALID_ARG;
+        return cudaMemcpy(N->params, host, sizeof(float) * n, cudaMemcpyHostToDevice) == cudaSuccess ? NPBS_OK
+                                                                                                      : NPBS_ERR_CUDA;
+    }
+    if (n != (int64_t)canon_param_count()) return NPBS_ERR_INVALID_ARG;
     std::vector<float> dv;
     canon_to_dev(host, dv);
     if (cudaMemcpy(N->params, dv.data(), sizeof(float) * dv.size(), cudaMemcpyHostToDevice) != cudaSuccess)
@@ -1039,20 +1061,20 @@ npbs_status npbs_net_get_params(const npbs_net* net, float* host, int64_t n) {
     if (!net) return NPBS_ERR_INVALID_ARG;
     const Net* N = reinterpret_cast<const Net*>(net);
     cudaSetDevice(N->device);
-    return copy_out(N->params, host, n);
+    return copy_out(*N, N->params, host, n);
 }
 
 npbs_status npbs_net_get_grads(const npbs_net* net, float* host, int64_t n) {
     if (!net) return NPBS_ERR_INVALID_ARG;
     const Net* N = reinterpret_cast<const Net*>(net);
     cudaSetDevice(N->device);
-    return copy_out(N->grads, host, n);
+    return copy_out(*N, N->grads, host, n);
 }
 
 npbs_status npbs_net_zero_grad(npbs_net* net, npbs_stream stream) {
     if (!net) return NPBS_ERR_INVALID_ARG;
     Net* N = reinterpret_cast<Net*>(net);
-    if (cudaMemsetAsync(N->grads, 0, sizeof(float) * dev_param_count(), reinterpret_cast<cudaStream_t>(stream)) !=
+    if (cudaMemsetAsync(N->grads, 0, sizeof(float) * N->count(), reinterpret_cast<cudaStream_t>(stream)) !=
         cudaSuccess)
         return NPBS_ERR_CUDA;
     return NPBS_OK;
@@ -1068,7 +1090,7 @@ npbs_status npbs_net_save(const npbs_net* net, const char* path) {
     if (!net || !path) return NPBS_ERR_INVALID_ARG;
     const Net* N = reinterpret_cast<const Net*>(net);
     cudaSetDevice(N->device);
-    const long long P = dev_param_count();
+    const long long P = N->count();
     std::vector<float> buf(3 * P);
     if (cudaMemcpy(buf.data(), N->params, sizeof(float) * P, cudaMemcpyDeviceToHost) != cudaSuccess ||
         cudaMemcpy(buf.data() + P, N->m1, sizeof(float) * P, cudaMemcpyDeviceToHost) != cudaSuccess ||
@@ -1076,9 +1098,13 @@ npbs_status npbs_net_save(const npbs_net* net, const char* path) {
         return NPBS_ERR_CUDA;
     FILE* f = fopen(path, "wb");
     if (!f) return NPBS_ERR_INVALID_ARG;
-    const char magic[8] = {'N', 'P', 'B', 'S', 'N', 'E', 'T', '1'};
+    // an FNO file carries its shape (n, width, modes, layers) after the magic
+    const char magic[8] = {'N', 'P', 'B', 'S', N->fno ? 'F' : 'N', N->fno ? 'N' : 'E', N->fno ? 'O' : 'T', '1'};
     const long long hdr[2] = {N->step, P};
-    bool ok = fwrite(magic, 1, 8, f) == 8 && fwrite(hdr, sizeof(long long), 2, f) == 2 &&
+    const int shape[4] = {N->fno ? N->fno->n : 0, N->fno ? N->fno->C : 0, N->fno ? N->fno->m : 0,
+                          N->fno ? N->fno->L : 0};
+    bool ok = fwrite(magic, 1, 8, f) == 8 && (!N->fno || fwrite(shape, sizeof(int), 4, f) == 4) &&
+              fwrite(hdr, sizeof(long long), 2, f) == 2 &&
               fwrite(buf.data(), sizeof(float), buf.size(), f) == buf.size();
     ok = (fclose(f) == 0) && ok;
     return ok ? NPBS_OK : NPBS_ERR_INVALID_ARG;
@@ -1091,21 +1117,28 @@ npbs_status npbs_net_load(npbs_net** out, int device, const char* path) {
     if (!f) return NPBS_ERR_INVALID_ARG;
     char magic[8];
     long long hdr[2];
-    const long long P = dev_param_count();
-    std::vector<float> buf(3 * P);
-    bool ok = fread(magic, 1, 8, f) == 8 && memcmp(magic, "NPBSNET1", 8) == 0 && fread(hdr, sizeof(long long), 2, f) == 2 &&
-              hdr[1] == P && fread(buf.data(), sizeof(float), buf.size(), f) == buf.size();
+    int shape[4] = {0, 0, 0, 0};
+    bool ok = fread(magic, 1, 8, f) == 8;
+    const bool is_fno = ok && memcmp(magic, "NPBSFNO1", 8) == 0;
+    ok = ok && (is_fno || memcmp(magic, "NPBSNET1", 8) == 0);
+    if (ok && is_fno) ok = fread(shape, sizeof(int), 4, f) == 4 && shape[0] > 0 && shape[0] <= kMaxN;
+    long long P = 0;
+    if (ok) P = is_fno ? fno_def(shape[0], shape[1], shape[2], shape[3]).count : dev_param_count();
+    ok = ok && P > 0 && fread(hdr, sizeof(long long), 2, f) == 2 && hdr[1] == P;
+    std::vector<float> buf(ok ? 3 * P : 0);
+    ok = ok && fread(buf.data(), sizeof(float), buf.size(), f) == buf.size();
     fclose(f);
     if (!ok) return NPBS_ERR_INVALID_ARG;
     npbs_net* h = nullptr;
-    npbs_status st = npbs_net_create(&h, device, 0);
+    npbs_status st = is_fno ? npbs_net_create_fno(&h, device, shape[0], shape[1], shape[2], shape[3], 0)
+                            : npbs_net_create(&h, device, 0);
     if (st != NPBS_OK) return st;
     Net* N = reinterpret_cast<Net*>(h);
     N->step = hdr[0];
     if (cudaMemcpy(N->params, buf.data(), sizeof(float) * P, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(N->m1, buf.data() + P, sizeof(float) * P, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(N->m2, buf.data() + 2 * P, sizeof(float) * P, cudaMemcpyHostToDevice) != cudaSuccess ||
-        N->refresh_bf16(nullptr) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) {
+        (!N->fno && N->refresh_bf16(nullptr) != cudaSuccess) || cudaDeviceSynchronize() != cudaSuccess) {
         npbs_net_destroy(h);
         return NPBS_ERR_CUDA;
     }
@@ -1134,7 +1167,7 @@ npbs_status npbs_net_forward(npbs_ctx* ctx, const npbs_net* net, const npbs_batc
     if (!r || !n || !c_out) return set_err(ctx, NPBS_ERR_INVALID_ARG, "npbs_net_forward: NULL field pointer");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     NetRun run;
-    st = net_prepare(ctx, *pl, which, false, &run, s);
+    st = net_prepare(ctx, *reinterpret_cast<const Net*>(net), *pl, which, false, &run, s);
     if (st != NPBS_OK) return st;
     return net_run_forward(ctx, *reinterpret_cast<const Net*>(net), run, static_cast<const float2*>(r), n,
                            static_cast<float2*>(c_out), 0, s);
@@ -1151,7 +1184,7 @@ npbs_status npbs_net_backward(npbs_ctx* ctx, npbs_net* net, const npbs_batch* ba
         return set_err(ctx, NPBS_ERR_INVALID_ARG, "npbs_net_backward: NULL field pointer");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     NetRun run;
-    st = net_prepare(ctx, *pl, which, true, &run, s);
+    st = net_prepare(ctx, *reinterpret_cast<const Net*>(net), *pl, which, true, &run, s);
     if (st != NPBS_OK) return st;
     return net_run_backward(ctx, *reinterpret_cast<Net*>(net), run, static_cast<const float2*>(r), n,
                             static_cast<const float2*>(grad_c), static_cast<float2*>(grad_r), 0, s);

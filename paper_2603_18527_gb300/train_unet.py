@@ -1,4 +1,4 @@
-"""Train the residual-to-correction U-Net with the library's own kernels.
+"""Train the residual-to-correction network (U-Net or FNO) with the library's own kernels.
 
 Training tuples (medium, source, residual) come from the method itself
 (the metric-matched objective, Eq. L_bs_Reta_integral): a pool of instances
@@ -192,6 +192,12 @@ def main():
     ap.add_argument("--out", default="")
     ap.add_argument("--eval", type=int, default=16)
     ap.add_argument("--max-snap", type=int, default=2048)
+    ap.add_argument("--backbone", default="unet", choices=["unet", "fno"],
+                    help="the residual-to-correction map: the 4-level U-Net or the FNO (App. Architectural "
+                         "Instantiations; width / modes / layers below, the network is tied to --grid)")
+    ap.add_argument("--fno-width", type=int, default=25)
+    ap.add_argument("--fno-modes", type=int, default=45)
+    ap.add_argument("--fno-layers", type=int, default=3)
     ap.add_argument("--ablation", action="store_true",
                     help="train and evaluate the three objectives (Direct+L_dir, NPBS+L_bs_l2, NPBS+L_bs_Reta)")
     args = ap.parse_args()
@@ -200,13 +206,19 @@ def main():
     if args.ablation:
         print(json.dumps(ablation(ctx, grid=args.grid, steps=args.steps)))
         return
+    def fresh():
+        if args.backbone == "fno":
+            return capi.Net.fno(args.grid, args.fno_width, min(args.fno_modes, args.grid // 2 + 1), args.fno_layers,
+                                seed=args.seed)
+        return capi.Net(0, seed=args.seed)
+
     if args.init.endswith(".npz"):
-        net = capi.Net(0, seed=args.seed)
+        net = fresh()
         net.set_params(np.load(args.init)["params"].astype(np.float32))
     elif args.init:
         net = capi.Net.load(args.init)
     else:
-        net = capi.Net(0, seed=args.seed)
+        net = fresh()
     train(ctx, net, grid=args.grid, steps=args.steps, batch=args.batch, lr=args.lr, max_snap=args.max_snap,
           pool_size=args.pool, lr_min=args.lr_min, loss=args.loss)
     if args.out.endswith(".npz"):
