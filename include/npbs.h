@@ -318,7 +318,8 @@ npbs_status fgmres_solve(npbs_ctx* ctx, const npbs_net* net, const npbs_batch* b
 
 /* Total number of parameters of the U-Net in the canonical order. */
 int64_t npbs_net_num_params(void);
-/* Parameters of a network of either kind (U-Net or FNO); -1 for NULL. */
+/* Parameters of a network of either kind in its canonical order (U-Net or
+ * FNO); -1 for NULL. */
 int64_t npbs_net_param_count(const npbs_net* net);
 
 /* The FNO map (App. Architectural Instantiations, Eqs. fno_impl, fno_lift,

@@ -865,7 +865,9 @@ npbs_status npbs_net_create_fno(npbs_net** out, int device, int n, int width, in
 }
 
 int64_t npbs_net_param_count(const npbs_net* net) {
-    return net ? (int64_t)reinterpret_cast<const Net*>(net)->count() : -1;
+    if (!net) return -1;
+    const Net* N = reinterpret_cast<const Net*>(net);
+    return N->fno ? (int64_t)N->fno->count : (int64_t)canon_param_count();
 }
 
 }  // extern "C"

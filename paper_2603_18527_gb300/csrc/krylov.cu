@@ -31,34 +31,54 @@ __device__ __forceinline__ double warp_sum(double v) {
 }
 
 // h[inst][i] += <V_i, w> for i < nv (V_i rows of length `stride` elements).
-// Each thread sums its (at most kVecChunk / blockDim) products in float32 and
-// the block and instance sums are float64: float64 arithmetic per element would
-// bound the kernel by the FP64 pipe, whose rate on GB300 is a small fraction
-// of the FP32 rate (the vectors themselves are float32).
+// The basis vectors are taken kDotGroup at a time: each thread reads its
+// elements of w once per group and accumulates kDotGroup products, so w is
+// read ceil(nv / kDotGroup) times instead of nv times and the block reduces
+// once per group.  Each thread sums its (at most kVecChunk / blockDim)
+// products in float32 and the block and instance sums are float64: float64
+// arithmetic per element would bound the kernel by the FP64 pipe, whose rate
+// on GB300 is a small fraction of the FP32 rate (the vectors are float32).
+constexpr int kDotGroup = 8;
 __global__ void k_dots(const VecItem* items, const InstDev* inst, const int* active, const float2* __restrict__ Vb,
                        long long stride, int nv, const float2* __restrict__ w, double2* h, int ldh) {
     const VecItem it = items[blockIdx.x];
     if (active && !active[it.inst]) return;
     const long long base = inst[it.inst].offset + it.start;
-    __shared__ double red[2][kVecThreads / 32];
-    for (int i = 0; i < nv; ++i) {
-        const float2* v = Vb + (long long)i * stride + base;
-        float pr = 0.f, pi = 0.f;
+    __shared__ double red[2 * kDotGroup][kVecThreads / 32];
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    for (int i0 = 0; i0 < nv; i0 += kDotGroup) {
+        float pr[kDotGroup], pi[kDotGroup];
+#pragma unroll
+        for (int q = 0; q < kDotGroup; ++q) pr[q] = pi[q] = 0.f;
         for (int e = threadIdx.x; e < it.len; e += blockDim.x) {
-            const float2 a = v[e], b = w[base + e];
-            pr = fmaf(a.x, b.x, fmaf(a.y, b.y, pr));   // conj(a) b
-            pi = fmaf(a.x, b.y, fmaf(-a.y, b.x, pi));
+            const float2 b = w[base + e];
+#pragma unroll
+            for (int q = 0; q < kDotGroup; ++q) {
+                if (i0 + q < nv) {
+                    const float2 a = Vb[(long long)(i0 + q) * stride + base + e];
+                    pr[q] = fmaf(a.x, b.x, fmaf(a.y, b.y, pr[q]));  // conj(a) b
+                    pi[q] = fmaf(a.x, b.y, fmaf(-a.y, b.x, pi[q]));
+                }
+            }
         }
-        const double sr = warp_sum((double)pr);
-        const double si = warp_sum((double)pi);
-        const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
-        if (lane == 0) { red[0][wp] = sr; red[1][wp] = si; }
+#pragma unroll
+        for (int q = 0; q < kDotGroup; ++q) {
+            const double sr = warp_sum((double)pr[q]);
+            const double si = warp_sum((double)pi[q]);
+            if (lane == 0) {
+                red[2 * q][wp] = sr;
+                red[2 * q + 1][wp] = si;
+            }
+        }
         __syncthreads();
-        if (threadIdx.x == 0) {
-            double a = 0, b = 0;
-            for (int k = 0; k < (int)(blockDim.x >> 5); ++k) { a += red[0][k]; b += red[1][k]; }
-            atomicAdd(&h[(long long)it.inst * ldh + i].x, a);
-            atomicAdd(&h[(long long)it.inst * ldh + i].y, b);
+        if (threadIdx.x < 2 * kDotGroup) {
+            const int q = threadIdx.x >> 1, part = threadIdx.x & 1;
+            if (i0 + q < nv) {
+                double a = 0;
+                for (int k = 0; k < (int)(blockDim.x >> 5); ++k) a += red[threadIdx.x][k];
+                double2* hp = &h[(long long)it.inst * ldh + i0 + q];
+                atomicAdd(part ? &hp->y : &hp->x, a);
+            }
         }
         __syncthreads();
     }
