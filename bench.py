@@ -37,10 +37,10 @@ UNIT = "ms/solve"
 TOL = 1e-5
 B_PER_PT = 32  # algorithmic bytes per point of one CBS apply: read u, f, V, write u (complex64)
 # DRAM bytes per point of the cluster apply (dram__bytes_read + dram__bytes_write) from one ncu
-# capture of a 64 x 256^2 CBS_STEP launch, scaled to the bench batch by its point count; None
-# whenever the apply kernel has changed since the capture.  The last capture (106.18 MB + 17.81 MB
-# over 4,194,304 points) predates the float32 per-thread norm accumulator, so none is reported.
-TRAFFIC_B_PER_PT = None
+# capture of a 64 x 256^2 CBS_STEP launch of the 256^2 variant the autotuner picks (106.59 MB read +
+# 20.10 MB written over 4,194,304 points), scaled to the bench batch by its point count; set to None
+# whenever the apply kernel changes until it is captured again.
+TRAFFIC_B_PER_PT = (106.590208e6 + 20.095744e6) / 4194304
 
 
 def peaks():
