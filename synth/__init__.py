@@ -240,3 +240,43 @@ def random_weights(shapes, seed: int = 0, out_scale: float = 0.1) -> np.ndarray:
             std = math.sqrt(2.0 / fan_in) * (out_scale if i == len(shapes) - 1 else 1.0)
             parts.append(std * rng.standard_normal(int(np.prod(shape))))
     return np.concatenate(parts).astype(np.float32)
+
+
+@dataclasses.dataclass
+class CdrInstance:
+    """One periodic convection-diffusion-reaction problem on the unit square."""
+    n: int
+    h: float
+    kappa: np.ndarray    # float64 [n, n] diffusion (> 0)
+    vx: np.ndarray       # float64 [n, n] velocity along the last axis
+    vy: np.ndarray       # float64 [n, n] velocity along the first axis
+    sigma: np.ndarray    # float64 [n, n] reaction (> 0)
+    f: np.ndarray        # complex128 [n, n] source (real Gaussian bump)
+    seed: int
+
+
+def cdr_instance(n: int = 128, seed: int = 0, kappa_mean: float = 0.01, speed: float = 1.0) -> CdrInstance:
+    """The CDR benchmark's recipe on a periodic n x n grid of [0, 1)^2 (h = 1/n):
+    kappa from a GRF (log-normal around kappa_mean), an incompressible velocity
+    v = (d psi / dy, -d psi / dx) from a GRF stream function psi (spectral
+    derivatives; scaled to a maximum speed `speed`), sigma = 1 + 0.5 tanh(GRF),
+    and a Gaussian bump source of random centre and width (periodic distance)."""
+    rng = np.random.default_rng(seed)
+    h = 1.0 / n
+    kappa = kappa_mean * np.exp(0.5 * grf(rng, n, n, n / 16.0))
+    psi = grf(rng, n, n, n / 8.0)
+    k = 2.0 * math.pi * np.fft.fftfreq(n, d=h)
+    P = np.fft.fft2(psi)
+    vx = np.fft.ifft2(1j * k[:, None] * P).real       # d psi / dy (first axis)
+    vy = -np.fft.ifft2(1j * k[None, :] * P).real      # -d psi / dx (last axis)
+    vmax = max(float(np.max(np.hypot(vx, vy))), 1e-30)
+    vx, vy = vx * (speed / vmax), vy * (speed / vmax)
+    sigma = 1.0 + 0.5 * np.tanh(grf(rng, n, n, n / 16.0))
+    cy, cx = rng.uniform(0.0, 1.0, size=2)
+    width = rng.uniform(0.03, 0.08)
+    y = np.arange(n)[:, None] * h
+    x = np.arange(n)[None, :] * h
+    dy = np.minimum(np.abs(y - cy), 1.0 - np.abs(y - cy))
+    dx = np.minimum(np.abs(x - cx), 1.0 - np.abs(x - cx))
+    f = np.exp(-(dy ** 2 + dx ** 2) / (2.0 * width * width)).astype(np.complex128)
+    return CdrInstance(n=n, h=h, kappa=kappa, vx=vx, vy=vy, sigma=sigma, f=f, seed=seed)
