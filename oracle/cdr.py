@@ -18,10 +18,14 @@ and the same NPBS template as for Helmholtz: u <- u + M(G(V u + f) - u).
 
 Readings where the paper is silent: the periodic grid of the Helmholtz
 problem (x_j = j h, the same mode set, first derivatives with symbol i xi on
-every mode); the background constants are the grid means of kappa, v and
-sigma (for a velocity from a periodic stream function the mean velocity is
-zero, so L0 is the symmetric -kappa0 Lap + sigma0 and all of the convection
-sits in V); fields are complex (real data stay real up to rounding).
+every mode); the background constants are kappa0 = the midpoint of the range
+of kappa, sigma0 = the midpoint of the range of sigma and v0 = the grid mean
+of v (the choice that makes the diffusion and reaction parts of G V contract,
+|kappa - kappa0| / kappa0 < 1 and |sigma - sigma0| / sigma0 < 1, as the
+midpoint k0^2 and eps = max |k^2 - k0^2| do for Helmholtz; for a velocity from
+a periodic stream function the mean is zero, so L0 is the symmetric
+-kappa0 Lap + sigma0 and all of the convection sits in V); fields are complex
+(real data stay real up to rounding).
 """
 from __future__ import annotations
 
@@ -63,12 +67,14 @@ def wavenumbers(ny: int, nx: int, h: float):
 
 
 def make_problem(kappa, vx, vy, sigma, f, h: float, consts=None) -> CdrProblem:
-    """consts = (kappa0, v0x, v0y, sigma0), by default the grid means."""
+    """consts = (kappa0, v0x, v0y, sigma0), by default the midpoints of the
+    ranges of kappa and sigma and the grid means of v."""
     t = lambda a: torch.as_tensor(np.asarray(a), dtype=F64)
     kappa, vx, vy, sigma = t(kappa), t(vx), t(vy), t(sigma)
     f = H.as_c128(f)
     if consts is None:
-        consts = (float(kappa.mean()), float(vx.mean()), float(vy.mean()), float(sigma.mean()))
+        consts = (0.5 * (float(kappa.min()) + float(kappa.max())), float(vx.mean()), float(vy.mean()),
+                  0.5 * (float(sigma.min()) + float(sigma.max())))
     k0, v0x, v0y, s0 = (float(c) for c in consts)
     ky, kx = wavenumbers(*kappa.shape, h)
     lam = (k0 * (kx ** 2 + ky ** 2)).to(C128) + 1j * (v0x * kx + v0y * ky) + s0
@@ -114,6 +120,24 @@ def born_residual(p: CdrProblem, u: torch.Tensor) -> torch.Tensor:
 def op_B(p: CdrProblem, x: torch.Tensor) -> torch.Tensor:
     """(I - G V) x."""
     return x - green(p, apply_V(p, x))
+
+
+def green_adjoint(p: CdrProblem, q: torch.Tensor) -> torch.Tensor:
+    """G^* q = F^{-1}(F q / conj(symbol(L0)))."""
+    return torch.fft.ifft2(torch.fft.fft2(q) / p.lam.conj())
+
+
+def apply_A_adjoint(p: CdrProblem, g: torch.Tensor) -> torch.Tensor:
+    """A^* g = -div(kappa grad g) - div(v g) + sigma g (the real coefficients
+    make the diffusion and reaction parts self-adjoint; the adjoint of v . grad
+    is -div(v .))."""
+    gx, gy = ddx(p, g), ddy(p, g)
+    return -(ddx(p, p.kappa * gx + p.vx * g) + ddy(p, p.kappa * gy + p.vy * g)) + p.sigma * g
+
+
+def op_BH(p: CdrProblem, y: torch.Tensor) -> torch.Tensor:
+    """(I - G V)^* y = (G A)^* y = A^* G^* y (Eq. cdr_identity)."""
+    return apply_A_adjoint(p, green_adjoint(p, y))
 
 
 def rtol(p: CdrProblem, u: torch.Tensor) -> float:

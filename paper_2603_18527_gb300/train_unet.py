@@ -150,6 +150,33 @@ def evaluate(ctx, net, grid=64, count=16, seed=9000, tol=1e-5, max_iter=20000, s
     return res
 
 
+def compare(ctx, nets, grid=256, count=64, seed=2000, tol=1e-5, max_iter=2500):
+    """NPBS with each network of `nets` (name -> npbs_net) against plain CBS on
+    `count` held-out media of the contrast law: converged count, mean and
+    median iterations of the converged instances, CBS hand-overs by the
+    divergence guard, and ms per solve (batch time / count)."""
+    insts = media(grid, count, seed)
+    pool = Pool(ctx, insts)
+    out = {}
+    for name, net in [("cbs", None)] + list(nets.items()):
+        u = torch.zeros(pool.b.extent, dtype=torch.complex128, device="cuda")
+        torch.cuda.synchronize()
+        t = time.time()
+        if net is None:
+            st, rep = capi.cbs_solve(ctx, pool.b, pool.k2, pool.f, u, rtol=tol, max_iter=max_iter, check_every=16)
+        else:
+            st, rep = capi.npbs_solve(ctx, net, pool.b, pool.k2, pool.f, pool.n, u, rtol=tol, max_iter=max_iter,
+                                      check_every=4)
+        torch.cuda.synchronize()
+        dt = time.time() - t
+        it = np.array(rep["iters"])
+        ok = np.array(rep["status"]) == capi.OK
+        out[name] = {"converged": int(ok.sum()), "iters_mean_converged": float(it[ok].mean()) if ok.any() else None,
+                     "iters_median_converged": float(np.median(it[ok])) if ok.any() else None,
+                     "fallback": int(sum(rep.get("fallback") or [0])), "ms_per_solve": dt * 1e3 / count}
+    return out
+
+
 def ablation(ctx, grid=256, steps=2000, count=32, tol=1e-5, max_iter=2500, log=print):
     """The format / objective ablation of Sec. 4 (Table 2's U-Net row): three
     networks from the same initialisation on the same media pool and snapshot
@@ -198,6 +225,9 @@ def main():
     ap.add_argument("--fno-width", type=int, default=25)
     ap.add_argument("--fno-modes", type=int, default=45)
     ap.add_argument("--fno-layers", type=int, default=3)
+    ap.add_argument("--compare-unet", default="",
+                    help="after training, compare NPBS with this network and with the U-Net of this .npz on the "
+                         "64 held-out media of the bench (seeds 2000+) against CBS")
     ap.add_argument("--ablation", action="store_true",
                     help="train and evaluate the three objectives (Direct+L_dir, NPBS+L_bs_l2, NPBS+L_bs_Reta)")
     args = ap.parse_args()
@@ -225,7 +255,11 @@ def main():
         np.savez_compressed(args.out, params=net.get_params().astype(np.float16))
     elif args.out:
         net.save(args.out)
-    if args.eval:
+    if args.compare_unet:
+        unet = capi.Net(0, seed=0)
+        unet.set_params(np.load(args.compare_unet)["params"].astype(np.float32))
+        print(json.dumps({"compare": compare(ctx, {args.backbone: net, "unet": unet}, grid=args.grid)}))
+    elif args.eval:
         solvers = ("cbs", "direct") if args.loss == "dir" else ("cbs", "npbs")
         print(json.dumps(evaluate(ctx, net, grid=args.grid, count=args.eval, solvers=solvers)))
 

@@ -255,15 +255,16 @@ class CdrInstance:
     seed: int
 
 
-def cdr_instance(n: int = 128, seed: int = 0, kappa_mean: float = 0.01, speed: float = 1.0) -> CdrInstance:
+def cdr_instance(n: int = 128, seed: int = 0, kappa_mean: float = 0.01, speed: float = 1.0,
+                 kappa_contrast: float = 0.5) -> CdrInstance:
     """The CDR benchmark's recipe on a periodic n x n grid of [0, 1)^2 (h = 1/n):
-    kappa from a GRF (log-normal around kappa_mean), an incompressible velocity
+    kappa from a GRF (log-normal around kappa_mean, log-amplitude kappa_contrast), an incompressible velocity
     v = (d psi / dy, -d psi / dx) from a GRF stream function psi (spectral
     derivatives; scaled to a maximum speed `speed`), sigma = 1 + 0.5 tanh(GRF),
     and a Gaussian bump source of random centre and width (periodic distance)."""
     rng = np.random.default_rng(seed)
     h = 1.0 / n
-    kappa = kappa_mean * np.exp(0.5 * grf(rng, n, n, n / 16.0))
+    kappa = kappa_mean * np.exp(kappa_contrast * grf(rng, n, n, n / 16.0))
     psi = grf(rng, n, n, n / 8.0)
     k = 2.0 * math.pi * np.fft.fftfreq(n, d=h)
     P = np.fft.fft2(psi)

@@ -101,3 +101,17 @@ def test_recipe_velocity_is_incompressible():
     div = CD.ddx(p, torch.from_numpy(inst.vx).to(torch.complex128)) + CD.ddy(p, torch.from_numpy(inst.vy).to(torch.complex128))
     assert float(div.abs().max()) < 1e-10 * float(np.abs(inst.vx).max() / inst.h)
     assert abs(p.v0x) < 1e-12 and abs(p.v0y) < 1e-12 and inst.kappa.min() > 0 and inst.sigma.min() > 0
+
+
+def test_adjoint_dot_product_and_dense_transpose():
+    """<B x, y> = <x, B^* y> with B = I - G V; and B^* equals the conjugate
+    transpose of B's dense matrix."""
+    n = 8
+    p = _random_problem(n=n, seed=7)
+    x, y = _rand(n, 8), _rand(n, 9)
+    lhs = torch.vdot(y.reshape(-1), CD.op_B(p, x).reshape(-1))
+    rhs = torch.vdot(CD.op_BH(p, y).reshape(-1), x.reshape(-1))
+    assert abs(complex(lhs - rhs)) <= 1e-12 * abs(complex(lhs))
+    B = np.stack([CD.op_B(p, torch.from_numpy(e.reshape(n, n))).numpy().reshape(-1) for e in np.eye(n * n)], axis=1)
+    BH = np.stack([CD.op_BH(p, torch.from_numpy(e.reshape(n, n))).numpy().reshape(-1) for e in np.eye(n * n)], axis=1)
+    assert np.allclose(BH, B.conj().T, atol=1e-10)
