@@ -28,10 +28,11 @@ the full bandwidth (N/2 + 1).  Readings where the paper is silent:
 * the lifting / projection and W^loc are 1x1 convolutions; only the
   coefficient branch (lift and NLFL layers) carries biases, so that M is
   linear in r (the paper's design principle) and no scale wrapper is needed;
-* LayerNorm normalises the single coefficient channel over the grid of each
+* LayerNorm normalises each coefficient channel over the grid of each
   instance (zero mean, unit variance, eps 1e-5, no affine: the lifting
   supplies it); pad / unpad are the identity, since the periodic grid already
-  carries the absorbing layer;
+  carries the absorbing layer; the CDR problems feed several coefficient
+  channels (kappa, v, sigma), Helmholtz one;
 * the coefficient channel a is the one the U-Net reads (the local wavenumber
   omega n(x)); GELU is the erf form.
 
@@ -55,6 +56,7 @@ class FnoConfig:
     width: int = 25   # hidden channels
     modes: int = 45   # retained modes of the NLFL and fusion layers
     layers: int = 3   # NLFL layers on the coefficient branch
+    coef: int = 1     # coefficient channels of a
 
     @property
     def full(self) -> int:
@@ -80,7 +82,7 @@ def param_spec(cfg: FnoConfig) -> List[Tuple[str, Tuple[int, ...]]]:
     C = cfg.width
     ky, kx = spectral_shape(cfg, cfg.modes)
     fy, fx = spectral_shape(cfg, cfg.full)
-    spec = [("lift_a.w", (C, 1)), ("lift_a.b", (C,))]
+    spec = [("lift_a.w", (C, cfg.coef)), ("lift_a.b", (C,))]
     for l in range(cfg.layers):
         spec += [(f"spec{l}.w", (C, C, ky, kx, 2)), (f"loc{l}.w", (C, C)), (f"loc{l}.b", (C,))]
     spec += [("lift_r.w", (C, 2)), ("spec_r.w", (C, C, fy, fx, 2)), ("loc_r.w", (C, C)),
@@ -126,15 +128,18 @@ def conv1x1(x: torch.Tensor, w: torch.Tensor, b: torch.Tensor | None = None) -> 
 
 
 def layer_norm(a: torch.Tensor, eps: float = 1e-5) -> torch.Tensor:
-    """Normalise each instance's field over its grid: a [B, N, N]."""
+    """Normalise each instance's field (each channel) over its grid: a [..., N, N]."""
     mu = a.mean(dim=(-2, -1), keepdim=True)
     var = ((a - mu) ** 2).mean(dim=(-2, -1), keepdim=True)
     return (a - mu) / torch.sqrt(var + eps)
 
 
 def coefficient_features(a: torch.Tensor, P: Dict[str, torch.Tensor], cfg: FnoConfig) -> torch.Tensor:
-    """NLFL_L(...NLFL_1(Phi(a))): a [B, N, N] real -> [B, C, N, N]."""
-    c = conv1x1(layer_norm(a)[:, None], P["lift_a.w"], P["lift_a.b"])
+    """NLFL_L(...NLFL_1(Phi(a))): a [B, N, N] (one channel) or [B, coef, N, N]
+    real -> [B, C, N, N]."""
+    if a.dim() == 3:
+        a = a[:, None]
+    c = conv1x1(layer_norm(a), P["lift_a.w"], P["lift_a.b"])
     for l in range(cfg.layers):
         c = Fnn.gelu(spectral(c, P[f"spec{l}.w"], cfg.modes) + conv1x1(c, P[f"loc{l}.w"], P[f"loc{l}.b"]))
     return c

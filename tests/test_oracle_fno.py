@@ -149,3 +149,42 @@ def test_param_count_of_the_paper_configuration():
     spec = lambda ky, kx: C * C * ky * kx * 2
     expect = (C + C) + 3 * (spec(89, 45) + C * C + C) + 2 * C + spec(256, 129) + C * C + spec(89, 45) + C * C + 2 * C
     assert FN.n_params(cfg) == expect
+
+
+def test_layer_norm_normalises_each_coefficient_channel_separately():
+    """Several coefficient channels (the CDR input kappa, v, sigma): each
+    channel of each instance gets zero mean and unit variance on its own."""
+    rng = np.random.default_rng(8)
+    scale = np.array([1.0, 30.0, 0.01])[None, :, None, None]
+    a = torch.from_numpy(5.0 + scale * rng.standard_normal((2, 3, 16, 16)))
+    z = FN.layer_norm(a)
+    assert torch.allclose(z.mean(dim=(-2, -1)), torch.zeros(2, 3, dtype=torch.float64), atol=1e-12)
+    # unit variance up to the eps in the denominator (var / (var + 1e-5))
+    v = a.var(dim=(-2, -1), unbiased=False)
+    assert torch.allclose((z ** 2).mean(dim=(-2, -1)), v / (v + 1e-5), rtol=1e-12)
+
+
+def test_several_coefficient_channels_reduce_to_one_and_permute():
+    """With lift_a.w nonzero in column 0 only, a coef = 3 network equals the
+    coef = 1 network fed channel 0; permuting the channels of a together
+    with the columns of lift_a.w leaves M unchanged."""
+    rng = np.random.default_rng(9)
+    c1 = FN.FnoConfig(n=16, width=4, modes=3, layers=2)
+    c3 = FN.FnoConfig(n=16, width=4, modes=3, layers=2, coef=3)
+    flat1 = FN.init_params(c1, 3) + 0.05
+    P1 = FN.unflatten(c1, flat1)
+    P3 = dict(P1)
+    w3 = torch.zeros(4, 3, dtype=torch.float64)
+    w3[:, 0] = P1["lift_a.w"][:, 0]
+    P3["lift_a.w"] = w3
+    a = torch.from_numpy(rng.standard_normal((2, 3, 16, 16)) * np.array([1.0, 4.0, 0.1])[None, :, None, None])
+    r = torch.from_numpy(rng.standard_normal((2, 16, 16)) + 1j * rng.standard_normal((2, 16, 16)))
+    y1 = FN.correction(r, a[:, 0], P1, c1)
+    y3 = FN.correction(r, a, P3, c3)
+    assert torch.allclose(y1, y3, rtol=1e-12, atol=1e-12)
+    P3["lift_a.w"] = torch.from_numpy(rng.standard_normal((4, 3)))
+    perm = [2, 0, 1]
+    Pp = dict(P3)
+    Pp["lift_a.w"] = P3["lift_a.w"][:, perm]
+    assert torch.allclose(FN.correction(r, a, P3, c3), FN.correction(r, a[:, perm], Pp, c3), rtol=1e-12, atol=1e-12)
+    assert FN.n_params(c3) == FN.n_params(c1) + 2 * 4
