@@ -305,6 +305,62 @@ npbs_status fgmres_solve(npbs_ctx* ctx, const npbs_net* net, const npbs_batch* b
                          const npbs_solve_opts* opts, npbs_report* report, npbs_stream stream);
 
 
+/* ---- convection-diffusion-reaction (App. Full Derivations, CDR) ------------
+ * The paper's CDR extension on the same periodic pseudospectral grid:
+ *   A u  = -div(kappa grad u) + v . grad u + sigma u            (Eq. cdr_pde)
+ *   L0   = -kappa0 Lap + v0 . grad + sigma0, G = L0^{-1}         (Eqs. cdr_L0, cdr_G_symbol)
+ *   V    = L0 - A, so I - G V = G A and G(V u + f) - u = G(f - A u)  (Eqs. cdr_V, cdr_identity)
+ * First derivatives are i xi on the mode set of the Helmholtz operators.
+ * kappa, vx (along x, the row direction), vy, sigma: DEVICE float32 with the
+ * batch layout; fields complex64.  Instances: square grids whose side is a
+ * multiple of 16 and 2^a 3^b <= 1024; h > 0; the k0sq / eps fields of the
+ * batch are ignored.  Background constants per instance (HOST array). */
+typedef struct {
+    double kappa0, v0x, v0y, sigma0;  /* kappa0 > 0 */
+} npbs_cdr_consts;
+
+/* The library's reading of the background constants, per instance: kappa0 and
+ * sigma0 the midpoints of the ranges of kappa and sigma (so that the diffusion
+ * and reaction parts of G V contract, as the midpoint k0^2 does for Helmholtz),
+ * v0 the grid mean of v.  out: HOST [count].  Synchronises the stream. */
+npbs_status npbs_cdr_background(npbs_ctx* ctx, const npbs_batch* batch, const float* kappa, const float* vx,
+                                const float* vy, const float* sigma, npbs_cdr_consts* out, npbs_stream stream);
+
+/* One CDR apply: mode RESIDUAL out = G(V x + f) - x = G(f - A x); OP_B out = G A x
+ * (= x - G V x); TRUE_RESIDUAL out = f - A x; ADJ_B out = (G A)^* x = A^* G^* x
+ * (G^* of symbol 1/conj(lambda0), A^* g = -div(kappa grad g + v g) + sigma g).
+ * f may be NULL for OP_B and ADJ_B; out may alias x.  norm2 (nullable, DEVICE
+ * double [count]) receives ||out||^2 per instance.  Asynchronous. */
+npbs_status cdr_apply(npbs_ctx* ctx, const npbs_batch* batch, const npbs_cdr_consts* consts, const float* kappa,
+                      const float* vx, const float* vy, const float* sigma, const void* f, const void* x, void* out,
+                      npbs_mode mode, double* norm2, npbs_stream stream);
+
+/* NPBS for CDR (the template of Eq. npbs_integral with the CDR operators):
+ * u <- u + M(G(V u + f) - u), M the network `net` fed the coefficient field
+ * `a` (DEVICE float32: the FNO's coef_channels planes of the batch extent one
+ * after another, e.g. kappa, vx, vy, sigma; one plane for a U-Net), or the
+ * identity when net is NULL
+ * (the Born series, which converges when ||G V|| < 1).  u: DEVICE complex64,
+ * initial guess in, iterate out.  rTol = ||f - A u|| / ||f|| (float64 sums) is
+ * checked every opts->check_every iterations; every instance iterates until
+ * all have passed or opts->max_iter; the report holds each instance's count
+ * at its first passing check.  Synchronises. */
+npbs_status cdr_solve(npbs_ctx* ctx, const npbs_net* net, const npbs_batch* batch, const npbs_cdr_consts* consts,
+                      const float* kappa, const float* vx, const float* vy, const float* sigma, const void* f,
+                      const float* a, void* u, const npbs_solve_opts* opts, npbs_report* report, npbs_stream stream);
+
+/* The metric-matched training step for CDR (Eq. cdr_bs_loss, the template of
+ * npbs_train_step with (G, A, V) the CDR operators): r_0 = G(V u + f) - u of the
+ * snapshots u_snap, r_{k+1} = r_k - (I - G V) M(r_k), loss = mean_j (1/U)
+ * sum_k ||r_k||^2 / ||r_0||^2, gradients by the CDR adjoint and the network
+ * backward, one AdamW update.  a: the network's coefficient field, laid out
+ * as for cdr_solve.
+ * Synchronises the stream once (to read the loss). */
+npbs_status cdr_train_step(npbs_ctx* ctx, npbs_net* net, const npbs_batch* batch, const npbs_cdr_consts* consts,
+                           const float* kappa, const float* vx, const float* vy, const float* sigma, const void* f,
+                           const float* a, const void* u_snap, int32_t unroll, float lr, float weight_decay,
+                           float* loss_host, npbs_stream stream);
+
 /* ---- the learned correction M_theta (App. Experimental Setup, U-Net) -------
  * M(r; n) = s N([Re r / s, Im r / s, n]), s = ||r||_2 / sqrt(nx ny) per
  * instance, N a 4-level U-Net (32/64/128/256 channels, two 3x3 conv + GELU per
@@ -329,20 +385,24 @@ int64_t npbs_net_param_count(const npbs_net* net);
  *   M(r; a) = P( LFL_f[ NLFL_L(...NLFL_1(Phi(a))) * LFL_r(Psi(r)) ] ),
  *   Phi(a) = W_a LayerNorm(a) + b_a, Psi(r) = W_r [Re r, Im r], P(z) = W_p z,
  *   LFL(x) = irfft2(W^F * R(rfft2(x))) + W^loc x (+ b), NLFL = GELU(LFL);
- * a is the network's coefficient channel (the `n` argument of the entries).
+ * a is the network's coefficient field (the `n` argument of the entries):
+ * coef_channels planes of the batch extent one after another (1 for
+ * Helmholtz; the CDR problems pass kappa, v, sigma), each LayerNorm-ed over
+ * the grid of its instance.
  * M is linear in r (no bias on the residual path, no scale wrapper).  The
  * NLFL and fusion layers keep the modes with min(ky, N - ky) < modes and
  * kx < modes of the half plane, the residual layer all of them (N/2 + 1
  * columns).  The paper's configuration is width 25, modes 45, layers 3.  The
  * network is tied to one grid: every instance must be n x n.  n: even,
- * 2^a 3^b, 4..1024; width 1..32; modes 1..n/2+1; layers 0..8.  Float32
- * throughout.  Canonical parameter order: lift_a.w [C], lift_a.b [C]; per
+ * 2^a 3^b, 4..1024; width 1..32; modes 1..n/2+1; layers 0..8;
+ * coef_channels 1..32.  Float32
+ * throughout.  Canonical parameter order: lift_a.w [C][coef], lift_a.b [C]; per
  * layer spec [C][C][Ky][Kx][2 = re, im], loc.w [C out][C in], loc.b [C];
  * lift_r.w [C][2]; spec_r [C][C][n][n/2+1][2]; loc_r.w [C][C];
  * spec_f [C][C][Ky][Kx][2]; loc_f.w [C][C]; proj.w [2][C].  Seeded initial
  * weights. */
 npbs_status npbs_net_create_fno(npbs_net** out, int device, int n, int width, int modes, int layers,
-                                uint64_t seed);
+                                int coef_channels, uint64_t seed);
 /* Create a network on `device` with seeded He-normal weights. */
 npbs_status npbs_net_create(npbs_net** out, int device, uint64_t seed);
 npbs_status npbs_net_destroy(npbs_net* net);

@@ -44,6 +44,10 @@ class npbs_report(C.Structure):
                 ("status", C.POINTER(C.c_int32)), ("flags", C.POINTER(C.c_int32))]
 
 
+class npbs_cdr_consts(C.Structure):
+    _fields_ = [("kappa0", C.c_double), ("v0x", C.c_double), ("v0y", C.c_double), ("sigma0", C.c_double)]
+
+
 class NpbsError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"{STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else status}: {msg}")
@@ -85,10 +89,21 @@ _SIGS = {
                                       C.c_int32, C.c_void_p, C.c_void_p]),
     "cbs_apply_static": (C.c_int, [C.POINTER(npbs_batch), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
                                    C.c_void_p, C.c_void_p, C.c_char_p, C.c_int32]),
+    "npbs_cdr_background": (C.c_int, [C.c_void_p, C.POINTER(npbs_batch), C.c_void_p, C.c_void_p, C.c_void_p,
+                                      C.c_void_p, C.POINTER(npbs_cdr_consts), C.c_void_p]),
+    "cdr_apply": (C.c_int, [C.c_void_p, C.POINTER(npbs_batch), C.POINTER(npbs_cdr_consts), C.c_void_p, C.c_void_p,
+                            C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p,
+                            C.c_void_p]),
+    "cdr_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(npbs_batch), C.POINTER(npbs_cdr_consts), C.c_void_p,
+                            C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                            C.POINTER(npbs_solve_opts), C.POINTER(npbs_report), C.c_void_p]),
+    "cdr_train_step": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(npbs_batch), C.POINTER(npbs_cdr_consts),
+                                 C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                 C.c_int32, C.c_float, C.c_float, C.POINTER(C.c_float), C.c_void_p]),
     "npbs_net_num_params": (C.c_int64, []),
     "npbs_net_param_count": (C.c_int64, [C.c_void_p]),
     "npbs_net_create_fno": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
-                                      C.c_uint64]),
+                                      C.c_int, C.c_uint64]),
     "npbs_net_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_uint64]),
     "npbs_net_destroy": (C.c_int, [C.c_void_p]),
     "npbs_net_set_params": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64]),
@@ -164,11 +179,11 @@ class Context:
 
     @classmethod
     def fno(cls, n: int, width: int = 25, modes: int = 45, layers: int = 3, device: int = 0,
-            seed: int = 0) -> "Net":
+            seed: int = 0, coef_channels: int = 1) -> "Net":
         """An FNO network (App. Architectural Instantiations) for n x n grids."""
         h = C.c_void_p()
         st = lib().npbs_net_create_fno(C.byref(h), int(device), int(n), int(width), int(modes), int(layers),
-                                       C.c_uint64(seed))
+                                       int(coef_channels), C.c_uint64(seed))
         if st != OK:
             raise NpbsError(st, "npbs_net_create_fno failed")
         return cls(device, handle=h)
@@ -436,11 +451,11 @@ class Net:
 
     @classmethod
     def fno(cls, n: int, width: int = 25, modes: int = 45, layers: int = 3, device: int = 0,
-            seed: int = 0) -> "Net":
+            seed: int = 0, coef_channels: int = 1) -> "Net":
         """An FNO network (App. Architectural Instantiations) for n x n grids."""
         h = C.c_void_p()
         st = lib().npbs_net_create_fno(C.byref(h), int(device), int(n), int(width), int(modes), int(layers),
-                                       C.c_uint64(seed))
+                                       int(coef_channels), C.c_uint64(seed))
         if st != OK:
             raise NpbsError(st, "npbs_net_create_fno failed")
         return cls(device, handle=h)
@@ -524,4 +539,62 @@ def npbs_train_step(ctx: Context, net: Net, batch: Batch, V, f, n, u_snap, unrol
         ctx.check(lib().npbs_train_step_loss(ctx.handle, net.handle, C.byref(batch.c_batch()), _ptr(V), _ptr(f),
                                              _ptr(n), _ptr(u_snap), int(unroll), LOSS_KINDS[loss], float(lr),
                                              float(weight_decay), C.byref(out), _stream(stream)))
+    return float(out.value)
+
+
+# ---- convection-diffusion-reaction ------------------------------------------
+
+class CdrFields:
+    """Packed DEVICE float32 coefficient fields (kappa, vx, vy, sigma) of a CDR batch."""
+
+    def __init__(self, batch: "Batch", kappa, vx, vy, sigma):
+        self.kappa = batch.pack(kappa, dtype=torch.float32)
+        self.vx = batch.pack(vx, dtype=torch.float32)
+        self.vy = batch.pack(vy, dtype=torch.float32)
+        self.sigma = batch.pack(sigma, dtype=torch.float32)
+
+    def ptrs(self):
+        return _ptr(self.kappa), _ptr(self.vx), _ptr(self.vy), _ptr(self.sigma)
+
+
+def _consts(consts):
+    arr = (npbs_cdr_consts * max(1, len(consts)))()
+    for j, c in enumerate(consts):
+        arr[j] = npbs_cdr_consts(*[float(v) for v in c])
+    return arr
+
+
+def npbs_cdr_background(ctx: Context, batch: "Batch", fields: CdrFields, stream=None):
+    """Background constants (kappa0, v0x, v0y, sigma0) per instance: range midpoints of kappa and sigma, means of v."""
+    out = (npbs_cdr_consts * max(1, batch.count))()
+    ctx.check(lib().npbs_cdr_background(ctx.handle, C.byref(batch.c_batch()), *fields.ptrs(), out, _stream(stream)))
+    return [(out[j].kappa0, out[j].v0x, out[j].v0y, out[j].sigma0) for j in range(batch.count)]
+
+
+def cdr_apply(ctx: Context, batch: "Batch", consts, fields: CdrFields, f, x, out, mode: int,
+              norm2: Optional[torch.Tensor] = None, stream=None):
+    ctx.check(lib().cdr_apply(ctx.handle, C.byref(batch.c_batch()), _consts(consts), *fields.ptrs(), _ptr(f), _ptr(x),
+                              _ptr(out), int(mode), _ptr(norm2), _stream(stream)))
+
+
+def cdr_solve(ctx: Context, net, batch: "Batch", consts, fields: CdrFields, f, a, u, rtol=1e-6, max_iter=2500,
+              check_every=4, stream=None):
+    """NPBS (net) or the Born series (net None) for CDR; u complex64 in/out."""
+    rep = Report(batch.count)
+    o = _opts(rtol, max_iter, check_every, 0)
+    st = lib().cdr_solve(ctx.handle, net.handle if net is not None else None, C.byref(batch.c_batch()),
+                         _consts(consts), *fields.ptrs(), _ptr(f), _ptr(a), _ptr(u), C.byref(o), C.byref(rep.c),
+                         _stream(stream))
+    if st not in (OK, NOT_CONVERGED, ERR_NONFINITE):
+        ctx.check(st)
+    return st, rep.as_dict()
+
+
+def cdr_train_step(ctx: Context, net, batch: "Batch", consts, fields: CdrFields, f, a, u_snap, unroll=4, lr=1e-3,
+                   weight_decay=1e-6, stream=None) -> float:
+    """One metric-matched training step with the CDR operators; returns the loss."""
+    out = C.c_float(0.0)
+    ctx.check(lib().cdr_train_step(ctx.handle, net.handle, C.byref(batch.c_batch()), _consts(consts), *fields.ptrs(),
+                                   _ptr(f), _ptr(a), _ptr(u_snap), int(unroll), float(lr), float(weight_decay),
+                                   C.byref(out), _stream(stream)))
     return float(out.value)

@@ -1,0 +1,568 @@
+// Convection-diffusion-reaction operators (App. Full Derivations, CDR; Eqs.
+// cdr_pde, cdr_L0, cdr_V, cdr_integral, cdr_identity, cdr_G_symbol) and their
+// Born / NPBS iteration on the GPU:
+//
+//   A u  = -div(kappa grad u) + v . grad u + sigma u
+//   L0   = -kappa0 Lap + v0 . grad + sigma0,  G = L0^{-1} (symbol 1 / lambda0,
+//          lambda0 = kappa0 |xi|^2 + i v0 . xi + sigma0)
+//   V    = L0 - A,  I - G V = G A  (so G(V x + f) - x = G(f - A x))
+//
+// On the same periodic pseudospectral grid as the Helmholtz operators (first
+// derivatives by i xi on the mode set n in -N/2..N/2-1).  One apply:
+//   b0 = F x;  b1, b2 = F^{-1}(i xi_x b0), F^{-1}(i xi_y b0)        (grad x)
+//   b3, b4 = F(kappa grad x),  b5 = F(v . grad x + sigma x [- f])
+//   W = -i xi_x b3 - i xi_y b4 + b5 = F(A x [- f])
+//   RESIDUAL: F^{-1}(-W / lambda0) = G(f - A x);  OP_B: F^{-1}(W / lambda0) = G A x;
+//   TRUE_RESIDUAL: F^{-1}(-W) = f - A x
+// and the adjoint ADJ_B: (G A)^* y = A^* G^* y with G^* of symbol 1/conj(lambda0)
+// and A^* g = -div(kappa grad g + v g) + sigma g.  Seven (eight) batched 2D
+// FFTs of the instances' square grids (fft2d.cuh) and four pointwise kernels.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <vector>
+
+#include "ctx.cuh"
+#include "fft2d.cuh"
+#include "net.cuh"
+
+namespace npbs {
+namespace {
+
+struct CdrInst {
+    int n;
+    double h;
+    long long off;
+    double k0, v0x, v0y, s0;
+};
+
+__device__ __forceinline__ float xi_of(int i, int n, double h) {
+    return (float)(6.283185307179586476925 * (double)signed_mode(i, n) / ((double)n * h));
+}
+
+__device__ __forceinline__ void field_point(const CdrInst* ins, long long np, long long g, int* j, long long* p) {
+    *j = (int)(g / np);
+    *p = g - (long long)(*j) * np;
+}
+
+// b0 = x (then transformed in place)
+__global__ void k_cdr_copy(const CdrInst* ins, int cnt, long long np, const float2* x, float2* b0) {
+    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < cnt * np; g += (long long)gridDim.x * blockDim.x) {
+        int j; long long p;
+        field_point(ins, np, g, &j, &p);
+        const long long o = ins[j].off + p;
+        b0[o] = x[o];
+    }
+}
+
+// spectral gradients b1 = i xi_x b0, b2 = i xi_y b0 (optionally b0 /= conj(lambda0) first: G^*)
+__global__ void k_cdr_grad(const CdrInst* ins, int cnt, long long np, float2* b0, float2* b1, float2* b2, int adj) {
+    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < cnt * np; g += (long long)gridDim.x * blockDim.x) {
+        int j; long long p;
+        field_point(ins, np, g, &j, &p);
+        const CdrInst in = ins[j];
+        const int y = (int)(p / in.n), x = (int)(p % in.n);
+        const float kx = xi_of(x, in.n, in.h), ky = xi_of(y, in.n, in.h);
+        const long long o = in.off + p;
+        float2 u = b0[o];
+        if (adj) {
+            // G^*: divide by conj(lambda0) = kappa0 |xi|^2 + sigma0 - i v0 . xi
+            const float lr = (float)in.k0 * (kx * kx + ky * ky) + (float)in.s0;
+            const float li = -((float)in.v0x * kx + (float)in.v0y * ky);
+            const float d = 1.f / (lr * lr + li * li);
+            u = make_float2((u.x * lr + u.y * li) * d, (u.y * lr - u.x * li) * d);
+            b0[o] = u;
+        }
+        b1[o] = make_float2(-kx * u.y, kx * u.x);
+        b2[o] = make_float2(-ky * u.y, ky * u.x);
+    }
+}
+
+// pointwise products in physical space (s = 1/n^2 undoes the unnormalised transforms)
+//   forward:  b3 = kappa ux, b4 = kappa uy, b5 = vx ux + vy uy + sigma x - f
+//   adjoint:  g = b0 s: b3 = kappa gx + vx g, b4 = kappa gy + vy g, b5 = sigma g
+__global__ void k_cdr_flux(const CdrInst* ins, int cnt, long long np, const float* kappa, const float* vx,
+                           const float* vy, const float* sigma, const float2* x, const float2* f, const float2* b0,
+                           const float2* b1, const float2* b2, float2* b3, float2* b4, float2* b5, int adj) {
+    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < cnt * np; g += (long long)gridDim.x * blockDim.x) {
+        int j; long long p;
+        field_point(ins, np, g, &j, &p);
+        const CdrInst in = ins[j];
+        const long long o = in.off + p;
+        const float s = 1.f / ((float)in.n * (float)in.n);
+        const float k = kappa[o], ax = vx[o], ay = vy[o], sg = sigma[o];
+        const float2 ux = make_float2(b1[o].x * s, b1[o].y * s), uy = make_float2(b2[o].x * s, b2[o].y * s);
+        if (!adj) {
+            const float2 xv = x[o];
+            float2 r = make_float2(ax * ux.x + ay * uy.x + sg * xv.x, ax * ux.y + ay * uy.y + sg * xv.y);
+            if (f) r = make_float2(r.x - f[o].x, r.y - f[o].y);
+            b3[o] = make_float2(k * ux.x, k * ux.y);
+            b4[o] = make_float2(k * uy.x, k * uy.y);
+            b5[o] = r;
+        } else {
+            const float2 gv = make_float2(b0[o].x * s, b0[o].y * s);
+            b3[o] = make_float2(k * ux.x + ax * gv.x, k * ux.y + ax * gv.y);
+            b4[o] = make_float2(k * uy.x + ay * gv.x, k * uy.y + ay * gv.y);
+            b5[o] = make_float2(sg * gv.x, sg * gv.y);
+        }
+    }
+}
+
+// W = -i xi_x b3 - i xi_y b4 + b5; b0 = mode-dependent multiple of W
+//   kind 0 (RESIDUAL): -W / lambda0, 1 (OP_B): W / lambda0, 2 (TRUE_RESIDUAL): -W, 3 (ADJ_B): W
+__global__ void k_cdr_assemble(const CdrInst* ins, int cnt, long long np, const float2* b3, const float2* b4,
+                               const float2* b5, float2* b0, int kind) {
+    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < cnt * np; g += (long long)gridDim.x * blockDim.x) {
+        int j; long long p;
+        field_point(ins, np, g, &j, &p);
+        const CdrInst in = ins[j];
+        const int y = (int)(p / in.n), x = (int)(p % in.n);
+        const float kx = xi_of(x, in.n, in.h), ky = xi_of(y, in.n, in.h);
+        const long long o = in.off + p;
+        const float2 a = b3[o], b = b4[o], c = b5[o];
+        // -i xi (a) = (xi a.y, -xi a.x)
+        float2 w = make_float2(kx * a.y + ky * b.y + c.x, -kx * a.x - ky * b.x + c.y);
+        if (kind == 0 || kind == 2) w = make_float2(-w.x, -w.y);
+        if (kind == 0 || kind == 1) {
+            const float lr = (float)in.k0 * (kx * kx + ky * ky) + (float)in.s0;
+            const float li = (float)in.v0x * kx + (float)in.v0y * ky;
+            const float d = 1.f / (lr * lr + li * li);
+            w = make_float2((w.x * lr + w.y * li) * d, (w.y * lr - w.x * li) * d);
+        }
+        b0[o] = w;
+    }
+}
+
+// out = b0 / n^2, norm2[j] += ||out||^2 (float32 per thread, float64 across)
+__global__ void k_cdr_out(const CdrInst* ins, int cnt, long long np, const float2* b0, float2* out, const int* ids,
+                          double* norm2) {
+    __shared__ double red[8];
+    const long long tot = cnt * np;
+    for (long long base = (long long)blockIdx.x * blockDim.x; base < tot; base += (long long)gridDim.x * blockDim.x) {
+        const long long g = base + threadIdx.x;
+        float acc = 0.f;
+        int j = (int)(base / np);
+        if (g < tot) {
+            long long p;
+            field_point(ins, np, g, &j, &p);
+            const CdrInst in = ins[j];
+            const float s = 1.f / ((float)in.n * (float)in.n);
+            const long long o = in.off + p;
+            const float2 v = make_float2(b0[o].x * s, b0[o].y * s);
+            out[o] = v;
+            acc = v.x * v.x + v.y * v.y;
+        }
+        if (norm2) {
+            // a block of 256 points never straddles two instances (np is a multiple of 256)
+            double a = acc;
+            for (int w = 16; w > 0; w >>= 1) a += __shfl_xor_sync(0xffffffffu, a, w);
+            if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = a;
+            __syncthreads();
+            if (threadIdx.x == 0 && base < tot) {
+                double t = 0;
+                for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+                atomicAdd(norm2 + ids[j], t);
+            }
+            __syncthreads();
+        }
+    }
+}
+
+}  // namespace
+}  // namespace npbs
+
+namespace npbs {
+namespace {
+
+bool cdr_radix_plan(int n, RadixPlan* p) {
+    if (n < 2 || n > kMaxN) return false;
+    p->n = n;
+    p->npass = 0;
+    int m = n;
+    while (m % 8 == 0) { p->radix[p->npass++] = 8; m /= 8; }
+    while (m % 4 == 0) { p->radix[p->npass++] = 4; m /= 4; }
+    while (m % 2 == 0) { p->radix[p->npass++] = 2; m /= 2; }
+    while (m % 3 == 0) { p->radix[p->npass++] = 3; m /= 3; }
+    return m == 1 && p->npass <= kMaxPass;
+}
+
+// One grid size of a CDR batch, prepared on the device.
+struct CdrGroup {
+    int n = 0, cnt = 0;
+    RadixPlan plan{};
+    const float2* tw = nullptr;
+    const CdrInst* ins = nullptr;   // device [cnt]
+    const int* ids = nullptr;       // device [cnt]: batch index of each
+    const long long* off = nullptr; // device [6 cnt]: field offsets of buffer k (k * extent + offset)
+};
+
+struct CdrPrep {
+    std::vector<CdrGroup> groups;
+    long long extent = 0;
+    float2* buf = nullptr;  // 6 complex fields of the batch extent
+};
+
+npbs_status cdr_prepare(npbs_ctx* ctx, const npbs_batch* batch, const npbs_cdr_consts* consts, CdrPrep* P,
+                        cudaStream_t st) {
+    if (!batch || batch->count < 0 || (batch->count > 0 && (!batch->inst || !consts)))
+        return set_err(ctx, NPBS_ERR_INVALID_ARG, "cdr: NULL batch or constants");
+    std::map<int, std::vector<int>> by;
+    long long ext = 0;
+    for (int j = 0; j < batch->count; ++j) {
+        const npbs_instance& s = batch->inst[j];
+        RadixPlan rp;
+        if (s.nx != s.ny || s.nx % 16 != 0 || !cdr_radix_plan(s.nx, &rp)) {
+            char buf[160];
+            snprintf(buf, sizeof buf, "cdr: instance %d is %d x %d; need square grids, side a multiple of 16, 2^a 3^b <= %d",
+                     j, s.ny, s.nx, kMaxN);
+            return set_err(ctx, NPBS_ERR_UNSUPPORTED_SIZE, buf);
+        }
+        if (!(s.h > 0.0) || !std::isfinite(s.h) || s.offset < 0 || s.offset % 32 != 0)
+            return set_err(ctx, NPBS_ERR_INVALID_ARG, "cdr: need h > 0 and offsets >= 0, multiples of 32");
+        const npbs_cdr_consts& c = consts[j];
+        if (!(c.kappa0 > 0.0) || !std::isfinite(c.v0x) || !std::isfinite(c.v0y) || !std::isfinite(c.sigma0) ||
+            !std::isfinite(c.kappa0))
+            return set_err(ctx, NPBS_ERR_INVALID_ARG, "cdr: need kappa0 > 0 and finite background constants");
+        by[s.nx].push_back(j);
+        ext = std::max<long long>(ext, s.offset + (long long)s.nx * s.ny);
+    }
+    P->extent = ext;
+    P->groups.clear();
+    // host staging of every group's tables, then one upload
+    std::vector<char> host;
+    auto put = [&](const void* src, size_t bytes) {
+        const size_t o = (host.size() + 255) & ~size_t(255);
+        host.resize(o + bytes);
+        memcpy(host.data() + o, src, bytes);
+        return o;
+    };
+    struct Offs { size_t tw, ins, ids, off; };
+    std::vector<Offs> offs;
+    for (auto& kv : by) {
+        const int n = kv.first;
+        CdrGroup g;
+        g.n = n;
+        g.cnt = (int)kv.second.size();
+        cdr_radix_plan(n, &g.plan);
+        std::vector<float2> tw(n);
+        for (int k = 0; k < n; ++k) {
+            const double a = -2.0 * M_PI * (double)k / (double)n;
+            tw[k] = make_float2((float)std::cos(a), (float)std::sin(a));
+        }
+        std::vector<CdrInst> ins;
+        std::vector<long long> off;
+        for (int j : kv.second) {
+            const npbs_instance& s = batch->inst[j];
+            const npbs_cdr_consts& c = consts[j];
+            ins.push_back(CdrInst{s.nx, s.h, s.offset, c.kappa0, c.v0x, c.v0y, c.sigma0});
+        }
+        for (int k = 0; k < 6; ++k)
+            for (int j : kv.second) off.push_back((long long)k * ext + batch->inst[j].offset);
+        Offs o;
+        o.tw = put(tw.data(), sizeof(float2) * tw.size());
+        o.ins = put(ins.data(), sizeof(CdrInst) * ins.size());
+        o.ids = put(kv.second.data(), sizeof(int) * kv.second.size());
+        o.off = put(off.data(), sizeof(long long) * off.size());
+        offs.push_back(o);
+        P->groups.push_back(g);
+    }
+    NPBS_CK(ctx, ctx->work[12].ensure(std::max<size_t>(host.size(), 256)));
+    NPBS_CK(ctx, ctx->work[13].ensure(sizeof(float2) * 6 * (size_t)std::max<long long>(ext, 1)));
+    char* d = static_cast<char*>(ctx->work[12].p);
+    NPBS_CK(ctx, cudaMemcpyAsync(d, host.data(), host.size(), cudaMemcpyHostToDevice, st));
+    NPBS_CK(ctx, cudaStreamSynchronize(st));  // the staging vector goes out of scope
+    for (size_t i = 0; i < P->groups.size(); ++i) {
+        P->groups[i].tw = reinterpret_cast<const float2*>(d + offs[i].tw);
+        P->groups[i].ins = reinterpret_cast<const CdrInst*>(d + offs[i].ins);
+        P->groups[i].ids = reinterpret_cast<const int*>(d + offs[i].ids);
+        P->groups[i].off = reinterpret_cast<const long long*>(d + offs[i].off);
+    }
+    P->buf = static_cast<float2*>(ctx->work[13].p);
+    NPBS_CK(ctx, fft2d::set_attrs());
+    return NPBS_OK;
+}
+
+int cdr_grid(long long n) { return (int)std::min<long long>((n + 255) / 256, 152LL * 32); }
+
+// One CDR apply over a prepared batch (mode: RESIDUAL, OP_B, TRUE_RESIDUAL, ADJ_B).
+npbs_status cdr_run(npbs_ctx* ctx, const CdrPrep& P, int mode, const float* kappa, const float* vx, const float* vy,
+                    const float* sigma, const float2* f, const float2* x, float2* out, double* norm2, int count,
+                    cudaStream_t st) {
+    const long long E = P.extent;
+    float2* b[6];
+    for (int k = 0; k < 6; ++k) b[k] = P.buf + k * E;
+    if (norm2) NPBS_CK(ctx, cudaMemsetAsync(norm2, 0, sizeof(double) * count, st));
+    const bool adj = mode == NPBS_ADJ_B;
+    const int kind = mode == NPBS_RESIDUAL ? 0 : mode == NPBS_OP_B ? 1 : mode == NPBS_TRUE_RESIDUAL ? 2 : 3;
+    for (const CdrGroup& g : P.groups) {
+        const long long np = (long long)g.n * g.n, tot = (long long)g.cnt * np;
+        const int grid = cdr_grid(tot);
+        k_cdr_copy<<<grid, 256, 0, st>>>(g.ins, g.cnt, np, x, b[0]);
+        NPBS_CK(ctx, fft2d::run(P.buf, g.off, g.cnt, g.n, -1, g.plan, g.tw, st));
+        k_cdr_grad<<<grid, 256, 0, st>>>(g.ins, g.cnt, np, b[0], b[1], b[2], adj ? 1 : 0);
+        // b1, b2 (and for the adjoint b0 = G^* x) back to physical space
+        NPBS_CK(ctx, fft2d::run(P.buf, g.off + g.cnt, 2LL * g.cnt, g.n, 1, g.plan, g.tw, st));
+        if (adj) NPBS_CK(ctx, fft2d::run(P.buf, g.off, g.cnt, g.n, 1, g.plan, g.tw, st));
+        k_cdr_flux<<<grid, 256, 0, st>>>(g.ins, g.cnt, np, kappa, vx, vy, sigma, x,
+                                         (mode == NPBS_OP_B || adj) ? nullptr : f, b[0], b[1], b[2], b[3], b[4], b[5],
+                                         adj ? 1 : 0);
+        NPBS_CK(ctx, fft2d::run(P.buf, g.off + 3 * g.cnt, 3LL * g.cnt, g.n, -1, g.plan, g.tw, st));
+        k_cdr_assemble<<<grid, 256, 0, st>>>(g.ins, g.cnt, np, b[3], b[4], b[5], b[0], kind);
+        NPBS_CK(ctx, fft2d::run(P.buf, g.off, g.cnt, g.n, 1, g.plan, g.tw, st));
+        k_cdr_out<<<grid, 256, 0, st>>>(g.ins, g.cnt, np, b[0], out, g.ids, norm2);
+        NPBS_CK(ctx, cudaGetLastError());
+        ctx->count(st, 5 + 2 * (adj ? 5 : 4));
+    }
+    return NPBS_OK;
+}
+
+// background constants per instance: the midpoints of the ranges of kappa and
+// sigma, the grid means of vx and vy
+__global__ void k_cdr_background(const CdrInst* ins, const int* ids, const float* kappa, const float* vx,
+                                 const float* vy, const float* sigma, double* out) {
+    const CdrInst in = ins[blockIdx.x];
+    const long long np = (long long)in.n * in.n;
+    double mx = 0, my = 0;
+    float kmin = 3.0e38f, kmax = -3.0e38f, smin = 3.0e38f, smax = -3.0e38f;
+    for (long long p = threadIdx.x; p < np; p += blockDim.x) {
+        const long long o = in.off + p;
+        kmin = fminf(kmin, kappa[o]);
+        kmax = fmaxf(kmax, kappa[o]);
+        smin = fminf(smin, sigma[o]);
+        smax = fmaxf(smax, sigma[o]);
+        mx += vx[o];
+        my += vy[o];
+    }
+    for (int w = 16; w > 0; w >>= 1) {
+        mx += __shfl_xor_sync(0xffffffffu, mx, w);
+        my += __shfl_xor_sync(0xffffffffu, my, w);
+        kmin = fminf(kmin, __shfl_xor_sync(0xffffffffu, kmin, w));
+        kmax = fmaxf(kmax, __shfl_xor_sync(0xffffffffu, kmax, w));
+        smin = fminf(smin, __shfl_xor_sync(0xffffffffu, smin, w));
+        smax = fmaxf(smax, __shfl_xor_sync(0xffffffffu, smax, w));
+    }
+    __shared__ double rd[2][8];
+    __shared__ float rf[4][8];
+    const int wp = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+        rd[0][wp] = mx;
+        rd[1][wp] = my;
+        rf[0][wp] = kmin;
+        rf[1][wp] = kmax;
+        rf[2][wp] = smin;
+        rf[3][wp] = smax;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int nw = (int)(blockDim.x >> 5);
+        double a = 0, b = 0;
+        float k0 = rf[0][0], k1 = rf[1][0], s0 = rf[2][0], s1 = rf[3][0];
+        for (int w = 0; w < nw; ++w) {
+            a += rd[0][w];
+            b += rd[1][w];
+            k0 = fminf(k0, rf[0][w]);
+            k1 = fmaxf(k1, rf[1][w]);
+            s0 = fminf(s0, rf[2][w]);
+            s1 = fmaxf(s1, rf[3][w]);
+        }
+        double* o = out + 4 * ids[blockIdx.x];
+        o[0] = 0.5 * ((double)k0 + (double)k1);
+        o[1] = a / (double)np;
+        o[2] = b / (double)np;
+        o[3] = 0.5 * ((double)s0 + (double)s1);
+    }
+}
+
+// u += r (the Born series step, M = identity)
+__global__ void k_cdr_axpy(const CdrInst* ins, int cnt, long long np, const float2* r, float2* u) {
+    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < cnt * np; g += (long long)gridDim.x * blockDim.x) {
+        int j; long long p;
+        field_point(ins, np, g, &j, &p);
+        const long long o = ins[j].off + p;
+        u[o] = make_float2(u[o].x + r[o].x, u[o].y + r[o].y);
+    }
+}
+
+}  // namespace
+}  // namespace npbs
+
+using namespace npbs;
+
+extern "C" {
+
+npbs_status npbs_cdr_background(npbs_ctx* ctx, const npbs_batch* batch, const float* kappa, const float* vx,
+                                const float* vy, const float* sigma, npbs_cdr_consts* out, npbs_stream stream) {
+    if (!ctx) return NPBS_ERR_INVALID_ARG;
+    if (!batch || batch->count < 0 || (batch->count > 0 && (!kappa || !vx || !vy || !sigma || !out)))
+        return set_err(ctx, NPBS_ERR_INVALID_ARG, "npbs_cdr_background: NULL argument");
+    if (batch->count == 0) return NPBS_OK;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    std::vector<npbs_cdr_consts> dummy(batch->count, npbs_cdr_consts{1.0, 0.0, 0.0, 0.0});
+    CdrPrep P;
+    npbs_status st = cdr_prepare(ctx, batch, dummy.data(), &P, s);
+    if (st != NPBS_OK) return st;
+    NPBS_CK(ctx, ctx->work[14].ensure(sizeof(double) * 4 * batch->count));
+    double* dm = static_cast<double*>(ctx->work[14].p);
+    for (const CdrGroup& g : P.groups) k_cdr_background<<<g.cnt, 256, 0, s>>>(g.ins, g.ids, kappa, vx, vy, sigma, dm);
+    NPBS_CK(ctx, cudaGetLastError());
+    ctx->count(s, (long long)P.groups.size());
+    std::vector<double> h(4 * batch->count);
+    NPBS_CK(ctx, cudaMemcpyAsync(h.data(), dm, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, s));
+    NPBS_CK(ctx, cudaStreamSynchronize(s));
+    for (int j = 0; j < batch->count; ++j) out[j] = npbs_cdr_consts{h[4 * j], h[4 * j + 1], h[4 * j + 2], h[4 * j + 3]};
+    return NPBS_OK;
+}
+
+npbs_status cdr_apply(npbs_ctx* ctx, const npbs_batch* batch, const npbs_cdr_consts* consts, const float* kappa,
+                      const float* vx, const float* vy, const float* sigma, const void* f, const void* x, void* out,
+                      npbs_mode mode, double* norm2, npbs_stream stream) {
+    if (!ctx) return NPBS_ERR_INVALID_ARG;
+    if (mode != NPBS_RESIDUAL && mode != NPBS_OP_B && mode != NPBS_TRUE_RESIDUAL && mode != NPBS_ADJ_B)
+        return set_err(ctx, NPBS_ERR_INVALID_ARG, "cdr_apply: mode must be RESIDUAL, OP_B, TRUE_RESIDUAL or ADJ_B");
+    if (!batch || batch->count == 0) return batch ? NPBS_OK : NPBS_ERR_INVALID_ARG;
+    const bool need_f = mode == NPBS_RESIDUAL || mode == NPBS_TRUE_RESIDUAL;
+    if (!kappa || !vx || !vy || !sigma || !x || !out || (need_f && !f))
+        return set_err(ctx, NPBS_ERR_INVALID_ARG, "cdr_apply: NULL field pointer");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    CdrPrep P;
+    npbs_status st = cdr_prepare(ctx, batch, consts, &P, s);
+    if (st != NPBS_OK) return st;
+    return cdr_run(ctx, P, (int)mode, kappa, vx, vy, sigma, static_cast<const float2*>(f),
+                   static_cast<const float2*>(x), static_cast<float2*>(out), norm2, batch->count, s);
+}
+
+npbs_status cdr_solve(npbs_ctx* ctx, const npbs_net* net, const npbs_batch* batch, const npbs_cdr_consts* consts,
+                      const float* kappa, const float* vx, const float* vy, const float* sigma, const void* f,
+                      const float* a, void* u, const npbs_solve_opts* opts, npbs_report* report, npbs_stream stream) {
+    if (!ctx) return NPBS_ERR_INVALID_ARG;
+    if (!batch || batch->count < 0) return set_err(ctx, NPBS_ERR_INVALID_ARG, "cdr_solve: NULL batch");
+    const int cnt = batch->count;
+    if (cnt == 0) return NPBS_OK;
+    if (!opts || !(opts->rtol >= 0.0) || opts->max_iter < 0 || opts->check_every < 1)
+        return set_err(ctx, NPBS_ERR_INVALID_ARG, "cdr_solve: need rtol >= 0, max_iter >= 0, check_every >= 1");
+    if (!kappa || !vx || !vy || !sigma || !f || !u || (net && !a))
+        return set_err(ctx, NPBS_ERR_INVALID_ARG, "cdr_solve: NULL field pointer");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    CdrPrep P;
+    npbs_status st = cdr_prepare(ctx, batch, consts, &P, s);
+    if (st != NPBS_OK) return st;
+    const long long E = P.extent;
+    NPBS_CK(ctx, ctx->work[15].ensure(sizeof(float2) * (size_t)std::max<long long>(E, 1) + sizeof(double) * 2 * cnt));
+    float2* r = static_cast<float2*>(ctx->work[15].p);
+    double* n2 = reinterpret_cast<double*>(r + E);
+    double* f2 = n2 + cnt;
+    float2* U = static_cast<float2*>(u);
+    const float2* F = static_cast<const float2*>(f);
+    // ||f||^2 per instance: TRUE_RESIDUAL of x = 0 is f (u is the iterate, so use r as a zero field)
+    NPBS_CK(ctx, cudaMemsetAsync(r, 0, sizeof(float2) * E, s));
+    st = cdr_run(ctx, P, NPBS_TRUE_RESIDUAL, kappa, vx, vy, sigma, F, r, r, f2, cnt, s);
+    if (st != NPBS_OK) return st;
+    std::vector<double> hf(cnt), hr(cnt);
+    NPBS_CK(ctx, cudaMemcpyAsync(hf.data(), f2, sizeof(double) * cnt, cudaMemcpyDeviceToHost, s));
+    NetRun run;
+    std::vector<int> all(cnt);
+    for (int j = 0; j < cnt; ++j) all[j] = j;
+    const Net* N = reinterpret_cast<const Net*>(net);
+    if (N) {
+        npbs_status s2;
+        const Plan* pl = nullptr;
+        // the network groups instances through a context plan (constants there are placeholders)
+        std::vector<npbs_instance> tmp(batch->inst, batch->inst + cnt);
+        for (auto& t : tmp) { t.k0sq = 0.0; t.eps = 1.0; }
+        npbs_batch b2{cnt, tmp.data()};
+        pl = get_plan(ctx, &b2, &s2);
+        if (!pl) return s2;
+        s2 = net_prepare(ctx, *N, *pl, all, false, &run, s, a);
+        if (s2 != NPBS_OK) return s2;
+    }
+    std::vector<int> iters(cnt, 0);
+    std::vector<double> rt(cnt, 1.0);
+    std::vector<npbs_status> stat(cnt, NPBS_NOT_CONVERGED);
+    int it = 0;
+    auto check = [&]() -> npbs_status {
+        npbs_status s2 = cdr_run(ctx, P, NPBS_TRUE_RESIDUAL, kappa, vx, vy, sigma, F, U, r, n2, cnt, s);
+        if (s2 != NPBS_OK) return s2;
+        NPBS_CK(ctx, cudaMemcpyAsync(hr.data(), n2, sizeof(double) * cnt, cudaMemcpyDeviceToHost, s));
+        NPBS_CK(ctx, cudaStreamSynchronize(s));
+        for (int j = 0; j < cnt; ++j) {
+            if (stat[j] != NPBS_NOT_CONVERGED) continue;
+            rt[j] = std::sqrt(hr[j] / std::max(hf[j], 1e-300));
+            iters[j] = it;
+            if (!std::isfinite(rt[j])) stat[j] = NPBS_ERR_NONFINITE;
+            else if (rt[j] <= opts->rtol) stat[j] = NPBS_OK;
+        }
+        return NPBS_OK;
+    };
+    st = check();
+    if (st != NPBS_OK) return st;
+    while (it < opts->max_iter) {
+        bool any = false;
+        for (int j = 0; j < cnt; ++j) any |= stat[j] == NPBS_NOT_CONVERGED;
+        if (!any) break;
+        // every instance iterates (converged ones keep improving); reports keep their first passing check
+        for (int k = 0; k < opts->check_every && it < opts->max_iter; ++k, ++it) {
+            st = cdr_run(ctx, P, NPBS_RESIDUAL, kappa, vx, vy, sigma, F, U, r, nullptr, cnt, s);
+            if (st != NPBS_OK) return st;
+            if (N) {
+                st = net_run_forward(ctx, *N, run, r, a, U, 1, s);
+                if (st != NPBS_OK) return st;
+            } else {
+                for (const CdrGroup& g : P.groups) {
+                    const long long np = (long long)g.n * g.n;
+                    k_cdr_axpy<<<cdr_grid(g.cnt * np), 256, 0, s>>>(g.ins, g.cnt, np, r, U);
+                }
+                NPBS_CK(ctx, cudaGetLastError());
+                ctx->count(s, (long long)P.groups.size());
+            }
+        }
+        st = check();
+        if (st != NPBS_OK) return st;
+    }
+    npbs_status ret = NPBS_OK;
+    for (int j = 0; j < cnt; ++j) {
+        if (stat[j] == NPBS_NOT_CONVERGED) iters[j] = it;
+        if (report) {
+            if (report->iters) report->iters[j] = iters[j];
+            if (report->rtol) report->rtol[j] = rt[j];
+            if (report->status) report->status[j] = stat[j];
+            if (report->flags) report->flags[j] = 0;
+        }
+        if (stat[j] == NPBS_ERR_NONFINITE) ret = NPBS_ERR_NONFINITE;
+        else if (stat[j] != NPBS_OK && ret == NPBS_OK) ret = NPBS_NOT_CONVERGED;
+    }
+    return ret;
+}
+
+npbs_status cdr_train_step(npbs_ctx* ctx, npbs_net* net, const npbs_batch* batch, const npbs_cdr_consts* consts,
+                           const float* kappa, const float* vx, const float* vy, const float* sigma, const void* f,
+                           const float* a, const void* u_snap, int32_t unroll, float lr, float weight_decay,
+                           float* loss_host, npbs_stream stream) {
+    if (!ctx) return NPBS_ERR_INVALID_ARG;
+    if (!net || !batch || !kappa || !vx || !vy || !sigma || !f || !a || !u_snap || !loss_host)
+        return set_err(ctx, NPBS_ERR_INVALID_ARG, "cdr_train_step: NULL argument");
+    if (unroll < 1 || unroll > 16 || !(lr >= 0.f) || !(weight_decay >= 0.f))
+        return set_err(ctx, NPBS_ERR_INVALID_ARG, "cdr_train_step: need 1 <= unroll <= 16, lr >= 0, weight_decay >= 0");
+    *loss_host = 0.f;
+    const int cnt = batch->count;
+    if (cnt <= 0) return cnt == 0 ? NPBS_OK : NPBS_ERR_INVALID_ARG;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    CdrPrep P;
+    npbs_status st = cdr_prepare(ctx, batch, consts, &P, s);
+    if (st != NPBS_OK) return st;
+    // the network and the step's vector kernels walk the instances through a
+    // context plan (its k0sq / eps are placeholders, unused here)
+    std::vector<npbs_instance> tmp(batch->inst, batch->inst + cnt);
+    for (auto& t : tmp) { t.k0sq = 0.0; t.eps = 1.0; }
+    npbs_batch b2{cnt, tmp.data()};
+    const Plan* pl = get_plan(ctx, &b2, &st);
+    if (!pl) return st;
+    const float2* F = static_cast<const float2*>(f);
+    const float2* usnap = static_cast<const float2*>(u_snap);
+    BornOp op = [&](int mode, const float2* x, float2* out, double* norm2) -> npbs_status {
+        return cdr_run(ctx, P, mode, kappa, vx, vy, sigma, F, mode == NPBS_RESIDUAL ? usnap : x, out, norm2, cnt, s);
+    };
+    return train_step_reta(ctx, *reinterpret_cast<Net*>(net), pl, a, unroll, lr, weight_decay, loss_host, s, op);
+}
+
+}  // extern "C"

@@ -33,7 +33,7 @@
 #include <cstring>
 #include <vector>
 
-#include "fft.cuh"
+#include "fft2d.cuh"
 #include "net.cuh"
 
 namespace npbs {
@@ -41,7 +41,6 @@ namespace npbs {
 namespace {
 
 constexpr int kMaxC = 32;     // channel bound of the register-blocked kernels
-constexpr int kTile = 4096;   // complex elements of one FFT tile buffer (two per block)
 constexpr int kModesPerBlock = 8;
 
 int grid_of(long long n, int per = 256) { return (int)std::min<long long>((n + per - 1) / per, 152LL * 64); }
@@ -70,58 +69,19 @@ __device__ __forceinline__ float gelu_grad(float x) {
     return 0.5f * (1.f + erff(x * 0.70710678118654752f)) + x * 0.39894228040143268f * expf(-0.5f * x * x);
 }
 
-// ------------------------------------------------------------- 2D FFT passes
-
-// rb rows of one field per block, the transform along each row
-template <int DIR>
-__global__ void __launch_bounds__(256) k_fft_rows(float2* data, int n, int rb, RadixPlan plan, const float2* tw) {
-    extern __shared__ __align__(16) float2 sm[];
-    const int nb = n / rb;
-    const long long field = blockIdx.x / nb;
-    float2* p = data + field * n * n + (long long)(blockIdx.x % nb) * rb * n;
-    const int cnt = rb * n;
-    for (int e = threadIdx.x; e < cnt; e += blockDim.x) sm[e] = p[e];
-    __syncthreads();
-    float2* res = fft_tile<float2, DIR, false>(sm, sm + kTile, plan, rb, 1, n, tw, threadIdx.x, blockDim.x);
-    for (int e = threadIdx.x; e < cnt; e += blockDim.x) p[e] = res[e];
-}
-
-// cb columns of one field per block, the transform along each column
-template <int DIR>
-__global__ void __launch_bounds__(256) k_fft_cols(float2* data, int n, int cb, RadixPlan plan, const float2* tw) {
-    extern __shared__ __align__(16) float2 sm[];
-    const int nb = n / cb;
-    const long long field = blockIdx.x / nb;
-    float2* p = data + field * n * n + (long long)(blockIdx.x % nb) * cb;
-    const int cnt = cb * n;
-    for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
-        const int i = e / cb, b = e - i * cb;
-        sm[e] = p[(long long)i * n + b];
-    }
-    __syncthreads();
-    float2* res = fft_tile<float2, DIR, true>(sm, sm + kTile, plan, cb, cb, 1, tw, threadIdx.x, blockDim.x);
-    for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
-        const int i = e / cb, b = e - i * cb;
-        p[(long long)i * n + b] = res[e];
-    }
-}
-
-int largest_divisor_at_most(int n, int lim) {
-    for (int d = std::min(n, lim); d >= 1; --d)
-        if (n % d == 0) return d;
-    return 1;
-}
-
 }  // namespace
 
 namespace {
 
 // ------------------------------------------------------------- pointwise kernels
 
-// LayerNorm statistics of each instance's coefficient field: mean and 1/sqrt(var + 1e-5)
-__global__ void k_ln_stats(SlotDev sd, const float* a, float* stats) {
+// LayerNorm statistics of each instance's coefficient channels: mean and
+// 1/sqrt(var + 1e-5); block b * ca + c reads channel c (ca channels, astride
+// elements apart) of instance b
+__global__ void k_ln_stats(SlotDev sd, const float* a, int ca, long long astride, float* stats) {
     __shared__ double s1[32], s2[32];
-    const float* p = a + sd.off[blockIdx.x];
+    const int b = blockIdx.x / ca, ch = blockIdx.x - (blockIdx.x / ca) * ca;
+    const float* p = a + (long long)ch * astride + sd.off[b];
     double m = 0.0, q = 0.0;
     for (long long e = threadIdx.x; e < sd.np; e += blockDim.x) {
         const double v = p[e];
@@ -145,13 +105,14 @@ __global__ void k_ln_stats(SlotDev sd, const float* a, float* stats) {
     }
 }
 
-// z = LayerNorm(a) as a one-channel plane [nb][1][np]
-__global__ void k_ln_plane(SlotDev sd, const float* a, const float* stats, float* z) {
-    const long long tot = (long long)sd.nb * sd.np;
+// z = LayerNorm(a) as channel planes [nb][ca][np]
+__global__ void k_ln_plane(SlotDev sd, const float* a, int ca, long long astride, const float* stats, float* z) {
+    const long long tot = (long long)sd.nb * ca * sd.np;
     for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < tot; g += (long long)gridDim.x * blockDim.x) {
-        const int b = (int)(g / sd.np);
-        const long long p = g - (long long)b * sd.np;
-        z[g] = (a[sd.off[b] + p] - stats[2 * b]) * stats[2 * b + 1];
+        const long long bc = g / sd.np;
+        const long long p = g - bc * sd.np;
+        const int b = (int)(bc / ca), ch = (int)(bc - (long long)b * ca);
+        z[g] = (a[(long long)ch * astride + sd.off[b] + p] - stats[2 * bc]) * stats[2 * bc + 1];
     }
 }
 
@@ -478,20 +439,21 @@ static bool fno_radix_plan(int n, RadixPlan* p) {
     return m == 1 && p->npass <= kMaxPass;
 }
 
-FnoDef fno_def(int n, int C, int m, int L) {
+FnoDef fno_def(int n, int C, int m, int L, int ca) {
     FnoDef d;
     d.n = n;
     d.C = C;
     d.m = m;
     d.L = L;
-    if (n < 2 || C < 1 || m < 1 || L < 0 || L > 8) return d;  // count stays 0: invalid
+    d.ca = ca;
+    if (n < 2 || C < 1 || m < 1 || L < 0 || L > 8 || ca < 1 || ca > kMaxC) return d;  // count stays 0: invalid
     d.ky = rows_kept(n, m);
     d.kx = std::min(m, n / 2 + 1);
     d.fy = n;
     d.fx = n / 2 + 1;
     const long long spec = 2LL * C * C * d.ky * d.kx, full = 2LL * C * C * d.fy * d.fx;
     long long o = 0;
-    d.lift_a_w = o; o += C;
+    d.lift_a_w = o; o += (long long)C * ca;
     d.lift_a_b = o; o += C;
     for (int l = 0; l < L; ++l) {
         d.spec[l] = o; o += spec;
@@ -535,8 +497,8 @@ size_t ws_layout(const FnoDef& d, int nb, bool train, FnoWS* w, char* base) {
     auto f = [&](long long n) { return reinterpret_cast<float*>(take(sizeof(float) * n)); };
     auto c2 = [&](long long n) { return reinterpret_cast<float2*>(take(sizeof(float2) * n)); };
     FnoWS t;
-    t.stats = f(2LL * nb);
-    t.lnp = f(plane);
+    t.stats = f(2LL * nb * d.ca);
+    t.lnp = f(d.ca * plane);
     t.rp = f(2 * plane);
     const int ncoef = train ? d.L + 1 : 2;
     for (int l = 0; l < ncoef; ++l) t.c[l] = f(d.C * plane);
@@ -564,17 +526,7 @@ size_t ws_layout(const FnoDef& d, int nb, bool train, FnoWS* w, char* base) {
 float* coef(const FnoWS& w, const FnoDef& d, int l, bool train) { return train ? w.c[l] : w.c[l & 1]; }
 
 cudaError_t fft2(const FnoDef& d, float2* Z, long long fields, int dir, cudaStream_t st) {
-    const int n = d.n;
-    const int rb = largest_divisor_at_most(n, kTile / n), cb = largest_divisor_at_most(n, std::min(16, kTile / n));
-    const size_t sm = 2 * kTile * sizeof(float2);
-    if (dir < 0) {
-        k_fft_rows<-1><<<(unsigned)(fields * (n / rb)), 256, sm, st>>>(Z, n, rb, d.plan, d.tw);
-        k_fft_cols<-1><<<(unsigned)(fields * (n / cb)), 256, sm, st>>>(Z, n, cb, d.plan, d.tw);
-    } else {
-        k_fft_rows<1><<<(unsigned)(fields * (n / rb)), 256, sm, st>>>(Z, n, rb, d.plan, d.tw);
-        k_fft_cols<1><<<(unsigned)(fields * (n / cb)), 256, sm, st>>>(Z, n, cb, d.plan, d.tw);
-    }
-    return cudaGetLastError();
+    return fft2d::run(Z, nullptr, fields, d.n, dir, d.plan, d.tw, st);
 }
 
 // Retained-mode spectra of the real channel planes x [nb][Ci][np] into X [nb][Ci][K].
@@ -648,28 +600,46 @@ cudaError_t layer_bwd(const FnoDef& d, const FnoWS& w, int nb, const float* x, c
     return synthesize(d, w, nb, w.Yc, C, m, G, C, wl, 1, C, nullptr, 0, nullptr, dx, 0, st, kc);
 }
 
-// The forward of one group, keeping every activation when `train`.
-cudaError_t forward_group(const FnoDef& d, const float* P, const FnoWS& w, const SlotDev& sd, const float2* r,
-                          const float* a, float2* out, int add, bool train, cudaStream_t st, long long* kc) {
+// NLFL_L(...NLFL_1(Phi(a))) of one group into coef(w, d, L), keeping every
+// activation when `train`.
+cudaError_t coefficient_branch(const FnoDef& d, const float* P, const FnoWS& w, const SlotDev& sd, const float* a,
+                               long long astride, bool train, cudaStream_t st, long long* kc) {
     const int C = d.C, nb = sd.nb;
     const long long np = sd.np;
-    k_ln_stats<<<nb, 256, 0, st>>>(sd, a, w.stats);
-    k_ln_plane<<<grid_of((long long)nb * np), 256, 0, st>>>(sd, a, w.stats, w.lnp);
-    k_mix_points<<<grid_of((long long)nb * np), 256, 0, st>>>(nb, np, w.lnp, 1, P + d.lift_a_w, 1, 1, P + d.lift_a_b,
-                                                              nullptr, 0.f, C, 0, nullptr, coef(w, d, 0, train), 0);
+    k_ln_stats<<<nb * d.ca, 256, 0, st>>>(sd, a, d.ca, astride, w.stats);
+    k_ln_plane<<<grid_of((long long)nb * d.ca * np), 256, 0, st>>>(sd, a, d.ca, astride, w.stats, w.lnp);
+    k_mix_points<<<grid_of((long long)nb * np), 256, 0, st>>>(nb, np, w.lnp, d.ca, P + d.lift_a_w, d.ca, 1,
+                                                              P + d.lift_a_b, nullptr, 0.f, C, 0, nullptr,
+                                                              coef(w, d, 0, train), 0);
     *kc += 3;
     cudaError_t e = cudaGetLastError();
     for (int l = 0; l < d.L && e == cudaSuccess; ++l)
         e = layer_fwd(d, w, nb, coef(w, d, l, train), P + d.spec[l], d.m, P + d.loc_w[l], P + d.loc_b[l], 1,
                       train ? w.pre[l] : nullptr, coef(w, d, l + 1, train), st, kc);
-    if (e != cudaSuccess) return e;
+    return e;
+}
+
+// The forward of one group, keeping every activation when `train`; cf (nullable)
+// holds the coefficient branch's output already (the inference cache).
+cudaError_t forward_group(const FnoDef& d, const float* P, const FnoWS& w, const NetGroup& grp, const float2* r,
+                          const float* a, float2* out, int add, bool train, cudaStream_t st, long long* kc,
+                          const float* cf = nullptr) {
+    const SlotDev& sd = grp.sd;
+    const int C = d.C, nb = sd.nb;
+    const long long np = sd.np;
+    cudaError_t e = cudaSuccess;
+    if (!cf) {
+        e = coefficient_branch(d, P, w, sd, a, grp.astride, train, st, kc);
+        if (e != cudaSuccess) return e;
+        cf = coef(w, d, d.L, train);
+    }
     k_complex_planes<<<grid_of((long long)nb * np), 256, 0, st>>>(sd, r, w.rp);
     k_mix_points<<<grid_of((long long)nb * np), 256, 0, st>>>(nb, np, w.rp, 2, P + d.lift_r, 2, 1, nullptr, nullptr,
                                                               0.f, C, 0, nullptr, w.x0, 0);
     *kc += 2;
     e = layer_fwd(d, w, nb, w.x0, P + d.spec_r, d.fx, P + d.loc_r, nullptr, 0, nullptr, w.x1, st, kc);
     if (e != cudaSuccess) return e;
-    k_mul<<<grid_of((long long)nb * C * np), 256, 0, st>>>((long long)nb * C * np, coef(w, d, d.L, train), w.x1, w.z);
+    k_mul<<<grid_of((long long)nb * C * np), 256, 0, st>>>((long long)nb * C * np, cf, w.x1, w.z);
     *kc += 1;
     e = layer_fwd(d, w, nb, w.z, P + d.spec_f, d.m, P + d.loc_f, nullptr, 0, nullptr, w.z1, st, kc);
     if (e != cudaSuccess) return e;
@@ -679,19 +649,13 @@ cudaError_t forward_group(const FnoDef& d, const float* P, const FnoWS& w, const
     return cudaGetLastError();
 }
 
-cudaError_t set_fft_attrs() {
-    const int sm = (int)(2 * kTile * sizeof(float2));
-    cudaError_t e = cudaFuncSetAttribute(k_fft_rows<-1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_fft_rows<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_fft_cols<-1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_fft_cols<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    return e;
-}
+cudaError_t set_fft_attrs() { return fft2d::set_attrs(); }
 
 }  // namespace
 
-npbs_status fno_prepare(npbs_ctx* ctx, const FnoDef& d, const Plan& pl, const std::vector<int>& which, bool train,
-                        NetRun* run, cudaStream_t st) {
+npbs_status fno_prepare(npbs_ctx* ctx, const Net& net, const Plan& pl, const std::vector<int>& which, bool train,
+                        NetRun* run, cudaStream_t st, const float* a) {
+    const FnoDef& d = *net.fno;
     run->groups.clear();
     run->train = train;
     std::vector<long long> off;
@@ -717,7 +681,38 @@ npbs_status fno_prepare(npbs_ctx* ctx, const FnoDef& d, const Plan& pl, const st
     g.sd.nb = (int)off.size();
     g.sd.np = (long long)d.n * d.n;
     g.sd.off = doff;
+    unsigned long long h = 1469598103934665603ull;  // FNV-1a over the offsets
+    for (long long o : off) {
+        for (int b = 0; b < 8; ++b) {
+            h ^= (unsigned long long)((o >> (8 * b)) & 0xff);
+            h *= 1099511628211ull;
+        }
+    }
+    g.key = h;
+    g.astride = pl.extent;
     run->groups.push_back(g);
+    // inference: compute the coefficient branch once for this instance set,
+    // outside any capture, so that the runs (and graphs captured from them)
+    // only evaluate the residual path
+    if (!train && a) {
+        const size_t need = sizeof(float) * (size_t)g.sd.nb * d.C * g.sd.np;
+        if (d.cache_bytes < need) {
+            cudaFree(d.cache);
+            d.cache = nullptr;
+            d.cache_bytes = 0;
+            NPBS_CK(ctx, cudaMalloc(&d.cache, need));
+            d.cache_bytes = need;
+        }
+        FnoWS w;
+        ws_layout(d, g.sd.nb, false, &w, static_cast<char*>(ctx->net_ws.p));
+        long long kc = 0;
+        NPBS_CK(ctx, coefficient_branch(d, net.params, w, g.sd, a, g.astride, false, st, &kc));
+        NPBS_CK(ctx, cudaMemcpyAsync(d.cache, coef(w, d, d.L, false), need, cudaMemcpyDeviceToDevice, st));
+        ctx->count(st, kc);
+        d.cache_a = a;
+        d.cache_key = g.key;
+        d.cache_version = net.version;
+    }
     return NPBS_OK;
 }
 
@@ -728,7 +723,10 @@ npbs_status fno_run_forward(npbs_ctx* ctx, const Net& net, const NetRun& run, co
         FnoWS w;
         ws_layout(d, g.sd.nb, run.train, &w, static_cast<char*>(ctx->net_ws.p));
         long long kc = 0;
-        NPBS_CK(ctx, forward_group(d, net.params, w, g.sd, r, a, out, add, run.train, st, &kc));
+        const bool cached = !run.train && d.cache && d.cache_a == a && d.cache_key == g.key &&
+                            d.cache_version == net.version;
+        NPBS_CK(ctx, forward_group(d, net.params, w, g, r, a, out, add, run.train, st, &kc,
+                                   cached ? d.cache : nullptr));
         ctx->count(st, kc);
     }
     return NPBS_OK;
@@ -749,7 +747,7 @@ npbs_status fno_run_backward(npbs_ctx* ctx, Net& net, const NetRun& run, const f
         const int nb = sd.nb;
         const long long np = sd.np, cnt = (long long)nb * C * np;
         long long kc = 0;
-        NPBS_CK(ctx, forward_group(d, P, w, sd, r, a, nullptr, 0, true, st, &kc));
+        NPBS_CK(ctx, forward_group(d, P, w, g, r, a, nullptr, 0, true, st, &kc));
         // projection
         k_complex_planes<<<grid_of((long long)nb * np), 256, 0, st>>>(sd, gc, w.gp);
         k_wgrad_points<<<304, 256, 0, st>>>(nb, np, w.gp, 2, w.z1, C, dP + d.proj, nullptr);
@@ -775,7 +773,7 @@ npbs_status fno_run_backward(npbs_ctx* ctx, Net& net, const NetRun& run, const f
             NPBS_CK(ctx, layer_bwd(d, w, nb, w.c[l], P + d.spec[l], dP + d.spec[l], d.m, P + d.loc_w[l],
                                    dP + d.loc_w[l], dP + d.loc_b[l], w.g1, w.dc, st, &kc));
         }
-        k_wgrad_points<<<304, 256, 0, st>>>(nb, np, w.dc, C, w.lnp, 1, dP + d.lift_a_w, dP + d.lift_a_b);
+        k_wgrad_points<<<304, 256, 0, st>>>(nb, np, w.dc, C, w.lnp, d.ca, dP + d.lift_a_w, dP + d.lift_a_b);
         kc += 1;
         NPBS_CK(ctx, cudaGetLastError());
         ctx->count(st, kc);
@@ -789,18 +787,19 @@ using namespace npbs;
 
 extern "C" {
 
-npbs_status npbs_net_create_fno(npbs_net** out, int device, int n, int width, int modes, int layers, uint64_t seed) {
+npbs_status npbs_net_create_fno(npbs_net** out, int device, int n, int width, int modes, int layers,
+                                int coef_channels, uint64_t seed) {
     if (!out) return NPBS_ERR_INVALID_ARG;
     *out = nullptr;
     RadixPlan plan;
     if (n < 4 || n % 2 || !fno_radix_plan(n, &plan) || width < 1 || width > kMaxC || layers < 0 || layers > 8 ||
-        modes < 1 || modes > n / 2 + 1)
+        modes < 1 || modes > n / 2 + 1 || coef_channels < 1 || coef_channels > kMaxC)
         return NPBS_ERR_INVALID_ARG;
     if (cudaSetDevice(device) != cudaSuccess) return NPBS_ERR_INVALID_ARG;
     Net* net = new (std::nothrow) Net();
     if (!net) return NPBS_ERR_OOM;
     net->device = device;
-    net->fno = new (std::nothrow) FnoDef(fno_def(n, width, modes, layers));
+    net->fno = new (std::nothrow) FnoDef(fno_def(n, width, modes, layers, coef_channels));
     if (!net->fno || net->fno->count <= 0) {
         delete net;
         return NPBS_ERR_OOM;
@@ -840,7 +839,7 @@ npbs_status npbs_net_create_fno(npbs_net** out, int device, int n, int width, in
         for (long long i = 0; i < cnt; ++i) h[o + i] = (float)(uni() / (double)(width * width));
     };
     const long long spec = 2LL * width * width * d.ky * d.kx, full = 2LL * width * width * d.fy * d.fx;
-    fill_w(d.lift_a_w, width, 1);
+    fill_w(d.lift_a_w, (long long)width * coef_channels, coef_channels);
     for (int l = 0; l < layers; ++l) {
         fill_s(d.spec[l], spec);
         fill_w(d.loc_w[l], (long long)width * width, width);

@@ -349,7 +349,7 @@ extern "C" npbs_status fgmres_solve(npbs_ctx* ctx, const npbs_net* net, const np
         for (int q = 0; q < cnt; ++q)
             if (cyc[q]) which.push_back(q);
         NetRun runp;
-        npbs_status s2 = net_prepare(ctx, *reinterpret_cast<const Net*>(net), *pl, which, false, &runp, s);
+        npbs_status s2 = net_prepare(ctx, *reinterpret_cast<const Net*>(net), *pl, which, false, &runp, s, n);
         if (s2 != NPBS_OK) return s2;
         return net_run_forward(ctx, *reinterpret_cast<const Net*>(net), runp, v, n, z, 0, s);
     };

@@ -1,6 +1,7 @@
 // Network internals shared by the network, solver and training files.
 #pragma once
 
+#include <functional>
 #include <vector>
 
 #include "conv.cuh"
@@ -25,6 +26,7 @@ long long canon_param_count();
 // (Ky x Kx of them), the full-bandwidth residual layer (Fy x Fx modes).
 struct FnoDef {
     int n = 0, C = 0, m = 0, L = 0;
+    int ca = 1;  // coefficient channels (planes of the batch extent, one after another)
     int ky = 0, kx = 0, fy = 0, fx = 0;
     long long lift_a_w = 0, lift_a_b = 0;
     long long spec[8] = {}, loc_w[8] = {}, loc_b[8] = {};
@@ -32,8 +34,16 @@ struct FnoDef {
     long long count = 0;
     float2* tw = nullptr;  // device W_N^k = exp(-2 pi i k / N), k < N
     RadixPlan plan{};
+    // Coefficient-branch cache for inference: NLFL_L(...Phi(a)) of the last
+    // prepared instance set, valid while the coefficient field, the instances
+    // and the parameters (Net::version) stay the same.
+    mutable float* cache = nullptr;
+    mutable size_t cache_bytes = 0;
+    mutable const float* cache_a = nullptr;
+    mutable unsigned long long cache_key = 0;
+    mutable long long cache_version = -1;
 };
-FnoDef fno_def(int n, int C, int m, int L);
+FnoDef fno_def(int n, int C, int m, int L, int ca = 1);
 
 // Weights, gradients and AdamW moments on one device (U-Net device layout: per
 // conv [Cout][9][Cin_pad] then bias, then the 2 x 32 head; an FNO keeps the
@@ -42,6 +52,7 @@ struct Net {
     int device = 0;
     long long step = 0;
     FnoDef* fno = nullptr;  // non-null: this network is the FNO map of fno.cu
+    long long version = 0;  // bumped whenever the parameters change
     long long count() const { return fno ? fno->count : dev_param_count(); }
     float* params = nullptr;
     float* grads = nullptr;
@@ -70,18 +81,22 @@ struct SlotDev {
 struct NetGroup {
     int H, W;
     SlotDev sd;
+    unsigned long long key = 0;  // hash of the instance offsets (host side)
+    long long astride = 0;       // elements between coefficient channels (the batch extent)
 };
 struct NetRun {
     std::vector<NetGroup> groups;
     bool train = false;
 };
 
+// a: the coefficient channel the runs will read (the FNO precomputes its
+// coefficient branch here for inference runs; nullable: no precomputation)
 npbs_status net_prepare(npbs_ctx* ctx, const Net& net, const Plan& pl, const std::vector<int>& which, bool train,
-                        NetRun* run, cudaStream_t st);
+                        NetRun* run, cudaStream_t st, const float* a = nullptr);
 
 // The FNO counterparts (fno.cu), called by the net_* functions for an FNO network.
-npbs_status fno_prepare(npbs_ctx* ctx, const FnoDef& d, const Plan& pl, const std::vector<int>& which, bool train,
-                        NetRun* run, cudaStream_t st);
+npbs_status fno_prepare(npbs_ctx* ctx, const Net& net, const Plan& pl, const std::vector<int>& which, bool train,
+                        NetRun* run, cudaStream_t st, const float* a);
 npbs_status fno_run_forward(npbs_ctx* ctx, const Net& net, const NetRun& run, const float2* r, const float* a,
                             float2* out, int add, cudaStream_t st);
 npbs_status fno_run_backward(npbs_ctx* ctx, Net& net, const NetRun& run, const float2* r, const float* a,
@@ -93,5 +108,14 @@ npbs_status net_run_forward(npbs_ctx* ctx, const Net& net, const NetRun& run, co
 npbs_status net_run_backward(npbs_ctx* ctx, Net& net, const NetRun& run, const float2* r, const float* n,
                              const float2* gc, float2* gr, int add, cudaStream_t st);
 npbs_status net_adamw(npbs_ctx* ctx, Net& net, float lr, float wd, cudaStream_t st);
+
+// The Born-type operator of a training step: mode RESIDUAL writes r_0 of the
+// snapshots (x unused), OP_B applies B = I - G V to x, ADJ_B its adjoint;
+// norm2 (nullable) receives ||out||^2 per instance.
+using BornOp = std::function<npbs_status(int mode, const float2* x, float2* out, double* norm2)>;
+// One metric-matched training step (Eq. L_bs_Reta_integral, unrolled, squared)
+// for any Born operator over the instances of pl, then one AdamW update.
+npbs_status train_step_reta(npbs_ctx* ctx, Net& N, const Plan* pl, const float* n, int unroll, float lr,
+                            float weight_decay, float* loss_host, cudaStream_t s, const BornOp& op);
 
 }  // namespace npbs

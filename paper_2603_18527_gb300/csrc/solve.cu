@@ -398,7 +398,7 @@ static npbs_status learned_solve(npbs_ctx* ctx, const npbs_net* net, const npbs_
         for (int j : list)
             if (mode[j] == 0) netl.push_back(j);
         NPBS_CK(ctx, cudaMemcpyAsync(cbs_mode, mode.data(), sizeof(int) * cnt, cudaMemcpyHostToDevice, s));
-        return net_prepare(ctx, N, *pl, netl, false, &run, s);
+        return net_prepare(ctx, N, *pl, netl, false, &run, s, n);
     };
     InnerStep step = [&](bool last) -> npbs_status {
         ApplyArgs a{};

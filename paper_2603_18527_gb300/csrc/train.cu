@@ -85,6 +85,78 @@ __global__ void k_conj(const VecItem* items, const InstDev* inst, const float2* 
     }
 }
 
+npbs_status train_step_reta(npbs_ctx* ctx, Net& N, const Plan* pl, const float* n, int unroll, float lr,
+                            float weight_decay, float* loss_host, cudaStream_t s, const BornOp& op) {
+    npbs_status st;
+    const int cnt = pl->count;
+    const int U = unroll;
+    const size_t ext = (size_t)std::max<long long>(pl->extent, 1);
+    NPBS_CK(ctx, ctx->work[6].ensure(ext * sizeof(float2) * (size_t)(U + 1 + 4)));
+    NPBS_CK(ctx, ctx->work[7].ensure(sizeof(double) * (size_t)cnt * (U + 3) + 256));
+    float2* R = static_cast<float2*>(ctx->work[6].p);
+    float2* c = R + ext * (U + 1);
+    float2* wv = c + ext;
+    float2* gr = wv + ext;
+    float2* gn = gr + ext;
+    double* r0n2 = static_cast<double*>(ctx->work[7].p);
+    double* nk2 = r0n2 + cnt;
+    double* wgt = nk2 + (size_t)cnt * U;
+    const VecItem* vi = pl->vitems;
+    const int vb = pl->nvec;
+    auto Rk = [&](int k) { return R + ext * k; };
+
+    std::vector<int> which(cnt);
+    for (int j = 0; j < cnt; ++j) which[j] = j;
+    NetRun run;
+    st = net_prepare(ctx, N, *pl, which, true, &run, s);
+    if (st != NPBS_OK) return st;
+    NPBS_CK(ctx, cudaMemsetAsync(N.grads, 0, sizeof(float) * N.count(), s));
+    NPBS_CK(ctx, cudaMemsetAsync(nk2, 0, sizeof(double) * cnt * U, s));
+
+    // forward: r_0 and the unrolled residuals
+    st = op(NPBS_RESIDUAL, nullptr, Rk(0), r0n2);
+    if (st != NPBS_OK) return st;
+    for (int k = 0; k < U; ++k) {
+        st = net_run_forward(ctx, N, run, Rk(k), n, c, 0, s);
+        if (st != NPBS_OK) return st;
+        st = op(NPBS_OP_B, c, wv, nullptr);
+        if (st != NPBS_OK) return st;
+        k_sub_norm<<<vb, 256, 0, s>>>(vi, pl->inst, Rk(k), wv, Rk(k + 1), nk2 + (size_t)k * cnt);
+        ctx->count(s, 1);
+    }
+    std::vector<double> h0(cnt), hk((size_t)cnt * U), hw(cnt);
+    NPBS_CK(ctx, cudaMemcpyAsync(h0.data(), r0n2, sizeof(double) * cnt, cudaMemcpyDeviceToHost, s));
+    NPBS_CK(ctx, cudaMemcpyAsync(hk.data(), nk2, sizeof(double) * cnt * U, cudaMemcpyDeviceToHost, s));
+    NPBS_CK(ctx, cudaStreamSynchronize(s));
+    double loss = 0.0;
+    for (int j = 0; j < cnt; ++j) {
+        hw[j] = h0[j] > 0 ? 1.0 / ((double)U * cnt * h0[j]) : 0.0;
+        for (int k = 0; k < U; ++k) loss += hk[(size_t)k * cnt + j] * hw[j];
+    }
+    if (!std::isfinite(loss)) return set_err(ctx, NPBS_ERR_NONFINITE, "npbs_train_step: non-finite loss");
+    *loss_host = (float)loss;
+    NPBS_CK(ctx, cudaMemcpyAsync(wgt, hw.data(), sizeof(double) * cnt, cudaMemcpyHostToDevice, s));
+
+    // backward sweep
+    k_axpby_inst<<<vb, 256, 0, s>>>(vi, pl->inst, Rk(U), wgt, 2.f, nullptr, nullptr, gr);
+    ctx->count(s, 1);
+    for (int k = U - 1; k >= 0; --k) {
+        st = op(NPBS_ADJ_B, gr, c, nullptr);  // B^* g_r
+        if (st != NPBS_OK) return st;
+        k_axpby_inst<<<vb, 256, 0, s>>>(vi, pl->inst, c, nullptr, -1.f, nullptr, nullptr, c);  // g_c = -B^* g_r
+        ctx->count(s, 1);
+        st = net_run_backward(ctx, N, run, Rk(k), n, c, gn, 0, s);
+        if (st != NPBS_OK) return st;
+        if (k > 0) {
+            // g_r <- g_r + J^* g_c + 2 w r_k
+            k_axpby_inst<<<vb, 256, 0, s>>>(vi, pl->inst, Rk(k), wgt, 2.f, gr, gn, gr);
+            ctx->count(s, 1);
+        }
+    }
+    NPBS_CK(ctx, cudaGetLastError());
+    return net_adamw(ctx, N, lr, weight_decay, s);
+}
+
 }  // namespace npbs
 
 using namespace npbs;
@@ -116,90 +188,19 @@ extern "C" npbs_status npbs_train_step_loss(npbs_ctx* ctx, npbs_net* net, const 
         return train_step_euclid(ctx, N, pl, static_cast<const float2*>(V), static_cast<const float2*>(f), n,
                                  static_cast<const float2*>(u_snap), unroll, kind == NPBS_LOSS_BS_L2, lr,
                                  weight_decay, loss_host, s);
-    const int U = unroll;
-    const size_t ext = (size_t)std::max<long long>(pl->extent, 1);
-    NPBS_CK(ctx, ctx->work[6].ensure(ext * sizeof(float2) * (size_t)(U + 1 + 4)));
-    NPBS_CK(ctx, ctx->work[7].ensure(sizeof(double) * (size_t)cnt * (U + 3) + 256));
-    float2* R = static_cast<float2*>(ctx->work[6].p);
-    float2* c = R + ext * (U + 1);
-    float2* wv = c + ext;
-    float2* gr = wv + ext;
-    float2* gn = gr + ext;
-    double* r0n2 = static_cast<double*>(ctx->work[7].p);
-    double* nk2 = r0n2 + cnt;
-    double* wgt = nk2 + (size_t)cnt * U;
-    const VecItem* vi = pl->vitems;
-    const int vb = pl->nvec;
-    auto Rk = [&](int k) { return R + ext * k; };
-
-    std::vector<int> which(cnt);
-    for (int j = 0; j < cnt; ++j) which[j] = j;
-    NetRun run;
-    st = net_prepare(ctx, N, *pl, which, true, &run, s);
-    if (st != NPBS_OK) return st;
-    NPBS_CK(ctx, cudaMemsetAsync(N.grads, 0, sizeof(float) * N.count(), s));
-    NPBS_CK(ctx, cudaMemsetAsync(nk2, 0, sizeof(double) * cnt * U, s));
-
-    // forward: r_0 and the unrolled residuals
-    {
+    const float2* Vp = static_cast<const float2*>(V);
+    const float2* fp = static_cast<const float2*>(f);
+    const float2* usnap = static_cast<const float2*>(u_snap);
+    BornOp op = [&](int mode, const float2* x, float2* out, double* norm2) -> npbs_status {
         ApplyArgs a{};
-        a.V = static_cast<const float2*>(V);
-        a.f = static_cast<const float2*>(f);
-        a.x = static_cast<const float2*>(u_snap);
-        a.out = Rk(0);
-        a.norm2 = r0n2;
-        st = run_apply(ctx, *pl, NPBS_RESIDUAL, a, nullptr, s);
-        if (st != NPBS_OK) return st;
-    }
-    for (int k = 0; k < U; ++k) {
-        st = net_run_forward(ctx, N, run, Rk(k), n, c, 0, s);
-        if (st != NPBS_OK) return st;
-        ApplyArgs a{};
-        a.V = static_cast<const float2*>(V);
-        a.x = c;
-        a.out = wv;
-        st = run_apply(ctx, *pl, NPBS_OP_B, a, nullptr, s);
-        if (st != NPBS_OK) return st;
-        k_sub_norm<<<vb, 256, 0, s>>>(vi, pl->inst, Rk(k), wv, Rk(k + 1), nk2 + (size_t)k * cnt);
-        ctx->count(s, 1);
-    }
-    std::vector<double> h0(cnt), hk((size_t)cnt * U), hw(cnt);
-    NPBS_CK(ctx, cudaMemcpyAsync(h0.data(), r0n2, sizeof(double) * cnt, cudaMemcpyDeviceToHost, s));
-    NPBS_CK(ctx, cudaMemcpyAsync(hk.data(), nk2, sizeof(double) * cnt * U, cudaMemcpyDeviceToHost, s));
-    NPBS_CK(ctx, cudaStreamSynchronize(s));
-    double loss = 0.0;
-    for (int j = 0; j < cnt; ++j) {
-        hw[j] = h0[j] > 0 ? 1.0 / ((double)U * cnt * h0[j]) : 0.0;
-        for (int k = 0; k < U; ++k) loss += hk[(size_t)k * cnt + j] * hw[j];
-    }
-    if (!std::isfinite(loss)) return set_err(ctx, NPBS_ERR_NONFINITE, "npbs_train_step: non-finite loss");
-    *loss_host = (float)loss;
-    NPBS_CK(ctx, cudaMemcpyAsync(wgt, hw.data(), sizeof(double) * cnt, cudaMemcpyHostToDevice, s));
-
-    // backward sweep
-    k_axpby_inst<<<vb, 256, 0, s>>>(vi, pl->inst, Rk(U), wgt, 2.f, nullptr, nullptr, gr);
-    ctx->count(s, 1);
-    for (int k = U - 1; k >= 0; --k) {
-        {
-            ApplyArgs a{};
-            a.V = static_cast<const float2*>(V);
-            a.x = gr;
-            a.out = c;  // B^* g_r
-            st = run_apply(ctx, *pl, NPBS_ADJ_B, a, nullptr, s);
-            if (st != NPBS_OK) return st;
-        }
-        k_axpby_inst<<<vb, 256, 0, s>>>(vi, pl->inst, c, nullptr, -1.f, nullptr, nullptr, c);  // g_c = -B^* g_r
-        ctx->count(s, 1);
-        st = net_run_backward(ctx, N, run, Rk(k), n, c, gn, 0, s);
-        if (st != NPBS_OK) return st;
-        if (k > 0) {
-            // g_r <- g_r + J^* g_c + 2 w r_k
-            k_axpby_inst<<<vb, 256, 0, s>>>(vi, pl->inst, Rk(k), wgt, 2.f, gr, gn, gr);
-            ctx->count(s, 1);
-        }
-    }
-    NPBS_CK(ctx, cudaGetLastError());
-    return net_adamw(ctx, N, lr, weight_decay, s);
+        a.V = Vp;
+        a.f = mode == NPBS_RESIDUAL ? fp : nullptr;
+        a.x = mode == NPBS_RESIDUAL ? usnap : x;
+        a.out = out;
+        a.norm2 = norm2;
+        return run_apply(ctx, *pl, mode, a, nullptr, s);
+    };
+    return train_step_reta(ctx, N, pl, n, unroll, lr, weight_decay, loss_host, s, op);
 }
 
 extern "C" npbs_status npbs_train_step(npbs_ctx* ctx, npbs_net* net, const npbs_batch* batch, const void* V,

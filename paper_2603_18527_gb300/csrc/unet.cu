@@ -535,6 +535,7 @@ Net::~Net() {
     cudaFree(wsub);
     if (fno) {
         cudaFree(fno->tw);
+        cudaFree(fno->cache);
         delete fno;
     }
 }
@@ -727,8 +728,8 @@ static std::map<std::pair<int, int>, std::vector<int>> group(const Plan& pl, con
 }
 
 npbs_status net_prepare(npbs_ctx* ctx, const Net& net, const Plan& pl, const std::vector<int>& which, bool train,
-                        NetRun* run, cudaStream_t st) {
-    if (net.fno) return fno_prepare(ctx, *net.fno, pl, which, train, run, st);
+                        NetRun* run, cudaStream_t st, const float* a) {
+    if (net.fno) return fno_prepare(ctx, net, pl, which, train, run, st, a);
     run->groups.clear();
     run->train = train;
     auto gr = group(pl, which);
@@ -950,6 +951,7 @@ npbs_status net_run_backward(npbs_ctx* ctx, Net& net, const NetRun& run, const f
 
 npbs_status net_adamw(npbs_ctx* ctx, Net& net, float lr, float wd, cudaStream_t st) {
     net.step += 1;
+    net.version += 1;
     const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
     const float bc1 = 1.f - std::pow(b1, (float)net.step), bc2 = 1.f - std::pow(b2, (float)net.step);
     const long long P = net.count();
@@ -1043,6 +1045,7 @@ npbs_status npbs_net_set_params(npbs_net* net, const float* host, int64_t n) {
     if (!net || !host) return NPBS_ERR_INVALID_ARG;
     Net* N = reinterpret_cast<Net*>(net);
     cudaSetDevice(N->device);
+    N->version += 1;
     if (N->fno) {
         if (n != (int64_t)N->fno->count) return NPBS_ERR_INVALID_ARG;
         return cudaMemcpy(N->params, host, sizeof(float) * n, cudaMemcpyHostToDevice) == cudaSuccess ? NPBS_OK
@@ -1098,12 +1101,12 @@ npbs_status npbs_net_save(const npbs_net* net, const char* path) {
         return NPBS_ERR_CUDA;
     FILE* f = fopen(path, "wb");
     if (!f) return NPBS_ERR_INVALID_ARG;
-    // an FNO file carries its shape (n, width, modes, layers) after the magic
+    // an FNO file carries its shape (n, width, modes, layers, coefficient channels) after the magic
     const char magic[8] = {'N', 'P', 'B', 'S', N->fno ? 'F' : 'N', N->fno ? 'N' : 'E', N->fno ? 'O' : 'T', '1'};
     const long long hdr[2] = {N->step, P};
-    const int shape[4] = {N->fno ? N->fno->n : 0, N->fno ? N->fno->C : 0, N->fno ? N->fno->m : 0,
-                          N->fno ? N->fno->L : 0};
-    bool ok = fwrite(magic, 1, 8, f) == 8 && (!N->fno || fwrite(shape, sizeof(int), 4, f) == 4) &&
+    const int shape[5] = {N->fno ? N->fno->n : 0, N->fno ? N->fno->C : 0, N->fno ? N->fno->m : 0,
+                          N->fno ? N->fno->L : 0, N->fno ? N->fno->ca : 0};
+    bool ok = fwrite(magic, 1, 8, f) == 8 && (!N->fno || fwrite(shape, sizeof(int), 5, f) == 5) &&
               fwrite(hdr, sizeof(long long), 2, f) == 2 &&
               fwrite(buf.data(), sizeof(float), buf.size(), f) == buf.size();
     ok = (fclose(f) == 0) && ok;
@@ -1117,24 +1120,25 @@ npbs_status npbs_net_load(npbs_net** out, int device, const char* path) {
     if (!f) return NPBS_ERR_INVALID_ARG;
     char magic[8];
     long long hdr[2];
-    int shape[4] = {0, 0, 0, 0};
+    int shape[5] = {0, 0, 0, 0, 0};
     bool ok = fread(magic, 1, 8, f) == 8;
     const bool is_fno = ok && memcmp(magic, "NPBSFNO1", 8) == 0;
     ok = ok && (is_fno || memcmp(magic, "NPBSNET1", 8) == 0);
-    if (ok && is_fno) ok = fread(shape, sizeof(int), 4, f) == 4 && shape[0] > 0 && shape[0] <= kMaxN;
+    if (ok && is_fno) ok = fread(shape, sizeof(int), 5, f) == 5 && shape[0] > 0 && shape[0] <= kMaxN;
     long long P = 0;
-    if (ok) P = is_fno ? fno_def(shape[0], shape[1], shape[2], shape[3]).count : dev_param_count();
+    if (ok) P = is_fno ? fno_def(shape[0], shape[1], shape[2], shape[3], shape[4]).count : dev_param_count();
     ok = ok && P > 0 && fread(hdr, sizeof(long long), 2, f) == 2 && hdr[1] == P;
     std::vector<float> buf(ok ? 3 * P : 0);
     ok = ok && fread(buf.data(), sizeof(float), buf.size(), f) == buf.size();
     fclose(f);
     if (!ok) return NPBS_ERR_INVALID_ARG;
     npbs_net* h = nullptr;
-    npbs_status st = is_fno ? npbs_net_create_fno(&h, device, shape[0], shape[1], shape[2], shape[3], 0)
+    npbs_status st = is_fno ? npbs_net_create_fno(&h, device, shape[0], shape[1], shape[2], shape[3], shape[4], 0)
                             : npbs_net_create(&h, device, 0);
     if (st != NPBS_OK) return st;
     Net* N = reinterpret_cast<Net*>(h);
     N->step = hdr[0];
+    N->version += 1;
     if (cudaMemcpy(N->params, buf.data(), sizeof(float) * P, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(N->m1, buf.data() + P, sizeof(float) * P, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(N->m2, buf.data() + 2 * P, sizeof(float) * P, cudaMemcpyHostToDevice) != cudaSuccess ||
@@ -1167,7 +1171,7 @@ npbs_status npbs_net_forward(npbs_ctx* ctx, const npbs_net* net, const npbs_batc
     if (!r || !n || !c_out) return set_err(ctx, NPBS_ERR_INVALID_ARG, "npbs_net_forward: NULL field pointer");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     NetRun run;
-    st = net_prepare(ctx, *reinterpret_cast<const Net*>(net), *pl, which, false, &run, s);
+    st = net_prepare(ctx, *reinterpret_cast<const Net*>(net), *pl, which, false, &run, s, n);
     if (st != NPBS_OK) return st;
     return net_run_forward(ctx, *reinterpret_cast<const Net*>(net), run, static_cast<const float2*>(r), n,
                            static_cast<float2*>(c_out), 0, s);

@@ -167,3 +167,44 @@ def test_npbs_with_an_fno_converges_oracle_judged():
     st, rep = capi.fgmres_solve(c, net, b, k2, f, n, u, restart=20, precond=2, cbs_sweeps=16, rtol=1e-5, max_iter=40)
     assert st in (capi.OK, capi.NOT_CONVERGED)
     assert all(np.isfinite(rep["rtol"])) and all(i <= 40 for i in rep["iters"])
+
+
+def test_fno_with_four_coefficient_channels_forward_and_backward():
+    """coef_channels = 4 (the CDR input kappa, vx, vy, sigma as four planes of
+    the batch extent, one after another): forward at relative L2 <= 1e-4 and
+    the parameter gradient at <= 1e-3 against the oracle, on a ragged batch of
+    two grids' worth of instances at one size."""
+    cfg = FN.FnoConfig(n=32, width=8, modes=5, layers=2, coef=4)
+    capi, c = ctx()
+    insts = [synth.small_instance(32, 32, seed=570 + j) for j in range(3)]
+    b, k2, f, n, V = setup_batch(capi, c, insts)
+    rng = np.random.default_rng(571)
+    scale = np.array([0.01, 1.0, 1.0, 3.0])[:, None, None]
+    A = [(1.0 + rng.random((4, 32, 32))) * scale for _ in insts]
+    a_dev = torch.cat([b.pack([A[j][ch] for j in range(3)], dtype=torch.float32) for ch in range(4)])
+    net = capi.Net.fno(32, cfg.width, cfg.modes, cfg.layers, seed=1, coef_channels=4)
+    assert net.num_params() == FN.n_params(cfg)
+    net.set_params(_params(cfg, 13))
+    rs = [random_field((32, 32), 572 + j) for j in range(3)]
+    gs = [random_field((32, 32), 575 + j) for j in range(3)]
+    r, g = b.pack(rs), b.pack(gs)
+    out = torch.zeros_like(r)
+    capi.npbs_net_forward(c, net, b, r, a_dev, out)
+    gr = torch.zeros_like(r)
+    net.zero_grad()
+    capi.npbs_net_backward(c, net, b, r, a_dev, g, gr)
+    torch.cuda.synchronize()
+    flat, P = _oracle_params(cfg, 13, requires_grad=True)
+    a = torch.from_numpy(np.stack(A).astype(np.float32).astype(np.float64))
+    ref = FN.correction(torch.from_numpy(np.stack(rs)), a, P, cfg)
+    got = b.unpack(out)
+    for j in range(3):
+        assert rel_l2(got[j], ref[j].detach().numpy()) <= 1e-4
+    L = (torch.from_numpy(np.stack(gs)).real * ref.real + torch.from_numpy(np.stack(gs)).imag * ref.imag).sum()
+    (dth,) = torch.autograd.grad(L, [flat])
+    gw = net.get_grads()
+    o = 0
+    for name, shape in FN.param_spec(cfg):
+        k = int(np.prod(shape))
+        assert rel_l2(gw[o:o + k], dth.numpy()[o:o + k]) <= 1e-3, name
+        o += k
