@@ -339,12 +339,15 @@ npbs_status cdr_apply(npbs_ctx* ctx, const npbs_batch* batch, const npbs_cdr_con
  * u <- u + M(G(V u + f) - u), M the network `net` fed the coefficient field
  * `a` (DEVICE float32: the FNO's coef_channels planes of the batch extent one
  * after another, e.g. kappa, vx, vy, sigma; one plane for a U-Net), or the
- * identity when net is NULL
- * (the Born series, which converges when ||G V|| < 1).  u: DEVICE complex64,
- * initial guess in, iterate out.  rTol = ||f - A u|| / ||f|| (float64 sums) is
- * checked every opts->check_every iterations; every instance iterates until
- * all have passed or opts->max_iter; the report holds each instance's count
- * at its first passing check.  Synchronises. */
+ * identity when net is NULL (the Born series, which converges when
+ * ||G V|| < 1).  u: DEVICE complex128, initial guess in, iterate out.  The
+ * iteration runs in complex64 on the correction equation A delta = f - A u;
+ * every opts->check_every iterations delta is folded into u and rTol =
+ * ||f - A u|| / ||f|| is evaluated in float64 (so tolerances below the float32
+ * floor of about 1e-5 are reached, with the iteration count of the
+ * uninterrupted method).  Every instance iterates until all have passed or
+ * opts->max_iter; an instance's u and report are those of its first passing
+ * check.  Synchronises. */
 npbs_status cdr_solve(npbs_ctx* ctx, const npbs_net* net, const npbs_batch* batch, const npbs_cdr_consts* consts,
                       const float* kappa, const float* vx, const float* vy, const float* sigma, const void* f,
                       const float* a, void* u, const npbs_solve_opts* opts, npbs_report* report, npbs_stream stream);
@@ -386,9 +389,10 @@ int64_t npbs_net_param_count(const npbs_net* net);
  *   Phi(a) = W_a LayerNorm(a) + b_a, Psi(r) = W_r [Re r, Im r], P(z) = W_p z,
  *   LFL(x) = irfft2(W^F * R(rfft2(x))) + W^loc x (+ b), NLFL = GELU(LFL);
  * a is the network's coefficient field (the `n` argument of the entries):
- * coef_channels planes of the batch extent one after another (1 for
- * Helmholtz; the CDR problems pass kappa, v, sigma), each LayerNorm-ed over
- * the grid of its instance.
+ * coef_channels planes one after another, plane c starting at element
+ * c * E with E = max_j (offset_j + nx_j ny_j) the batch extent (1 plane for
+ * Helmholtz; the CDR problems pass kappa, vx, vy, sigma), each plane
+ * LayerNorm-ed over the grid of each instance.
  * M is linear in r (no bias on the residual path, no scale wrapper).  The
  * NLFL and fusion layers keep the modes with min(ky, N - ky) < modes and
  * kx < modes of the half plane, the residual layer all of them (N/2 + 1

@@ -227,6 +227,9 @@ class Batch:
             self.offsets.append(o)
             o += (ny * nx + ALIGN - 1) // ALIGN * ALIGN
         self.extent = o
+        # E = max_j (offset_j + nx_j ny_j): the stride of the planes of a
+        # several-channel network input
+        self.plane_stride = max((o + ny * nx for o, (ny, nx) in zip(self.offsets, self.shapes)), default=0)
         self._c = None
 
     @property
@@ -552,6 +555,9 @@ class CdrFields:
         self.vx = batch.pack(vx, dtype=torch.float32)
         self.vy = batch.pack(vy, dtype=torch.float32)
         self.sigma = batch.pack(sigma, dtype=torch.float32)
+        # the four-plane network input (kappa, vx, vy, sigma), planes batch.plane_stride apart
+        E = batch.plane_stride
+        self.a = torch.cat([t[:E] for t in (self.kappa, self.vx, self.vy, self.sigma)]).contiguous()
 
     def ptrs(self):
         return _ptr(self.kappa), _ptr(self.vx), _ptr(self.vy), _ptr(self.sigma)
@@ -579,7 +585,10 @@ def cdr_apply(ctx: Context, batch: "Batch", consts, fields: CdrFields, f, x, out
 
 def cdr_solve(ctx: Context, net, batch: "Batch", consts, fields: CdrFields, f, a, u, rtol=1e-6, max_iter=2500,
               check_every=4, stream=None):
-    """NPBS (net) or the Born series (net None) for CDR; u complex64 in/out."""
+    """NPBS (net) or the Born series (net None) for CDR; u (complex128) is
+    updated in place.  Returns (status, report dict)."""
+    if u.dtype != torch.complex128:
+        raise TypeError("cdr_solve: u must be complex128")
     rep = Report(batch.count)
     o = _opts(rtol, max_iter, check_every, 0)
     st = lib().cdr_solve(ctx.handle, net.handle if net is not None else None, C.byref(batch.c_batch()),

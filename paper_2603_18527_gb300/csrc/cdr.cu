@@ -37,8 +37,8 @@ struct CdrInst {
     double k0, v0x, v0y, s0;
 };
 
-__device__ __forceinline__ float xi_of(int i, int n, double h) {
-    return (float)(6.283185307179586476925 * (double)signed_mode(i, n) / ((double)n * h));
+template <typename R> __device__ __forceinline__ R xi_of(int i, int n, double h) {
+    return (R)(6.283185307179586476925 * (double)signed_mode(i, n) / ((double)n * h));
 }
 
 __device__ __forceinline__ void field_point(const CdrInst* ins, long long np, long long g, int* j, long long* p) {
@@ -46,8 +46,13 @@ __device__ __forceinline__ void field_point(const CdrInst* ins, long long np, lo
     *p = g - (long long)(*j) * np;
 }
 
+// The kernels below run in float32 (R = float: the complex64 iteration) or in
+// float64 (R = double: the stopping residual f - A u of a complex128 iterate).
+// Coefficient fields are float32 and the source complex64 in both.
+
 // b0 = x (then transformed in place)
-__global__ void k_cdr_copy(const CdrInst* ins, int cnt, long long np, const float2* x, float2* b0) {
+template <typename R>
+__global__ void k_cdr_copy(const CdrInst* ins, int cnt, long long np, const cpx<R>* x, cpx<R>* b0) {
     for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < cnt * np; g += (long long)gridDim.x * blockDim.x) {
         int j; long long p;
         field_point(ins, np, g, &j, &p);
@@ -57,101 +62,109 @@ __global__ void k_cdr_copy(const CdrInst* ins, int cnt, long long np, const floa
 }
 
 // spectral gradients b1 = i xi_x b0, b2 = i xi_y b0 (optionally b0 /= conj(lambda0) first: G^*)
-__global__ void k_cdr_grad(const CdrInst* ins, int cnt, long long np, float2* b0, float2* b1, float2* b2, int adj) {
+template <typename R>
+__global__ void k_cdr_grad(const CdrInst* ins, int cnt, long long np, cpx<R>* b0, cpx<R>* b1, cpx<R>* b2, int adj) {
+    using C = cpx<R>;
     for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < cnt * np; g += (long long)gridDim.x * blockDim.x) {
         int j; long long p;
         field_point(ins, np, g, &j, &p);
         const CdrInst in = ins[j];
         const int y = (int)(p / in.n), x = (int)(p % in.n);
-        const float kx = xi_of(x, in.n, in.h), ky = xi_of(y, in.n, in.h);
+        const R kx = xi_of<R>(x, in.n, in.h), ky = xi_of<R>(y, in.n, in.h);
         const long long o = in.off + p;
-        float2 u = b0[o];
+        C u = b0[o];
         if (adj) {
             // G^*: divide by conj(lambda0) = kappa0 |xi|^2 + sigma0 - i v0 . xi
-            const float lr = (float)in.k0 * (kx * kx + ky * ky) + (float)in.s0;
-            const float li = -((float)in.v0x * kx + (float)in.v0y * ky);
-            const float d = 1.f / (lr * lr + li * li);
-            u = make_float2((u.x * lr + u.y * li) * d, (u.y * lr - u.x * li) * d);
+            const R lr = (R)in.k0 * (kx * kx + ky * ky) + (R)in.s0;
+            const R li = -((R)in.v0x * kx + (R)in.v0y * ky);
+            const R d = (R)1 / (lr * lr + li * li);
+            u = mk<C>((u.x * lr + u.y * li) * d, (u.y * lr - u.x * li) * d);
             b0[o] = u;
         }
-        b1[o] = make_float2(-kx * u.y, kx * u.x);
-        b2[o] = make_float2(-ky * u.y, ky * u.x);
+        b1[o] = mk<C>(-kx * u.y, kx * u.x);
+        b2[o] = mk<C>(-ky * u.y, ky * u.x);
     }
 }
 
 // pointwise products in physical space (s = 1/n^2 undoes the unnormalised transforms)
 //   forward:  b3 = kappa ux, b4 = kappa uy, b5 = vx ux + vy uy + sigma x - f
 //   adjoint:  g = b0 s: b3 = kappa gx + vx g, b4 = kappa gy + vy g, b5 = sigma g
+template <typename R>
 __global__ void k_cdr_flux(const CdrInst* ins, int cnt, long long np, const float* kappa, const float* vx,
-                           const float* vy, const float* sigma, const float2* x, const float2* f, const float2* b0,
-                           const float2* b1, const float2* b2, float2* b3, float2* b4, float2* b5, int adj) {
+                           const float* vy, const float* sigma, const cpx<R>* x, const float2* f, const cpx<R>* b0,
+                           const cpx<R>* b1, const cpx<R>* b2, cpx<R>* b3, cpx<R>* b4, cpx<R>* b5, int adj) {
+    using C = cpx<R>;
     for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < cnt * np; g += (long long)gridDim.x * blockDim.x) {
         int j; long long p;
         field_point(ins, np, g, &j, &p);
         const CdrInst in = ins[j];
         const long long o = in.off + p;
-        const float s = 1.f / ((float)in.n * (float)in.n);
-        const float k = kappa[o], ax = vx[o], ay = vy[o], sg = sigma[o];
-        const float2 ux = make_float2(b1[o].x * s, b1[o].y * s), uy = make_float2(b2[o].x * s, b2[o].y * s);
+        const R s = (R)1 / ((R)in.n * (R)in.n);
+        const R k = kappa[o], ax = vx[o], ay = vy[o], sg = sigma[o];
+        const C ux = mk<C>(b1[o].x * s, b1[o].y * s), uy = mk<C>(b2[o].x * s, b2[o].y * s);
         if (!adj) {
-            const float2 xv = x[o];
-            float2 r = make_float2(ax * ux.x + ay * uy.x + sg * xv.x, ax * ux.y + ay * uy.y + sg * xv.y);
-            if (f) r = make_float2(r.x - f[o].x, r.y - f[o].y);
-            b3[o] = make_float2(k * ux.x, k * ux.y);
-            b4[o] = make_float2(k * uy.x, k * uy.y);
+            const C xv = x[o];
+            C r = mk<C>(ax * ux.x + ay * uy.x + sg * xv.x, ax * ux.y + ay * uy.y + sg * xv.y);
+            if (f) r = mk<C>(r.x - (R)f[o].x, r.y - (R)f[o].y);
+            b3[o] = mk<C>(k * ux.x, k * ux.y);
+            b4[o] = mk<C>(k * uy.x, k * uy.y);
             b5[o] = r;
         } else {
-            const float2 gv = make_float2(b0[o].x * s, b0[o].y * s);
-            b3[o] = make_float2(k * ux.x + ax * gv.x, k * ux.y + ax * gv.y);
-            b4[o] = make_float2(k * uy.x + ay * gv.x, k * uy.y + ay * gv.y);
-            b5[o] = make_float2(sg * gv.x, sg * gv.y);
+            const C gv = mk<C>(b0[o].x * s, b0[o].y * s);
+            b3[o] = mk<C>(k * ux.x + ax * gv.x, k * ux.y + ax * gv.y);
+            b4[o] = mk<C>(k * uy.x + ay * gv.x, k * uy.y + ay * gv.y);
+            b5[o] = mk<C>(sg * gv.x, sg * gv.y);
         }
     }
 }
 
 // W = -i xi_x b3 - i xi_y b4 + b5; b0 = mode-dependent multiple of W
 //   kind 0 (RESIDUAL): -W / lambda0, 1 (OP_B): W / lambda0, 2 (TRUE_RESIDUAL): -W, 3 (ADJ_B): W
-__global__ void k_cdr_assemble(const CdrInst* ins, int cnt, long long np, const float2* b3, const float2* b4,
-                               const float2* b5, float2* b0, int kind) {
+template <typename R>
+__global__ void k_cdr_assemble(const CdrInst* ins, int cnt, long long np, const cpx<R>* b3, const cpx<R>* b4,
+                               const cpx<R>* b5, cpx<R>* b0, int kind) {
+    using C = cpx<R>;
     for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < cnt * np; g += (long long)gridDim.x * blockDim.x) {
         int j; long long p;
         field_point(ins, np, g, &j, &p);
         const CdrInst in = ins[j];
         const int y = (int)(p / in.n), x = (int)(p % in.n);
-        const float kx = xi_of(x, in.n, in.h), ky = xi_of(y, in.n, in.h);
+        const R kx = xi_of<R>(x, in.n, in.h), ky = xi_of<R>(y, in.n, in.h);
         const long long o = in.off + p;
-        const float2 a = b3[o], b = b4[o], c = b5[o];
+        const C a = b3[o], b = b4[o], c = b5[o];
         // -i xi (a) = (xi a.y, -xi a.x)
-        float2 w = make_float2(kx * a.y + ky * b.y + c.x, -kx * a.x - ky * b.x + c.y);
-        if (kind == 0 || kind == 2) w = make_float2(-w.x, -w.y);
+        C w = mk<C>(kx * a.y + ky * b.y + c.x, -kx * a.x - ky * b.x + c.y);
+        if (kind == 0 || kind == 2) w = mk<C>(-w.x, -w.y);
         if (kind == 0 || kind == 1) {
-            const float lr = (float)in.k0 * (kx * kx + ky * ky) + (float)in.s0;
-            const float li = (float)in.v0x * kx + (float)in.v0y * ky;
-            const float d = 1.f / (lr * lr + li * li);
-            w = make_float2((w.x * lr + w.y * li) * d, (w.y * lr - w.x * li) * d);
+            const R lr = (R)in.k0 * (kx * kx + ky * ky) + (R)in.s0;
+            const R li = (R)in.v0x * kx + (R)in.v0y * ky;
+            const R d = (R)1 / (lr * lr + li * li);
+            w = mk<C>((w.x * lr + w.y * li) * d, (w.y * lr - w.x * li) * d);
         }
         b0[o] = w;
     }
 }
 
-// out = b0 / n^2, norm2[j] += ||out||^2 (float32 per thread, float64 across)
-__global__ void k_cdr_out(const CdrInst* ins, int cnt, long long np, const float2* b0, float2* out, const int* ids,
+// out = b0 / n^2 (rounded to complex64), norm2[j] += ||b0 / n^2||^2 (R per
+// thread, float64 across threads)
+template <typename R>
+__global__ void k_cdr_out(const CdrInst* ins, int cnt, long long np, const cpx<R>* b0, float2* out, const int* ids,
                           double* norm2) {
     __shared__ double red[8];
     const long long tot = cnt * np;
     for (long long base = (long long)blockIdx.x * blockDim.x; base < tot; base += (long long)gridDim.x * blockDim.x) {
         const long long g = base + threadIdx.x;
-        float acc = 0.f;
+        R acc = 0;
         int j = (int)(base / np);
         if (g < tot) {
             long long p;
             field_point(ins, np, g, &j, &p);
             const CdrInst in = ins[j];
-            const float s = 1.f / ((float)in.n * (float)in.n);
+            const R s = (R)1 / ((R)in.n * (R)in.n);
             const long long o = in.off + p;
-            const float2 v = make_float2(b0[o].x * s, b0[o].y * s);
-            out[o] = v;
-            acc = v.x * v.x + v.y * v.y;
+            const R vr = b0[o].x * s, vi = b0[o].y * s;
+            out[o] = make_float2((float)vr, (float)vi);
+            acc = vr * vr + vi * vi;
         }
         if (norm2) {
             // a block of 256 points never straddles two instances (np is a multiple of 256)
@@ -166,6 +179,48 @@ __global__ void k_cdr_out(const CdrInst* ins, int cnt, long long np, const float
             }
             __syncthreads();
         }
+    }
+}
+
+// norm2[j] += ||f_j||^2 (float64)
+__global__ void k_cdr_norm2(const CdrInst* ins, int cnt, long long np, const float2* f, const int* ids,
+                            double* norm2) {
+    __shared__ double red[8];
+    const long long tot = cnt * np;
+    for (long long base = (long long)blockIdx.x * blockDim.x; base < tot; base += (long long)gridDim.x * blockDim.x) {
+        const long long g = base + threadIdx.x;
+        double acc = 0;
+        int j = (int)(base / np);
+        if (g < tot) {
+            long long p;
+            field_point(ins, np, g, &j, &p);
+            const float2 v = f[ins[j].off + p];
+            acc = (double)v.x * v.x + (double)v.y * v.y;
+        }
+        for (int w = 16; w > 0; w >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, w);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+        __syncthreads();
+        if (threadIdx.x == 0 && base < tot) {
+            double t = 0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+            atomicAdd(norm2 + ids[j], t);
+        }
+        __syncthreads();
+    }
+}
+
+// u += delta, delta = 0 (the float32 correction folded into the complex128
+// iterate) on the instances not yet frozen (frozen: by batch index)
+__global__ void k_cdr_fold(const CdrInst* ins, const int* ids, const int* frozen, int cnt, long long np, float2* delta,
+                           double2* u) {
+    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < cnt * np; g += (long long)gridDim.x * blockDim.x) {
+        int j; long long p;
+        field_point(ins, np, g, &j, &p);
+        if (frozen[ids[j]]) continue;
+        const long long o = ins[j].off + p;
+        const float2 d = delta[o];
+        u[o] = make_double2(u[o].x + (double)d.x, u[o].y + (double)d.y);
+        delta[o] = make_float2(0.f, 0.f);
     }
 }
 
@@ -192,6 +247,7 @@ struct CdrGroup {
     int n = 0, cnt = 0;
     RadixPlan plan{};
     const float2* tw = nullptr;
+    const double2* tw64 = nullptr;
     const CdrInst* ins = nullptr;   // device [cnt]
     const int* ids = nullptr;       // device [cnt]: batch index of each
     const long long* off = nullptr; // device [6 cnt]: field offsets of buffer k (k * extent + offset)
@@ -200,8 +256,15 @@ struct CdrGroup {
 struct CdrPrep {
     std::vector<CdrGroup> groups;
     long long extent = 0;
-    float2* buf = nullptr;  // 6 complex fields of the batch extent
+    float2* buf = nullptr;     // 6 complex64 fields of the batch extent
+    double2* buf64 = nullptr;  // 6 complex128 fields (cdr_prepare64 only)
+    template <typename R> cpx<R>* fields() const;
+    template <typename R> const cpx<R>* twiddles(const CdrGroup& g) const;
 };
+template <> float2* CdrPrep::fields<float>() const { return buf; }
+template <> double2* CdrPrep::fields<double>() const { return buf64; }
+template <> const float2* CdrPrep::twiddles<float>(const CdrGroup& g) const { return g.tw; }
+template <> const double2* CdrPrep::twiddles<double>(const CdrGroup& g) const { return g.tw64; }
 
 npbs_status cdr_prepare(npbs_ctx* ctx, const npbs_batch* batch, const npbs_cdr_consts* consts, CdrPrep* P,
                         cudaStream_t st) {
@@ -237,7 +300,7 @@ npbs_status cdr_prepare(npbs_ctx* ctx, const npbs_batch* batch, const npbs_cdr_c
         memcpy(host.data() + o, src, bytes);
         return o;
     };
-    struct Offs { size_t tw, ins, ids, off; };
+    struct Offs { size_t tw, tw64, ins, ids, off; };
     std::vector<Offs> offs;
     for (auto& kv : by) {
         const int n = kv.first;
@@ -246,9 +309,11 @@ npbs_status cdr_prepare(npbs_ctx* ctx, const npbs_batch* batch, const npbs_cdr_c
         g.cnt = (int)kv.second.size();
         cdr_radix_plan(n, &g.plan);
         std::vector<float2> tw(n);
+        std::vector<double2> tw64(n);
         for (int k = 0; k < n; ++k) {
             const double a = -2.0 * M_PI * (double)k / (double)n;
             tw[k] = make_float2((float)std::cos(a), (float)std::sin(a));
+            tw64[k] = make_double2(std::cos(a), std::sin(a));
         }
         std::vector<CdrInst> ins;
         std::vector<long long> off;
@@ -261,6 +326,7 @@ npbs_status cdr_prepare(npbs_ctx* ctx, const npbs_batch* batch, const npbs_cdr_c
             for (int j : kv.second) off.push_back((long long)k * ext + batch->inst[j].offset);
         Offs o;
         o.tw = put(tw.data(), sizeof(float2) * tw.size());
+        o.tw64 = put(tw64.data(), sizeof(double2) * tw64.size());
         o.ins = put(ins.data(), sizeof(CdrInst) * ins.size());
         o.ids = put(kv.second.data(), sizeof(int) * kv.second.size());
         o.off = put(off.data(), sizeof(long long) * off.size());
@@ -274,6 +340,7 @@ npbs_status cdr_prepare(npbs_ctx* ctx, const npbs_batch* batch, const npbs_cdr_c
     NPBS_CK(ctx, cudaStreamSynchronize(st));  // the staging vector goes out of scope
     for (size_t i = 0; i < P->groups.size(); ++i) {
         P->groups[i].tw = reinterpret_cast<const float2*>(d + offs[i].tw);
+        P->groups[i].tw64 = reinterpret_cast<const double2*>(d + offs[i].tw64);
         P->groups[i].ins = reinterpret_cast<const CdrInst*>(d + offs[i].ins);
         P->groups[i].ids = reinterpret_cast<const int*>(d + offs[i].ids);
         P->groups[i].off = reinterpret_cast<const long long*>(d + offs[i].off);
@@ -283,34 +350,48 @@ npbs_status cdr_prepare(npbs_ctx* ctx, const npbs_batch* batch, const npbs_cdr_c
     return NPBS_OK;
 }
 
+// the complex128 field buffers of the float64 residual (after cdr_prepare)
+npbs_status cdr_prepare64(npbs_ctx* ctx, CdrPrep* P) {
+    NPBS_CK(ctx, ctx->work[16].ensure(sizeof(double2) * 6 * (size_t)std::max<long long>(P->extent, 1)));
+    P->buf64 = static_cast<double2*>(ctx->work[16].p);
+    NPBS_CK(ctx, fft2d::set_attrs_of<double2>());
+    return NPBS_OK;
+}
+
 int cdr_grid(long long n) { return (int)std::min<long long>((n + 255) / 256, 152LL * 32); }
 
-// One CDR apply over a prepared batch (mode: RESIDUAL, OP_B, TRUE_RESIDUAL, ADJ_B).
+// One CDR apply over a prepared batch (mode: RESIDUAL, OP_B, TRUE_RESIDUAL,
+// ADJ_B) in precision R; out is complex64 in both.
+template <typename R>
 npbs_status cdr_run(npbs_ctx* ctx, const CdrPrep& P, int mode, const float* kappa, const float* vx, const float* vy,
-                    const float* sigma, const float2* f, const float2* x, float2* out, double* norm2, int count,
+                    const float* sigma, const float2* f, const cpx<R>* x, float2* out, double* norm2, int count,
                     cudaStream_t st) {
+    using C = cpx<R>;
     const long long E = P.extent;
-    float2* b[6];
-    for (int k = 0; k < 6; ++k) b[k] = P.buf + k * E;
+    C* const buf = P.fields<R>();
+    if (!buf) return set_err(ctx, NPBS_ERR_CUDA, "cdr: float64 buffers not prepared");
+    C* b[6];
+    for (int k = 0; k < 6; ++k) b[k] = buf + k * E;
     if (norm2) NPBS_CK(ctx, cudaMemsetAsync(norm2, 0, sizeof(double) * count, st));
     const bool adj = mode == NPBS_ADJ_B;
     const int kind = mode == NPBS_RESIDUAL ? 0 : mode == NPBS_OP_B ? 1 : mode == NPBS_TRUE_RESIDUAL ? 2 : 3;
     for (const CdrGroup& g : P.groups) {
         const long long np = (long long)g.n * g.n, tot = (long long)g.cnt * np;
         const int grid = cdr_grid(tot);
-        k_cdr_copy<<<grid, 256, 0, st>>>(g.ins, g.cnt, np, x, b[0]);
-        NPBS_CK(ctx, fft2d::run(P.buf, g.off, g.cnt, g.n, -1, g.plan, g.tw, st));
-        k_cdr_grad<<<grid, 256, 0, st>>>(g.ins, g.cnt, np, b[0], b[1], b[2], adj ? 1 : 0);
+        const C* tw = P.twiddles<R>(g);
+        k_cdr_copy<R><<<grid, 256, 0, st>>>(g.ins, g.cnt, np, x, b[0]);
+        NPBS_CK(ctx, fft2d::run<C>(buf, g.off, g.cnt, g.n, -1, g.plan, tw, st));
+        k_cdr_grad<R><<<grid, 256, 0, st>>>(g.ins, g.cnt, np, b[0], b[1], b[2], adj ? 1 : 0);
         // b1, b2 (and for the adjoint b0 = G^* x) back to physical space
-        NPBS_CK(ctx, fft2d::run(P.buf, g.off + g.cnt, 2LL * g.cnt, g.n, 1, g.plan, g.tw, st));
-        if (adj) NPBS_CK(ctx, fft2d::run(P.buf, g.off, g.cnt, g.n, 1, g.plan, g.tw, st));
-        k_cdr_flux<<<grid, 256, 0, st>>>(g.ins, g.cnt, np, kappa, vx, vy, sigma, x,
-                                         (mode == NPBS_OP_B || adj) ? nullptr : f, b[0], b[1], b[2], b[3], b[4], b[5],
-                                         adj ? 1 : 0);
-        NPBS_CK(ctx, fft2d::run(P.buf, g.off + 3 * g.cnt, 3LL * g.cnt, g.n, -1, g.plan, g.tw, st));
-        k_cdr_assemble<<<grid, 256, 0, st>>>(g.ins, g.cnt, np, b[3], b[4], b[5], b[0], kind);
-        NPBS_CK(ctx, fft2d::run(P.buf, g.off, g.cnt, g.n, 1, g.plan, g.tw, st));
-        k_cdr_out<<<grid, 256, 0, st>>>(g.ins, g.cnt, np, b[0], out, g.ids, norm2);
+        NPBS_CK(ctx, fft2d::run<C>(buf, g.off + g.cnt, 2LL * g.cnt, g.n, 1, g.plan, tw, st));
+        if (adj) NPBS_CK(ctx, fft2d::run<C>(buf, g.off, g.cnt, g.n, 1, g.plan, tw, st));
+        k_cdr_flux<R><<<grid, 256, 0, st>>>(g.ins, g.cnt, np, kappa, vx, vy, sigma, x,
+                                            (mode == NPBS_OP_B || adj) ? nullptr : f, b[0], b[1], b[2], b[3], b[4],
+                                            b[5], adj ? 1 : 0);
+        NPBS_CK(ctx, fft2d::run<C>(buf, g.off + 3 * g.cnt, 3LL * g.cnt, g.n, -1, g.plan, tw, st));
+        k_cdr_assemble<R><<<grid, 256, 0, st>>>(g.ins, g.cnt, np, b[3], b[4], b[5], b[0], kind);
+        NPBS_CK(ctx, fft2d::run<C>(buf, g.off, g.cnt, g.n, 1, g.plan, tw, st));
+        k_cdr_out<R><<<grid, 256, 0, st>>>(g.ins, g.cnt, np, b[0], out, g.ids, norm2);
         NPBS_CK(ctx, cudaGetLastError());
         ctx->count(st, 5 + 2 * (adj ? 5 : 4));
     }
@@ -428,7 +509,7 @@ npbs_status cdr_apply(npbs_ctx* ctx, const npbs_batch* batch, const npbs_cdr_con
     CdrPrep P;
     npbs_status st = cdr_prepare(ctx, batch, consts, &P, s);
     if (st != NPBS_OK) return st;
-    return cdr_run(ctx, P, (int)mode, kappa, vx, vy, sigma, static_cast<const float2*>(f),
+    return cdr_run<float>(ctx, P, (int)mode, kappa, vx, vy, sigma, static_cast<const float2*>(f),
                    static_cast<const float2*>(x), static_cast<float2*>(out), norm2, batch->count, s);
 }
 
@@ -447,17 +528,31 @@ npbs_status cdr_solve(npbs_ctx* ctx, const npbs_net* net, const npbs_batch* batc
     CdrPrep P;
     npbs_status st = cdr_prepare(ctx, batch, consts, &P, s);
     if (st != NPBS_OK) return st;
-    const long long E = P.extent;
-    NPBS_CK(ctx, ctx->work[15].ensure(sizeof(float2) * (size_t)std::max<long long>(E, 1) + sizeof(double) * 2 * cnt));
-    float2* r = static_cast<float2*>(ctx->work[15].p);
-    double* n2 = reinterpret_cast<double*>(r + E);
-    double* f2 = n2 + cnt;
-    float2* U = static_cast<float2*>(u);
-    const float2* F = static_cast<const float2*>(f);
-    // ||f||^2 per instance: TRUE_RESIDUAL of x = 0 is f (u is the iterate, so use r as a zero field)
-    NPBS_CK(ctx, cudaMemsetAsync(r, 0, sizeof(float2) * E, s));
-    st = cdr_run(ctx, P, NPBS_TRUE_RESIDUAL, kappa, vx, vy, sigma, F, r, r, f2, cnt, s);
+    st = cdr_prepare64(ctx, &P);
     if (st != NPBS_OK) return st;
+    const long long E = P.extent;
+    const size_t ext = (size_t)std::max<long long>(E, 1);
+    // r: the Born residual of the correction equation; rho = f - A u (complex64
+    // copy of the float64 residual); delta: the correction since the last fold
+    NPBS_CK(ctx, ctx->work[15].ensure(sizeof(double) * 2 * cnt + sizeof(int) * cnt));
+    NPBS_CK(ctx, ctx->work[17].ensure(sizeof(float2) * 3 * ext));
+    double* n2 = static_cast<double*>(ctx->work[15].p);
+    double* f2 = n2 + cnt;
+    int* frozen = reinterpret_cast<int*>(f2 + cnt);
+    float2* r = static_cast<float2*>(ctx->work[17].p);
+    float2* rho = r + ext;
+    float2* delta = rho + ext;
+    double2* U = static_cast<double2*>(u);
+    const float2* F = static_cast<const float2*>(f);
+    NPBS_CK(ctx, cudaMemsetAsync(delta, 0, sizeof(float2) * ext, s));
+    NPBS_CK(ctx, cudaMemsetAsync(f2, 0, sizeof(double) * cnt, s));
+    NPBS_CK(ctx, cudaMemsetAsync(frozen, 0, sizeof(int) * cnt, s));
+    for (const CdrGroup& g : P.groups) {
+        const long long np = (long long)g.n * g.n;
+        k_cdr_norm2<<<cdr_grid(g.cnt * np), 256, 0, s>>>(g.ins, g.cnt, np, F, g.ids, f2);
+    }
+    NPBS_CK(ctx, cudaGetLastError());
+    ctx->count(s, (long long)P.groups.size());
     std::vector<double> hf(cnt), hr(cnt);
     NPBS_CK(ctx, cudaMemcpyAsync(hf.data(), f2, sizeof(double) * cnt, cudaMemcpyDeviceToHost, s));
     NetRun run;
@@ -466,12 +561,11 @@ npbs_status cdr_solve(npbs_ctx* ctx, const npbs_net* net, const npbs_batch* batc
     const Net* N = reinterpret_cast<const Net*>(net);
     if (N) {
         npbs_status s2;
-        const Plan* pl = nullptr;
         // the network groups instances through a context plan (constants there are placeholders)
         std::vector<npbs_instance> tmp(batch->inst, batch->inst + cnt);
         for (auto& t : tmp) { t.k0sq = 0.0; t.eps = 1.0; }
         npbs_batch b2{cnt, tmp.data()};
-        pl = get_plan(ctx, &b2, &s2);
+        const Plan* pl = get_plan(ctx, &b2, &s2);
         if (!pl) return s2;
         s2 = net_prepare(ctx, *N, *pl, all, false, &run, s, a);
         if (s2 != NPBS_OK) return s2;
@@ -480,8 +574,21 @@ npbs_status cdr_solve(npbs_ctx* ctx, const npbs_net* net, const npbs_batch* batc
     std::vector<double> rt(cnt, 1.0);
     std::vector<npbs_status> stat(cnt, NPBS_NOT_CONVERGED);
     int it = 0;
+    // every check folds delta into u and recomputes rho = f - A u in float64:
+    // the inner complex64 iteration then solves A delta = rho from delta = 0,
+    // whose Born residuals G(rho - A delta) are those of the uninterrupted
+    // iteration (M is linear in r), so the count is the method's while the
+    // stopping test carries no float32 floor.  An instance that passed is
+    // frozen: its u stays the iterate of its first passing check.
+    std::vector<int> hfrozen(cnt, 0);
     auto check = [&]() -> npbs_status {
-        npbs_status s2 = cdr_run(ctx, P, NPBS_TRUE_RESIDUAL, kappa, vx, vy, sigma, F, U, r, n2, cnt, s);
+        for (const CdrGroup& g : P.groups) {
+            const long long np = (long long)g.n * g.n;
+            k_cdr_fold<<<cdr_grid(g.cnt * np), 256, 0, s>>>(g.ins, g.ids, frozen, g.cnt, np, delta, U);
+        }
+        NPBS_CK(ctx, cudaGetLastError());
+        ctx->count(s, (long long)P.groups.size());
+        npbs_status s2 = cdr_run<double>(ctx, P, NPBS_TRUE_RESIDUAL, kappa, vx, vy, sigma, F, U, rho, n2, cnt, s);
         if (s2 != NPBS_OK) return s2;
         NPBS_CK(ctx, cudaMemcpyAsync(hr.data(), n2, sizeof(double) * cnt, cudaMemcpyDeviceToHost, s));
         NPBS_CK(ctx, cudaStreamSynchronize(s));
@@ -491,7 +598,9 @@ npbs_status cdr_solve(npbs_ctx* ctx, const npbs_net* net, const npbs_batch* batc
             iters[j] = it;
             if (!std::isfinite(rt[j])) stat[j] = NPBS_ERR_NONFINITE;
             else if (rt[j] <= opts->rtol) stat[j] = NPBS_OK;
+            hfrozen[j] = stat[j] != NPBS_NOT_CONVERGED;
         }
+        NPBS_CK(ctx, cudaMemcpyAsync(frozen, hfrozen.data(), sizeof(int) * cnt, cudaMemcpyHostToDevice, s));
         return NPBS_OK;
     };
     st = check();
@@ -500,17 +609,17 @@ npbs_status cdr_solve(npbs_ctx* ctx, const npbs_net* net, const npbs_batch* batc
         bool any = false;
         for (int j = 0; j < cnt; ++j) any |= stat[j] == NPBS_NOT_CONVERGED;
         if (!any) break;
-        // every instance iterates (converged ones keep improving); reports keep their first passing check
+        // every instance iterates; frozen ones are no longer folded into u
         for (int k = 0; k < opts->check_every && it < opts->max_iter; ++k, ++it) {
-            st = cdr_run(ctx, P, NPBS_RESIDUAL, kappa, vx, vy, sigma, F, U, r, nullptr, cnt, s);
+            st = cdr_run<float>(ctx, P, NPBS_RESIDUAL, kappa, vx, vy, sigma, rho, delta, r, nullptr, cnt, s);
             if (st != NPBS_OK) return st;
             if (N) {
-                st = net_run_forward(ctx, *N, run, r, a, U, 1, s);
+                st = net_run_forward(ctx, *N, run, r, a, delta, 1, s);
                 if (st != NPBS_OK) return st;
             } else {
                 for (const CdrGroup& g : P.groups) {
                     const long long np = (long long)g.n * g.n;
-                    k_cdr_axpy<<<cdr_grid(g.cnt * np), 256, 0, s>>>(g.ins, g.cnt, np, r, U);
+                    k_cdr_axpy<<<cdr_grid(g.cnt * np), 256, 0, s>>>(g.ins, g.cnt, np, r, delta);
                 }
                 NPBS_CK(ctx, cudaGetLastError());
                 ctx->count(s, (long long)P.groups.size());
@@ -560,7 +669,8 @@ npbs_status cdr_train_step(npbs_ctx* ctx, npbs_net* net, const npbs_batch* batch
     const float2* F = static_cast<const float2*>(f);
     const float2* usnap = static_cast<const float2*>(u_snap);
     BornOp op = [&](int mode, const float2* x, float2* out, double* norm2) -> npbs_status {
-        return cdr_run(ctx, P, mode, kappa, vx, vy, sigma, F, mode == NPBS_RESIDUAL ? usnap : x, out, norm2, cnt, s);
+        return cdr_run<float>(ctx, P, mode, kappa, vx, vy, sigma, F, mode == NPBS_RESIDUAL ? usnap : x, out, norm2,
+                              cnt, s);
     };
     return train_step_reta(ctx, *reinterpret_cast<Net*>(net), pl, a, unroll, lr, weight_decay, loss_host, s, op);
 }

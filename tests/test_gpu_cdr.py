@@ -83,20 +83,61 @@ def test_cdr_adjoint_dot_product_on_the_gpu():
 
 def test_cdr_born_series_solve_is_oracle_judged():
     """Weak convection (the Born series contracts): cdr_solve without a network
-    reaches the float32 floor of the iterate; the oracle judges the returned u."""
+    reaches rTol 1e-7, below the float32 floor, through its float64 refresh of
+    the iterate; the oracle judges the returned u, the reported rTol is the
+    float64 one, and the count is the oracle's Born-series count (checked
+    every iteration there, every 4 here: rounded up to a multiple of 4, one
+    check of slack for the float32 inner iteration)."""
     capi, c = ctx()
     insts = [synth.cdr_instance(64, seed=15, speed=0.05), synth.cdr_instance(128, seed=16, speed=0.05)]
     b, fields, f = _setup(capi, insts)
     consts = capi.npbs_cdr_background(c, b, fields)
-    u = torch.zeros_like(f)
-    st, rep = capi.cdr_solve(c, None, b, consts, fields, f, None, u, rtol=1e-4, max_iter=600, check_every=4)
+    u = torch.zeros(b.extent, dtype=torch.complex128, device="cuda")
+    tol = 1e-7
+    st, rep = capi.cdr_solve(c, None, b, consts, fields, f, None, u, rtol=tol, max_iter=600, check_every=4)
     assert st == capi.OK, rep
     U = b.unpack(u)
     for j, inst in enumerate(insts):
         p = _oracle(inst, consts[j])
-        r = CD.rtol(p, torch.from_numpy(U[j].astype(np.complex128)))
-        assert r <= 1e-4, (j, r, rep)
-        # the reported rtol is ||f - A u|| / ||f|| evaluated in float32 (seven
-        # FFTs and the flux products): near 1e-4 its rounding error is a few
-        # 1e-5 of ||f|| (eps32 times ||kappa grad u|| |xi|_max / ||f||)
-        assert abs(r - rep["rtol"][j]) <= 0.05 * r + 3e-5
+        r = CD.rtol(p, torch.from_numpy(U[j]))
+        assert r <= tol * (1 + 1e-3), (j, r, rep)
+        assert rep["rtol"][j] == pytest.approx(r, rel=1e-3)
+        ref = CD.npbs_solve(p, lambda q: q, tol=tol, max_iter=600).iters
+        up4 = -(-ref // 4) * 4
+        assert up4 - 4 <= rep["iters"][j] <= up4 + 4, (j, ref, rep["iters"][j])
+
+
+def test_cdr_train_step_matches_the_oracle_loss_and_gradient():
+    """cdr_train_step (an FNO with the four coefficient channels kappa, vx,
+    vy, sigma; 3 unrolls; lr = 0) against the metric-matched unrolled loss
+    composed from the oracle's CDR operators, r_0 = G(V u + f) - u,
+    r_{k+1} = r_k - (I - G V) M(r_k), loss = mean_j (1/U) sum_k ||r_k||^2 /
+    ||r_0||^2, and its autograd gradient."""
+    from oracle import fno as FN
+    from tests.test_gpu_fno import _oracle_params, _params
+    cfg = FN.FnoConfig(n=32, width=8, modes=5, layers=2, coef=4)
+    capi, c = ctx()
+    insts = [synth.cdr_instance(32, seed=800 + j, speed=1.0) for j in range(4)]
+    b, fields, f = _setup(capi, insts)
+    consts = capi.npbs_cdr_background(c, b, fields)
+    snaps = [np.zeros((32, 32), np.complex64)] + [(0.1 * random_field((32, 32), 810 + j)).astype(np.complex64)
+                                                 for j in range(3)]
+    u0 = b.pack(snaps)
+    net = capi.Net.fno(32, cfg.width, cfg.modes, cfg.layers, seed=1, coef_channels=4)
+    net.set_params(_params(cfg, 14))
+    loss = capi.cdr_train_step(c, net, b, consts, fields, f, fields.a, u0, unroll=3, lr=0.0, weight_decay=0.0)
+    flat, P = _oracle_params(cfg, 14, requires_grad=True)
+    probs = [_oracle(i, consts[j]) for j, i in enumerate(insts)]
+    A = torch.stack([torch.stack([p.kappa, p.vx, p.vy, p.sigma]) for p in probs])
+    feats = FN.coefficient_features(A, P, cfg)
+    r = torch.stack([CD.born_residual(p, torch.from_numpy(s.astype(np.complex128))) for p, s in zip(probs, snaps)])
+    r0 = (r.real ** 2 + r.imag ** 2).sum(dim=(-2, -1))
+    acc = torch.zeros_like(r0)
+    for _ in range(3):
+        corr = FN.correction_from_features(r, feats, P, cfg)
+        r = r - torch.stack([CD.op_B(p, corr[j]) for j, p in enumerate(probs)])
+        acc = acc + (r.real ** 2 + r.imag ** 2).sum(dim=(-2, -1)) / r0
+    L = (acc / 3).mean()
+    (gref,) = torch.autograd.grad(L, flat)
+    assert loss == pytest.approx(float(L), rel=1e-3)
+    assert rel_l2(net.get_grads(), gref.numpy()) <= 2e-3
