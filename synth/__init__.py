@@ -281,3 +281,34 @@ def cdr_instance(n: int = 128, seed: int = 0, kappa_mean: float = 0.01, speed: f
     dx = np.minimum(np.abs(x - cx), 1.0 - np.abs(x - cx))
     f = np.exp(-(dy ** 2 + dx ** 2) / (2.0 * width * width)).astype(np.complex128)
     return CdrInstance(n=n, h=h, kappa=kappa, vx=vx, vy=vy, sigma=sigma, f=f, seed=seed)
+
+
+@dataclasses.dataclass
+class NewtonInstance:
+    """The nonlinear Dirichlet problem -Lap u - u^2 = f on [0, 1]^2 with N x N
+    interior unknowns (h = 1/(N + 1)) and an initial guess."""
+    n: int
+    h: float
+    f: np.ndarray        # float64 [n, n] source -s sin(pi x) sin(pi y)
+    u0: np.ndarray       # float64 [n, n] initial guess
+    seed: int
+
+
+def newton_instance(n: int = 64, seed: int = 0, amplitude: float = 1600.0, base: float = -20.0,
+                    alpha: float = 4.0) -> NewtonInstance:
+    """The Newton benchmark's recipe (N = 64, h = 1/65, s = 1600): f = -s
+    sin(pi x) sin(pi y) on the interior nodes x_j = j h, and an initial guess
+    base sin(pi x) sin(pi y) + alpha sum_{i,j=1..4} c_ij sin(i pi x) sin(j pi y)
+    with c_ij ~ N(0, 0.1^2) (the paper perturbs a reference solution; here the
+    perturbation rides on a fixed smooth guess, and Newton finds the branch)."""
+    rng = np.random.default_rng(seed)
+    h = 1.0 / (n + 1)
+    t = np.arange(1, n + 1) * h
+    y, x = t[:, None], t[None, :]
+    f = -amplitude * np.sin(math.pi * x) * np.sin(math.pi * y)
+    c = rng.normal(0.0, 0.1, size=(4, 4))
+    u0 = base * np.sin(math.pi * x) * np.sin(math.pi * y)
+    for i in range(4):
+        for j in range(4):
+            u0 = u0 + alpha * c[i, j] * np.sin((i + 1) * math.pi * x) * np.sin((j + 1) * math.pi * y)
+    return NewtonInstance(n=n, h=h, f=f, u0=u0, seed=seed)

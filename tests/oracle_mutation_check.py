@@ -3,7 +3,7 @@
 Plants one plausible mistake at a time (a dropped term, a wrong sign or
 conjugate, swapped operands or indices, a different reading of a convention)
 in a temporary copy of ``oracle/`` and runs the oracle pins
-(``tests/test_oracle_pins.py``, ``tests/test_oracle_unet.py``) against it.
+(``tests/test_oracle_{pins,unet,fno,cdr,newton}.py``) against it.
 Every mutant must make at least one pin fail.
 
     python tests/oracle_mutation_check.py [index ...]
@@ -64,7 +64,29 @@ M = [
  ("fgmres.py", "sign of g", "g[j + 1] = -sn[j] * gj", "g[j + 1] = sn[j] * gj"),
  ("fgmres.py", "dot operands swapped", "hij = _dot(Vb[i], w)", "hij = _dot(w, Vb[i])"),
  ("fgmres.py", "earlier rotations skipped", "for i in range(j):\n                a, c", "for i in range(0):\n                a, c"),
+ ("fno.py", "retained rows <=", "return [k for k in range(n) if min(k, n - k) < m]", "return [k for k in range(n) if min(k, n - k) <= m]"),
+ ("fno.py", "conv1x1 transposed", 'y = torch.einsum("oi,bihw->bohw", w, x)', 'y = torch.einsum("io,bihw->bohw", w, x)'),
+ ("fno.py", "spectral weights conj", 'Yr = torch.einsum("bikl,iokl->bokl", Xr, W)', 'Yr = torch.einsum("bikl,iokl->bokl", Xr, W.conj())'),
+ ("fno.py", "residual branch re/im swapped", "x = conv1x1(torch.stack([r.real, r.imag], dim=1), P[\"lift_r.w\"])", "x = conv1x1(torch.stack([r.imag, r.real], dim=1), P[\"lift_r.w\"])"),
+ ("fno.py", "layer norm over channels too", "mu = a.mean(dim=(-2, -1), keepdim=True)", "mu = a.mean(dim=(-3, -2, -1), keepdim=True)"),
+ ("cdr.py", "A convection sign", "+ p.vx * ux + p.vy * uy + p.sigma * u", "- p.vx * ux - p.vy * uy + p.sigma * u"),
+ ("cdr.py", "L0 symbol convection sign", "lam = (k0 * (kx ** 2 + ky ** 2)).to(C128) + 1j * (v0x * kx + v0y * ky) + s0", "lam = (k0 * (kx ** 2 + ky ** 2)).to(C128) - 1j * (v0x * kx + v0y * ky) + s0"),
+ ("cdr.py", "A* without the v g flux", "return -(ddx(p, p.kappa * gx + p.vx * g) + ddy(p, p.kappa * gy + p.vy * g)) + p.sigma * g", "return -(ddx(p, p.kappa * gx) + ddy(p, p.kappa * gy)) + p.sigma * g"),
+ ("cdr.py", "G* without conj", "return torch.fft.ifft2(torch.fft.fft2(q) / p.lam.conj())", "return torch.fft.ifft2(torch.fft.fft2(q) / p.lam)"),
+ ("cdr.py", "V drops dkappa", "return (ddx(p, dk * ux) + ddy(p, dk * uy)) - (p.vx - p.v0x) * ux", "return - (p.vx - p.v0x) * ux"),
+ ("newton.py", "stencil centre 2", "return (4.0 * c - p[2:, 1:-1]", "return (2.0 * c - p[2:, 1:-1]"),
+ ("newton.py", "jacobian factor 2 dropped", "return lap_D(x, h) - 2.0 * u * x", "return lap_D(x, h) - u * x"),
+ ("newton.py", "dst normalisation", "type=1, axis=1) / 4.0)", "type=1, axis=1) / 2.0)"),
+ ("newton.py", "eigenvalue full angle", "* math.pi * h / 2.0) ** 2", "* math.pi * h) ** 2"),
+ ("newton.py", "shift sign of the mean", "shift = alpha - 2.0 * float(u.real.mean())", "shift = alpha + 2.0 * float(u.real.mean())"),
+ ("newton.py", "inverse normalisation 1D", "* (2.0 / (N + 1)) ** 2", "* (2.0 / (N + 1))"),
+ ("newton.py", "V sign of u", "return (s.shift + 2.0 * s.u) * x", "return (s.shift - 2.0 * s.u) * x"),
+ ("newton.py", "B* order", "return y - apply_V(s, green(s, y))", "return y - green(s, apply_V(s, y))"),
+ ("newton.py", "born residual sign", "return green(s, r - jacobian(s.u, d, s.h))", "return green(s, r + jacobian(s.u, d, s.h))"),
+ ("newton.py", "nonlinear residual u^2 sign", "return lap_D(u, h) - u * u - f", "return lap_D(u, h) + u * u - f"),
 ]
+PINS = ["tests/test_oracle_pins.py", "tests/test_oracle_unet.py", "tests/test_oracle_fno.py", "tests/test_oracle_cdr.py",
+        "tests/test_oracle_newton.py"]
 def run(i):
     fn, label, a, b = M[i]
     d = tempfile.mkdtemp(prefix=f"mut{i}_")
@@ -76,7 +98,7 @@ def run(i):
         return i, label, "PATTERN-MISSING", ""
     open(p, "w").write(s.replace(a, b, 1))
     env = dict(os.environ, OMP_NUM_THREADS="2", PYTHONDONTWRITEBYTECODE="1")
-    r = subprocess.run([sys.executable, "-m", "pytest", "tests/test_oracle_pins.py", "tests/test_oracle_unet.py", "-x", "-q", "-p", "no:cacheprovider"],
+    r = subprocess.run([sys.executable, "-m", "pytest", *PINS, "-x", "-q", "-p", "no:cacheprovider"],
                        cwd=d, capture_output=True, text=True, env=env, timeout=900)
     shutil.rmtree(d, ignore_errors=True)
     last = [l for l in r.stdout.splitlines() if "FAILED" in l or "passed" in l or "failed" in l]

@@ -188,3 +188,22 @@ def test_several_coefficient_channels_reduce_to_one_and_permute():
     Pp["lift_a.w"] = P3["lift_a.w"][:, perm]
     assert torch.allclose(FN.correction(r, a, P3, c3), FN.correction(r, a[:, perm], Pp, c3), rtol=1e-12, atol=1e-12)
     assert FN.n_params(c3) == FN.n_params(c1) + 2 * 4
+
+
+def test_residual_branch_reads_re_then_im_and_projects_to_re_then_im():
+    """With the lifting's Im column zero, M sees only Re r: M(i s) = 0 for a
+    real field s while M(s) != 0; with proj's second row zero the output is
+    real.  Pins the (Re, Im) order of Psi's input and of P's output."""
+    rng = np.random.default_rng(10)
+    cfg = FN.FnoConfig(n=16, width=4, modes=3, layers=1)
+    P = FN.unflatten(cfg, FN.init_params(cfg, 4) + 0.05)
+    P["lift_r.w"] = P["lift_r.w"].clone()
+    P["lift_r.w"][:, 1] = 0.0
+    a = torch.from_numpy(rng.standard_normal((1, 16, 16)))
+    s = torch.from_numpy(rng.standard_normal((1, 16, 16))).to(torch.complex128)
+    assert FN.correction(1j * s, a, P, cfg).abs().max() == 0.0
+    assert FN.correction(s, a, P, cfg).abs().max() > 1e-6
+    P["proj.w"] = P["proj.w"].clone()
+    P["proj.w"][1] = 0.0
+    y = FN.correction(s, a, P, cfg)
+    assert y.imag.abs().max() == 0.0 and y.real.abs().max() > 1e-6
