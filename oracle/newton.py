@@ -26,9 +26,9 @@ rTol (rTol = 1e-4 in the paper); the outer loop stops when ||F(u)|| / ||f|| <=
 tol or after a given number of Newton steps.  Fields may be complex (the
 library carries complex64 fields; real data stay real).
 
-The DST-I is ``scipy.fft.dst(type=1)`` as a library step (scipy's
-unnormalised sum 2 sum_n x_n sin(pi (k+1)(n+1)/(N+1)), so S = dst / 2 per
-axis and S^{-1} = (2 / (N + 1)) S).
+The DST-I is written as products with the sine matrix (S^2 = (N + 1)/2 I
+per axis, so S^{-1} = (2 / (N + 1)) S); the pins check it against scipy's
+DST-I.
 """
 from __future__ import annotations
 
@@ -37,7 +37,6 @@ import math
 from typing import Callable, List, Optional
 
 import numpy as np
-import scipy.fft as sfft
 import torch
 
 F64 = torch.float64
@@ -79,13 +78,17 @@ def jacobian(u: torch.Tensor, x: torch.Tensor, h: float) -> torch.Tensor:
     return lap_D(x, h) - 2.0 * u * x
 
 
+def sine_matrix(N: int) -> torch.Tensor:
+    """S_jk = sin(pi j k / (N + 1)), j, k = 1..N (symmetric)."""
+    j = torch.arange(1, N + 1, dtype=F64)
+    return torch.sin(math.pi * torch.outer(j, j) / (N + 1))
+
+
 def dst2(q: torch.Tensor) -> torch.Tensor:
-    """The 2D DST-I S q, S_jk = sin(pi j k / (N + 1)) per axis (j, k = 1..N)."""
-    def one(a):
-        return torch.from_numpy(sfft.dst(sfft.dst(a.numpy(), type=1, axis=0), type=1, axis=1) / 4.0)
-    if q.is_complex():
-        return torch.complex(one(q.real), one(q.imag))
-    return one(q)
+    """The 2D DST-I: S q S along both axes (a plain matrix product, so that
+    autograd passes through the Green operator)."""
+    S = sine_matrix(q.shape[0]).to(q.dtype)
+    return S @ q @ S
 
 
 def laplacian_eigenvalues(N: int) -> torch.Tensor:

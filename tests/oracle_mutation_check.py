@@ -76,7 +76,8 @@ M = [
  ("cdr.py", "V drops dkappa", "return (ddx(p, dk * ux) + ddy(p, dk * uy)) - (p.vx - p.v0x) * ux", "return - (p.vx - p.v0x) * ux"),
  ("newton.py", "stencil centre 2", "return (4.0 * c - p[2:, 1:-1]", "return (2.0 * c - p[2:, 1:-1]"),
  ("newton.py", "jacobian factor 2 dropped", "return lap_D(x, h) - 2.0 * u * x", "return lap_D(x, h) - u * x"),
- ("newton.py", "dst normalisation", "type=1, axis=1) / 4.0)", "type=1, axis=1) / 2.0)"),
+ ("newton.py", "sine matrix over N", "return torch.sin(math.pi * torch.outer(j, j) / (N + 1))", "return torch.sin(math.pi * torch.outer(j, j) / N)"),
+ ("newton.py", "dst one axis", "return S @ q @ S", "return S @ q"),
  ("newton.py", "eigenvalue full angle", "* math.pi * h / 2.0) ** 2", "* math.pi * h) ** 2"),
  ("newton.py", "shift sign of the mean", "shift = alpha - 2.0 * float(u.real.mean())", "shift = alpha + 2.0 * float(u.real.mean())"),
  ("newton.py", "inverse normalisation 1D", "* (2.0 / (N + 1)) ** 2", "* (2.0 / (N + 1))"),

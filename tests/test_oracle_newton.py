@@ -1,7 +1,7 @@
 """Pins of the Newton-Born oracle (App. Full Derivations, Nonlinear PDE via
 Newton-Born Linearization; App. Verification, Newton linear systems): the
 five-point Laplacian against the dense Kronecker matrix, the DST-I against
-the dense sine matrix from its definition, the closed-form eigenpairs of L_D,
+scipy's DST-I, the closed-form eigenpairs of L_D,
 the Born identity I - G V = G J, the adjoint, and Newton against a
 manufactured exact solution."""
 import math
@@ -34,13 +34,16 @@ def test_lap_D_is_the_kronecker_five_point_matrix(N):
 
 
 @pytest.mark.parametrize("N", [4, 7])
-def test_dst2_is_the_dense_sine_transform(N):
+def test_dst2_is_scipys_dst_one_on_both_axes(N):
+    """Against a library routine: scipy's DST-I is 2 sum_n x_n sin(pi (k+1)(n+1)/(N+1)),
+    so S q S = dst(dst(q, axis 0), axis 1) / 4; and S^2 = (N + 1)/2 I per axis."""
+    import scipy.fft as sfft
     rng = np.random.default_rng(2)
     q = rng.standard_normal((N, N)) + 1j * rng.standard_normal((N, N))
-    S = _dense_sine(N)
+    ref = sfft.dst(sfft.dst(q, type=1, axis=0), type=1, axis=1) / 4.0
     got = NW.dst2(torch.from_numpy(q)).numpy()
-    assert np.allclose(got, S @ q @ S.T, rtol=1e-12, atol=1e-12)
-    # S^2 = (N + 1)/2 I per axis
+    assert np.allclose(got, ref, rtol=1e-12, atol=1e-12)
+    S = _dense_sine(N)
     assert np.allclose(S @ S, (N + 1) / 2 * np.eye(N), atol=1e-12)
 
 
