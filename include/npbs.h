@@ -463,6 +463,23 @@ npbs_status npbs_train_step_loss(npbs_ctx* ctx, npbs_net* net, const npbs_batch*
                                  npbs_loss kind, float lr, float weight_decay, float* loss_host,
                                  npbs_stream stream);
 
+/* The CDR counterparts of the format/loss comparison (the CDR column of the
+ * comparison across other PDEs): cdr_train_step with a choice of objective
+ * (BS_L2 and DIR use the explicit adjoints A^* g = -div(kappa grad g + v g)
+ * + sigma g and G^* of symbol 1/conj(lambda0), since convection makes A not
+ * complex symmetric), and the Direct format u <- u + M(f - A u) with the
+ * float64 stopping test of cdr_solve (net required).  Arguments as in
+ * cdr_train_step and cdr_solve. */
+npbs_status cdr_train_step_loss(npbs_ctx* ctx, npbs_net* net, const npbs_batch* batch,
+                                const npbs_cdr_consts* consts, const float* kappa, const float* vx, const float* vy,
+                                const float* sigma, const void* f, const float* a, const void* u_snap,
+                                int32_t unroll, npbs_loss kind, float lr, float weight_decay, float* loss_host,
+                                npbs_stream stream);
+npbs_status cdr_solve_direct(npbs_ctx* ctx, const npbs_net* net, const npbs_batch* batch,
+                             const npbs_cdr_consts* consts, const float* kappa, const float* vx, const float* vy,
+                             const float* sigma, const void* f, const float* a, void* u, const npbs_solve_opts* opts,
+                             npbs_report* report, npbs_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

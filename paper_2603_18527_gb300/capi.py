@@ -100,6 +100,13 @@ _SIGS = {
     "cdr_train_step": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(npbs_batch), C.POINTER(npbs_cdr_consts),
                                  C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                  C.c_int32, C.c_float, C.c_float, C.POINTER(C.c_float), C.c_void_p]),
+    "cdr_solve_direct": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(npbs_batch), C.POINTER(npbs_cdr_consts),
+                                   C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                   C.c_void_p, C.POINTER(npbs_solve_opts), C.POINTER(npbs_report), C.c_void_p]),
+    "cdr_train_step_loss": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(npbs_batch), C.POINTER(npbs_cdr_consts),
+                                      C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                      C.c_void_p, C.c_int32, C.c_int, C.c_float, C.c_float, C.POINTER(C.c_float),
+                                      C.c_void_p]),
     "npbs_net_num_params": (C.c_int64, []),
     "npbs_net_param_count": (C.c_int64, [C.c_void_p]),
     "npbs_net_create_fno": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
@@ -584,26 +591,29 @@ def cdr_apply(ctx: Context, batch: "Batch", consts, fields: CdrFields, f, x, out
 
 
 def cdr_solve(ctx: Context, net, batch: "Batch", consts, fields: CdrFields, f, a, u, rtol=1e-6, max_iter=2500,
-              check_every=4, stream=None):
-    """NPBS (net) or the Born series (net None) for CDR; u (complex128) is
-    updated in place.  Returns (status, report dict)."""
+              check_every=4, stream=None, direct: bool = False):
+    """NPBS (net) or the Born series (net None) for CDR, or with direct=True
+    the Direct format u <- u + M(f - A u); u (complex128) is updated in place.
+    Returns (status, report dict)."""
     if u.dtype != torch.complex128:
         raise TypeError("cdr_solve: u must be complex128")
     rep = Report(batch.count)
     o = _opts(rtol, max_iter, check_every, 0)
-    st = lib().cdr_solve(ctx.handle, net.handle if net is not None else None, C.byref(batch.c_batch()),
-                         _consts(consts), *fields.ptrs(), _ptr(f), _ptr(a), _ptr(u), C.byref(o), C.byref(rep.c),
-                         _stream(stream))
+    fn = lib().cdr_solve_direct if direct else lib().cdr_solve
+    st = fn(ctx.handle, net.handle if net is not None else None, C.byref(batch.c_batch()), _consts(consts),
+            *fields.ptrs(), _ptr(f), _ptr(a), _ptr(u), C.byref(o), C.byref(rep.c), _stream(stream))
     if st not in (OK, NOT_CONVERGED, ERR_NONFINITE):
         ctx.check(st)
     return st, rep.as_dict()
 
 
 def cdr_train_step(ctx: Context, net, batch: "Batch", consts, fields: CdrFields, f, a, u_snap, unroll=4, lr=1e-3,
-                   weight_decay=1e-6, stream=None) -> float:
-    """One metric-matched training step with the CDR operators; returns the loss."""
+                   weight_decay=1e-6, stream=None, loss: str = "bs_reta") -> float:
+    """One training step with the CDR operators; loss "bs_reta"
+    (metric-matched), "bs_l2" or "dir".  Returns the loss before the update."""
     out = C.c_float(0.0)
-    ctx.check(lib().cdr_train_step(ctx.handle, net.handle, C.byref(batch.c_batch()), _consts(consts), *fields.ptrs(),
-                                   _ptr(f), _ptr(a), _ptr(u_snap), int(unroll), float(lr), float(weight_decay),
-                                   C.byref(out), _stream(stream)))
+    ctx.check(lib().cdr_train_step_loss(ctx.handle, net.handle, C.byref(batch.c_batch()), _consts(consts),
+                                        *fields.ptrs(), _ptr(f), _ptr(a), _ptr(u_snap), int(unroll),
+                                        LOSS_KINDS[loss], float(lr), float(weight_decay), C.byref(out),
+                                        _stream(stream)))
     return float(out.value)

@@ -61,7 +61,7 @@ __global__ void k_cdr_copy(const CdrInst* ins, int cnt, long long np, const cpx<
     }
 }
 
-// spectral gradients b1 = i xi_x b0, b2 = i xi_y b0 (optionally b0 /= conj(lambda0) first: G^*)
+// spectral gradients b1 = i xi_x b0, b2 = i xi_y b0 (adj == 1: b0 /= conj(lambda0) first, G^*)
 template <typename R>
 __global__ void k_cdr_grad(const CdrInst* ins, int cnt, long long np, cpx<R>* b0, cpx<R>* b1, cpx<R>* b2, int adj) {
     using C = cpx<R>;
@@ -73,7 +73,7 @@ __global__ void k_cdr_grad(const CdrInst* ins, int cnt, long long np, cpx<R>* b0
         const R kx = xi_of<R>(x, in.n, in.h), ky = xi_of<R>(y, in.n, in.h);
         const long long o = in.off + p;
         C u = b0[o];
-        if (adj) {
+        if (adj == 1) {
             // G^*: divide by conj(lambda0) = kappa0 |xi|^2 + sigma0 - i v0 . xi
             const R lr = (R)in.k0 * (kx * kx + ky * ky) + (R)in.s0;
             const R li = -((R)in.v0x * kx + (R)in.v0y * ky);
@@ -142,6 +142,25 @@ __global__ void k_cdr_assemble(const CdrInst* ins, int cnt, long long np, const 
             w = mk<C>((w.x * lr + w.y * li) * d, (w.y * lr - w.x * li) * d);
         }
         b0[o] = w;
+    }
+}
+
+// b0 /= lambda0 (G) or conj(lambda0) (G^*)
+template <typename R>
+__global__ void k_cdr_green(const CdrInst* ins, int cnt, long long np, cpx<R>* b0, int adj) {
+    using C = cpx<R>;
+    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < cnt * np; g += (long long)gridDim.x * blockDim.x) {
+        int j; long long p;
+        field_point(ins, np, g, &j, &p);
+        const CdrInst in = ins[j];
+        const int y = (int)(p / in.n), x = (int)(p % in.n);
+        const R kx = xi_of<R>(x, in.n, in.h), ky = xi_of<R>(y, in.n, in.h);
+        const long long o = in.off + p;
+        const R lr = (R)in.k0 * (kx * kx + ky * ky) + (R)in.s0;
+        const R li = (adj ? (R)-1 : (R)1) * ((R)in.v0x * kx + (R)in.v0y * ky);
+        const R d = (R)1 / (lr * lr + li * li);
+        const C w = b0[o];
+        b0[o] = mk<C>((w.x * lr + w.y * li) * d, (w.y * lr - w.x * li) * d);
     }
 }
 
@@ -360,8 +379,14 @@ npbs_status cdr_prepare64(npbs_ctx* ctx, CdrPrep* P) {
 
 int cdr_grid(long long n) { return (int)std::min<long long>((n + 255) / 256, 152LL * 32); }
 
+// internal apply modes beside the public ones: out = -A^* y, and the Green
+// operators alone
+constexpr int kCdrMinusAdjA = 100;
+constexpr int kCdrGreen = 101;
+constexpr int kCdrGreenAdj = 102;
+
 // One CDR apply over a prepared batch (mode: RESIDUAL, OP_B, TRUE_RESIDUAL,
-// ADJ_B) in precision R; out is complex64 in both.
+// ADJ_B or an internal one) in precision R; out is complex64 in both.
 template <typename R>
 npbs_status cdr_run(npbs_ctx* ctx, const CdrPrep& P, int mode, const float* kappa, const float* vx, const float* vy,
                     const float* sigma, const float2* f, const cpx<R>* x, float2* out, double* norm2, int count,
@@ -373,15 +398,32 @@ npbs_status cdr_run(npbs_ctx* ctx, const CdrPrep& P, int mode, const float* kapp
     C* b[6];
     for (int k = 0; k < 6; ++k) b[k] = buf + k * E;
     if (norm2) NPBS_CK(ctx, cudaMemsetAsync(norm2, 0, sizeof(double) * count, st));
-    const bool adj = mode == NPBS_ADJ_B;
-    const int kind = mode == NPBS_RESIDUAL ? 0 : mode == NPBS_OP_B ? 1 : mode == NPBS_TRUE_RESIDUAL ? 2 : 3;
+    if (mode == kCdrGreen || mode == kCdrGreenAdj) {
+        for (const CdrGroup& g : P.groups) {
+            const long long np = (long long)g.n * g.n, tot = (long long)g.cnt * np;
+            const int grid = cdr_grid(tot);
+            const C* tw = P.twiddles<R>(g);
+            k_cdr_copy<R><<<grid, 256, 0, st>>>(g.ins, g.cnt, np, x, b[0]);
+            NPBS_CK(ctx, fft2d::run<C>(buf, g.off, g.cnt, g.n, -1, g.plan, tw, st));
+            k_cdr_green<R><<<grid, 256, 0, st>>>(g.ins, g.cnt, np, b[0], mode == kCdrGreenAdj ? 1 : 0);
+            NPBS_CK(ctx, fft2d::run<C>(buf, g.off, g.cnt, g.n, 1, g.plan, tw, st));
+            k_cdr_out<R><<<grid, 256, 0, st>>>(g.ins, g.cnt, np, b[0], out, g.ids, norm2);
+            NPBS_CK(ctx, cudaGetLastError());
+            ctx->count(st, 3 + 2 * 2);
+        }
+        return NPBS_OK;
+    }
+    const bool adj = mode == NPBS_ADJ_B || mode == kCdrMinusAdjA;
+    const int kind = mode == NPBS_RESIDUAL ? 0 : mode == NPBS_OP_B ? 1
+                   : (mode == NPBS_TRUE_RESIDUAL || mode == kCdrMinusAdjA) ? 2 : 3;
     for (const CdrGroup& g : P.groups) {
         const long long np = (long long)g.n * g.n, tot = (long long)g.cnt * np;
         const int grid = cdr_grid(tot);
         const C* tw = P.twiddles<R>(g);
         k_cdr_copy<R><<<grid, 256, 0, st>>>(g.ins, g.cnt, np, x, b[0]);
         NPBS_CK(ctx, fft2d::run<C>(buf, g.off, g.cnt, g.n, -1, g.plan, tw, st));
-        k_cdr_grad<R><<<grid, 256, 0, st>>>(g.ins, g.cnt, np, b[0], b[1], b[2], adj ? 1 : 0);
+        k_cdr_grad<R><<<grid, 256, 0, st>>>(g.ins, g.cnt, np, b[0], b[1], b[2],
+                                            mode == NPBS_ADJ_B ? 1 : adj ? 2 : 0);
         // b1, b2 (and for the adjoint b0 = G^* x) back to physical space
         NPBS_CK(ctx, fft2d::run<C>(buf, g.off + g.cnt, 2LL * g.cnt, g.n, 1, g.plan, tw, st));
         if (adj) NPBS_CK(ctx, fft2d::run<C>(buf, g.off, g.cnt, g.n, 1, g.plan, tw, st));
@@ -513,10 +555,16 @@ npbs_status cdr_apply(npbs_ctx* ctx, const npbs_batch* batch, const npbs_cdr_con
                    static_cast<const float2*>(x), static_cast<float2*>(out), norm2, batch->count, s);
 }
 
-npbs_status cdr_solve(npbs_ctx* ctx, const npbs_net* net, const npbs_batch* batch, const npbs_cdr_consts* consts,
-                      const float* kappa, const float* vx, const float* vy, const float* sigma, const void* f,
-                      const float* a, void* u, const npbs_solve_opts* opts, npbs_report* report, npbs_stream stream) {
+}  // extern "C"
+
+// NPBS (direct = false: u <- u + M(G(f - A u))) or the Direct format
+// (direct = true: u <- u + M(f - A u)) with the CDR operators
+static npbs_status cdr_solve_impl(npbs_ctx* ctx, const npbs_net* net, const npbs_batch* batch,
+                                  const npbs_cdr_consts* consts, const float* kappa, const float* vx, const float* vy,
+                                  const float* sigma, const void* f, const float* a, void* u,
+                                  const npbs_solve_opts* opts, npbs_report* report, npbs_stream stream, bool direct) {
     if (!ctx) return NPBS_ERR_INVALID_ARG;
+    if (direct && !net) return set_err(ctx, NPBS_ERR_INVALID_ARG, "cdr_solve_direct: need a network");
     if (!batch || batch->count < 0) return set_err(ctx, NPBS_ERR_INVALID_ARG, "cdr_solve: NULL batch");
     const int cnt = batch->count;
     if (cnt == 0) return NPBS_OK;
@@ -611,7 +659,9 @@ npbs_status cdr_solve(npbs_ctx* ctx, const npbs_net* net, const npbs_batch* batc
         if (!any) break;
         // every instance iterates; frozen ones are no longer folded into u
         for (int k = 0; k < opts->check_every && it < opts->max_iter; ++k, ++it) {
-            st = cdr_run<float>(ctx, P, NPBS_RESIDUAL, kappa, vx, vy, sigma, rho, delta, r, nullptr, cnt, s);
+            // the network input of the correction equation: G(rho - A delta), or rho - A delta
+            st = cdr_run<float>(ctx, P, direct ? NPBS_TRUE_RESIDUAL : NPBS_RESIDUAL, kappa, vx, vy, sigma, rho, delta,
+                                r, nullptr, cnt, s);
             if (st != NPBS_OK) return st;
             if (N) {
                 st = net_run_forward(ctx, *N, run, r, a, delta, 1, s);
@@ -643,11 +693,29 @@ npbs_status cdr_solve(npbs_ctx* ctx, const npbs_net* net, const npbs_batch* batc
     return ret;
 }
 
-npbs_status cdr_train_step(npbs_ctx* ctx, npbs_net* net, const npbs_batch* batch, const npbs_cdr_consts* consts,
-                           const float* kappa, const float* vx, const float* vy, const float* sigma, const void* f,
-                           const float* a, const void* u_snap, int32_t unroll, float lr, float weight_decay,
-                           float* loss_host, npbs_stream stream) {
+extern "C" {
+
+npbs_status cdr_solve(npbs_ctx* ctx, const npbs_net* net, const npbs_batch* batch, const npbs_cdr_consts* consts,
+                      const float* kappa, const float* vx, const float* vy, const float* sigma, const void* f,
+                      const float* a, void* u, const npbs_solve_opts* opts, npbs_report* report, npbs_stream stream) {
+    return cdr_solve_impl(ctx, net, batch, consts, kappa, vx, vy, sigma, f, a, u, opts, report, stream, false);
+}
+
+npbs_status cdr_solve_direct(npbs_ctx* ctx, const npbs_net* net, const npbs_batch* batch,
+                             const npbs_cdr_consts* consts, const float* kappa, const float* vx, const float* vy,
+                             const float* sigma, const void* f, const float* a, void* u, const npbs_solve_opts* opts,
+                             npbs_report* report, npbs_stream stream) {
+    return cdr_solve_impl(ctx, net, batch, consts, kappa, vx, vy, sigma, f, a, u, opts, report, stream, true);
+}
+
+npbs_status cdr_train_step_loss(npbs_ctx* ctx, npbs_net* net, const npbs_batch* batch,
+                                const npbs_cdr_consts* consts, const float* kappa, const float* vx, const float* vy,
+                                const float* sigma, const void* f, const float* a, const void* u_snap,
+                                int32_t unroll, npbs_loss kind, float lr, float weight_decay, float* loss_host,
+                                npbs_stream stream) {
     if (!ctx) return NPBS_ERR_INVALID_ARG;
+    if (kind != NPBS_LOSS_BS_RETA && kind != NPBS_LOSS_BS_L2 && kind != NPBS_LOSS_DIR)
+        return set_err(ctx, NPBS_ERR_INVALID_ARG, "cdr_train_step: unknown loss");
     if (!net || !batch || !kappa || !vx || !vy || !sigma || !f || !a || !u_snap || !loss_host)
         return set_err(ctx, NPBS_ERR_INVALID_ARG, "cdr_train_step: NULL argument");
     if (unroll < 1 || unroll > 16 || !(lr >= 0.f) || !(weight_decay >= 0.f))
@@ -668,11 +736,38 @@ npbs_status cdr_train_step(npbs_ctx* ctx, npbs_net* net, const npbs_batch* batch
     if (!pl) return st;
     const float2* F = static_cast<const float2*>(f);
     const float2* usnap = static_cast<const float2*>(u_snap);
+    Net& N = *reinterpret_cast<Net*>(net);
+    if (kind != NPBS_LOSS_BS_RETA) {
+        // explicit adjoints: the convection term makes A not complex symmetric
+        EuclidOps op;
+        op.minus_a = [&](const float2* x, const float2* f_in, float2* out, double* norm2) -> npbs_status {
+            return cdr_run<float>(ctx, P, NPBS_TRUE_RESIDUAL, kappa, vx, vy, sigma, f_in, x, out, norm2, cnt, s);
+        };
+        op.minus_a_adj = [&](const float2* y, float2* out) -> npbs_status {
+            return cdr_run<float>(ctx, P, kCdrMinusAdjA, kappa, vx, vy, sigma, nullptr, y, out, nullptr, cnt, s);
+        };
+        op.green = [&](const float2* x, float2* out) -> npbs_status {
+            return cdr_run<float>(ctx, P, kCdrGreen, kappa, vx, vy, sigma, nullptr, x, out, nullptr, cnt, s);
+        };
+        op.green_adj = [&](const float2* y, float2* out) -> npbs_status {
+            return cdr_run<float>(ctx, P, kCdrGreenAdj, kappa, vx, vy, sigma, nullptr, y, out, nullptr, cnt, s);
+        };
+        return train_step_euclid(ctx, N, pl, a, F, usnap, unroll, kind == NPBS_LOSS_BS_L2, lr, weight_decay,
+                                 loss_host, s, op);
+    }
     BornOp op = [&](int mode, const float2* x, float2* out, double* norm2) -> npbs_status {
         return cdr_run<float>(ctx, P, mode, kappa, vx, vy, sigma, F, mode == NPBS_RESIDUAL ? usnap : x, out, norm2,
                               cnt, s);
     };
-    return train_step_reta(ctx, *reinterpret_cast<Net*>(net), pl, a, unroll, lr, weight_decay, loss_host, s, op);
+    return train_step_reta(ctx, N, pl, a, unroll, lr, weight_decay, loss_host, s, op);
+}
+
+npbs_status cdr_train_step(npbs_ctx* ctx, npbs_net* net, const npbs_batch* batch, const npbs_cdr_consts* consts,
+                           const float* kappa, const float* vx, const float* vy, const float* sigma, const void* f,
+                           const float* a, const void* u_snap, int32_t unroll, float lr, float weight_decay,
+                           float* loss_host, npbs_stream stream) {
+    return cdr_train_step_loss(ctx, net, batch, consts, kappa, vx, vy, sigma, f, a, u_snap, unroll,
+                               NPBS_LOSS_BS_RETA, lr, weight_decay, loss_host, stream);
 }
 
 }  // extern "C"

@@ -118,4 +118,21 @@ using BornOp = std::function<npbs_status(int mode, const float2* x, float2* out,
 npbs_status train_step_reta(npbs_ctx* ctx, Net& N, const Plan* pl, const float* n, int unroll, float lr,
                             float weight_decay, float* loss_host, cudaStream_t s, const BornOp& op);
 
+// The operators of the Euclidean objectives (Eqs. L_bs_l2, L_dir):
+//   minus_a(x, f_in, out, norm2): out = f_in - A x, norm2 (nullable) += ||out||^2
+//   minus_a_adj(y, out):          out = -A^* y
+//   green(x, out), green_adj(y, out): G x, G^* y
+// out may alias the input of minus_a_adj, green and green_adj.
+struct EuclidOps {
+    std::function<npbs_status(const float2* x, const float2* f_in, float2* out, double* norm2)> minus_a;
+    std::function<npbs_status(const float2* y, float2* out)> minus_a_adj;
+    std::function<npbs_status(const float2* x, float2* out)> green;
+    std::function<npbs_status(const float2* y, float2* out)> green_adj;
+};
+// One training step of L_bs_l2 (green_input: the network sees G t) or L_dir
+// (the network sees t = f - A u), unrolled from the snapshots, then AdamW.
+npbs_status train_step_euclid(npbs_ctx* ctx, Net& N, const Plan* pl, const float* n, const float2* f,
+                              const float2* u_snap, int U, bool green_input, float lr, float weight_decay,
+                              float* loss_host, cudaStream_t s, const EuclidOps& op);
+
 }  // namespace npbs

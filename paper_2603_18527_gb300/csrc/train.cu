@@ -161,10 +161,6 @@ npbs_status train_step_reta(npbs_ctx* ctx, Net& N, const Plan* pl, const float* 
 
 using namespace npbs;
 
-static npbs_status train_step_euclid(npbs_ctx* ctx, Net& N, const Plan* pl, const float2* V, const float2* f,
-                                     const float* n, const float2* u_snap, int U, bool green_input, float lr,
-                                     float weight_decay, float* loss_host, cudaStream_t s);
-
 extern "C" npbs_status npbs_train_step_loss(npbs_ctx* ctx, npbs_net* net, const npbs_batch* batch, const void* V,
                                             const void* f, const float* n, const void* u_snap, int32_t unroll,
                                             npbs_loss kind, float lr, float weight_decay, float* loss_host,
@@ -184,13 +180,59 @@ extern "C" npbs_status npbs_train_step_loss(npbs_ctx* ctx, npbs_net* net, const 
     if (cnt == 0) return NPBS_OK;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     Net& N = *reinterpret_cast<Net*>(net);
-    if (kind != NPBS_LOSS_BS_RETA)
-        return train_step_euclid(ctx, N, pl, static_cast<const float2*>(V), static_cast<const float2*>(f), n,
-                                 static_cast<const float2*>(u_snap), unroll, kind == NPBS_LOSS_BS_L2, lr,
-                                 weight_decay, loss_host, s);
     const float2* Vp = static_cast<const float2*>(V);
     const float2* fp = static_cast<const float2*>(f);
     const float2* usnap = static_cast<const float2*>(u_snap);
+    if (kind != NPBS_LOSS_BS_RETA) {
+        // A and G are complex symmetric (even symbols, diagonal potential), so
+        // A^* y = conj(A conj(y)) and likewise for G; scratch: zero, t1, t2
+        const size_t ext = (size_t)std::max<long long>(pl->extent, 1);
+        NPBS_CK(ctx, ctx->work[9].ensure(3 * ext * sizeof(float2)));
+        float2* zero = static_cast<float2*>(ctx->work[9].p);
+        float2* t1 = zero + ext;
+        float2* t2 = t1 + ext;
+        NPBS_CK(ctx, cudaMemsetAsync(zero, 0, ext * sizeof(float2), s));
+        const VecItem* vi = pl->vitems;
+        const int vb = pl->nvec;
+        auto conj = [&](const float2* x, float2* out) {
+            k_conj<<<vb, 256, 0, s>>>(vi, pl->inst, x, out);
+            ctx->count(s, 1);
+        };
+        EuclidOps op;
+        op.minus_a = [&](const float2* x, const float2* f_in, float2* out, double* norm2) -> npbs_status {
+            ApplyArgs a{};
+            a.V = Vp;
+            a.f = f_in;
+            a.x = x;
+            a.out = out;
+            a.norm2 = norm2;
+            return run_apply(ctx, *pl, NPBS_TRUE_RESIDUAL, a, nullptr, s);
+        };
+        op.green = [&](const float2* x, float2* out) -> npbs_status {
+            ApplyArgs a{};  // RESIDUAL with x = 0 and f = x: G x
+            a.V = Vp;
+            a.f = x;
+            a.x = zero;
+            a.out = out;
+            return run_apply(ctx, *pl, NPBS_RESIDUAL, a, nullptr, s);
+        };
+        op.minus_a_adj = [&](const float2* y, float2* out) -> npbs_status {
+            conj(y, t1);
+            npbs_status r = op.minus_a(t1, zero, t2, nullptr);
+            if (r != NPBS_OK) return r;
+            conj(t2, out);
+            return NPBS_OK;
+        };
+        op.green_adj = [&](const float2* y, float2* out) -> npbs_status {
+            conj(y, t1);
+            npbs_status r = op.green(t1, t2);
+            if (r != NPBS_OK) return r;
+            conj(t2, out);
+            return NPBS_OK;
+        };
+        return train_step_euclid(ctx, N, pl, n, fp, usnap, unroll, kind == NPBS_LOSS_BS_L2, lr, weight_decay,
+                                 loss_host, s, op);
+    }
     BornOp op = [&](int mode, const float2* x, float2* out, double* norm2) -> npbs_status {
         ApplyArgs a{};
         a.V = Vp;
@@ -210,10 +252,12 @@ extern "C" npbs_status npbs_train_step(npbs_ctx* ctx, npbs_net* net, const npbs_
                                 loss_host, stream);
 }
 
+namespace npbs {
+
 // Eq. L_bs_l2 (green_input) and Eq. L_dir in true-residual coordinates.
-static npbs_status train_step_euclid(npbs_ctx* ctx, Net& N, const Plan* pl, const float2* V, const float2* f,
-                                     const float* n, const float2* u_snap, int U, bool green_input, float lr,
-                                     float weight_decay, float* loss_host, cudaStream_t s) {
+npbs_status train_step_euclid(npbs_ctx* ctx, Net& N, const Plan* pl, const float* n, const float2* f,
+                              const float2* u_snap, int U, bool green_input, float lr, float weight_decay,
+                              float* loss_host, cudaStream_t s, const EuclidOps& op) {
     const int cnt = pl->count;
     const size_t ext = (size_t)std::max<long long>(pl->extent, 1);
     // states t_0..t_U, network inputs x_0..x_{U-1} (green_input only), c, wv, gr, gn, zero
@@ -238,46 +282,23 @@ static npbs_status train_step_euclid(npbs_ctx* ctx, Net& N, const Plan* pl, cons
     std::vector<int> which(cnt);
     for (int j = 0; j < cnt; ++j) which[j] = j;
     NetRun run;
-    st = net_prepare(ctx, N, *pl, which, true, &run, s);
+    st = net_prepare(ctx, N, *pl, which, true, &run, s, n);
     if (st != NPBS_OK) return st;
     NPBS_CK(ctx, cudaMemsetAsync(N.grads, 0, sizeof(float) * N.count(), s));
     NPBS_CK(ctx, cudaMemsetAsync(nk2, 0, sizeof(double) * cnt * U, s));
     NPBS_CK(ctx, cudaMemsetAsync(zero, 0, sizeof(float2) * ext, s));
-    // out = f_in - A x (TRUE_RESIDUAL); with f_in = 0 it is -A x
-    auto minusA = [&](const float2* x, const float2* f_in, float2* out, double* norm2) -> npbs_status {
-        ApplyArgs a{};
-        a.V = V;
-        a.f = f_in;
-        a.x = x;
-        a.out = out;
-        a.norm2 = norm2;
-        return run_apply(ctx, *pl, NPBS_TRUE_RESIDUAL, a, nullptr, s);
-    };
-    // out = G x (RESIDUAL with x = 0 and f = x)
-    auto green = [&](const float2* x, float2* out) -> npbs_status {
-        ApplyArgs a{};
-        a.V = V;
-        a.f = x;
-        a.x = zero;
-        a.out = out;
-        return run_apply(ctx, *pl, NPBS_RESIDUAL, a, nullptr, s);
-    };
-    auto conj = [&](const float2* x, float2* out) {
-        k_conj<<<vb, 256, 0, s>>>(vi, pl->inst, x, out);
-        ctx->count(s, 1);
-    };
 
     // forward
-    st = minusA(u_snap, f, Tk(0), t0n2);  // t_0 = f - A u
+    st = op.minus_a(u_snap, f, Tk(0), t0n2);  // t_0 = f - A u
     if (st != NPBS_OK) return st;
     for (int k = 0; k < U; ++k) {
         if (green_input) {
-            st = green(Tk(k), Xk(k));
+            st = op.green(Tk(k), Xk(k));
             if (st != NPBS_OK) return st;
         }
         st = net_run_forward(ctx, N, run, Xk(k), n, c, 0, s);
         if (st != NPBS_OK) return st;
-        st = minusA(c, zero, wv, nullptr);  // -A c
+        st = op.minus_a(c, zero, wv, nullptr);  // -A c
         if (st != NPBS_OK) return st;
         k_sub_norm<<<vb, 256, 0, s>>>(vi, pl->inst, Tk(k), wv, Tk(k + 1), nk2 + (size_t)k * cnt, 1.f);
         ctx->count(s, 1);
@@ -299,19 +320,13 @@ static npbs_status train_step_euclid(npbs_ctx* ctx, Net& N, const Plan* pl, cons
     k_axpby_inst<<<vb, 256, 0, s>>>(vi, pl->inst, Tk(U), wgt, 2.f, nullptr, nullptr, gr);
     ctx->count(s, 1);
     for (int k = U - 1; k >= 0; --k) {
-        // g_c = -A^* g_t = conj(-A conj(g_t))
-        conj(gr, c);
-        st = minusA(c, zero, wv, nullptr);
+        st = op.minus_a_adj(gr, c);  // g_c = -A^* g_t
         if (st != NPBS_OK) return st;
-        conj(wv, c);
         st = net_run_backward(ctx, N, run, Xk(k), n, c, gn, 0, s);
         if (st != NPBS_OK) return st;
         if (green_input) {
-            // G^* gn = conj(G conj(gn))
-            conj(gn, c);
-            st = green(c, wv);
+            st = op.green_adj(gn, gn);  // P^* = G^*
             if (st != NPBS_OK) return st;
-            conj(wv, gn);
         }
         if (k > 0) {
             // g_t <- g_t + P^* J^* g_c + 2 w t_k
@@ -322,3 +337,5 @@ static npbs_status train_step_euclid(npbs_ctx* ctx, Net& N, const Plan* pl, cons
     NPBS_CK(ctx, cudaGetLastError());
     return net_adamw(ctx, N, lr, weight_decay, s);
 }
+
+}  // namespace npbs

@@ -32,7 +32,8 @@ def _oracle(inst, consts):
                            inst.f.astype(np.complex64).astype(np.complex128), inst.h, consts)
 
 
-INSTS = [(64, 11, 1.0), (128, 12, 1.0), (64, 13, 0.1)]
+# grid sides 64, 128 and 256 run the compile-time fused kernels, 96 the run-time ones
+INSTS = [(64, 11, 1.0), (128, 12, 1.0), (64, 13, 0.1), (96, 14, 0.5), (256, 15, 1.0)]
 
 
 def test_cdr_background_constants():
@@ -107,37 +108,84 @@ def test_cdr_born_series_solve_is_oracle_judged():
         assert up4 - 4 <= rep["iters"][j] <= up4 + 4, (j, ref, rep["iters"][j])
 
 
-def test_cdr_train_step_matches_the_oracle_loss_and_gradient():
-    """cdr_train_step (an FNO with the four coefficient channels kappa, vx,
-    vy, sigma; 3 unrolls; lr = 0) against the metric-matched unrolled loss
-    composed from the oracle's CDR operators, r_0 = G(V u + f) - u,
-    r_{k+1} = r_k - (I - G V) M(r_k), loss = mean_j (1/U) sum_k ||r_k||^2 /
-    ||r_0||^2, and its autograd gradient."""
+def _fno_case(capi, c, seed, cfg=None):
+    """A four-channel FNO with seeded parameters and four 32^2 CDR instances at
+    full convection speed; the oracle's parameters and problems beside them."""
     from oracle import fno as FN
     from tests.test_gpu_fno import _oracle_params, _params
-    cfg = FN.FnoConfig(n=32, width=8, modes=5, layers=2, coef=4)
-    capi, c = ctx()
-    insts = [synth.cdr_instance(32, seed=800 + j, speed=1.0) for j in range(4)]
+    cfg = cfg or FN.FnoConfig(n=32, width=8, modes=5, layers=2, coef=4)
+    insts = [synth.cdr_instance(32, seed=seed + j, speed=1.0) for j in range(4)]
     b, fields, f = _setup(capi, insts)
     consts = capi.npbs_cdr_background(c, b, fields)
+    net = capi.Net.fno(32, cfg.width, cfg.modes, cfg.layers, seed=1, coef_channels=4)
+    net.set_params(_params(cfg, seed))
+    flat, P = _oracle_params(cfg, seed, requires_grad=True)
+    probs = [_oracle(i, consts[j]) for j, i in enumerate(insts)]
+    A = torch.stack([torch.stack([p.kappa, p.vx, p.vy, p.sigma]) for p in probs])
+    return cfg, b, fields, f, consts, net, flat, P, probs, A
+
+
+@pytest.mark.parametrize("loss", ["bs_reta", "bs_l2", "dir"])
+def test_cdr_train_step_matches_the_oracle_loss_and_gradient(loss):
+    """cdr_train_step (an FNO with the four coefficient channels kappa, vx,
+    vy, sigma; 3 unrolls; lr = 0) against the unrolled losses composed from
+    the oracle's CDR operators, and their autograd gradients:
+    bs_reta: r_0 = G(V u + f) - u, r_{k+1} = r_k - (I - G V) M(r_k), weights 1/||r_0||^2;
+    bs_l2 / dir: t_0 = f - A u, t_{k+1} = t_k - A M(G t_k) / A M(t_k), weights 1/||t_0||^2;
+    loss = mean_j (1/U) sum_k ||state_k||^2 * weight.  Autograd through the
+    oracle's A and G pins the library's explicit adjoints A^* and G^* (convection
+    makes A not complex symmetric)."""
+    from oracle import fno as FN
+    capi, c = ctx()
+    cfg, b, fields, f, consts, net, flat, P, probs, A = _fno_case(capi, c, 800)
     snaps = [np.zeros((32, 32), np.complex64)] + [(0.1 * random_field((32, 32), 810 + j)).astype(np.complex64)
                                                  for j in range(3)]
     u0 = b.pack(snaps)
-    net = capi.Net.fno(32, cfg.width, cfg.modes, cfg.layers, seed=1, coef_channels=4)
-    net.set_params(_params(cfg, 14))
-    loss = capi.cdr_train_step(c, net, b, consts, fields, f, fields.a, u0, unroll=3, lr=0.0, weight_decay=0.0)
-    flat, P = _oracle_params(cfg, 14, requires_grad=True)
-    probs = [_oracle(i, consts[j]) for j, i in enumerate(insts)]
-    A = torch.stack([torch.stack([p.kappa, p.vx, p.vy, p.sigma]) for p in probs])
+    got = capi.cdr_train_step(c, net, b, consts, fields, f, fields.a, u0, unroll=3, lr=0.0, weight_decay=0.0,
+                              loss=loss)
     feats = FN.coefficient_features(A, P, cfg)
-    r = torch.stack([CD.born_residual(p, torch.from_numpy(s.astype(np.complex128))) for p, s in zip(probs, snaps)])
-    r0 = (r.real ** 2 + r.imag ** 2).sum(dim=(-2, -1))
-    acc = torch.zeros_like(r0)
+    us = [torch.from_numpy(s.astype(np.complex128)) for s in snaps]
+    if loss == "bs_reta":
+        x = torch.stack([CD.born_residual(p, u) for p, u in zip(probs, us)])
+        step = lambda j, cj: CD.op_B(probs[j], cj)
+    else:
+        x = torch.stack([p.f - CD.apply_A(p, u) for p, u in zip(probs, us)])
+        step = lambda j, cj: CD.apply_A(probs[j], cj)
+    inp = (lambda t: torch.stack([CD.green(p, t[j]) for j, p in enumerate(probs)])) if loss == "bs_l2" else \
+        (lambda t: t)
+    n0 = (x.real ** 2 + x.imag ** 2).sum(dim=(-2, -1))
+    acc = torch.zeros_like(n0)
     for _ in range(3):
-        corr = FN.correction_from_features(r, feats, P, cfg)
-        r = r - torch.stack([CD.op_B(p, corr[j]) for j, p in enumerate(probs)])
-        acc = acc + (r.real ** 2 + r.imag ** 2).sum(dim=(-2, -1)) / r0
+        corr = FN.correction_from_features(inp(x), feats, P, cfg)
+        x = x - torch.stack([step(j, corr[j]) for j in range(len(probs))])
+        acc = acc + (x.real ** 2 + x.imag ** 2).sum(dim=(-2, -1)) / n0
     L = (acc / 3).mean()
     (gref,) = torch.autograd.grad(L, flat)
-    assert loss == pytest.approx(float(L), rel=1e-3)
+    assert got == pytest.approx(float(L.detach()), rel=1e-3)
     assert rel_l2(net.get_grads(), gref.numpy()) <= 2e-3
+
+
+@pytest.mark.parametrize("direct", [False, True])
+def test_cdr_solve_with_a_network_follows_the_oracle_iteration(direct):
+    """Three iterations of NPBS (u <- u + M(G(f - A u))) or of the Direct
+    format (u <- u + M(f - A u)) with an FNO from u = 0, against the same
+    iteration written with the oracle's operators and network; the reported
+    rTol is the oracle's rTol of the returned u."""
+    from oracle import fno as FN
+    capi, c = ctx()
+    cfg, b, fields, f, consts, net, flat, P, probs, A = _fno_case(capi, c, 820)
+    u = torch.zeros(b.extent, dtype=torch.complex128, device="cuda")
+    st, rep = capi.cdr_solve(c, net, b, consts, fields, f, fields.a, u, rtol=0.0, max_iter=3, check_every=3,
+                             direct=direct)
+    assert st == capi.NOT_CONVERGED
+    got = b.unpack(u)
+    with torch.no_grad():
+        feats = FN.coefficient_features(A, P, cfg)
+        U = torch.zeros(len(probs), 32, 32, dtype=torch.complex128)
+        for _ in range(3):
+            t = torch.stack([p.f - CD.apply_A(p, U[j]) for j, p in enumerate(probs)])
+            x = t if direct else torch.stack([CD.green(p, t[j]) for j, p in enumerate(probs)])
+            U = U + FN.correction_from_features(x, feats, P, cfg)
+    for j, p in enumerate(probs):
+        assert rel_l2(got[j], U[j].numpy()) <= 1e-3, j
+        assert rep["rtol"][j] == pytest.approx(CD.rtol(p, torch.from_numpy(got[j])), rel=1e-6)
