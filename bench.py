@@ -221,6 +221,64 @@ def bench_learned(capi, ctx, args, stream):
     return out
 
 
+def bench_extensions(capi, ctx, args, stream):
+    """The FNO backbone and the CDR operators: network forward and training
+    step times, and the CDR apply against its algorithmic HBM bytes (read x,
+    f, kappa, vx, vy, sigma; write out: 40 B per point)."""
+    import synth
+    from paper_2603_18527_gb300 import train_cdr as TC
+    from paper_2603_18527_gb300 import train_unet as T
+    out = {}
+    # FNO at the paper's Helmholtz configuration (25 channels, 45 modes, 3 NLFL layers) on 64 x 256^2;
+    # the coefficient branch is computed once per (network, a) and cached, as in a solve
+    insts = T.media(256, args.npbs_count, 2000)
+    pool = T.Pool(ctx, insts)
+    fno = capi.Net.fno(256, 25, 45, 3, seed=0)
+    r = torch.randn(pool.b.extent, dtype=torch.complex64, device="cuda")
+    c = torch.zeros_like(r)
+    fwd = lambda: capi.npbs_net_forward(ctx, fno, pool.b, r, pool.n, c)
+    fwd()
+    out["fno_forward_256"] = {"instances": len(insts), "ms": timed(stream, fwd, 5),
+                              "params": fno.num_params(), "coefficient_branch": "cached"}
+    sel = insts[:32]
+    tp = T.Pool(ctx, sel)
+    u0 = torch.zeros(tp.b.extent, dtype=torch.complex64, device="cuda")
+    step = lambda: capi.npbs_train_step(ctx, fno, tp.b, tp.V, tp.f, tp.n, u0, unroll=4, lr=0.0, weight_decay=0.0)
+    step()
+    out["fno_train_step_256"] = {"batch": 32, "unroll": 4, "ms": timed(stream, step, 2)}
+    del fno
+    # CDR at the paper's 128^2 grid: 256 instances for the apply, 32 for the training step
+    cinsts = [synth.cdr_instance(128, seed=60000 + j, speed=1.0) for j in range(256)]
+    g = TC.Group(ctx, cinsts)
+    x = torch.randn(g.b.extent, dtype=torch.complex64, device="cuda")
+    y = torch.zeros_like(x)
+    ap = lambda: capi.cdr_apply(ctx, g.b, g.consts, g.fields, g.f, x, y, capi.RESIDUAL)
+    ap()
+    ms = timed(stream, ap, 20)
+    pts = sum(i.n * i.n for i in cinsts)
+    hbm, kind = peaks()
+    ach = 40.0 * pts / (ms * 1e-3) / 1e9
+    out["cdr_apply_128"] = {"instances": len(cinsts), "mode": "RESIDUAL", "ms": ms, "algorithmic_gbs": ach,
+                            "frac_of_hbm": ach / hbm, "peak_kind": kind, "bytes_per_point": 40,
+                            "launches": "5 fused kernels (transforms with the pointwise steps inside)"}
+    tg = TC.Group(ctx, cinsts[:32])
+    net = TC.make_net(128, 25, 32, 3)
+    u0 = torch.zeros(tg.b.extent, dtype=torch.complex64, device="cuda")
+    st = lambda: capi.cdr_train_step(ctx, net, tg.b, tg.consts, tg.fields, tg.f, tg.fields.a, u0, unroll=4, lr=0.0,
+                                     weight_decay=0.0)
+    st()
+    out["cdr_fno_train_step_128"] = {"batch": 32, "unroll": 4, "ms": timed(stream, st, 3)}
+    u = torch.zeros(tg.b.extent, dtype=torch.complex128, device="cuda")
+    K = 40
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    capi.cdr_solve(ctx, net, tg.b, tg.consts, tg.fields, tg.f, tg.fields.a, u, rtol=0.0, max_iter=K, check_every=4)
+    out["cdr_npbs_iteration_ms_128"] = {"batch": 32, "ms": (time.perf_counter() - t0) * 1e3 / K,
+                                        "note": "one NPBS iteration of the batch (apply + FNO forward), float64 "
+                                                "check every 4"}
+    return out
+
+
 def load_net(capi, args):
     """The network of --net (.npz params or a saved network), else untrained; (net, name)."""
     if args.net and os.path.exists(args.net) and args.net.endswith(".npz"):
@@ -447,9 +505,30 @@ def main():
     ap.add_argument("--train-step-only", action="store_true",
                     help="time only npbs_train_step (batch --train-batch at 256^2, 4 unrolls) for profiler captures")
     ap.add_argument("--train-batch", type=int, default=32)
+    ap.add_argument("--train-backbone", default="unet", choices=["unet", "fno"],
+                    help="network of --train-step-only (fno: 25 channels, 45 modes, 3 NLFL layers at 256^2)")
+    ap.add_argument("--cdr-apply-only", type=int, default=0, metavar="COUNT",
+                    help="time only the CDR RESIDUAL apply on COUNT 128^2 instances (for profiler captures)")
     ap.add_argument("--net-forward-only", action="store_true",
                     help="time only the network forward on --npbs-count 256^2 instances (for profiler captures)")
     args = ap.parse_args()
+    if args.cdr_apply_only:
+        import synth
+        from paper_2603_18527_gb300 import build, capi
+        from paper_2603_18527_gb300 import train_cdr as TC
+        build.build()
+        ctx = capi.Context(0)
+        g = TC.Group(ctx, [synth.cdr_instance(128, seed=60000 + j, speed=1.0) for j in range(args.cdr_apply_only)])
+        x = torch.randn(g.b.extent, dtype=torch.complex64, device="cuda")
+        y = torch.zeros_like(x)
+        ap_ = lambda: capi.cdr_apply(ctx, g.b, g.consts, g.fields, g.f, x, y, capi.RESIDUAL)
+        for _ in range(args.warmup):
+            ap_()
+        ms = timed(torch.cuda.current_stream(), ap_, max(1, args.steps))
+        pts = args.cdr_apply_only * 128 * 128
+        print(json.dumps({"cdr_apply_only": args.cdr_apply_only, "ms": ms,
+                          "algorithmic_gbs": 40.0 * pts / (ms * 1e-3) / 1e9}))
+        return 0
     if args.workload == "layered1024" and not args.apply_only:
         ap.error("--workload layered1024 is an apply-only workload")
     if args.impl == "reference":
@@ -459,7 +538,7 @@ def main():
         from paper_2603_18527_gb300 import train_unet as T
         build.build()
         ctx = capi.Context(0)
-        net = capi.Net(0, seed=0)
+        net = capi.Net.fno(256, 25, 45, 3, seed=0) if args.train_backbone == "fno" else capi.Net(0, seed=0)
         pool = T.Pool(ctx, T.media(256, args.train_batch, 3000))
         u0 = torch.zeros(pool.b.extent, dtype=torch.complex64, device="cuda")
         step = lambda: capi.npbs_train_step(ctx, net, pool.b, pool.V, pool.f, pool.n, u0, unroll=4, lr=0.0)
@@ -609,10 +688,14 @@ def main():
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1) / e2e_steps
 
-    learned = fg = None
+    learned = fg = ext = None
     if not args.no_learned and rank == 0:
         learned = bench_learned(capi, ctx, args, stream)
         fg = bench_fgmres(capi, ctx, args)
+        try:
+            ext = bench_extensions(capi, ctx, args, stream)
+        except Exception as e:  # the headline line stands without the extension figures
+            ext = {"error": repr(e)}
 
     line = None
     if rank == 0:
@@ -650,7 +733,7 @@ def main():
                         "h2d_bytes_per_step": int(k2_h.numel() * 8 + f_h.numel() * 8),
                         "d2h_bytes_per_step": int(u_h.numel() * 16)},
                 "gpu_launches": int(launches), "clocks": clk.summary(),
-                "learned": learned, "fgmres": fg}
+                "learned": learned, "fgmres": fg, "extensions": ext}
         print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()

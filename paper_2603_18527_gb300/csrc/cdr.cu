@@ -21,6 +21,7 @@
 #include <cmath>
 #include <cstring>
 #include <map>
+#include <type_traits>
 #include <vector>
 
 #include "ctx.cuh"
@@ -243,6 +244,222 @@ __global__ void k_cdr_fold(const CdrInst* ins, const int* ids, const int* frozen
     }
 }
 
+// ---- the fused float32 apply: five launches per grid side -----------------
+// K1 rows:  x -> F_x x                                        (b0)
+// K2 cols:  F_y -> X; [adjoint: X /= conj(lambda0)]; i xi_x X, i xi_y X [, X]
+//           -> F_y^{-1}                                       (b1, b2 [, b0])
+// K3 rows:  F_x^{-1} of those fields; the flux of k_cdr_flux; F_x of the
+//           three flux fields                                 (b3, b4, b5)
+// K4 cols:  F_y of the three; W = -i xi_x b3 - i xi_y b4 + b5, the mode's
+//           multiple of W; F_y^{-1}                           (b0)
+// K5 rows:  F_x^{-1}, out = b0 / n^2 and ||out||^2
+// The same arithmetic as the unfused kernels, with the pointwise steps done
+// inside the transform kernels (about 160 B/point moved instead of 380).
+constexpr int kFTile = 6144;  // complex elements per tile buffer (48 KB); two per block
+
+__device__ __forceinline__ float2 cdr_lambda(const CdrInst& in, float kx, float ky, bool conj) {
+    return make_float2((float)in.k0 * (kx * kx + ky * ky) + (float)in.s0,
+                       (conj ? -1.f : 1.f) * ((float)in.v0x * kx + (float)in.v0y * ky));
+}
+__device__ __forceinline__ float2 cdiv(float2 w, float2 l) {
+    const float d = 1.f / (l.x * l.x + l.y * l.y);
+    return make_float2((w.x * l.x + w.y * l.y) * d, (w.y * l.x - w.x * l.y) * d);
+}
+
+// A tile transform: compile-time geometry when N > 0, else the run-time plan.
+template <int N, int NB, int SI, int SB, int DIR, bool COLS>
+__device__ __forceinline__ float2* tile_fft(float2* a, float2* b, const RadixPlan& plan, int nb, int si, int sb,
+                                            const float2* tw) {
+    if constexpr (N > 0) return fft_tile_ct<float2, DIR, COLS, N, NB, SI, SB>(a, b, tw, threadIdx.x, blockDim.x);
+    else return fft_tile<float2, DIR, COLS>(a, b, plan, nb, si, sb, tw, threadIdx.x, blockDim.x);
+}
+
+// The kernels take the grid side N, rows per row block RB, columns per column
+// block CB and the number F of gradient fields as template constants (N = 0:
+// run-time n, rb, cb; F is always a template constant).
+
+// K1: rb rows of one instance per block: b0 rows = F_x(x rows)
+template <int N, int RB>
+__global__ void __launch_bounds__(256) k_cdrf_rows_fwd(const CdrInst* ins, int n_, int rb_, RadixPlan plan,
+                                                       const float2* tw, const float2* x, float2* b0) {
+    extern __shared__ __align__(16) float2 sm[];
+    const int n = N ? N : n_, rb = N ? RB : rb_;
+    const int nbk = n / rb;
+    const CdrInst in = ins[blockIdx.x / nbk];
+    const long long base = in.off + (long long)(blockIdx.x % nbk) * rb * n;
+    const int cnt = rb * n;
+    for (int e = threadIdx.x; e < cnt; e += blockDim.x) sm[e] = x[base + e];
+    __syncthreads();
+    float2* res = tile_fft<N, RB, 1, N, -1, false>(sm, sm + kFTile, plan, rb, 1, n, tw);
+    for (int e = threadIdx.x; e < cnt; e += blockDim.x) b0[base + e] = res[e];
+}
+
+// K2: cb columns of one instance per block.  F fields out: forward 2 (gx, gy),
+// adjoint 3 (gx, gy, g), adj == 1 dividing by conj(lambda0) first (G^*).
+// Tile layout [row i][field f * cb + column b].
+template <int N, int CB, int F>
+__global__ void __launch_bounds__(256) k_cdrf_cols_grad(const CdrInst* ins, int n_, int cb_, RadixPlan plan,
+                                                        const float2* tw, float2* b0, float2* b1, float2* b2,
+                                                        int adj) {
+    extern __shared__ __align__(16) float2 sm[];
+    const int n = N ? N : n_, cb = N ? CB : cb_;
+    const int nbk = n / cb;
+    const CdrInst in = ins[blockIdx.x / nbk];
+    const int c0 = (blockIdx.x % nbk) * cb;
+    const long long base = in.off + c0;
+    const int cnt = cb * n;
+    for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+        const int i = e / cb, b = e - i * cb;
+        sm[e] = b0[base + (long long)i * n + b];
+    }
+    __syncthreads();
+    float2* X = tile_fft<N, CB, CB, 1, -1, true>(sm, sm + kFTile, plan, cb, cb, 1, tw);
+    // spread into F fields in the other buffer (X is in sm or sm + kFTile)
+    float2* T = X == sm ? sm + kFTile : sm;
+    for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+        const int i = e / cb, b = e - i * cb;
+        const float kx = xi_of<float>(c0 + b, n, in.h), ky = xi_of<float>(i, n, in.h);
+        float2 u = X[e];
+        if (adj == 1) u = cdiv(u, cdr_lambda(in, kx, ky, true));
+        float2* row = T + (long long)i * F * cb;
+        row[b] = make_float2(-kx * u.y, kx * u.x);
+        row[cb + b] = make_float2(-ky * u.y, ky * u.x);
+        if (F == 3) row[2 * cb + b] = u;
+    }
+    __syncthreads();
+    // the buffer X occupied is the scratch of the inverse
+    float2* res = tile_fft<N, F * CB, F * CB, 1, 1, true>(T, X, plan, F * cb, F * cb, 1, tw);
+    for (int e = threadIdx.x; e < F * cnt; e += blockDim.x) {
+        const int i = e / (F * cb), r = e - i * (F * cb), f = r / cb, b = r - f * cb;
+        float2* o = f == 0 ? b1 : f == 1 ? b2 : b0;
+        o[base + (long long)i * n + b] = res[e];
+    }
+}
+
+// K3: rb rows per block: F_x^{-1} of the F gradient fields, the flux, F_x of
+// the three flux fields.  Tile layout [field][row][n].
+template <int N, int RB, int F>
+__global__ void __launch_bounds__(256) k_cdrf_rows_flux(const CdrInst* ins, int n_, int rb_, RadixPlan plan,
+                                                        const float2* tw, const float* kappa, const float* vx,
+                                                        const float* vy, const float* sigma, const float2* x,
+                                                        const float2* f, float2* b0, float2* b1, float2* b2,
+                                                        float2* b3, float2* b4, float2* b5) {
+    extern __shared__ __align__(16) float2 sm[];
+    const int n = N ? N : n_, rb = N ? RB : rb_;
+    const int nbk = n / rb;
+    const CdrInst in = ins[blockIdx.x / nbk];
+    const long long base = in.off + (long long)(blockIdx.x % nbk) * rb * n;
+    const int cnt = rb * n;
+    for (int e = threadIdx.x; e < F * cnt; e += blockDim.x) {
+        const int fld = e / cnt, p = e - fld * cnt;
+        const float2* src = fld == 0 ? b1 : fld == 1 ? b2 : b0;
+        sm[e] = src[base + p];
+    }
+    __syncthreads();
+    float2* G = tile_fft<N, F * RB, 1, N, 1, false>(sm, sm + kFTile, plan, F * rb, 1, n, tw);
+    float2* T = G == sm ? sm + kFTile : sm;
+    const float s = 1.f / ((float)n * (float)n);
+    for (int p = threadIdx.x; p < cnt; p += blockDim.x) {
+        const long long o = base + p;
+        const float k = kappa[o], ax = vx[o], ay = vy[o], sg = sigma[o];
+        const float2 ux = make_float2(G[p].x * s, G[p].y * s), uy = make_float2(G[cnt + p].x * s, G[cnt + p].y * s);
+        if (F == 2) {
+            const float2 xv = x[o];
+            float2 r = make_float2(ax * ux.x + ay * uy.x + sg * xv.x, ax * ux.y + ay * uy.y + sg * xv.y);
+            if (f) r = make_float2(r.x - f[o].x, r.y - f[o].y);
+            T[p] = make_float2(k * ux.x, k * ux.y);
+            T[cnt + p] = make_float2(k * uy.x, k * uy.y);
+            T[2 * cnt + p] = r;
+        } else {
+            const float2 gv = make_float2(G[2 * cnt + p].x * s, G[2 * cnt + p].y * s);
+            T[p] = make_float2(k * ux.x + ax * gv.x, k * ux.y + ax * gv.y);
+            T[cnt + p] = make_float2(k * uy.x + ay * gv.x, k * uy.y + ay * gv.y);
+            T[2 * cnt + p] = make_float2(sg * gv.x, sg * gv.y);
+        }
+    }
+    __syncthreads();
+    float2* res = tile_fft<N, 3 * RB, 1, N, -1, false>(T, G, plan, 3 * rb, 1, n, tw);
+    for (int e = threadIdx.x; e < 3 * cnt; e += blockDim.x) {
+        const int fld = e / cnt, p = e - fld * cnt;
+        float2* o = fld == 0 ? b3 : fld == 1 ? b4 : b5;
+        o[base + p] = res[e];
+    }
+}
+
+// K4: cb columns per block: F_y of b3, b4, b5, the assembly (kinds of
+// k_cdr_assemble), F_y^{-1} of the result into b0.  Tile [row][field * cb + b].
+template <int N, int CB>
+__global__ void __launch_bounds__(256) k_cdrf_cols_asm(const CdrInst* ins, int n_, int cb_, RadixPlan plan,
+                                                       const float2* tw, const float2* b3, const float2* b4,
+                                                       const float2* b5, float2* b0, int kind) {
+    extern __shared__ __align__(16) float2 sm[];
+    const int n = N ? N : n_, cb = N ? CB : cb_;
+    const int nbk = n / cb;
+    const CdrInst in = ins[blockIdx.x / nbk];
+    const int c0 = (blockIdx.x % nbk) * cb;
+    const long long base = in.off + c0;
+    const int cnt = cb * n;
+    for (int e = threadIdx.x; e < 3 * cnt; e += blockDim.x) {
+        const int i = e / (3 * cb), r = e - i * (3 * cb), fld = r / cb, b = r - fld * cb;
+        const float2* src = fld == 0 ? b3 : fld == 1 ? b4 : b5;
+        sm[e] = src[base + (long long)i * n + b];
+    }
+    __syncthreads();
+    float2* S = tile_fft<N, 3 * CB, 3 * CB, 1, -1, true>(sm, sm + kFTile, plan, 3 * cb, 3 * cb, 1, tw);
+    float2* T = S == sm ? sm + kFTile : sm;
+    for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+        const int i = e / cb, b = e - i * cb;
+        const float kx = xi_of<float>(c0 + b, n, in.h), ky = xi_of<float>(i, n, in.h);
+        const float2* row = S + (long long)i * 3 * cb;
+        const float2 a = row[b], bb = row[cb + b], c = row[2 * cb + b];
+        float2 w = make_float2(kx * a.y + ky * bb.y + c.x, -kx * a.x - ky * bb.x + c.y);
+        if (kind == 0 || kind == 2) w = make_float2(-w.x, -w.y);
+        if (kind == 0 || kind == 1) w = cdiv(w, cdr_lambda(in, kx, ky, false));
+        T[e] = w;
+    }
+    __syncthreads();
+    float2* res = tile_fft<N, CB, CB, 1, 1, true>(T, S, plan, cb, cb, 1, tw);
+    for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+        const int i = e / cb, b = e - i * cb;
+        b0[base + (long long)i * n + b] = res[e];
+    }
+}
+
+// K5: rb rows per block: F_x^{-1}, out = b0 / n^2, norm2[ids[j]] += ||out||^2
+template <int N, int RB>
+__global__ void __launch_bounds__(256) k_cdrf_rows_out(const CdrInst* ins, const int* ids, int n_, int rb_,
+                                                       RadixPlan plan, const float2* tw, const float2* b0,
+                                                       float2* out, double* norm2) {
+    extern __shared__ __align__(16) float2 sm[];
+    __shared__ double red[8];
+    const int n = N ? N : n_, rb = N ? RB : rb_;
+    const int nbk = n / rb;
+    const int j = blockIdx.x / nbk;
+    const CdrInst in = ins[j];
+    const long long base = in.off + (long long)(blockIdx.x % nbk) * rb * n;
+    const int cnt = rb * n;
+    for (int e = threadIdx.x; e < cnt; e += blockDim.x) sm[e] = b0[base + e];
+    __syncthreads();
+    float2* res = tile_fft<N, RB, 1, N, 1, false>(sm, sm + kFTile, plan, rb, 1, n, tw);
+    const float s = 1.f / ((float)n * (float)n);
+    double acc = 0.0;
+    for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+        const float2 v = make_float2(res[e].x * s, res[e].y * s);
+        out[base + e] = v;
+        acc += (double)v.x * v.x + (double)v.y * v.y;
+    }
+    if (norm2) {
+        for (int w = 16; w > 0; w >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, w);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+            atomicAdd(norm2 + ids[j], t);
+        }
+    }
+}
+
 }  // namespace
 }  // namespace npbs
 
@@ -284,6 +501,8 @@ template <> float2* CdrPrep::fields<float>() const { return buf; }
 template <> double2* CdrPrep::fields<double>() const { return buf64; }
 template <> const float2* CdrPrep::twiddles<float>(const CdrGroup& g) const { return g.tw; }
 template <> const double2* CdrPrep::twiddles<double>(const CdrGroup& g) const { return g.tw64; }
+
+npbs_status cdr_fused_attrs(npbs_ctx* ctx);
 
 npbs_status cdr_prepare(npbs_ctx* ctx, const npbs_batch* batch, const npbs_cdr_consts* consts, CdrPrep* P,
                         cudaStream_t st) {
@@ -366,6 +585,8 @@ npbs_status cdr_prepare(npbs_ctx* ctx, const npbs_batch* batch, const npbs_cdr_c
     }
     P->buf = static_cast<float2*>(ctx->work[13].p);
     NPBS_CK(ctx, fft2d::set_attrs());
+    npbs_status fs = cdr_fused_attrs(ctx);
+    if (fs != NPBS_OK) return fs;
     return NPBS_OK;
 }
 
@@ -385,13 +606,101 @@ constexpr int kCdrMinusAdjA = 100;
 constexpr int kCdrGreen = 101;
 constexpr int kCdrGreenAdj = 102;
 
+inline int divisor_at_most(int n, int lim) {
+    for (int d = std::min(n, lim); d >= 1; --d)
+        if (n % d == 0) return d;
+    return 1;
+}
+
+template <int N, int RB, int CB> cudaError_t fused_attrs_of() {
+    const int sm = (int)(2 * kFTile * sizeof(float2));
+    const cudaFuncAttribute at = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    cudaError_t e = cudaFuncSetAttribute(k_cdrf_rows_fwd<N, RB>, at, sm);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_cdrf_cols_grad<N, CB, 2>, at, sm);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_cdrf_cols_grad<N, CB, 3>, at, sm);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_cdrf_rows_flux<N, RB, 2>, at, sm);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_cdrf_rows_flux<N, RB, 3>, at, sm);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_cdrf_cols_asm<N, CB>, at, sm);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_cdrf_rows_out<N, RB>, at, sm);
+    return e;
+}
+
+npbs_status cdr_fused_attrs(npbs_ctx* ctx) {
+    NPBS_CK(ctx, (fused_attrs_of<0, 0, 0>()));
+    NPBS_CK(ctx, (fused_attrs_of<64, 16, 16>()));
+    NPBS_CK(ctx, (fused_attrs_of<128, 16, 16>()));
+    NPBS_CK(ctx, (fused_attrs_of<256, 8, 8>()));
+    return NPBS_OK;
+}
+
+// The five launches of one grid side (N > 0: compile-time geometry RB, CB).
+template <int N, int RB, int CB>
+void fused_launch(const CdrGroup& g, int rb, int cb, int mode, const float* kappa, const float* vx, const float* vy,
+                  const float* sigma, const float2* f, const float2* x, float2* const* b, float2* out, double* norm2,
+                  cudaStream_t st) {
+    const int n = g.n;
+    const size_t sm = 2 * kFTile * sizeof(float2);
+    const bool adj = mode == NPBS_ADJ_B || mode == kCdrMinusAdjA;
+    const int kind = mode == NPBS_RESIDUAL ? 0 : mode == NPBS_OP_B ? 1
+                   : (mode == NPBS_TRUE_RESIDUAL || mode == kCdrMinusAdjA) ? 2 : 3;
+    const unsigned gr = (unsigned)(g.cnt * (n / rb)), gc = (unsigned)(g.cnt * (n / cb));
+    const float2* fs = (mode == NPBS_OP_B || adj) ? nullptr : f;
+    k_cdrf_rows_fwd<N, RB><<<gr, 256, sm, st>>>(g.ins, n, rb, g.plan, g.tw, x, b[0]);
+    if (adj) {
+        k_cdrf_cols_grad<N, CB, 3><<<gc, 256, sm, st>>>(g.ins, n, cb, g.plan, g.tw, b[0], b[1], b[2],
+                                                        mode == NPBS_ADJ_B ? 1 : 0);
+        k_cdrf_rows_flux<N, RB, 3><<<gr, 256, sm, st>>>(g.ins, n, rb, g.plan, g.tw, kappa, vx, vy, sigma, x, fs, b[0],
+                                                        b[1], b[2], b[3], b[4], b[5]);
+    } else {
+        k_cdrf_cols_grad<N, CB, 2><<<gc, 256, sm, st>>>(g.ins, n, cb, g.plan, g.tw, b[0], b[1], b[2], 0);
+        k_cdrf_rows_flux<N, RB, 2><<<gr, 256, sm, st>>>(g.ins, n, rb, g.plan, g.tw, kappa, vx, vy, sigma, x, fs, b[0],
+                                                        b[1], b[2], b[3], b[4], b[5]);
+    }
+    k_cdrf_cols_asm<N, CB><<<gc, 256, sm, st>>>(g.ins, n, cb, g.plan, g.tw, b[3], b[4], b[5], b[0], kind);
+    k_cdrf_rows_out<N, RB><<<gr, 256, sm, st>>>(g.ins, g.ids, n, rb, g.plan, g.tw, b[0], out, norm2);
+}
+
+// The fused float32 apply (RESIDUAL, OP_B, TRUE_RESIDUAL, ADJ_B, -A^*): grid
+// sides 64, 128 and 256 with compile-time geometry, the others at run time.
+npbs_status cdr_run_fused(npbs_ctx* ctx, const CdrPrep& P, int mode, const float* kappa, const float* vx,
+                          const float* vy, const float* sigma, const float2* f, const float2* x, float2* out,
+                          double* norm2, int count, cudaStream_t st) {
+    const long long E = P.extent;
+    float2* b[6];
+    for (int k = 0; k < 6; ++k) b[k] = P.buf + k * E;
+    if (norm2) NPBS_CK(ctx, cudaMemsetAsync(norm2, 0, sizeof(double) * count, st));
+    for (const CdrGroup& g : P.groups) {
+        const int n = g.n;
+        // three fields of rb rows (cb columns) fit one tile buffer
+        const int rb = divisor_at_most(n, std::min(16, kFTile / (3 * n)));
+        const int cb = divisor_at_most(n, std::min(16, kFTile / (3 * n)));
+        if (n == 64 && rb == 16 && cb == 16)
+            fused_launch<64, 16, 16>(g, rb, cb, mode, kappa, vx, vy, sigma, f, x, b, out, norm2, st);
+        else if (n == 128 && rb == 16 && cb == 16)
+            fused_launch<128, 16, 16>(g, rb, cb, mode, kappa, vx, vy, sigma, f, x, b, out, norm2, st);
+        else if (n == 256 && rb == 8 && cb == 8)
+            fused_launch<256, 8, 8>(g, rb, cb, mode, kappa, vx, vy, sigma, f, x, b, out, norm2, st);
+        else
+            fused_launch<0, 0, 0>(g, rb, cb, mode, kappa, vx, vy, sigma, f, x, b, out, norm2, st);
+        NPBS_CK(ctx, cudaGetLastError());
+        ctx->count(st, 5);
+    }
+    return NPBS_OK;
+}
+
 // One CDR apply over a prepared batch (mode: RESIDUAL, OP_B, TRUE_RESIDUAL,
-// ADJ_B or an internal one) in precision R; out is complex64 in both.
+// ADJ_B or an internal one) in precision R; out is complex64 in both.  The
+// float32 operator modes run fused (cdr_run_fused); the float64 residual and
+// the Green operators run the step-by-step kernels.
 template <typename R>
 npbs_status cdr_run(npbs_ctx* ctx, const CdrPrep& P, int mode, const float* kappa, const float* vx, const float* vy,
                     const float* sigma, const float2* f, const cpx<R>* x, float2* out, double* norm2, int count,
                     cudaStream_t st) {
     using C = cpx<R>;
+    if constexpr (std::is_same<R, float>::value) {
+        if (mode != kCdrGreen && mode != kCdrGreenAdj)
+            return cdr_run_fused(ctx, P, mode, kappa, vx, vy, sigma, f, x, out, norm2, count, st);
+    }
     const long long E = P.extent;
     C* const buf = P.fields<R>();
     if (!buf) return set_err(ctx, NPBS_ERR_CUDA, "cdr: float64 buffers not prepared");

@@ -139,6 +139,63 @@ __device__ C* fft_tile(C* a, C* b, const RadixPlan& p, int nbatch, int si, int s
     return a;
 }
 
+// Compile-time variants: the length, the pass stride and the tile geometry are
+// template constants, so the index arithmetic of every pass compiles to
+// shifts and multiplies.  Same radix order as the run-time plans (8s, then
+// 4, 2, 3) and the same length-N twiddle table.
+template <typename C, int RAD, int DIR, bool COLS, int N, int NS, int NB, int SI, int SB>
+__device__ __forceinline__ void stockham_pass_ct(const C* __restrict__ in, C* __restrict__ out,
+                                                 const C* __restrict__ tw, int tid, int nth) {
+    constexpr int nb = N / RAD;
+    constexpr int total = nb * NB;
+    constexpr int twstep = N / (NS * RAD);
+    for (int w = tid; w < total; w += nth) {
+        int b, j;
+        if (COLS) {
+            b = w % NB;
+            j = w / NB;
+        } else {
+            j = w % nb;
+            b = w / nb;
+        }
+        const int k = j % NS;
+        C v[RAD];
+#pragma unroll
+        for (int r = 0; r < RAD; ++r) v[r] = in[(j + r * nb) * SI + b * SB];
+        if (NS > 1) {
+#pragma unroll
+            for (int r = 1; r < RAD; ++r) {
+                C t = tw[r * k * twstep];
+                if (DIR > 0) t.y = -t.y;
+                v[r] = cmul(v[r], t);
+            }
+        }
+        Dft<RAD, DIR, C>::run(v);
+        const int d = (j / NS) * NS * RAD + k;
+#pragma unroll
+        for (int r = 0; r < RAD; ++r) out[(d + r * NS) * SI + b * SB] = v[r];
+    }
+}
+
+template <int M> struct NextRadix {
+    static constexpr int value = M % 8 == 0 ? 8 : M % 4 == 0 ? 4 : M % 2 == 0 ? 2 : 3;
+};
+
+// The transform of a tile with compile-time geometry (NB transforms of length
+// N, element i of transform b at tile[i * SI + b * SB]); returns the buffer
+// holding the result and ends with a __syncthreads().
+template <typename C, int DIR, bool COLS, int N, int NB, int SI, int SB, int NS = 1>
+__device__ __forceinline__ C* fft_tile_ct(C* a, C* b, const C* __restrict__ tw, int tid, int nth) {
+    if constexpr (NS >= N) {
+        return a;
+    } else {
+        constexpr int R = NextRadix<N / NS>::value;
+        stockham_pass_ct<C, R, DIR, COLS, N, NS, NB, SI, SB>(a, b, tw, tid, nth);
+        __syncthreads();
+        return fft_tile_ct<C, DIR, COLS, N, NB, SI, SB, NS * R>(b, a, tw, tid, nth);
+    }
+}
+
 // Signed mode of DFT index i for length N: 0..ceil(N/2)-1, then negative
 // (the Nyquist index of an even N maps to -N/2).
 __device__ __forceinline__ int signed_mode(int i, int N) { return i < (N + 1) / 2 ? i : i - N; }

@@ -9,6 +9,7 @@
 #pragma once
 
 #include <algorithm>
+#include <type_traits>
 
 #include "fft.cuh"
 
@@ -18,28 +19,38 @@ namespace {
 
 constexpr int kTile = 4096;
 
-// rb rows of one field per block, the transform along each row
-template <typename C, int DIR>
-__global__ void __launch_bounds__(256) k_rows(C* data, const long long* off, int n, int rb, RadixPlan plan,
+// A tile transform: compile-time geometry when N > 0, else the run-time plan.
+template <typename C, int N, int NB, int SI, int SB, int DIR, bool COLS>
+__device__ __forceinline__ C* tile(C* a, C* b, const RadixPlan& plan, int nb, int si, int sb, const C* tw) {
+    if constexpr (N > 0) return fft_tile_ct<C, DIR, COLS, N, NB, SI, SB>(a, b, tw, threadIdx.x, blockDim.x);
+    else return fft_tile<C, DIR, COLS>(a, b, plan, nb, si, sb, tw, threadIdx.x, blockDim.x);
+}
+
+// rb rows of one field per block, the transform along each row (N > 0: the
+// side and RB = rb are compile-time constants)
+template <typename C, int DIR, int N = 0, int RB = 0>
+__global__ void __launch_bounds__(256) k_rows(C* data, const long long* off, int n_, int rb_, RadixPlan plan,
                                               const C* tw) {
     extern __shared__ __align__(16) unsigned char smraw[];
     C* sm = reinterpret_cast<C*>(smraw);
+    const int n = N ? N : n_, rb = N ? RB : rb_;
     const int nb = n / rb;
     const long long field = blockIdx.x / nb;
     C* p = data + (off ? off[field] : field * n * n) + (long long)(blockIdx.x % nb) * rb * n;
     const int cnt = rb * n;
     for (int e = threadIdx.x; e < cnt; e += blockDim.x) sm[e] = p[e];
     __syncthreads();
-    C* res = fft_tile<C, DIR, false>(sm, sm + kTile, plan, rb, 1, n, tw, threadIdx.x, blockDim.x);
+    C* res = tile<C, N, RB, 1, N, DIR, false>(sm, sm + kTile, plan, rb, 1, n, tw);
     for (int e = threadIdx.x; e < cnt; e += blockDim.x) p[e] = res[e];
 }
 
 // cb columns of one field per block, the transform along each column
-template <typename C, int DIR>
-__global__ void __launch_bounds__(256) k_cols(C* data, const long long* off, int n, int cb, RadixPlan plan,
+template <typename C, int DIR, int N = 0, int CB = 0>
+__global__ void __launch_bounds__(256) k_cols(C* data, const long long* off, int n_, int cb_, RadixPlan plan,
                                               const C* tw) {
     extern __shared__ __align__(16) unsigned char smraw[];
     C* sm = reinterpret_cast<C*>(smraw);
+    const int n = N ? N : n_, cb = N ? CB : cb_;
     const int nb = n / cb;
     const long long field = blockIdx.x / nb;
     C* p = data + (off ? off[field] : field * n * n) + (long long)(blockIdx.x % nb) * cb;
@@ -49,7 +60,7 @@ __global__ void __launch_bounds__(256) k_cols(C* data, const long long* off, int
         sm[e] = p[(long long)i * n + b];
     }
     __syncthreads();
-    C* res = fft_tile<C, DIR, true>(sm, sm + kTile, plan, cb, cb, 1, tw, threadIdx.x, blockDim.x);
+    C* res = tile<C, N, CB, CB, 1, DIR, true>(sm, sm + kTile, plan, cb, cb, 1, tw);
     for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
         const int i = e / cb, b = e - i * cb;
         p[(long long)i * n + b] = res[e];
@@ -62,29 +73,54 @@ inline int largest_divisor_at_most(int n, int lim) {
     return 1;
 }
 
-template <typename C> inline cudaError_t set_attrs_of() {
+template <typename C, int N, int RB, int CB> inline cudaError_t set_attrs_one() {
     const int sm = (int)(2 * kTile * sizeof(C));
-    cudaError_t e = cudaFuncSetAttribute(k_rows<C, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rows<C, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_cols<C, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_cols<C, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    const cudaFuncAttribute at = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    cudaError_t e = cudaFuncSetAttribute(k_rows<C, -1, N, RB>, at, sm);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rows<C, 1, N, RB>, at, sm);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_cols<C, -1, N, CB>, at, sm);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_cols<C, 1, N, CB>, at, sm);
+    return e;
+}
+
+// compile-time sides (float32 only): 64, 128 and 256 with rb = min(n, kTile / n), cb = 16
+template <typename C> inline cudaError_t set_attrs_of() {
+    cudaError_t e = set_attrs_one<C, 0, 0, 0>();
+    if constexpr (std::is_same<C, float2>::value) {
+        if (e == cudaSuccess) e = set_attrs_one<C, 64, 64, 16>();
+        if (e == cudaSuccess) e = set_attrs_one<C, 128, 32, 16>();
+        if (e == cudaSuccess) e = set_attrs_one<C, 256, 16, 16>();
+    }
     return e;
 }
 
 inline cudaError_t set_attrs() { return set_attrs_of<float2>(); }
+
+template <typename C, int N, int RB, int CB>
+inline void launch(C* data, const long long* off, long long fields, int n, int rb, int cb, int dir,
+                   const RadixPlan& plan, const C* tw, cudaStream_t st) {
+    const size_t sm = 2 * kTile * sizeof(C);
+    if (dir < 0) {
+        k_rows<C, -1, N, RB><<<(unsigned)(fields * (n / rb)), 256, sm, st>>>(data, off, n, rb, plan, tw);
+        k_cols<C, -1, N, CB><<<(unsigned)(fields * (n / cb)), 256, sm, st>>>(data, off, n, cb, plan, tw);
+    } else {
+        k_rows<C, 1, N, RB><<<(unsigned)(fields * (n / rb)), 256, sm, st>>>(data, off, n, rb, plan, tw);
+        k_cols<C, 1, N, CB><<<(unsigned)(fields * (n / cb)), 256, sm, st>>>(data, off, n, cb, plan, tw);
+    }
+}
 
 // 2D transform of `fields` fields in place (dir < 0 forward, > 0 inverse)
 template <typename C>
 inline cudaError_t run(C* data, const long long* off, long long fields, int n, int dir, const RadixPlan& plan,
                        const C* tw, cudaStream_t st) {
     const int rb = largest_divisor_at_most(n, kTile / n), cb = largest_divisor_at_most(n, std::min(16, kTile / n));
-    const size_t sm = 2 * kTile * sizeof(C);
-    if (dir < 0) {
-        k_rows<C, -1><<<(unsigned)(fields * (n / rb)), 256, sm, st>>>(data, off, n, rb, plan, tw);
-        k_cols<C, -1><<<(unsigned)(fields * (n / cb)), 256, sm, st>>>(data, off, n, cb, plan, tw);
+    if constexpr (std::is_same<C, float2>::value) {
+        if (n == 64 && rb == 64 && cb == 16) launch<C, 64, 64, 16>(data, off, fields, n, rb, cb, dir, plan, tw, st);
+        else if (n == 128 && rb == 32 && cb == 16) launch<C, 128, 32, 16>(data, off, fields, n, rb, cb, dir, plan, tw, st);
+        else if (n == 256 && rb == 16 && cb == 16) launch<C, 256, 16, 16>(data, off, fields, n, rb, cb, dir, plan, tw, st);
+        else launch<C, 0, 0, 0>(data, off, fields, n, rb, cb, dir, plan, tw, st);
     } else {
-        k_rows<C, 1><<<(unsigned)(fields * (n / rb)), 256, sm, st>>>(data, off, n, rb, plan, tw);
-        k_cols<C, 1><<<(unsigned)(fields * (n / cb)), 256, sm, st>>>(data, off, n, cb, plan, tw);
+        launch<C, 0, 0, 0>(data, off, fields, n, rb, cb, dir, plan, tw, st);
     }
     return cudaGetLastError();
 }

@@ -133,31 +133,61 @@ __global__ void k_complex_planes(SlotDev sd, const float2* r, float* z) {
 // M(o, i) = w[o * so + i * si] (si = 1, so = Ci for the forward 1x1; swapped
 // strides give the transpose).  Z (nullable): channel o is the real (o even)
 // or imaginary (o odd) part of field o / 2 of [nb][ceil(Co/2)][np].
-__global__ void k_mix_points(int nb, long long np, const float* x, int Ci, const float* w, int so, int si,
-                             const float* bias, const float2* Z, float zscale, int Co, int act, float* pre,
-                             float* out, int add) {
-    const long long tot = (long long)nb * np;
+__global__ void __launch_bounds__(256) k_mix_points(int nb, long long np, const float* x, int Ci, const float* w,
+                                                    int so, int si, const float* bias, const float2* Z, float zscale,
+                                                    int Co, int act, float* pre, float* out, int add) {
+    // the matrix (rows padded to an even length) and the bias in shared
+    // memory; each thread takes two adjacent points (np is even: n is), so one
+    // shared load of two weights feeds four FMAs, and the plane accesses are
+    // float2 (every plane starts 256-byte aligned and np is a multiple of 4)
+    __shared__ __align__(16) float Ms[kMaxC * (kMaxC + 1)];
+    __shared__ float Bs[kMaxC];
+    const int Ci2 = (Ci + 1) & ~1;
+    for (int e = threadIdx.x; e < Co * Ci2; e += blockDim.x) {
+        const int o = e / Ci2, i = e - o * Ci2;
+        Ms[e] = i < Ci ? w[o * so + i * si] : 0.f;
+    }
+    for (int o = threadIdx.x; o < Co; o += blockDim.x) Bs[o] = bias ? bias[o] : 0.f;
+    __syncthreads();
     const int Q = (Co + 1) / 2;
-    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < tot; g += (long long)gridDim.x * blockDim.x) {
+    const long long pairs = (long long)nb * np / 2;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < pairs; q += (long long)gridDim.x * blockDim.x) {
+        const long long g = 2 * q;
         const int b = (int)(g / np);
         const long long p = g - (long long)b * np;
-        float xv[kMaxC];
+        float2 xv[kMaxC];
 #pragma unroll
         for (int i = 0; i < kMaxC; ++i)
-            if (i < Ci) xv[i] = x[((long long)b * Ci + i) * np + p];
+            if (i < Ci2)
+                xv[i] = i < Ci ? *reinterpret_cast<const float2*>(x + ((long long)b * Ci + i) * np + p)
+                               : make_float2(0.f, 0.f);
         for (int o = 0; o < Co; ++o) {
-            float s = bias ? bias[o] : 0.f;
+            float s0 = Bs[o], s1 = Bs[o];
+            const float* mo = Ms + o * Ci2;
 #pragma unroll
-            for (int i = 0; i < kMaxC; ++i)
-                if (i < Ci) s = fmaf(__ldg(w + o * so + i * si), xv[i], s);
+            for (int i = 0; i < kMaxC; i += 2) {
+                if (i < Ci2) {
+                    const float2 m = *reinterpret_cast<const float2*>(mo + i);
+                    s0 = fmaf(m.x, xv[i].x, s0);
+                    s1 = fmaf(m.x, xv[i].y, s1);
+                    s0 = fmaf(m.y, xv[i + 1].x, s0);
+                    s1 = fmaf(m.y, xv[i + 1].y, s1);
+                }
+            }
             if (Z) {
-                const float2 z = Z[((long long)b * Q + o / 2) * np + p];
-                s = fmaf((o & 1) ? z.y : z.x, zscale, s);
+                const float4 z = *reinterpret_cast<const float4*>(Z + ((long long)b * Q + o / 2) * np + p);
+                s0 = fmaf((o & 1) ? z.y : z.x, zscale, s0);
+                s1 = fmaf((o & 1) ? z.w : z.z, zscale, s1);
             }
             const long long oi = ((long long)b * Co + o) * np + p;
-            if (pre) pre[oi] = s;
-            const float v = act ? gelu_f(s) : s;
-            out[oi] = add ? out[oi] + v : v;
+            if (pre) *reinterpret_cast<float2*>(pre + oi) = make_float2(s0, s1);
+            float v0 = act ? gelu_f(s0) : s0, v1 = act ? gelu_f(s1) : s1;
+            if (add) {
+                const float2 old = *reinterpret_cast<const float2*>(out + oi);
+                v0 += old.x;
+                v1 += old.y;
+            }
+            *reinterpret_cast<float2*>(out + oi) = make_float2(v0, v1);
         }
     }
 }
@@ -194,35 +224,42 @@ __global__ void k_extract(int nb, int n, int m, int Kx, int K, const float2* Z, 
     }
 }
 
-// Channel mixing per retained mode: Y[b][o][k] = sum_i W[i][o][k] X[b][i][k]
-// (adj = 0, A = Ci inputs, Co outputs) or Y[b][i][k] = sum_o conj(W[i][o][k]) X[b][o][k]
-// (adj = 1, A = Co inputs, Ci outputs).  W is the canonical [Ci][Co][K] complex
-// block as (re, im) float pairs: its offset in the parameter vector may be odd,
-// so it is read as floats, never as float2.
-__global__ void k_mix_modes(int nb, int K, const float2* X, const float* W, int Ci, int Co, int adj, float2* Y) {
-    const int b = blockIdx.x % nb;
-    const int k = (blockIdx.x / nb) * blockDim.x + threadIdx.x;
-    if (k >= K) return;
+// Channel mixing on the retained modes: Y[b][o][k] = sum_a X[b][a][k] W[a][o][k]
+// (adj: Y[b][a][k] = sum_o conj(W[a][o][k]) X[b][o][k]), W the canonical
+// [Ci][Co][K] complex block as (re, im) float pairs, read as floats (its offset
+// in the parameter vector may be odd).  One thread per (mode k, output channel):
+// its A weights stay in registers while it walks the batch, so every weight is
+// read once per launch whatever the batch size (a warp covers 32 consecutive
+// modes, so the weight and X reads are coalesced).  Grid: (ceil(K/32),
+// ceil(O/8)), 256 threads.
+__global__ void __launch_bounds__(256) k_mix_modes(int nb, int K, const float2* X, const float* W, int Ci, int Co,
+                                                   int adj, float2* Y) {
+    const int k = blockIdx.x * 32 + (threadIdx.x & 31);
+    const int o = blockIdx.y * 8 + (threadIdx.x >> 5);
     const int A = adj ? Co : Ci, O = adj ? Ci : Co;
-    float2 acc[kMaxC];
+    if (k >= K || o >= O) return;
+    float2 w[kMaxC];
 #pragma unroll
-    for (int o = 0; o < kMaxC; ++o) acc[o] = make_float2(0.f, 0.f);
-    for (int a = 0; a < A; ++a) {
-        const float2 x = X[((long long)b * A + a) * K + k];
-#pragma unroll
-        for (int o = 0; o < kMaxC; ++o) {
-            if (o < O) {
-                const long long wi = adj ? ((long long)o * Co + a) * K + k : ((long long)a * Co + o) * K + k;
-                float2 w = make_float2(__ldg(W + 2 * wi), __ldg(W + 2 * wi + 1));
-                if (adj) w.y = -w.y;
-                acc[o].x = fmaf(w.x, x.x, fmaf(-w.y, x.y, acc[o].x));
-                acc[o].y = fmaf(w.x, x.y, fmaf(w.y, x.x, acc[o].y));
-            }
+    for (int a = 0; a < kMaxC; ++a) {
+        if (a < A) {
+            const long long wi = adj ? ((long long)o * Co + a) * K + k : ((long long)a * Co + o) * K + k;
+            const float wr = __ldg(W + 2 * wi), wv = __ldg(W + 2 * wi + 1);
+            w[a] = make_float2(wr, adj ? -wv : wv);
         }
     }
+    for (int b = 0; b < nb; ++b) {
+        const float2* xb = X + (long long)b * A * K + k;
+        float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
-    for (int o = 0; o < kMaxC; ++o)
-        if (o < O) Y[((long long)b * O + o) * K + k] = acc[o];
+        for (int a = 0; a < kMaxC; ++a) {
+            if (a < A) {
+                const float2 x = xb[(long long)a * K];
+                acc.x = fmaf(w[a].x, x.x, fmaf(-w[a].y, x.y, acc.x));
+                acc.y = fmaf(w[a].x, x.y, fmaf(w[a].y, x.x, acc.y));
+            }
+        }
+        Y[((long long)b * O + o) * K + k] = acc;
+    }
 }
 
 // Hermitian completion of the retained half-plane spectra, two channels per
@@ -554,13 +591,13 @@ cudaError_t synthesize(const FnoDef& d, const FnoWS& w, int nb, const float2* Y,
     k_hermite<<<grid_of((long long)nb * Q * np), 256, 0, st>>>(nb, d.n, m, Kx, K, Y, Co, w.Zp);
     cudaError_t e = fft2(d, w.Zp, (long long)nb * Q, 1, st);
     if (e != cudaSuccess) return e;
-    k_mix_points<<<grid_of((long long)nb * np), 256, 0, st>>>(nb, np, x, Ci, wl, so, si, bias, w.Zp,
+    k_mix_points<<<grid_of((long long)nb * np / 2), 256, 0, st>>>(nb, np, x, Ci, wl, so, si, bias, w.Zp,
                                                               1.f / (float)np, Co, act, pre, out, add);
     *kc += 4;
     return cudaGetLastError();
 }
 
-unsigned mix_grid(int nb, int K) { return (unsigned)(nb * ((K + 127) / 128)); }
+dim3 mix_grid(int K, int O) { return dim3((unsigned)((K + 31) / 32), (unsigned)((O + 7) / 8)); }
 
 // One Fourier layer: out = act(irfft2(W * R(rfft2(x))) + W^loc x + b)
 cudaError_t layer_fwd(const FnoDef& d, const FnoWS& w, int nb, const float* x, const float* Wsp, int m,
@@ -570,7 +607,7 @@ cudaError_t layer_fwd(const FnoDef& d, const FnoWS& w, int nb, const float* x, c
     const int K = rows_kept(d.n, m) * std::min(m, d.n / 2 + 1);
     cudaError_t e = spectra(d, w, nb, x, C, m, w.Xc, st, kc);
     if (e != cudaSuccess) return e;
-    k_mix_modes<<<mix_grid(nb, K), 128, 0, st>>>(nb, K, w.Xc, Wsp, C, C, 0, w.Yc);
+    k_mix_modes<<<mix_grid(K, C), 256, 0, st>>>(nb, K, w.Xc, Wsp, C, C, 0, w.Yc);
     *kc += 1;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     return synthesize(d, w, nb, w.Yc, C, m, x, C, wl, C, 1, bias, act, pre, out, 0, st, kc);
@@ -594,7 +631,7 @@ cudaError_t layer_bwd(const FnoDef& d, const FnoWS& w, int nb, const float* x, c
     *kc += 2;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (!dx) return cudaSuccess;
-    k_mix_modes<<<mix_grid(nb, K), 128, 0, st>>>(nb, K, w.Gc, Wsp, C, C, 1, w.Yc);
+    k_mix_modes<<<mix_grid(K, C), 256, 0, st>>>(nb, K, w.Gc, Wsp, C, C, 1, w.Yc);
     *kc += 1;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     return synthesize(d, w, nb, w.Yc, C, m, G, C, wl, 1, C, nullptr, 0, nullptr, dx, 0, st, kc);
@@ -608,7 +645,7 @@ cudaError_t coefficient_branch(const FnoDef& d, const float* P, const FnoWS& w, 
     const long long np = sd.np;
     k_ln_stats<<<nb * d.ca, 256, 0, st>>>(sd, a, d.ca, astride, w.stats);
     k_ln_plane<<<grid_of((long long)nb * d.ca * np), 256, 0, st>>>(sd, a, d.ca, astride, w.stats, w.lnp);
-    k_mix_points<<<grid_of((long long)nb * np), 256, 0, st>>>(nb, np, w.lnp, d.ca, P + d.lift_a_w, d.ca, 1,
+    k_mix_points<<<grid_of((long long)nb * np / 2), 256, 0, st>>>(nb, np, w.lnp, d.ca, P + d.lift_a_w, d.ca, 1,
                                                               P + d.lift_a_b, nullptr, 0.f, C, 0, nullptr,
                                                               coef(w, d, 0, train), 0);
     *kc += 3;
@@ -634,7 +671,7 @@ cudaError_t forward_group(const FnoDef& d, const float* P, const FnoWS& w, const
         cf = coef(w, d, d.L, train);
     }
     k_complex_planes<<<grid_of((long long)nb * np), 256, 0, st>>>(sd, r, w.rp);
-    k_mix_points<<<grid_of((long long)nb * np), 256, 0, st>>>(nb, np, w.rp, 2, P + d.lift_r, 2, 1, nullptr, nullptr,
+    k_mix_points<<<grid_of((long long)nb * np / 2), 256, 0, st>>>(nb, np, w.rp, 2, P + d.lift_r, 2, 1, nullptr, nullptr,
                                                               0.f, C, 0, nullptr, w.x0, 0);
     *kc += 2;
     e = layer_fwd(d, w, nb, w.x0, P + d.spec_r, d.fx, P + d.loc_r, nullptr, 0, nullptr, w.x1, st, kc);
