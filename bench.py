@@ -276,6 +276,38 @@ def bench_extensions(capi, ctx, args, stream):
     out["cdr_npbs_iteration_ms_128"] = {"batch": 32, "ms": (time.perf_counter() - t0) * 1e3 / K,
                                         "note": "one NPBS iteration of the batch (apply + FNO forward), float64 "
                                                 "check every 4"}
+    # Newton-Born at the paper's grid (N = 64 interior, s = 1600), 1000 states: the fused apply is bound by
+    # the FP32 pipe (four N^3 complex-by-real sine products: 16 N^3 FLOP per instance)
+    ninst = [synth.newton_instance(64, 70000 + j) for j in range(1000)]
+    nb = capi.Batch([(64, 64)] * len(ninst), h=[1.0 / 65] * len(ninst))
+    nf = nb.pack([i.f for i in ninst], dtype=torch.float64)
+    nu = nb.pack([i.u0 for i in ninst], dtype=torch.float64)
+    sh, u32, r = capi.newton_linearise(ctx, nb, nu, nf)
+    x = torch.randn(nb.extent, dtype=torch.complex64, device="cuda")
+    y = torch.zeros_like(x)
+    na = lambda: capi.newton_apply(ctx, nb, sh, u32, r, x, y, capi.RESIDUAL)
+    na()
+    ms = timed(stream, na, 20)
+    fl = 16.0 * 64 ** 3 * len(ninst)
+    fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12  # SMs x FP32 lanes x FMA x maximum SM clock (TFLOP/s)
+    out["newton_apply_64"] = {"instances": len(ninst), "mode": "RESIDUAL", "ms": ms,
+                              "tflops": fl / (ms * 1e-3) / 1e12, "fp32_peak_tflops": fp32_peak,
+                              "frac_of_fp32_peak": fl / (ms * 1e-3) / 1e12 / fp32_peak,
+                              "flop_per_instance": 16 * 64 ** 3}
+    test = ninst[:100]
+    tb = capi.Batch([(64, 64)] * len(test), h=[1.0 / 65] * len(test))
+    tf = tb.pack([i.f for i in test], dtype=torch.float64)
+    tu = tb.pack([i.u0 for i in test], dtype=torch.float64)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st_, rep = capi.newton_solve(ctx, None, tb, tf, tu, tol=1e-10, max_steps=12, inner_rtol=1e-4, check_every=1)
+    ms_s = (time.perf_counter() - t0) * 1e3
+    ok = [j for j, v in enumerate(rep["status"]) if v == capi.OK]
+    out["newton_born_solve_64"] = {"instances": len(test), "ms": ms_s, "converged": len(ok),
+                                   "newton_steps_mean": float(np.mean(rep["steps"])),
+                                   "inner_iters_per_step": float(np.mean([rep["inner_iters"][j] / max(1, rep["steps"][j])
+                                                                          for j in range(len(test))])),
+                                   "tol": 1e-10, "inner_rtol": 1e-4}
     return out
 
 

@@ -480,6 +480,81 @@ npbs_status cdr_solve_direct(npbs_ctx* ctx, const npbs_net* net, const npbs_batc
                              const float* sigma, const void* f, const float* a, void* u, const npbs_solve_opts* opts,
                              npbs_report* report, npbs_stream stream);
 
+
+/* ---- Newton-Born linearisation with a DST-I Green operator ------------------
+ * (App. Full Derivations, Nonlinear PDE via Newton-Born Linearization; Eqs.
+ * nonlinear_residual, newton_linear_system, newton_ref, newton_vm,
+ * newton_born_identity, newton_inner_iter; App. Verification, Newton linear
+ * systems; Sec. 5.2):
+ *   F(u) = L_D u - u^2 - f on the N x N interior unknowns of [0, 1]^2,
+ *          homogeneous Dirichlet, L_D the five-point negative Laplacian / h^2,
+ *          h = 1/(N + 1)  (the batch's h is ignored)
+ *   J = L_D - 2 diag(u_m), J0 = L_D + c I (c = alpha - 2 mean(u_m)),
+ *   V = J0 - J = c + 2 u_m, G = J0^{-1} by the 2D DST-I, I - G V = G J.
+ * Instances: square, N a multiple of 4 in 8..96 (else UNSUPPORTED_SIZE);
+ * offsets multiples of 32.  Fields use the batch layout. */
+
+/* One apply at linearisation points u (DEVICE float32) with shifts c (HOST
+ * double [count]): RESIDUAL out = G(r - J x); OP_B out = G J x = (I - G V) x;
+ * TRUE_RESIDUAL out = r - J x (r nullable: -J x); ADJ_B out = (G J)^* x =
+ * J G x (J and G are real symmetric).  r, x, out: DEVICE complex64 (out may
+ * alias x); norm2 (nullable, DEVICE double [count]) receives ||out||^2.
+ * Asynchronous. */
+npbs_status newton_apply(npbs_ctx* ctx, const npbs_batch* batch, const double* shift, const float* u,
+                         const void* r, const void* x, void* out, npbs_mode mode, double* norm2,
+                         npbs_stream stream);
+
+typedef struct {
+    double tol;             /* outer: ||F(u)|| / ||f|| <= tol */
+    int32_t max_steps;      /* Newton steps */
+    double inner_rtol;      /* inner: ||r - J delta|| / ||r|| <= inner_rtol (1e-4 in the paper) */
+    int32_t inner_max_iter; /* inner iterations per Newton step */
+    int32_t check_every;    /* inner iterations between float64 checks */
+    int32_t direct_format;  /* 0: NPBS (network input G(r - J delta)); 1: the Direct format (input
+                               r - J delta, Eq. direct_iter's template; net required) */
+} npbs_newton_opts;
+
+typedef struct {            /* HOST arrays [count], each nullable */
+    int32_t* steps;         /* Newton steps taken */
+    int32_t* inner_iters;   /* inner iterations summed over the steps */
+    double* residual;       /* final ||F(u)|| / ||f|| (float64) */
+    npbs_status* status;    /* OK, NOT_CONVERGED or ERR_NONFINITE */
+} npbs_newton_report;
+
+/* Newton's method with inner Born (net NULL) or NPBS solves (Eq.
+ * newton_inner_iter: delta <- delta + M(G(r - J delta)), M the network fed the
+ * linearisation point u_m as its coefficient channel).  f, u: DEVICE float64
+ * (u: initial guess in, solution out).  Each Newton step linearises at u in
+ * float64 (r = -F(u), c = alpha - 2 mean(u)); the inner iteration runs in
+ * complex64 on the correction of delta, which is folded into a complex128
+ * delta at every check where r - J delta is evaluated in float64; an instance
+ * leaves the inner loop at its first passing check (or inner_max_iter) and u
+ * += Re delta.  Instances stop at ||F(u)|| / ||f|| <= tol (u is left at that
+ * iterate) or after max_steps.  Synchronises. */
+npbs_status newton_solve(npbs_ctx* ctx, const npbs_net* net, const npbs_batch* batch, const double* f, double* u,
+                         double alpha, const npbs_newton_opts* opts, npbs_newton_report* report,
+                         npbs_stream stream);
+
+/* One linearisation per instance at u (DEVICE float64): shift_out (HOST double
+ * [count]) = alpha - 2 mean(u), u32_out (DEVICE float32) = u rounded, r_out
+ * (DEVICE complex64) = -F(u) = f - L_D u + u^2 evaluated in float64 and
+ * rounded: the state (u_m, c_m, r_m) of a Newton trajectory for
+ * newton_apply and newton_train_step_loss.  Synchronises. */
+npbs_status newton_linearise(npbs_ctx* ctx, const npbs_batch* batch, const double* u, const double* f, double alpha,
+                             double* shift_out, float* u32_out, void* r_out, npbs_stream stream);
+
+/* The training step for the Newton inner systems (Eq. nl_bs_loss for BS_RETA,
+ * the template of npbs_train_step_loss with (G, J, V) of each state): u
+ * (DEVICE float32) the linearisation points and network coefficient channel,
+ * shift (HOST double [count]) their c, r (DEVICE complex64) the right-hand
+ * sides -F(u_m), d_snap (DEVICE complex64) the inner iterates the unrolled
+ * loss starts from (r_0 = G(r - J d)).  BS_L2 and DIR use J^* = J, G^* = G.
+ * Synchronises once (to read the loss). */
+npbs_status newton_train_step_loss(npbs_ctx* ctx, npbs_net* net, const npbs_batch* batch, const double* shift,
+                                   const float* u, const void* r, const void* d_snap, int32_t unroll,
+                                   npbs_loss kind, float lr, float weight_decay, float* loss_host,
+                                   npbs_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -48,6 +48,16 @@ class npbs_cdr_consts(C.Structure):
     _fields_ = [("kappa0", C.c_double), ("v0x", C.c_double), ("v0y", C.c_double), ("sigma0", C.c_double)]
 
 
+class npbs_newton_opts(C.Structure):
+    _fields_ = [("tol", C.c_double), ("max_steps", C.c_int32), ("inner_rtol", C.c_double),
+                ("inner_max_iter", C.c_int32), ("check_every", C.c_int32), ("direct_format", C.c_int32)]
+
+
+class npbs_newton_report(C.Structure):
+    _fields_ = [("steps", C.POINTER(C.c_int32)), ("inner_iters", C.POINTER(C.c_int32)),
+                ("residual", C.POINTER(C.c_double)), ("status", C.POINTER(C.c_int32))]
+
+
 class NpbsError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"{STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else status}: {msg}")
@@ -107,6 +117,15 @@ _SIGS = {
                                       C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                       C.c_void_p, C.c_int32, C.c_int, C.c_float, C.c_float, C.POINTER(C.c_float),
                                       C.c_void_p]),
+    "newton_apply": (C.c_int, [C.c_void_p, C.POINTER(npbs_batch), C.POINTER(C.c_double), C.c_void_p, C.c_void_p,
+                               C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
+    "newton_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(npbs_batch), C.c_void_p, C.c_void_p, C.c_double,
+                               C.POINTER(npbs_newton_opts), C.POINTER(npbs_newton_report), C.c_void_p]),
+    "newton_linearise": (C.c_int, [C.c_void_p, C.POINTER(npbs_batch), C.c_void_p, C.c_void_p, C.c_double,
+                                   C.POINTER(C.c_double), C.c_void_p, C.c_void_p, C.c_void_p]),
+    "newton_train_step_loss": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(npbs_batch), C.POINTER(C.c_double),
+                                         C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_int, C.c_float,
+                                         C.c_float, C.POINTER(C.c_float), C.c_void_p]),
     "npbs_net_num_params": (C.c_int64, []),
     "npbs_net_param_count": (C.c_int64, [C.c_void_p]),
     "npbs_net_create_fno": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
@@ -616,4 +635,64 @@ def cdr_train_step(ctx: Context, net, batch: "Batch", consts, fields: CdrFields,
                                         *fields.ptrs(), _ptr(f), _ptr(a), _ptr(u_snap), int(unroll),
                                         LOSS_KINDS[loss], float(lr), float(weight_decay), C.byref(out),
                                         _stream(stream)))
+    return float(out.value)
+
+
+# ---- Newton-Born linearisation (Dirichlet, DST-I Green operator) --------------
+
+def _shifts(shift):
+    arr = (C.c_double * max(1, len(shift)))()
+    for j, c in enumerate(shift):
+        arr[j] = float(c)
+    return arr
+
+
+def newton_apply(ctx: Context, batch: "Batch", shift, u, r, x, out, mode, norm2=None, stream=None):
+    """One Newton-Born apply at linearisation points u (float32) with host shifts c."""
+    if u.dtype != torch.float32:
+        raise TypeError("newton_apply: u must be float32")
+    ctx.check(lib().newton_apply(ctx.handle, C.byref(batch.c_batch()), _shifts(shift), _ptr(u), _ptr(r), _ptr(x),
+                                 _ptr(out), int(mode), _ptr(norm2), _stream(stream)))
+
+
+def newton_linearise(ctx: Context, batch: "Batch", u, f, alpha=0.0, stream=None):
+    """The Newton state at u (float64): (shifts list, u32 float32, r complex64)."""
+    if f.dtype != torch.float64 or u.dtype != torch.float64:
+        raise TypeError("newton_linearise: f and u must be float64")
+    n = batch.count
+    sh = (C.c_double * max(1, n))()
+    u32 = torch.zeros(batch.extent, dtype=torch.float32, device=u.device)
+    r = torch.zeros(batch.extent, dtype=torch.complex64, device=u.device)
+    ctx.check(lib().newton_linearise(ctx.handle, C.byref(batch.c_batch()), _ptr(u), _ptr(f), float(alpha), sh,
+                                     _ptr(u32), _ptr(r), _stream(stream)))
+    return [sh[i] for i in range(n)], u32, r
+
+
+def newton_solve(ctx: Context, net, batch: "Batch", f, u, alpha=0.0, tol=1e-8, max_steps=20, inner_rtol=1e-4,
+                 inner_max_iter=1000, check_every=2, direct=False, stream=None):
+    """Newton with inner Born (net None) or NPBS solves (or the Direct format,
+    direct=True); f, u float64 (u in place).  Returns (status, report dict)."""
+    if f.dtype != torch.float64 or u.dtype != torch.float64:
+        raise TypeError("newton_solve: f and u must be float64")
+    n = batch.count
+    steps, inner = (C.c_int32 * max(1, n))(), (C.c_int32 * max(1, n))()
+    res, stat = (C.c_double * max(1, n))(), (C.c_int32 * max(1, n))()
+    rep = npbs_newton_report(steps, inner, res, stat)
+    o = npbs_newton_opts(float(tol), int(max_steps), float(inner_rtol), int(inner_max_iter), int(check_every),
+                         1 if direct else 0)
+    st = lib().newton_solve(ctx.handle, net.handle if net is not None else None, C.byref(batch.c_batch()), _ptr(f),
+                            _ptr(u), float(alpha), C.byref(o), C.byref(rep), _stream(stream))
+    if st not in (OK, NOT_CONVERGED, ERR_NONFINITE):
+        ctx.check(st)
+    return st, {"steps": [steps[i] for i in range(n)], "inner_iters": [inner[i] for i in range(n)],
+                "residual": [res[i] for i in range(n)], "status": [stat[i] for i in range(n)]}
+
+
+def newton_train_step(ctx: Context, net, batch: "Batch", shift, u, r, d_snap, unroll=4, lr=1e-3,
+                      weight_decay=1e-6, loss: str = "bs_reta", stream=None) -> float:
+    """One training step on Newton inner systems; returns the loss before the update."""
+    out = C.c_float(0.0)
+    ctx.check(lib().newton_train_step_loss(ctx.handle, net.handle, C.byref(batch.c_batch()), _shifts(shift), _ptr(u),
+                                           _ptr(r), _ptr(d_snap), int(unroll), LOSS_KINDS[loss], float(lr),
+                                           float(weight_decay), C.byref(out), _stream(stream)))
     return float(out.value)

@@ -79,7 +79,7 @@ struct npbs_ctx {
     std::map<std::string, std::unique_ptr<npbs::Plan>> plans;
     long long plan_clock = 0;
     npbs::DevBuf scratch;   // spectrum between apply passes
-    npbs::DevBuf work[18];  // solver workspaces (12-17: the CDR operators)
+    npbs::DevBuf work[21];  // solver workspaces (12-17: the CDR operators, 18-20: Newton)
     npbs::DevBuf net_ws;    // network activations
     bool use_fast = true;  // cluster apply for square 128..512 grids, band kernels for 1024
                            // (NPBS_APPLY_PATH=three_pass disables both)

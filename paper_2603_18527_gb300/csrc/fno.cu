@@ -306,7 +306,8 @@ __global__ void k_hermite(int nb, int n, int m, int Kx, int K, const float2* Y, 
 // modes per block, one thread per channel pair.
 __global__ void k_wgrad_modes(int nb, int n, int Kx, int K, const float2* G, const float2* X, int Ci, int Co,
                               float* dW) {
-    __shared__ float2 xs[kMaxC][kModesPerBlock], gs[kMaxC][kModesPerBlock];
+    // rows padded by one element: a warp reads gs[o][q] for up to kMaxC channels o at one q
+    __shared__ float2 xs[kMaxC][kModesPerBlock + 1], gs[kMaxC][kModesPerBlock + 1];
     const int k0 = blockIdx.x * kModesPerBlock;
     const int t = threadIdx.x;
     const int i = t / Co, o = t - (t / Co) * Co;
@@ -351,7 +352,10 @@ __global__ void k_wgrad_modes(int nb, int n, int Kx, int K, const float2* G, con
 constexpr int kPairsPerThread = 5;
 __global__ void __launch_bounds__(256) k_wgrad_points(int nb, long long np, const float* G, int Co, const float* X,
                                                       int Ci, float* dW, float* db) {
-    __shared__ float gs[kMaxC][32], xs[kMaxC][32];
+    // rows padded to 33 floats: the pair (o, i) loop reads xs[i][j] for up to
+    // kMaxC channels i at one j within a warp, which a 32-float stride would
+    // put in one bank
+    __shared__ float gs[kMaxC][33], xs[kMaxC][33];
     const int npair = Co * Ci + (db ? Co : 0);
     float acc[kPairsPerThread];
 #pragma unroll
