@@ -34,7 +34,12 @@ the full bandwidth (N/2 + 1).  Readings where the paper is silent:
   carries the absorbing layer; the CDR problems feed several coefficient
   channels (kappa, v, sigma), Helmholtz one;
 * the coefficient channel a is the one the U-Net reads (the local wavenumber
-  omega n(x)); GELU is the erf form.
+  omega n(x)); GELU is the erf form;
+* optionally (cfg.skip) M = I + N with N the network above and its
+  projection initialised to zero, so that M starts as the Born series: the
+  metric-matched loss weights a residual mode by 1/|lambda|^2 of the Green
+  symbol, so the high modes of N receive almost no gradient, and without the
+  identity their untrained response can make the iteration diverge there.
 
 The canonical flat parameter order (the exchange format with the CUDA
 library) is ``param_spec(cfg)``: real arrays, complex spectral weights stored
@@ -57,6 +62,7 @@ class FnoConfig:
     modes: int = 45   # retained modes of the NLFL and fusion layers
     layers: int = 3   # NLFL layers on the coefficient branch
     coef: int = 1     # coefficient channels of a
+    skip: bool = False  # M = I + N: the network's output plus its input (Born series at N = 0)
 
     @property
     def full(self) -> int:
@@ -147,13 +153,15 @@ def coefficient_features(a: torch.Tensor, P: Dict[str, torch.Tensor], cfg: FnoCo
 
 def correction_from_features(r: torch.Tensor, c: torch.Tensor, P: Dict[str, torch.Tensor],
                              cfg: FnoConfig) -> torch.Tensor:
-    """P(LFL_f[c * LFL_r(Psi(r))]): r [B, N, N] complex, c [B, C, N, N] -> [B, N, N] complex."""
+    """P(LFL_f[c * LFL_r(Psi(r))]) (plus r with cfg.skip): r [B, N, N] complex,
+    c [B, C, N, N] -> [B, N, N] complex."""
     x = conv1x1(torch.stack([r.real, r.imag], dim=1), P["lift_r.w"])
     x = spectral(x, P["spec_r.w"], cfg.full) + conv1x1(x, P["loc_r.w"])
     z = c * x
     z = spectral(z, P["spec_f.w"], cfg.modes) + conv1x1(z, P["loc_f.w"])
     y = conv1x1(z, P["proj.w"])
-    return torch.complex(y[:, 0], y[:, 1])
+    out = torch.complex(y[:, 0], y[:, 1])
+    return out + r if cfg.skip else out
 
 
 def correction(r: torch.Tensor, a: torch.Tensor, P: Dict[str, torch.Tensor], cfg: FnoConfig) -> torch.Tensor:
@@ -179,11 +187,12 @@ def unrolled_loss(P: Dict[str, torch.Tensor], cfg: FnoConfig, V, lam, f, a, u0, 
 def init_params(cfg: FnoConfig, seed: int) -> torch.Tensor:
     """Seeded initial parameters in the canonical order (float64): 1x1 weights
     uniform in +-1/sqrt(fan_in), spectral weights uniform in [0, 1/(C*C)) for
-    both parts, biases zero."""
+    both parts, biases zero; with cfg.skip the projection starts at zero, so
+    the initial M is the identity (the Born series)."""
     g = torch.Generator().manual_seed(seed)
     parts = []
     for name, shape in param_spec(cfg):
-        if name.endswith(".b"):
+        if name.endswith(".b") or (cfg.skip and name == "proj.w"):
             parts.append(torch.zeros(math.prod(shape), dtype=torch.float64))
         elif name.startswith("spec"):
             parts.append(torch.rand(math.prod(shape), generator=g, dtype=torch.float64) / (cfg.width ** 2))

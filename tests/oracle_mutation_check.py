@@ -69,6 +69,7 @@ M = [
  ("fno.py", "spectral weights conj", 'Yr = torch.einsum("bikl,iokl->bokl", Xr, W)', 'Yr = torch.einsum("bikl,iokl->bokl", Xr, W.conj())'),
  ("fno.py", "residual branch re/im swapped", "x = conv1x1(torch.stack([r.real, r.imag], dim=1), P[\"lift_r.w\"])", "x = conv1x1(torch.stack([r.imag, r.real], dim=1), P[\"lift_r.w\"])"),
  ("fno.py", "layer norm over channels too", "mu = a.mean(dim=(-2, -1), keepdim=True)", "mu = a.mean(dim=(-3, -2, -1), keepdim=True)"),
+ ("fno.py", "skip subtracts the input", "return out + r if cfg.skip else out", "return out - r if cfg.skip else out"),
  ("cdr.py", "A convection sign", "+ p.vx * ux + p.vy * uy + p.sigma * u", "- p.vx * ux - p.vy * uy + p.sigma * u"),
  ("cdr.py", "L0 symbol convection sign", "lam = (k0 * (kx ** 2 + ky ** 2)).to(C128) + 1j * (v0x * kx + v0y * ky) + s0", "lam = (k0 * (kx ** 2 + ky ** 2)).to(C128) - 1j * (v0x * kx + v0y * ky) + s0"),
  ("cdr.py", "A* without the v g flux", "return -(ddx(p, p.kappa * gx + p.vx * g) + ddy(p, p.kappa * gy + p.vy * g)) + p.sigma * g", "return -(ddx(p, p.kappa * gx) + ddy(p, p.kappa * gy)) + p.sigma * g"),

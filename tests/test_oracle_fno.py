@@ -207,3 +207,23 @@ def test_residual_branch_reads_re_then_im_and_projects_to_re_then_im():
     P["proj.w"][1] = 0.0
     y = FN.correction(s, a, P, cfg)
     assert y.imag.abs().max() == 0.0 and y.real.abs().max() > 1e-6
+
+
+def test_identity_skip_adds_the_input_and_starts_as_the_born_series():
+    """With cfg.skip, M(r) = r + N(r): the difference to the same parameters
+    without the skip is r itself, M stays real-linear in r, and the initial
+    parameters (zero projection) give M = I exactly."""
+    rng = np.random.default_rng(11)
+    c0 = FN.FnoConfig(n=16, width=4, modes=3, layers=1)
+    c1 = FN.FnoConfig(n=16, width=4, modes=3, layers=1, skip=True)
+    P = FN.unflatten(c0, FN.init_params(c0, 5) + 0.05)
+    a = torch.from_numpy(rng.standard_normal((2, 16, 16)))
+    r1 = torch.from_numpy(rng.standard_normal((2, 16, 16)) + 1j * rng.standard_normal((2, 16, 16)))
+    r2 = torch.from_numpy(rng.standard_normal((2, 16, 16)) + 1j * rng.standard_normal((2, 16, 16)))
+    assert torch.allclose(FN.correction(r1, a, P, c1) - FN.correction(r1, a, P, c0), r1, atol=1e-12)
+    lhs = FN.correction(2.0 * r1 - 3.0 * r2, a, P, c1)
+    rhs = 2.0 * FN.correction(r1, a, P, c1) - 3.0 * FN.correction(r2, a, P, c1)
+    assert torch.allclose(lhs, rhs, atol=1e-10)
+    P0 = FN.unflatten(c1, FN.init_params(c1, 6))
+    assert float(P0["proj.w"].abs().max()) == 0.0
+    assert torch.allclose(FN.correction(r1, a, P0, c1), r1, atol=0)
