@@ -407,6 +407,14 @@ int64_t npbs_net_param_count(const npbs_net* net);
  * weights. */
 npbs_status npbs_net_create_fno(npbs_net** out, int device, int n, int width, int modes, int layers,
                                 int coef_channels, uint64_t seed);
+
+/* Switches the FNO's identity skip: on, M(r) = r + N(r) with N the network
+ * above, so that zero weights give the Born series (NPBS leaves the form of
+ * M open, Eq. npbs_integral); turning it on zeroes the projection weights,
+ * so the network starts as the identity (call it before training or loading
+ * parameters).  Saved with the network.  NPBS_ERR_UNSUPPORTED_SIZE for a
+ * U-Net. */
+npbs_status npbs_net_fno_set_skip(npbs_net* net, int32_t on);
 /* Create a network on `device` with seeded He-normal weights. */
 npbs_status npbs_net_create(npbs_net** out, int device, uint64_t seed);
 npbs_status npbs_net_destroy(npbs_net* net);

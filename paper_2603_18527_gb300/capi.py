@@ -126,6 +126,7 @@ _SIGS = {
     "newton_train_step_loss": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(npbs_batch), C.POINTER(C.c_double),
                                          C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_int, C.c_float,
                                          C.c_float, C.POINTER(C.c_float), C.c_void_p]),
+    "npbs_net_fno_set_skip": (C.c_int, [C.c_void_p, C.c_int32]),
     "npbs_net_num_params": (C.c_int64, []),
     "npbs_net_param_count": (C.c_int64, [C.c_void_p]),
     "npbs_net_create_fno": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
@@ -202,20 +203,6 @@ class Context:
     @property
     def handle(self):
         return self._h
-
-    @classmethod
-    def fno(cls, n: int, width: int = 25, modes: int = 45, layers: int = 3, device: int = 0,
-            seed: int = 0, coef_channels: int = 1) -> "Net":
-        """An FNO network (App. Architectural Instantiations) for n x n grids."""
-        h = C.c_void_p()
-        st = lib().npbs_net_create_fno(C.byref(h), int(device), int(n), int(width), int(modes), int(layers),
-                                       int(coef_channels), C.c_uint64(seed))
-        if st != OK:
-            raise NpbsError(st, "npbs_net_create_fno failed")
-        return cls(device, handle=h)
-
-    def num_params(self) -> int:
-        return int(lib().npbs_net_param_count(self._h))
 
     def last_error(self) -> str:
         return lib().npbs_last_error(self._h).decode()
@@ -480,14 +467,20 @@ class Net:
 
     @classmethod
     def fno(cls, n: int, width: int = 25, modes: int = 45, layers: int = 3, device: int = 0,
-            seed: int = 0, coef_channels: int = 1) -> "Net":
-        """An FNO network (App. Architectural Instantiations) for n x n grids."""
+            seed: int = 0, coef_channels: int = 1, skip: bool = False) -> "Net":
+        """An FNO network (App. Architectural Instantiations) for n x n grids;
+        skip=True makes M = I + N (a zero projection: the Born series at start)."""
         h = C.c_void_p()
         st = lib().npbs_net_create_fno(C.byref(h), int(device), int(n), int(width), int(modes), int(layers),
                                        int(coef_channels), C.c_uint64(seed))
         if st != OK:
             raise NpbsError(st, "npbs_net_create_fno failed")
-        return cls(device, handle=h)
+        net = cls(device, handle=h)
+        if skip:
+            st = lib().npbs_net_fno_set_skip(h, 1)
+            if st != OK:
+                raise NpbsError(st, "npbs_net_fno_set_skip failed")
+        return net
 
     def num_params(self) -> int:
         return int(lib().npbs_net_param_count(self._h))

@@ -420,7 +420,8 @@ __global__ void k_mul_back(long long cnt, const float* dz, const float* c, const
 }
 
 // out (complex, batch offsets) (+)= (sum_c w[0][c] z[c], sum_c w[1][c] z[c])
-__global__ void k_proj(SlotDev sd, const float* z, int C, const float* w, float2* out, int add) {
+// out (+)= P z (+ r when r is non-null: the identity skip)
+__global__ void k_proj(SlotDev sd, const float* z, int C, const float* w, float2* out, int add, const float2* r) {
     const long long tot = (long long)sd.nb * sd.np;
     for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < tot; g += (long long)gridDim.x * blockDim.x) {
         const int b = (int)(g / sd.np);
@@ -430,6 +431,11 @@ __global__ void k_proj(SlotDev sd, const float* z, int C, const float* w, float2
             const float v = z[((long long)b * C + c) * sd.np + p];
             re = fmaf(__ldg(w + c), v, re);
             im = fmaf(__ldg(w + C + c), v, im);
+        }
+        if (r) {
+            const float2 rv = r[sd.off[b] + p];
+            re += rv.x;
+            im += rv.y;
         }
         float2* o = out + sd.off[b] + p;
         *o = add ? make_float2(o->x + re, o->y + im) : make_float2(re, im);
@@ -448,7 +454,9 @@ __global__ void k_proj_back(SlotDev sd, const float2* gc, int C, const float* w,
 }
 
 // gr (complex, batch offsets) (+)= (sum_c w[c][0] dx[c], sum_c w[c][1] dx[c])
-__global__ void k_lift_r_back(SlotDev sd, const float* dx, int C, const float* w, float2* gr, int add) {
+// gr (+)= Psi^T dx (+ gc when gc is non-null: the identity skip's gradient)
+__global__ void k_lift_r_back(SlotDev sd, const float* dx, int C, const float* w, float2* gr, int add,
+                              const float2* gc) {
     const long long tot = (long long)sd.nb * sd.np;
     for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < tot; g += (long long)gridDim.x * blockDim.x) {
         const int b = (int)(g / sd.np);
@@ -458,6 +466,11 @@ __global__ void k_lift_r_back(SlotDev sd, const float* dx, int C, const float* w
             const float v = dx[((long long)b * C + c) * sd.np + p];
             re = fmaf(__ldg(w + 2 * c), v, re);
             im = fmaf(__ldg(w + 2 * c + 1), v, im);
+        }
+        if (gc) {
+            const float2 gv = gc[sd.off[b] + p];
+            re += gv.x;
+            im += gv.y;
         }
         float2* o = gr + sd.off[b] + p;
         *o = add ? make_float2(o->x + re, o->y + im) : make_float2(re, im);
@@ -685,7 +698,7 @@ cudaError_t forward_group(const FnoDef& d, const float* P, const FnoWS& w, const
     e = layer_fwd(d, w, nb, w.z, P + d.spec_f, d.m, P + d.loc_f, nullptr, 0, nullptr, w.z1, st, kc);
     if (e != cudaSuccess) return e;
     if (!out) return cudaSuccess;  // a recomputation for the backward needs the activations only
-    k_proj<<<grid_of((long long)nb * np), 256, 0, st>>>(sd, w.z1, C, P + d.proj, out, add);
+    k_proj<<<grid_of((long long)nb * np), 256, 0, st>>>(sd, w.z1, C, P + d.proj, out, add, d.skip ? r : nullptr);
     *kc += 1;
     return cudaGetLastError();
 }
@@ -804,7 +817,8 @@ npbs_status fno_run_backward(npbs_ctx* ctx, Net& net, const NetRun& run, const f
         NPBS_CK(ctx, layer_bwd(d, w, nb, w.x0, P + d.spec_r, dP + d.spec_r, d.fx, P + d.loc_r, dP + d.loc_r,
                                nullptr, w.g1, w.g3, st, &kc));
         k_wgrad_points<<<304, 256, 0, st>>>(nb, np, w.g3, C, w.rp, 2, dP + d.lift_r, nullptr);
-        k_lift_r_back<<<grid_of((long long)nb * np), 256, 0, st>>>(sd, w.g3, C, P + d.lift_r, gr, add);
+        k_lift_r_back<<<grid_of((long long)nb * np), 256, 0, st>>>(sd, w.g3, C, P + d.lift_r, gr, add,
+                                                                   d.skip ? gc : nullptr);
         kc += 2;
         NPBS_CK(ctx, cudaGetLastError());
         // coefficient branch, last NLFL first
@@ -908,6 +922,23 @@ int64_t npbs_net_param_count(const npbs_net* net) {
     if (!net) return -1;
     const Net* N = reinterpret_cast<const Net*>(net);
     return N->fno ? (int64_t)N->fno->count : (int64_t)canon_param_count();
+}
+
+npbs_status npbs_net_fno_set_skip(npbs_net* net, int32_t on) {
+    if (!net) return NPBS_ERR_INVALID_ARG;
+    Net* N = reinterpret_cast<Net*>(net);
+    if (!N->fno) return NPBS_ERR_UNSUPPORTED_SIZE;
+    if (cudaSetDevice(N->device) != cudaSuccess) return NPBS_ERR_CUDA;
+    FnoDef& d = *N->fno;
+    if (on && !d.skip) {
+        // the network starts as the identity: zero projection (2 x C weights)
+        if (cudaMemset(N->params + d.proj, 0, sizeof(float) * 2 * d.C) != cudaSuccess ||
+            cudaDeviceSynchronize() != cudaSuccess)
+            return NPBS_ERR_CUDA;
+    }
+    d.skip = on ? 1 : 0;
+    N->version += 1;
+    return NPBS_OK;
 }
 
 }  // extern "C"

@@ -27,6 +27,7 @@ long long canon_param_count();
 struct FnoDef {
     int n = 0, C = 0, m = 0, L = 0;
     int ca = 1;  // coefficient channels (planes of the batch extent, one after another)
+    int skip = 0;  // 1: M = I + N (the output adds the residual input)
     int ky = 0, kx = 0, fy = 0, fx = 0;
     long long lift_a_w = 0, lift_a_b = 0;
     long long spec[8] = {}, loc_w[8] = {}, loc_b[8] = {};

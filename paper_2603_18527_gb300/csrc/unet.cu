@@ -1101,12 +1101,14 @@ npbs_status npbs_net_save(const npbs_net* net, const char* path) {
         return NPBS_ERR_CUDA;
     FILE* f = fopen(path, "wb");
     if (!f) return NPBS_ERR_INVALID_ARG;
-    // an FNO file carries its shape (n, width, modes, layers, coefficient channels) after the magic
-    const char magic[8] = {'N', 'P', 'B', 'S', N->fno ? 'F' : 'N', N->fno ? 'N' : 'E', N->fno ? 'O' : 'T', '1'};
+    // an FNO file carries its shape (n, width, modes, layers, coefficient channels, identity skip)
+    // after the magic
+    const char magic[8] = {'N', 'P', 'B', 'S', N->fno ? 'F' : 'N', N->fno ? 'N' : 'E', N->fno ? 'O' : 'T',
+                           N->fno ? '2' : '1'};
     const long long hdr[2] = {N->step, P};
-    const int shape[5] = {N->fno ? N->fno->n : 0, N->fno ? N->fno->C : 0, N->fno ? N->fno->m : 0,
-                          N->fno ? N->fno->L : 0, N->fno ? N->fno->ca : 0};
-    bool ok = fwrite(magic, 1, 8, f) == 8 && (!N->fno || fwrite(shape, sizeof(int), 5, f) == 5) &&
+    const int shape[6] = {N->fno ? N->fno->n : 0, N->fno ? N->fno->C : 0, N->fno ? N->fno->m : 0,
+                          N->fno ? N->fno->L : 0, N->fno ? N->fno->ca : 0, N->fno ? N->fno->skip : 0};
+    bool ok = fwrite(magic, 1, 8, f) == 8 && (!N->fno || fwrite(shape, sizeof(int), 6, f) == 6) &&
               fwrite(hdr, sizeof(long long), 2, f) == 2 &&
               fwrite(buf.data(), sizeof(float), buf.size(), f) == buf.size();
     ok = (fclose(f) == 0) && ok;
@@ -1120,11 +1122,16 @@ npbs_status npbs_net_load(npbs_net** out, int device, const char* path) {
     if (!f) return NPBS_ERR_INVALID_ARG;
     char magic[8];
     long long hdr[2];
-    int shape[5] = {0, 0, 0, 0, 0};
+    int shape[6] = {0, 0, 0, 0, 0, 0};
     bool ok = fread(magic, 1, 8, f) == 8;
-    const bool is_fno = ok && memcmp(magic, "NPBSFNO1", 8) == 0;
+    // FNO files: version 1 without the skip flag, version 2 with it
+    const bool fno1 = ok && memcmp(magic, "NPBSFNO1", 8) == 0, fno2 = ok && memcmp(magic, "NPBSFNO2", 8) == 0;
+    const bool is_fno = fno1 || fno2;
     ok = ok && (is_fno || memcmp(magic, "NPBSNET1", 8) == 0);
-    if (ok && is_fno) ok = fread(shape, sizeof(int), 5, f) == 5 && shape[0] > 0 && shape[0] <= kMaxN;
+    if (ok && is_fno) {
+        const size_t ns = fno2 ? 6 : 5;
+        ok = fread(shape, sizeof(int), ns, f) == ns && shape[0] > 0 && shape[0] <= kMaxN;
+    }
     long long P = 0;
     if (ok) P = is_fno ? fno_def(shape[0], shape[1], shape[2], shape[3], shape[4]).count : dev_param_count();
     ok = ok && P > 0 && fread(hdr, sizeof(long long), 2, f) == 2 && hdr[1] == P;
@@ -1139,6 +1146,7 @@ npbs_status npbs_net_load(npbs_net** out, int device, const char* path) {
     Net* N = reinterpret_cast<Net*>(h);
     N->step = hdr[0];
     N->version += 1;
+    if (N->fno) N->fno->skip = shape[5] ? 1 : 0;
     if (cudaMemcpy(N->params, buf.data(), sizeof(float) * P, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(N->m1, buf.data() + P, sizeof(float) * P, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(N->m2, buf.data() + 2 * P, sizeof(float) * P, cudaMemcpyHostToDevice) != cudaSuccess ||

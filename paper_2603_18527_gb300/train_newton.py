@@ -6,6 +6,9 @@ modes, batch 50, weight decay 1e-6, inner rTol 1e-4) through the library's
 C-ABI: ``newton_linearise`` for the trajectory states, ``newton_train_step``
 (Eq. nl_bs_loss and the two Euclidean objectives) and ``newton_solve``.
 
+The NPBS networks use the FNO's identity skip (M = I + N, zero projection at
+start: the Born series); ``--no-skip`` trains the paper's plain FNO.
+
 Training states: Newton trajectories with Born inner solves from the
 perturbed initial guesses of ``synth.newton_instance``; every step m gives a
 state (u_m, c_m, r_m).  The unrolled loss starts from an inner iterate delta
@@ -106,8 +109,9 @@ class StateGroup:
         return d
 
 
-def make_net(n=N_DEFAULT, width=25, modes=20, layers=2, seed=0):
-    return capi.Net.fno(n, width, modes, layers, seed=seed)
+def make_net(n=N_DEFAULT, width=25, modes=20, layers=2, seed=0, skip=True):
+    """The Newton FNO; skip: M = I + N (zero projection at start, the Born series)."""
+    return capi.Net.fno(n, width, modes, layers, seed=seed, skip=skip)
 
 
 def train(ctx, net, groups, steps, lr=1e-3, lr_min=1e-5, wd=1e-6, unroll=4, seed=0, loss="bs_reta", log=print,
@@ -168,7 +172,10 @@ def compare(ctx, groups, test, steps, log=print, **net_kw):
     initialisation and states, each solving in its own format."""
     res = {}
     for loss in ("dir", "bs_l2", "bs_reta"):
-        net = make_net(**net_kw)
+        # the Direct format feeds M the raw residual r - J delta: there M = I + N would start as an
+        # unscaled Richardson step, which diverges, so the Direct network is the plain FNO
+        kw = dict(net_kw, skip=net_kw.get("skip", True) and loss != "dir")
+        net = make_net(**kw)
         t = time.time()
         hist = train(ctx, net, groups, steps, loss=loss, log=log)
         res[loss] = {"train_s": round(time.time() - t, 1),
@@ -189,6 +196,7 @@ def main():
     ap.add_argument("--modes", type=int, default=20)
     ap.add_argument("--layers", type=int, default=2)
     ap.add_argument("--compare", action="store_true")
+    ap.add_argument("--no-skip", action="store_true", help="the paper's FNO without the identity skip")
     args = ap.parse_args()
     build.build()
     ctx = capi.Context(0)
@@ -199,7 +207,7 @@ def main():
     groups = [StateGroup([states[k] for k in order[i:i + args.batch]], seed=i)
               for i in range(0, len(order) - args.batch + 1, args.batch)]
     test = [synth.newton_instance(args.grid, 80000 + j) for j in range(args.test)]
-    kw = dict(n=args.grid, width=args.width, modes=args.modes, layers=args.layers)
+    kw = dict(n=args.grid, width=args.width, modes=args.modes, layers=args.layers, skip=not args.no_skip)
     born = solve_stats(ctx, None, test)
     print(json.dumps({"born": born}), flush=True)
     if args.compare:

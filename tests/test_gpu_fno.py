@@ -208,3 +208,48 @@ def test_fno_with_four_coefficient_channels_forward_and_backward():
         k = int(np.prod(shape))
         assert rel_l2(gw[o:o + k], dth.numpy()[o:o + k]) <= 1e-3, name
         o += k
+
+
+def test_fno_identity_skip_forward_backward_and_checkpoint(tmp_path):
+    """npbs_net_fno_set_skip: switching it on makes M = I at first (zero
+    projection); with random parameters the forward and the parameter and
+    residual gradients match the oracle's M = I + N; a saved network keeps
+    the skip."""
+    cfg = FN.FnoConfig(n=32, width=8, modes=5, layers=2, skip=True)
+    capi, c = ctx()
+    insts = [synth.small_instance(32, 32, seed=580 + j) for j in range(2)]
+    b, k2, f, n, V = setup_batch(capi, c, insts)
+    rs = [random_field((32, 32), 582 + j) for j in range(2)]
+    gs = [random_field((32, 32), 584 + j) for j in range(2)]
+    r, g = b.pack(rs), b.pack(gs)
+    net = capi.Net.fno(32, cfg.width, cfg.modes, cfg.layers, seed=3, skip=True)
+    out = torch.zeros_like(r)
+    capi.npbs_net_forward(c, net, b, r, n, out)
+    torch.cuda.synchronize()
+    assert np.array_equal(b.unpack(out)[0], rs[0].astype(np.complex64))
+    net.set_params(_params(cfg, 15))
+    capi.npbs_net_forward(c, net, b, r, n, out)
+    gr = torch.zeros_like(r)
+    net.zero_grad()
+    capi.npbs_net_backward(c, net, b, r, n, g, gr)
+    torch.cuda.synchronize()
+    flat, P = _oracle_params(cfg, 15, requires_grad=True)
+    rr = torch.from_numpy(np.stack(rs).real.copy()).requires_grad_(True)
+    ri = torch.from_numpy(np.stack(rs).imag.copy()).requires_grad_(True)
+    a = torch.from_numpy(np.stack([i.n.astype(np.float32).astype(np.float64) for i in insts]))
+    ref = FN.correction(torch.complex(rr, ri), a, P, cfg)
+    got = b.unpack(out)
+    for j in range(2):
+        assert rel_l2(got[j], ref[j].detach().numpy()) <= 1e-4
+    gt = torch.from_numpy(np.stack(gs))
+    L = (gt.real * ref.real + gt.imag * ref.imag).sum()
+    dth, dre, dim = torch.autograd.grad(L, [flat, rr, ri])
+    assert rel_l2(net.get_grads(), dth.numpy()) <= 1e-3
+    assert rel_l2(np.stack(b.unpack(gr)), (dre + 1j * dim).numpy()) <= 1e-3
+    p = str(tmp_path / "fno_skip.bin")
+    net.save(p)
+    net2 = capi.Net.load(p)
+    out2 = torch.zeros_like(r)
+    capi.npbs_net_forward(c, net2, b, r, n, out2)
+    torch.cuda.synchronize()
+    assert np.array_equal(b.unpack(out2)[1], got[1])
