@@ -255,7 +255,9 @@ __global__ void k_cdr_fold(const CdrInst* ins, const int* ids, const int* frozen
 // K5 rows:  F_x^{-1}, out = b0 / n^2 and ||out||^2
 // The same arithmetic as the unfused kernels, with the pointwise steps done
 // inside the transform kernels (about 160 B/point moved instead of 380).
-constexpr int kFTile = 6144;  // complex elements per tile buffer (48 KB); two per block
+// complex elements per tile buffer (24 KB); two per block, so four blocks of
+// 256 threads fit an SM (latency of the shared-memory passes needs the warps)
+constexpr int kFTile = 3072;
 
 __device__ __forceinline__ float2 cdr_lambda(const CdrInst& in, float kx, float ky, bool conj) {
     return make_float2((float)in.k0 * (kx * kx + ky * ky) + (float)in.s0,
@@ -627,9 +629,9 @@ template <int N, int RB, int CB> cudaError_t fused_attrs_of() {
 
 npbs_status cdr_fused_attrs(npbs_ctx* ctx) {
     NPBS_CK(ctx, (fused_attrs_of<0, 0, 0>()));
-    NPBS_CK(ctx, (fused_attrs_of<64, 16, 16>()));
-    NPBS_CK(ctx, (fused_attrs_of<128, 16, 16>()));
-    NPBS_CK(ctx, (fused_attrs_of<256, 8, 8>()));
+    NPBS_CK(ctx, (fused_attrs_of<64, 8, 8>()));
+    NPBS_CK(ctx, (fused_attrs_of<128, 8, 8>()));
+    NPBS_CK(ctx, (fused_attrs_of<256, 4, 4>()));
     return NPBS_OK;
 }
 
@@ -672,14 +674,14 @@ npbs_status cdr_run_fused(npbs_ctx* ctx, const CdrPrep& P, int mode, const float
     for (const CdrGroup& g : P.groups) {
         const int n = g.n;
         // three fields of rb rows (cb columns) fit one tile buffer
-        const int rb = divisor_at_most(n, std::min(16, kFTile / (3 * n)));
-        const int cb = divisor_at_most(n, std::min(16, kFTile / (3 * n)));
-        if (n == 64 && rb == 16 && cb == 16)
-            fused_launch<64, 16, 16>(g, rb, cb, mode, kappa, vx, vy, sigma, f, x, b, out, norm2, st);
-        else if (n == 128 && rb == 16 && cb == 16)
-            fused_launch<128, 16, 16>(g, rb, cb, mode, kappa, vx, vy, sigma, f, x, b, out, norm2, st);
-        else if (n == 256 && rb == 8 && cb == 8)
-            fused_launch<256, 8, 8>(g, rb, cb, mode, kappa, vx, vy, sigma, f, x, b, out, norm2, st);
+        const int rb = divisor_at_most(n, std::min(8, kFTile / (3 * n)));
+        const int cb = divisor_at_most(n, std::min(8, kFTile / (3 * n)));
+        if (n == 64 && rb == 8 && cb == 8)
+            fused_launch<64, 8, 8>(g, rb, cb, mode, kappa, vx, vy, sigma, f, x, b, out, norm2, st);
+        else if (n == 128 && rb == 8 && cb == 8)
+            fused_launch<128, 8, 8>(g, rb, cb, mode, kappa, vx, vy, sigma, f, x, b, out, norm2, st);
+        else if (n == 256 && rb == 4 && cb == 4)
+            fused_launch<256, 4, 4>(g, rb, cb, mode, kappa, vx, vy, sigma, f, x, b, out, norm2, st);
         else
             fused_launch<0, 0, 0>(g, rb, cb, mode, kappa, vx, vy, sigma, f, x, b, out, norm2, st);
         NPBS_CK(ctx, cudaGetLastError());

@@ -225,6 +225,8 @@ def main():
     ap.add_argument("--fno-width", type=int, default=25)
     ap.add_argument("--fno-modes", type=int, default=45)
     ap.add_argument("--fno-layers", type=int, default=3)
+    ap.add_argument("--fno-skip", action="store_true",
+                    help="the FNO as M = I + N (zero projection at start: the Born series, npbs_net_fno_set_skip)")
     ap.add_argument("--compare-unet", default="",
                     help="after training, compare NPBS with this network and with the U-Net of this .npz on the "
                          "64 held-out media of the bench (seeds 2000+) against CBS")
@@ -239,7 +241,7 @@ def main():
     def fresh():
         if args.backbone == "fno":
             return capi.Net.fno(args.grid, args.fno_width, min(args.fno_modes, args.grid // 2 + 1), args.fno_layers,
-                                seed=args.seed)
+                                seed=args.seed, skip=args.fno_skip)
         return capi.Net(0, seed=args.seed)
 
     if args.init.endswith(".npz"):
