@@ -252,7 +252,8 @@ def bench_extensions(capi, ctx, args, stream):
     g = TC.Group(ctx, cinsts)
     x = torch.randn(g.b.extent, dtype=torch.complex64, device="cuda")
     y = torch.zeros_like(x)
-    ap = lambda: capi.cdr_apply(ctx, g.b, g.consts, g.fields, g.f, x, y, capi.RESIDUAL)
+    cc = capi.cdr_consts_array(g.consts)
+    ap = lambda: capi.cdr_apply(ctx, g.b, cc, g.fields, g.f, x, y, capi.RESIDUAL)
     ap()
     ms = timed(stream, ap, 20)
     pts = sum(i.n * i.n for i in cinsts)
@@ -285,7 +286,8 @@ def bench_extensions(capi, ctx, args, stream):
     sh, u32, r = capi.newton_linearise(ctx, nb, nu, nf)
     x = torch.randn(nb.extent, dtype=torch.complex64, device="cuda")
     y = torch.zeros_like(x)
-    na = lambda: capi.newton_apply(ctx, nb, sh, u32, r, x, y, capi.RESIDUAL)
+    sha = capi.newton_shifts_array(sh)
+    na = lambda: capi.newton_apply(ctx, nb, sha, u32, r, x, y, capi.RESIDUAL)
     na()
     ms = timed(stream, na, 20)
     fl = 16.0 * 64 ** 3 * len(ninst)
@@ -543,7 +545,29 @@ def main():
                     help="time only the CDR RESIDUAL apply on COUNT 128^2 instances (for profiler captures)")
     ap.add_argument("--net-forward-only", action="store_true",
                     help="time only the network forward on --npbs-count 256^2 instances (for profiler captures)")
+    ap.add_argument("--newton-apply-only", type=int, default=0, metavar="COUNT",
+                    help="time only the Newton RESIDUAL apply on COUNT 64^2 states (for profiler captures)")
     args = ap.parse_args()
+    if args.newton_apply_only:
+        import synth
+        from paper_2603_18527_gb300 import build, capi
+        build.build()
+        ctx = capi.Context(0)
+        ninst = [synth.newton_instance(64, 70000 + j) for j in range(args.newton_apply_only)]
+        nb = capi.Batch([(64, 64)] * len(ninst), h=[1.0 / 65] * len(ninst))
+        nf = nb.pack([i.f for i in ninst], dtype=torch.float64)
+        nu = nb.pack([i.u0 for i in ninst], dtype=torch.float64)
+        sh, u32, r = capi.newton_linearise(ctx, nb, nu, nf)
+        x = torch.randn(nb.extent, dtype=torch.complex64, device="cuda")
+        y = torch.zeros_like(x)
+        sha = capi.newton_shifts_array(sh)
+        na = lambda: capi.newton_apply(ctx, nb, sha, u32, r, x, y, capi.RESIDUAL)
+        for _ in range(args.warmup):
+            na()
+        ms = timed(torch.cuda.current_stream(), na, max(1, args.steps))
+        fl = 16.0 * 64 ** 3 * len(ninst)
+        print(json.dumps({"newton_apply_only": len(ninst), "ms": ms, "tflops": fl / (ms * 1e-3) / 1e12}))
+        return 0
     if args.cdr_apply_only:
         import synth
         from paper_2603_18527_gb300 import build, capi
@@ -553,7 +577,8 @@ def main():
         g = TC.Group(ctx, [synth.cdr_instance(128, seed=60000 + j, speed=1.0) for j in range(args.cdr_apply_only)])
         x = torch.randn(g.b.extent, dtype=torch.complex64, device="cuda")
         y = torch.zeros_like(x)
-        ap_ = lambda: capi.cdr_apply(ctx, g.b, g.consts, g.fields, g.f, x, y, capi.RESIDUAL)
+        cc = capi.cdr_consts_array(g.consts)
+        ap_ = lambda: capi.cdr_apply(ctx, g.b, cc, g.fields, g.f, x, y, capi.RESIDUAL)
         for _ in range(args.warmup):
             ap_()
         ms = timed(torch.cuda.current_stream(), ap_, max(1, args.steps))

@@ -253,11 +253,15 @@ class Batch:
         return sum(ny * nx for ny, nx in self.shapes)
 
     def c_batch(self):
+        """The C description; rebuilt only when h, k0sq or eps changed since the last call."""
+        key = (tuple(self.h), tuple(self.k0sq), tuple(self.eps))
+        if self._c is not None and self._c[2] == key:
+            return self._c[1]
         arr = (npbs_instance * max(1, self.count))()
         for j, (ny, nx) in enumerate(self.shapes):
             arr[j] = npbs_instance(nx, ny, float(self.h[j]), float(self.k0sq[j]), float(self.eps[j]),
                                    int(self.offsets[j]))
-        self._c = (arr, npbs_batch(self.count, arr))
+        self._c = (arr, npbs_batch(self.count, arr), key)
         return self._c[1]
 
     def pack(self, fields: Sequence[np.ndarray], dtype=torch.complex64, device="cuda") -> torch.Tensor:
@@ -582,11 +586,18 @@ class CdrFields:
         return _ptr(self.kappa), _ptr(self.vx), _ptr(self.vy), _ptr(self.sigma)
 
 
-def _consts(consts):
+def cdr_consts_array(consts):
+    """The per-instance constants as the C array the entries take; pass the
+    result instead of a list to skip the conversion on repeated calls."""
+    if isinstance(consts, C.Array):
+        return consts
     arr = (npbs_cdr_consts * max(1, len(consts)))()
     for j, c in enumerate(consts):
         arr[j] = npbs_cdr_consts(*[float(v) for v in c])
     return arr
+
+
+_consts = cdr_consts_array
 
 
 def npbs_cdr_background(ctx: Context, batch: "Batch", fields: CdrFields, stream=None):
@@ -633,11 +644,18 @@ def cdr_train_step(ctx: Context, net, batch: "Batch", consts, fields: CdrFields,
 
 # ---- Newton-Born linearisation (Dirichlet, DST-I Green operator) --------------
 
-def _shifts(shift):
+def newton_shifts_array(shift):
+    """The per-instance shifts as the C array the entries take; pass the
+    result instead of a list to skip the conversion on repeated calls."""
+    if isinstance(shift, C.Array):
+        return shift
     arr = (C.c_double * max(1, len(shift)))()
     for j, c in enumerate(shift):
         arr[j] = float(c)
     return arr
+
+
+_shifts = newton_shifts_array
 
 
 def newton_apply(ctx: Context, batch: "Batch", shift, u, r, x, out, mode, norm2=None, stream=None):

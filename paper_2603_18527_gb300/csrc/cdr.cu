@@ -25,6 +25,7 @@
 #include <vector>
 
 #include "ctx.cuh"
+#include "dftreg.cuh"
 #include "fft2d.cuh"
 #include "net.cuh"
 
@@ -462,6 +463,185 @@ __global__ void __launch_bounds__(256) k_cdrf_rows_out(const CdrInst* ins, const
     }
 }
 
+// ---- register four-step column kernels (compile-time sides) --------------
+// The column transforms of K2 and K4 as four-step FFTs in registers (N = N1 N2,
+// n = N2 n1 + n2, k = k1 + N1 k2): pass 1 reads each column's N1 points n2 +
+// N2 m from global, transforms them and writes the twiddled results to a
+// padded shared slab; pass 2 transforms along n2, so that a thread holds the
+// spectrum X[k1 + N1 k2] of one column for all k2 in registers, where the
+// spectral step runs before the inverse length-N2 transform; pass 3 finishes
+// the inverse and writes natural rows.  Two shared round trips per transform
+// pair, against two per Stockham pass.
+template <int N2> __device__ __forceinline__ int rpad(int p) { return p + p / N2; }
+template <int N1, int N2> constexpr int rld() { return ((N1 * N2 + N1 + 13) / 16) * 16 + 2; }
+template <int N1, int N2, int CB, int NF> constexpr size_t reg_smem() {
+    return sizeof(float2) * ((size_t)NF * CB * rld<N1, N2>() + (size_t)N1 * (N2 + 1));
+}
+__device__ __forceinline__ float2 rmul(float2 t, float2 w) {
+    return make_float2(t.x * w.x - t.y * w.y, t.x * w.y + t.y * w.x);
+}
+__device__ __forceinline__ float2 rmulc(float2 t, float2 w) {  // t * conj(w)
+    return make_float2(t.x * w.x + t.y * w.y, t.y * w.x - t.x * w.y);
+}
+// twiddles W_N^{n2 k1} stored [k1][N2 + 1] from the length-N table
+template <int N1, int N2> __device__ __forceinline__ void reg_twiddles(float2* tw, const float2* src) {
+    for (int e = threadIdx.x; e < N1 * N2; e += blockDim.x) {
+        const int k1 = e / N2, n2 = e - k1 * N2;
+        tw[k1 * (N2 + 1) + n2] = src[n2 * k1];
+    }
+}
+// pass 1 on field f of the slab: length-N1 DFTs over rows n2 + N2 m of cb columns
+template <int N1, int N2, int CB>
+__device__ __forceinline__ void reg_pass1(const float2* src, long long base, float2* S, const float2* tw) {
+    constexpr int N = N1 * N2, LD = rld<N1, N2>();
+    for (int j = threadIdx.x; j < CB * N2; j += blockDim.x) {
+        const int c = j % CB, n2 = j / CB;
+        float2 v[N1];
+#pragma unroll
+        for (int m = 0; m < N1; ++m) v[m] = src[base + (long long)(n2 + N2 * m) * N + c];
+        DftR<N1, -1>::run(v);
+        float2* col = S + c * LD;
+#pragma unroll
+        for (int k1 = 0; k1 < N1; ++k1) col[rpad<N2>(N2 * k1 + n2)] = rmul(v[k1], tw[k1 * (N2 + 1) + n2]);
+    }
+}
+
+// K2 (register form): b0 columns -> X; [adjoint: / conj(lambda0)]; i xi_x X,
+// i xi_y X [, X] -> inverse; F output fields (b1, b2 [, b0]).
+template <int N1, int N2, int CB, int F>
+__global__ void __launch_bounds__(256) k_cdrr_cols_grad(const CdrInst* ins, const float2* twg, float2* b0,
+                                                        float2* b1, float2* b2, int adj) {
+    constexpr int N = N1 * N2, LD = rld<N1, N2>(), NBK = N / CB;
+    extern __shared__ __align__(16) float2 smem[];
+    float2* S = smem;                  // [F][CB][LD]
+    float2* tw = smem + F * CB * LD;   // [N1][N2 + 1]
+    const CdrInst in = ins[blockIdx.x / NBK];
+    const int c0 = (blockIdx.x % NBK) * CB;
+    const long long base = in.off + c0;
+    reg_twiddles<N1, N2>(tw, twg);
+    __syncthreads();
+    reg_pass1<N1, N2, CB>(b0, base, S, tw);
+    __syncthreads();
+    // pass 2: forward along n2, the spectral step, inverse along k2 per output field
+    for (int j = threadIdx.x; j < CB * N1; j += blockDim.x) {
+        const int k1 = j % N1, c = j / N1;
+        float2 v[N2];
+        const float2* col = S + c * LD;
+#pragma unroll
+        for (int i = 0; i < N2; ++i) v[i] = col[rpad<N2>(N2 * k1 + i)];
+        DftR<N2, -1>::run(v);
+        const float kx = xi_of<float>(c0 + c, N, in.h);
+        if (adj == 1) {
+#pragma unroll
+            for (int k2 = 0; k2 < N2; ++k2) {
+                const float ky = xi_of<float>(k1 + N1 * k2, N, in.h);
+                v[k2] = cdiv(v[k2], cdr_lambda(in, kx, ky, true));
+            }
+        }
+#pragma unroll
+        for (int f = 0; f < F; ++f) {
+            float2 w[N2];
+#pragma unroll
+            for (int k2 = 0; k2 < N2; ++k2) {
+                const float u = f == 0 ? kx : xi_of<float>(k1 + N1 * k2, N, in.h);
+                w[k2] = f < 2 ? make_float2(-u * v[k2].y, u * v[k2].x) : v[k2];
+            }
+            DftR<N2, +1>::run(w);
+            float2* out = S + (f * CB + c) * LD;
+#pragma unroll
+            for (int n2 = 0; n2 < N2; ++n2) out[rpad<N2>(N2 * k1 + n2)] = rmulc(w[n2], tw[k1 * (N2 + 1) + n2]);
+        }
+    }
+    __syncthreads();
+    // pass 3: inverse along k1 -> natural rows N2 n1 + n2
+    for (int j = threadIdx.x; j < F * CB * N2; j += blockDim.x) {
+        const int f = j / (CB * N2), rem = j - f * (CB * N2);
+        const int c = rem % CB, n2 = rem / CB;
+        const float2* col = S + (f * CB + c) * LD;
+        float2 v[N1];
+#pragma unroll
+        for (int k1 = 0; k1 < N1; ++k1) v[k1] = col[rpad<N2>(N2 * k1 + n2)];
+        DftR<N1, +1>::run(v);
+        float2* o = f == 0 ? b1 : f == 1 ? b2 : b0;
+#pragma unroll
+        for (int n1 = 0; n1 < N1; ++n1) o[base + (long long)(N2 * n1 + n2) * N + c] = v[n1];
+    }
+}
+
+// K4 (register form): b3, b4, b5 columns -> spectra; W = -i xi_x F1 - i xi_y F2
+// + F3 with the mode's multiple (kinds of k_cdr_assemble); inverse into b0.
+template <int N1, int N2, int CB>
+__global__ void __launch_bounds__(256) k_cdrr_cols_asm(const CdrInst* ins, const float2* twg, const float2* b3,
+                                                       const float2* b4, const float2* b5, float2* b0, int kind) {
+    constexpr int N = N1 * N2, LD = rld<N1, N2>(), NBK = N / CB;
+    extern __shared__ __align__(16) float2 smem[];
+    float2* S = smem;                  // [3][CB][LD]
+    float2* tw = smem + 3 * CB * LD;   // [N1][N2 + 1]
+    const CdrInst in = ins[blockIdx.x / NBK];
+    const int c0 = (blockIdx.x % NBK) * CB;
+    const long long base = in.off + c0;
+    reg_twiddles<N1, N2>(tw, twg);
+    __syncthreads();
+    reg_pass1<N1, N2, CB>(b3, base, S, tw);
+    reg_pass1<N1, N2, CB>(b4, base, S + CB * LD, tw);
+    reg_pass1<N1, N2, CB>(b5, base, S + 2 * CB * LD, tw);
+    __syncthreads();
+    // pass 2a: forward along n2 for each field, spectra back in place (slot N2 k1 + k2 holds k1 + N1 k2)
+    for (int j = threadIdx.x; j < 3 * CB * N1; j += blockDim.x) {
+        const int fc = j / N1, k1 = j - fc * N1;
+        float2* col = S + fc * LD;
+        float2 v[N2];
+#pragma unroll
+        for (int i = 0; i < N2; ++i) v[i] = col[rpad<N2>(N2 * k1 + i)];
+        DftR<N2, -1>::run(v);
+#pragma unroll
+        for (int k2 = 0; k2 < N2; ++k2) col[rpad<N2>(N2 * k1 + k2)] = v[k2];
+    }
+    __syncthreads();
+    // pass 2b: the assembly, the inverse along k2 into field 0
+    for (int j = threadIdx.x; j < CB * N1; j += blockDim.x) {
+        const int k1 = j % N1, c = j / N1;
+        const float kx = xi_of<float>(c0 + c, N, in.h);
+        const float2* c3 = S + c * LD;
+        const float2* c4 = S + (CB + c) * LD;
+        const float2* c5 = S + (2 * CB + c) * LD;
+        float2 w[N2];
+#pragma unroll
+        for (int k2 = 0; k2 < N2; ++k2) {
+            const int p = rpad<N2>(N2 * k1 + k2);
+            const float ky = xi_of<float>(k1 + N1 * k2, N, in.h);
+            const float2 a = c3[p], bb = c4[p], cc = c5[p];
+            float2 x = make_float2(kx * a.y + ky * bb.y + cc.x, -kx * a.x - ky * bb.x + cc.y);
+            if (kind == 0 || kind == 2) x = make_float2(-x.x, -x.y);
+            if (kind == 0 || kind == 1) x = cdiv(x, cdr_lambda(in, kx, ky, false));
+            w[k2] = x;
+        }
+        DftR<N2, +1>::run(w);
+        // field 0's slots of this (c, k1) were read above by this thread only
+        float2* out = S + c * LD;
+#pragma unroll
+        for (int n2 = 0; n2 < N2; ++n2) out[rpad<N2>(N2 * k1 + n2)] = rmulc(w[n2], tw[k1 * (N2 + 1) + n2]);
+    }
+    __syncthreads();
+    // pass 3: inverse along k1 -> natural rows
+    for (int j = threadIdx.x; j < CB * N2; j += blockDim.x) {
+        const int c = j % CB, n2 = j / CB;
+        const float2* col = S + c * LD;
+        float2 v[N1];
+#pragma unroll
+        for (int k1 = 0; k1 < N1; ++k1) v[k1] = col[rpad<N2>(N2 * k1 + n2)];
+        DftR<N1, +1>::run(v);
+#pragma unroll
+        for (int n1 = 0; n1 < N1; ++n1) b0[base + (long long)(N2 * n1 + n2) * N + c] = v[n1];
+    }
+}
+
+// the register column configuration of a compile-time side
+template <int N> struct RegCols;
+template <> struct RegCols<64> { static constexpr int N1 = 8, N2 = 8, CB = 16; };
+template <> struct RegCols<128> { static constexpr int N1 = 8, N2 = 16, CB = 16; };
+template <> struct RegCols<256> { static constexpr int N1 = 16, N2 = 16, CB = 8; };
+
 }  // namespace
 }  // namespace npbs
 
@@ -506,10 +686,32 @@ template <> const double2* CdrPrep::twiddles<double>(const CdrGroup& g) const { 
 
 npbs_status cdr_fused_attrs(npbs_ctx* ctx);
 
+// The last prepared batch: its exact description (instances and constants)
+// and the prepared plan, whose device tables stay in work[12].
+struct CdrCached {
+    std::vector<char> desc;
+    CdrPrep P;
+};
+
 npbs_status cdr_prepare(npbs_ctx* ctx, const npbs_batch* batch, const npbs_cdr_consts* consts, CdrPrep* P,
                         cudaStream_t st) {
     if (!batch || batch->count < 0 || (batch->count > 0 && (!batch->inst || !consts)))
         return set_err(ctx, NPBS_ERR_INVALID_ARG, "cdr: NULL batch or constants");
+    // a batch identical to the last one prepared reuses its tables: no upload, no synchronisation
+    std::vector<char> desc(sizeof(int) + (size_t)batch->count * (sizeof(npbs_instance) + sizeof(npbs_cdr_consts)));
+    memcpy(desc.data(), &batch->count, sizeof(int));
+    if (batch->count > 0) {
+        memcpy(desc.data() + sizeof(int), batch->inst, sizeof(npbs_instance) * batch->count);
+        memcpy(desc.data() + sizeof(int) + sizeof(npbs_instance) * batch->count, consts,
+               sizeof(npbs_cdr_consts) * batch->count);
+    }
+    if (ctx->cdr_prep) {
+        const CdrCached* c = static_cast<const CdrCached*>(ctx->cdr_prep.get());
+        if (c->desc == desc) {
+            *P = c->P;
+            return NPBS_OK;
+        }
+    }
     std::map<int, std::vector<int>> by;
     long long ext = 0;
     for (int j = 0; j < batch->count; ++j) {
@@ -589,6 +791,11 @@ npbs_status cdr_prepare(npbs_ctx* ctx, const npbs_batch* batch, const npbs_cdr_c
     NPBS_CK(ctx, fft2d::set_attrs());
     npbs_status fs = cdr_fused_attrs(ctx);
     if (fs != NPBS_OK) return fs;
+    auto cached = std::make_shared<CdrCached>();
+    cached->desc = std::move(desc);
+    cached->P = *P;
+    cached->P.buf64 = nullptr;  // cdr_prepare64 sets it per call
+    ctx->cdr_prep = cached;
     return NPBS_OK;
 }
 
@@ -617,7 +824,15 @@ inline int divisor_at_most(int n, int lim) {
 template <int N, int RB, int CB> cudaError_t fused_attrs_of() {
     const int sm = (int)(2 * kFTile * sizeof(float2));
     const cudaFuncAttribute at = cudaFuncAttributeMaxDynamicSharedMemorySize;
-    cudaError_t e = cudaFuncSetAttribute(k_cdrf_rows_fwd<N, RB>, at, sm);
+    cudaError_t e = cudaSuccess;
+    if constexpr (N > 0) {
+        using RC = RegCols<N>;
+        const int rs = (int)reg_smem<RC::N1, RC::N2, RC::CB, 3>();
+        e = cudaFuncSetAttribute(k_cdrr_cols_grad<RC::N1, RC::N2, RC::CB, 2>, at, rs);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_cdrr_cols_grad<RC::N1, RC::N2, RC::CB, 3>, at, rs);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_cdrr_cols_asm<RC::N1, RC::N2, RC::CB>, at, rs);
+    }
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_cdrf_rows_fwd<N, RB>, at, sm);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_cdrf_cols_grad<N, CB, 2>, at, sm);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_cdrf_cols_grad<N, CB, 3>, at, sm);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_cdrf_rows_flux<N, RB, 2>, at, sm);
@@ -648,17 +863,36 @@ void fused_launch(const CdrGroup& g, int rb, int cb, int mode, const float* kapp
     const unsigned gr = (unsigned)(g.cnt * (n / rb)), gc = (unsigned)(g.cnt * (n / cb));
     const float2* fs = (mode == NPBS_OP_B || adj) ? nullptr : f;
     k_cdrf_rows_fwd<N, RB><<<gr, 256, sm, st>>>(g.ins, n, rb, g.plan, g.tw, x, b[0]);
+    // column kernels: register four-step transforms for the compile-time sides
+    auto cols_grad = [&](auto fct) {
+        constexpr int F = decltype(fct)::value;
+        if constexpr (N > 0) {
+            using RC = RegCols<N>;
+            const unsigned gcr = (unsigned)(g.cnt * (N / RC::CB));
+            k_cdrr_cols_grad<RC::N1, RC::N2, RC::CB, F><<<gcr, 256, reg_smem<RC::N1, RC::N2, RC::CB, 3>(), st>>>(
+                g.ins, g.tw, b[0], b[1], b[2], mode == NPBS_ADJ_B ? 1 : 0);
+        } else {
+            k_cdrf_cols_grad<N, CB, F><<<gc, 256, sm, st>>>(g.ins, n, cb, g.plan, g.tw, b[0], b[1], b[2],
+                                                            mode == NPBS_ADJ_B ? 1 : 0);
+        }
+    };
     if (adj) {
-        k_cdrf_cols_grad<N, CB, 3><<<gc, 256, sm, st>>>(g.ins, n, cb, g.plan, g.tw, b[0], b[1], b[2],
-                                                        mode == NPBS_ADJ_B ? 1 : 0);
+        cols_grad(std::integral_constant<int, 3>{});
         k_cdrf_rows_flux<N, RB, 3><<<gr, 256, sm, st>>>(g.ins, n, rb, g.plan, g.tw, kappa, vx, vy, sigma, x, fs, b[0],
                                                         b[1], b[2], b[3], b[4], b[5]);
     } else {
-        k_cdrf_cols_grad<N, CB, 2><<<gc, 256, sm, st>>>(g.ins, n, cb, g.plan, g.tw, b[0], b[1], b[2], 0);
+        cols_grad(std::integral_constant<int, 2>{});
         k_cdrf_rows_flux<N, RB, 2><<<gr, 256, sm, st>>>(g.ins, n, rb, g.plan, g.tw, kappa, vx, vy, sigma, x, fs, b[0],
                                                         b[1], b[2], b[3], b[4], b[5]);
     }
-    k_cdrf_cols_asm<N, CB><<<gc, 256, sm, st>>>(g.ins, n, cb, g.plan, g.tw, b[3], b[4], b[5], b[0], kind);
+    if constexpr (N > 0) {
+        using RC = RegCols<N>;
+        const unsigned gcr = (unsigned)(g.cnt * (N / RC::CB));
+        k_cdrr_cols_asm<RC::N1, RC::N2, RC::CB><<<gcr, 256, reg_smem<RC::N1, RC::N2, RC::CB, 3>(), st>>>(
+            g.ins, g.tw, b[3], b[4], b[5], b[0], kind);
+    } else {
+        k_cdrf_cols_asm<N, CB><<<gc, 256, sm, st>>>(g.ins, n, cb, g.plan, g.tw, b[3], b[4], b[5], b[0], kind);
+    }
     k_cdrf_rows_out<N, RB><<<gr, 256, sm, st>>>(g.ins, g.ids, n, rb, g.plan, g.tw, b[0], out, norm2);
 }
 

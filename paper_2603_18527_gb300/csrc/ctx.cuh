@@ -80,6 +80,9 @@ struct npbs_ctx {
     long long plan_clock = 0;
     npbs::DevBuf scratch;   // spectrum between apply passes
     npbs::DevBuf work[21];  // solver workspaces (12-17: the CDR operators, 18-20: Newton)
+    // the last prepared CDR / Newton batch (its device tables stay in work[12] /
+    // work[18]): reused while a call describes exactly the same batch
+    std::shared_ptr<void> cdr_prep, nt_prep;
     npbs::DevBuf net_ws;    // network activations
     bool use_fast = true;  // cluster apply for square 128..512 grids, band kernels for 1024
                            // (NPBS_APPLY_PATH=three_pass disables both)

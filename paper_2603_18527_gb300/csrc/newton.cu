@@ -328,9 +328,27 @@ struct NtPrep {
 
 size_t nt_smem(int n) { return sizeof(float) * ((size_t)n * n + ((n + 3) & ~3)) + 2 * sizeof(float2) * (size_t)n * n; }
 
+// The last prepared batch: its exact description and the prepared plan, whose
+// device tables stay in work[18].
+struct NtCached {
+    std::vector<char> desc;
+    NtPrep P;
+};
+
 npbs_status nt_prepare(npbs_ctx* ctx, const npbs_batch* batch, NtPrep* P, cudaStream_t st) {
     if (!batch || batch->count < 0 || (batch->count > 0 && !batch->inst))
         return set_err(ctx, NPBS_ERR_INVALID_ARG, "newton: NULL batch");
+    // a batch identical to the last one prepared reuses its tables: no upload, no synchronisation
+    std::vector<char> desc(sizeof(int) + (size_t)batch->count * sizeof(npbs_instance));
+    memcpy(desc.data(), &batch->count, sizeof(int));
+    if (batch->count > 0) memcpy(desc.data() + sizeof(int), batch->inst, sizeof(npbs_instance) * batch->count);
+    if (ctx->nt_prep) {
+        const NtCached* c = static_cast<const NtCached*>(ctx->nt_prep.get());
+        if (c->desc == desc) {
+            *P = c->P;
+            return NPBS_OK;
+        }
+    }
     std::map<int, std::vector<int>> by;
     long long ext = 0;
     for (int j = 0; j < batch->count; ++j) {
@@ -394,6 +412,10 @@ npbs_status nt_prepare(npbs_ctx* ctx, const npbs_batch* batch, NtPrep* P, cudaSt
     }
     NPBS_CK(ctx, cudaFuncSetAttribute(k_nt_apply, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)nt_smem(kNtMaxN)));
+    auto cached = std::make_shared<NtCached>();
+    cached->desc = std::move(desc);
+    cached->P = *P;
+    ctx->nt_prep = cached;
     return NPBS_OK;
 }
 
