@@ -648,9 +648,11 @@ def main():
         for _ in range(args.warmup):
             fwd()
         ms = timed(torch.cuda.current_stream(), fwd, max(1, args.steps))
-        fl = unet_forward_flops(256, 256) * args.npbs_count
-        print(json.dumps({"net_forward_only": args.npbs_count, "ms": ms, "tflops": fl / (ms * 1e-3) / 1e12,
-                          "conv_launches": capi.npbs_conv_stats()}), flush=True)
+        rec = {"net_forward_only": args.npbs_count, "backbone": args.train_backbone, "ms": ms}
+        if args.train_backbone == "unet":
+            rec["tflops"] = unet_forward_flops(256, 256) * args.npbs_count / (ms * 1e-3) / 1e12
+            rec["conv_launches"] = capi.npbs_conv_stats()
+        print(json.dumps(rec), flush=True)
         return 0
 
     world = int(os.environ.get("WORLD_SIZE", "1"))

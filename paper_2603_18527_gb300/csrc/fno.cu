@@ -44,6 +44,11 @@ constexpr int kMaxC = 32;     // channel bound of the register-blocked kernels
 constexpr int kModesPerBlock = 8;
 
 int grid_of(long long n, int per = 256) { return (int)std::min<long long>((n + per - 1) / per, 152LL * 64); }
+// grid of the points x fields kernels: 256-thread blocks along the points,
+// one field per block row (fields past 65535 are looped over)
+dim3 grid2(long long points, long long fields) {
+    return dim3((unsigned)((points + 255) / 256), (unsigned)std::max(1LL, std::min<long long>(fields, 65535)));
+}
 
 // rows of the compact mode list for m retained modes: min(ky, n - ky) < m
 __host__ __device__ inline int rows_kept(int n, int m) {
@@ -63,6 +68,14 @@ __device__ __forceinline__ int row_of(int ri, int n, int m) {
     if (2 * m - 1 >= n) return ri;
     return ri < m ? ri : ri + (n - 2 * m + 1);
 }
+
+// Mode-major layouts (complex elements), padded so that every mode's block
+// and every channel row starts 16-byte aligned: weights
+// Wt[k * wstride(C) + i * C + o]; spectra X[k * xstride(nb, C) + c * nbp(nb) + b]
+// (per mode, one row of samples per channel).
+__host__ __device__ inline long long wstride(int C) { return ((long long)C * C + 1) & ~1LL; }
+__host__ __device__ inline int nbp(int nb) { return (nb + 1) & ~1; }
+__host__ __device__ inline long long xstride(int nb, int C) { return (long long)C * nbp(nb); }
 
 __device__ __forceinline__ float gelu_f(float x) { return 0.5f * x * (1.f + erff(x * 0.70710678118654752f)); }
 __device__ __forceinline__ float gelu_grad(float x) {
@@ -129,13 +142,15 @@ __global__ void k_complex_planes(SlotDev sd, const float2* r, float* z) {
 }
 
 // out[b][o][p] = sum_i M(o, i) x[b][i][p] + bias[o] (+ part of a spectral
-// result Z / N^2), pre-activation optionally kept, GELU optionally applied.
+// result Z / N^2), pre-activation optionally kept, GELU optionally applied,
+// then optionally multiplied by mul[b][o][p] and added to the old out.
 // M(o, i) = w[o * so + i * si] (si = 1, so = Ci for the forward 1x1; swapped
 // strides give the transpose).  Z (nullable): channel o is the real (o even)
 // or imaginary (o odd) part of field o / 2 of [nb][ceil(Co/2)][np].
 __global__ void __launch_bounds__(256) k_mix_points(int nb, long long np, const float* x, int Ci, const float* w,
                                                     int so, int si, const float* bias, const float2* Z, float zscale,
-                                                    int Co, int act, float* pre, float* out, int add) {
+                                                    int Co, int act, float* pre, const float* mul, float* out,
+                                                    int add) {
     // the matrix (rows padded to an even length) and the bias in shared
     // memory; each thread takes two adjacent points (np is even: n is), so one
     // shared load of two weights feeds four FMAs, and the plane accesses are
@@ -161,149 +176,333 @@ __global__ void __launch_bounds__(256) k_mix_points(int nb, long long np, const 
             if (i < Ci2)
                 xv[i] = i < Ci ? *reinterpret_cast<const float2*>(x + ((long long)b * Ci + i) * np + p)
                                : make_float2(0.f, 0.f);
-        for (int o = 0; o < Co; ++o) {
-            float s0 = Bs[o], s1 = Bs[o];
-            const float* mo = Ms + o * Ci2;
+        // output channels in pairs (one complex field of Z each); the next
+        // pair's Z values and old outputs are loaded before this pair's
+        // stores, so their latency overlaps the arithmetic
+        const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        auto ldz = [&](int o) -> float4 {
+            return Z ? *reinterpret_cast<const float4*>(Z + ((long long)b * Q + o / 2) * np + p) : zero4;
+        };
+        // two adjacent points of planes o and o + 1 of a [nb][Co][np] array
+        auto ld2 = [&](const float* a, int o) -> float4 {
+            const float2 u = *reinterpret_cast<const float2*>(a + ((long long)b * Co + o) * np + p);
+            const float2 v = o + 1 < Co ? *reinterpret_cast<const float2*>(a + ((long long)b * Co + o + 1) * np + p)
+                                        : make_float2(0.f, 0.f);
+            return make_float4(u.x, u.y, v.x, v.y);
+        };
+        auto ldo = [&](int o) -> float4 { return add ? ld2(out, o) : zero4; };
+        auto ldm = [&](int o) -> float4 { return mul ? ld2(mul, o) : make_float4(1.f, 1.f, 1.f, 1.f); };
+        float4 zn = ldz(0), on = ldo(0), mn = ldm(0);
+        for (int o = 0; o < Co; o += 2) {
+            const float4 z = zn, old = on, mv = mn;
+            if (o + 2 < Co) {
+                zn = ldz(o + 2);
+                on = ldo(o + 2);
+                mn = ldm(o + 2);
+            }
 #pragma unroll
-            for (int i = 0; i < kMaxC; i += 2) {
-                if (i < Ci2) {
-                    const float2 m = *reinterpret_cast<const float2*>(mo + i);
-                    s0 = fmaf(m.x, xv[i].x, s0);
-                    s1 = fmaf(m.x, xv[i].y, s1);
-                    s0 = fmaf(m.y, xv[i + 1].x, s0);
-                    s1 = fmaf(m.y, xv[i + 1].y, s1);
+            for (int t = 0; t < 2; ++t) {
+                const int oo = o + t;
+                if (oo >= Co) break;
+                float s0 = Bs[oo], s1 = Bs[oo];
+                const float* mo = Ms + oo * Ci2;
+#pragma unroll
+                for (int i = 0; i < kMaxC; i += 2) {
+                    if (i < Ci2) {
+                        const float2 m = *reinterpret_cast<const float2*>(mo + i);
+                        s0 = fmaf(m.x, xv[i].x, s0);
+                        s1 = fmaf(m.x, xv[i].y, s1);
+                        s0 = fmaf(m.y, xv[i + 1].x, s0);
+                        s1 = fmaf(m.y, xv[i + 1].y, s1);
+                    }
                 }
+                s0 = fmaf(t ? z.y : z.x, zscale, s0);
+                s1 = fmaf(t ? z.w : z.z, zscale, s1);
+                const long long oi = ((long long)b * Co + oo) * np + p;
+                if (pre) *reinterpret_cast<float2*>(pre + oi) = make_float2(s0, s1);
+                float v0 = act ? gelu_f(s0) : s0, v1 = act ? gelu_f(s1) : s1;
+                v0 = fmaf(v0, t ? mv.z : mv.x, t ? old.z : old.x);
+                v1 = fmaf(v1, t ? mv.w : mv.y, t ? old.w : old.y);
+                *reinterpret_cast<float2*>(out + oi) = make_float2(v0, v1);
             }
-            if (Z) {
-                const float4 z = *reinterpret_cast<const float4*>(Z + ((long long)b * Q + o / 2) * np + p);
-                s0 = fmaf((o & 1) ? z.y : z.x, zscale, s0);
-                s1 = fmaf((o & 1) ? z.w : z.z, zscale, s1);
-            }
-            const long long oi = ((long long)b * Co + o) * np + p;
-            if (pre) *reinterpret_cast<float2*>(pre + oi) = make_float2(s0, s1);
-            float v0 = act ? gelu_f(s0) : s0, v1 = act ? gelu_f(s1) : s1;
-            if (add) {
-                const float2 old = *reinterpret_cast<const float2*>(out + oi);
-                v0 += old.x;
-                v1 += old.y;
-            }
-            *reinterpret_cast<float2*>(out + oi) = make_float2(v0, v1);
         }
     }
 }
 
 // pack real channel planes [nb][Ci][np] into complex pair fields [nb][P][np]
-__global__ void k_pack(int nb, long long np, const float* x, int Ci, float2* Z) {
+// (grid: points x fields, field f = b * P + j)
+__global__ void k_pack(int nb, int np, const float* __restrict__ x, int Ci, float2* __restrict__ Z) {
     const int P = (Ci + 1) / 2;
-    const long long tot = (long long)nb * P * np;
-    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < tot; g += (long long)gridDim.x * blockDim.x) {
-        const long long p = g % np;
-        const long long bj = g / np;
-        const int j = (int)(bj % P), b = (int)(bj / P);
-        const float re = x[((long long)b * Ci + 2 * j) * np + p];
-        const float im = 2 * j + 1 < Ci ? x[((long long)b * Ci + 2 * j + 1) * np + p] : 0.f;
-        Z[g] = make_float2(re, im);
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= np) return;
+    for (int f = blockIdx.y; f < nb * P; f += gridDim.y) {
+        const int b = f / P, j = f - b * P;
+        const float* xb = x + ((long long)b * Ci + 2 * j) * np + p;
+        const float re = xb[0];
+        const float im = 2 * j + 1 < Ci ? xb[np] : 0.f;
+        Z[(long long)f * np + p] = make_float2(re, im);
     }
 }
 
-// retained half-plane modes of each real channel from the pair spectra
-__global__ void k_extract(int nb, int n, int m, int Kx, int K, const float2* Z, int Ci, float2* X) {
-    const int P = (Ci + 1) / 2;
+// Retained half-plane modes of each real channel from the pair spectra, in
+// the mode-major layout X[k * xstride(nb, Ci) + i * nbp(nb) + b] (row
+// f = i * nb + b).  A block takes 32 modes x 32 rows through a shared tile:
+// the spectra are read along the modes (consecutive k are consecutive kx of a
+// row) and X is written along the rows.
+__global__ void k_extract(int nb, int n, int m, int Kx, int K, const float2* __restrict__ Z, int Ci,
+                          float2* __restrict__ X) {
+    __shared__ float2 t[32][33];  // [channel row][mode]
+    const int P = (Ci + 1) / 2, F = nb * Ci;
     const long long np = (long long)n * n;
-    const long long tot = (long long)nb * Ci * K;
-    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < tot; g += (long long)gridDim.x * blockDim.x) {
-        const int k = (int)(g % K);
-        const long long bi = g / K;
-        const int i = (int)(bi % Ci), b = (int)(bi / Ci);
+    const int k0 = blockIdx.x * 32, f0 = blockIdx.y * 32;
+    const int k = k0 + threadIdx.x;
+    if (k < K) {
         const int ky = row_of(k / Kx, n, m), kx = k % Kx;
-        const int my = (n - ky) % n, mx = (n - kx) % n;
-        const float2* f = Z + ((long long)b * P + i / 2) * np;
-        const float2 zk = f[(long long)ky * n + kx], zm = f[(long long)my * n + mx];
-        X[g] = (i & 1) ? make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x))
-                       : make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
-    }
-}
-
-// Channel mixing on the retained modes: Y[b][o][k] = sum_a X[b][a][k] W[a][o][k]
-// (adj: Y[b][a][k] = sum_o conj(W[a][o][k]) X[b][o][k]), W the canonical
-// [Ci][Co][K] complex block as (re, im) float pairs, read as floats (its offset
-// in the parameter vector may be odd).  One thread per (mode k, output channel):
-// its A weights stay in registers while it walks the batch, so every weight is
-// read once per launch whatever the batch size (a warp covers 32 consecutive
-// modes, so the weight and X reads are coalesced).  Grid: (ceil(K/32),
-// ceil(O/8)), 256 threads.
-__global__ void __launch_bounds__(256) k_mix_modes(int nb, int K, const float2* X, const float* W, int Ci, int Co,
-                                                   int adj, float2* Y) {
-    const int k = blockIdx.x * 32 + (threadIdx.x & 31);
-    const int o = blockIdx.y * 8 + (threadIdx.x >> 5);
-    const int A = adj ? Co : Ci, O = adj ? Ci : Co;
-    if (k >= K || o >= O) return;
-    float2 w[kMaxC];
-#pragma unroll
-    for (int a = 0; a < kMaxC; ++a) {
-        if (a < A) {
-            const long long wi = adj ? ((long long)o * Co + a) * K + k : ((long long)a * Co + o) * K + k;
-            const float wr = __ldg(W + 2 * wi), wv = __ldg(W + 2 * wi + 1);
-            w[a] = make_float2(wr, adj ? -wv : wv);
+        const int my = ky == 0 ? 0 : n - ky, mx = kx == 0 ? 0 : n - kx;
+        const long long ik = (long long)ky * n + kx, im = (long long)my * n + mx;
+        for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+            const int f = f0 + r;
+            if (f >= F) break;
+            const int i = f / nb, b = f - i * nb;
+            const float2* z = Z + ((long long)b * P + i / 2) * np;
+            const float2 zk = z[ik], zm = z[im];
+            t[r][threadIdx.x] = (i & 1) ? make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x))
+                                        : make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
         }
     }
-    for (int b = 0; b < nb; ++b) {
-        const float2* xb = X + (long long)b * A * K + k;
-        float2 acc = make_float2(0.f, 0.f);
+    __syncthreads();
+    const int f = f0 + threadIdx.x;
+    if (f >= F) return;
+    const int i = f / nb, b = f - i * nb;
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int kk = k0 + r;
+        if (kk >= K) break;
+        X[(long long)kk * xstride(nb, Ci) + (long long)i * nbp(nb) + b] = t[threadIdx.x][r];
+    }
+}
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, int bytes) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// Channel mixing on the retained modes, mode-major: Y[k][b][o] = sum_i
+// X[k][i][b] Wt[k][i][o] (adj: Y[k][b][i] = sum_o conj(Wt[k][i][o]) X[k][o][b]),
+// Wt the mode-major copy of the [Ci][Co][K] weight block, X in the padded
+// layout above, Y unpadded [K][nb][O].  Work items are (mode, chunk of kMixNB
+// samples), mode-major, so the items of one mode are neighbours and share its
+// weights in L2.  Every warp runs its own kMixStages-deep cp.async ring: the
+// weight matrix and the X chunk ([channel][kMixNB], zero past the batch) of
+// the items ahead stream into the warp's shared stages while it mixes the
+// current item.  Lane q = output channel; per summed channel one weight load
+// and kMixNB / 2 broadcast 16-byte X loads feed 4 kMixNB FMAs.
+constexpr int kMixNB = 8;
+constexpr int kMixStages = 3;
+constexpr int kMixWarps = 4;
+__host__ __device__ inline int mix_stage(int C) {  // complex elements per stage
+    return (int)(wstride(C) + kMixNB * C);
+}
+__global__ void __launch_bounds__(32 * kMixWarps) k_mix_modes(int nb, int K, const float2* __restrict__ X,
+                                                              const float2* __restrict__ Wt, int C, int adj,
+                                                              float2* __restrict__ Y) {
+    extern __shared__ __align__(16) float2 ring_all[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int SZ = mix_stage(C);
+    float2* ring = ring_all + (long long)wib * kMixStages * SZ;
+    const long long WS = wstride(C), XS = xstride(nb, C);
+    const int nch = (nb + kMixNB - 1) / kMixNB;
+    const long long items = (long long)K * nch;
+    const long long nw = (long long)gridDim.x * kMixWarps;
+    const long long w0 = (long long)blockIdx.x * kMixWarps + wib;
+    // stage item `it` into ring slot `slot` (16-byte pieces; the tail of the
+    // last sample chunk is zero-filled, nothing past it is read)
+    auto issue = [&](long long it, int slot) {
+        const long long k = it / nch;
+        const int c = (int)(it - k * nch);
+        float2* sw = ring + (long long)slot * SZ;
+        float2* sx = sw + WS;
+        const char* gw = reinterpret_cast<const char*>(Wt + k * WS);
+        const int wb = (int)(WS * 8);
+        for (int o = lane * 16; o < wb; o += 32 * 16) cp_async16(reinterpret_cast<char*>(sw) + o, gw + o, 16);
+        // channel p's kMixNB samples: kMixNB / 2 pieces of 16 bytes, zero-filled past nb
+        const int xb = min(kMixNB, nb - c * kMixNB) * 8;
+        const char* gx = reinterpret_cast<const char*>(X + k * XS + (long long)c * kMixNB);
+        for (int q = lane; q < (kMixNB / 2) * C; q += 32) {
+            const int p = q / (kMixNB / 2), h = q % (kMixNB / 2);
+            const int bytes = max(0, min(16, xb - 16 * h));
+            const char* src = gx + (long long)p * nbp(nb) * 8 + (bytes > 0 ? 16 * h : 0);
+            cp_async16(reinterpret_cast<char*>(sx + p * kMixNB) + 16 * h, src, bytes);
+        }
+    };
 #pragma unroll
-        for (int a = 0; a < kMaxC; ++a) {
-            if (a < A) {
-                const float2 x = xb[(long long)a * K];
-                acc.x = fmaf(w[a].x, x.x, fmaf(-w[a].y, x.y, acc.x));
-                acc.y = fmaf(w[a].x, x.y, fmaf(w[a].y, x.x, acc.y));
+    for (int s = 0; s < kMixStages - 1; ++s) {
+        const long long it = w0 + s * nw;
+        if (it < items) issue(it, s);
+        cp_async_commit();
+    }
+    const bool on = lane < C;
+    for (long long i = 0;; ++i) {
+        const long long it = w0 + i * nw;
+        if (it >= items) break;
+        const long long ahead = it + (kMixStages - 1) * nw;
+        if (ahead < items) issue(ahead, (int)((i + kMixStages - 1) % kMixStages));
+        cp_async_commit();
+        cp_async_wait<kMixStages - 1>();
+        __syncwarp();
+        const float2* sw = ring + (long long)(i % kMixStages) * SZ;
+        const float2* sx = sw + WS;
+        const long long k = it / nch;
+        const int c = (int)(it - k * nch);
+        const int b0 = c * kMixNB, nbc = min(kMixNB, nb - b0);
+        float2 acc[kMixNB];
+#pragma unroll
+        for (int j = 0; j < kMixNB; ++j) acc[j] = make_float2(0.f, 0.f);
+        // lane q's weight for summed channel p: Wt[k][p][q], or conj(Wt[k][q][p])
+        const float2* wq = sw + (adj ? lane * C : lane);
+        const int ws = adj ? 1 : C;
+#pragma unroll 2
+        for (int p = 0; p < C; ++p) {
+            float2 w = on ? wq[p * ws] : make_float2(0.f, 0.f);
+            if (adj) w.y = -w.y;
+            const float4* xp = reinterpret_cast<const float4*>(sx + p * kMixNB);
+#pragma unroll
+            for (int h = 0; h < kMixNB / 2; ++h) {
+                const float4 x2 = xp[h];
+                acc[2 * h].x = fmaf(w.x, x2.x, fmaf(-w.y, x2.y, acc[2 * h].x));
+                acc[2 * h].y = fmaf(w.x, x2.y, fmaf(w.y, x2.x, acc[2 * h].y));
+                acc[2 * h + 1].x = fmaf(w.x, x2.z, fmaf(-w.y, x2.w, acc[2 * h + 1].x));
+                acc[2 * h + 1].y = fmaf(w.x, x2.w, fmaf(w.y, x2.z, acc[2 * h + 1].y));
             }
         }
-        Y[((long long)b * O + o) * K + k] = acc;
+        if (on) {
+            float2* yk = Y + (k * nb + b0) * C + lane;
+#pragma unroll
+            for (int j = 0; j < kMixNB; ++j)
+                if (j < nbc) yk[(long long)j * C] = acc[j];
+        }
+        __syncwarp();  // this slot is refilled by the next iteration's issue
+    }
+    cp_async_wait<0>();
+}
+
+size_t mix_smem(int C) { return sizeof(float2) * (size_t)kMixWarps * kMixStages * mix_stage(C); }
+
+// Y = mix(X) on K modes (see k_mix_modes); square C x C blocks
+cudaError_t mix_modes(int nb, int K, const float2* X, const float2* Wt, int C, int adj, float2* Y,
+                      cudaStream_t st) {
+    const size_t sm = mix_smem(C);  // within the limit set_fft_attrs() raised for C <= kMaxC
+    const long long items = (long long)K * ((nb + kMixNB - 1) / kMixNB);
+    const int blocks = (int)std::min<long long>((items + kMixWarps - 1) / kMixWarps, 152LL * 4);
+    k_mix_modes<<<blocks, 32 * kMixWarps, sm, st>>>(nb, K, X, Wt, C, adj, Y);
+    return cudaGetLastError();
+}
+
+// Wt[k * WS + io] = W[io][k] for one spectral block (io = i * Co + o, W as
+// float pairs at a possibly odd offset), through a 32 x 32 shared tile.
+__global__ void k_wt_transpose(const float* __restrict__ W, int K, int IO, long long WS, float2* __restrict__ Wt) {
+    __shared__ float2 t[32][33];
+    const int k0 = blockIdx.x * 32, io0 = blockIdx.y * 32;
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int io = io0 + r, k = k0 + threadIdx.x;
+        if (io < IO && k < K) {
+            const long long e = 2 * ((long long)io * K + k);
+            t[r][threadIdx.x] = make_float2(W[e], W[e + 1]);
+        }
+    }
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int k = k0 + r, io = io0 + threadIdx.x;
+        if (io < IO && k < K) Wt[(long long)k * WS + io] = t[threadIdx.x][r];
     }
 }
 
 // Hermitian completion of the retained half-plane spectra, two channels per
-// complex field: Z[b][q] = H(Y[b][2q]) + i H(Y[b][2q + 1]).
-__global__ void k_hermite(int nb, int n, int m, int Kx, int K, const float2* Y, int Co, float2* Z) {
+// complex field: Z[b][q] = H(Y[.][b][2q]) + i H(Y[.][b][2q + 1]), Y mode-major
+// [K][nb][Co].  A block takes 32 points; where each point takes its value
+// from (one or two) retained modes is decided once.  Samples go in chunks:
+// the (sample, channel) rows of the points' source modes are read into a
+// shared tile along the rows, then Z is written along the points.
+constexpr int kHermE = 128;  // (sample, channel) entries of one chunk
+__global__ void k_hermite(int nb, int n, int m, int Kx, int K, const float2* __restrict__ Y, int Co,
+                          float2* __restrict__ Z) {
+    __shared__ float2 s1[32][kHermE + 1];
+    __shared__ int I1[32], I2[32], FM[32];
     const int Q = (Co + 1) / 2;
-    const long long np = (long long)n * n;
-    const long long tot = (long long)nb * Q * np;
-    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < tot; g += (long long)gridDim.x * blockDim.x) {
-        const long long p = g % np;
-        const long long bq = g / np;
-        const int q = (int)(bq % Q), b = (int)(bq / Q);
-        const int ky = (int)(p / n), kx = (int)(p % n);
-        const int mky = (n - ky) % n;
-        float2 h[2];
-#pragma unroll
-        for (int t = 0; t < 2; ++t) {
-            const int c = 2 * q + t;
-            h[t] = make_float2(0.f, 0.f);
-            if (c >= Co) continue;
-            const float2* y = Y + ((long long)b * Co + c) * K;
-            auto at = [&](int yy, int xx) -> float2 {
-                const int ri = row_index(yy, n, m);
-                if (ri < 0 || xx >= Kx) return make_float2(0.f, 0.f);
-                return y[(long long)ri * Kx + xx];
-            };
+    const int np = n * n;
+    const int p0 = blockIdx.x * 32;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    if (ty == 0) {
+        // value = the mode itself (form 1, kx < n/2), the conjugate of the
+        // mirrored mode (form 2, kx > n/2), or half the sum of the mode and the
+        // conjugate of its mirror (form 0, kx = 0 or n/2)
+        const int p = p0 + tx;
+        int i1 = -1, i2 = -1, form = 1;
+        auto idx = [&](int yy, int xx) -> int {
+            const int ri = row_index(yy, n, m);
+            return (ri < 0 || xx >= Kx) ? -1 : ri * Kx + xx;
+        };
+        if (p < np) {
+            const int ky = p / n, kx = p - ky * n;
+            const int mky = ky == 0 ? 0 : n - ky;
             if (kx == 0 || 2 * kx == n) {
-                const float2 u = at(ky, kx), v = at(mky, kx);
-                h[t] = make_float2(0.5f * (u.x + v.x), 0.5f * (u.y - v.y));
+                form = 0;
+                i1 = idx(ky, kx);
+                i2 = idx(mky, kx);
             } else if (2 * kx < n) {
-                h[t] = at(ky, kx);
+                i1 = idx(ky, kx);
             } else {
-                const float2 v = at(mky, n - kx);
-                h[t] = make_float2(v.x, -v.y);
+                form = 2;
+                i1 = idx(mky, n - kx);
             }
         }
-        Z[g] = make_float2(h[0].x - h[1].y, h[0].y + h[1].x);
+        I1[tx] = i1;
+        I2[tx] = i2;
+        FM[tx] = form;
+    }
+    __syncthreads();
+    const long long rowY = (long long)nb * Co;  // entries per mode
+    const int bc = kHermE / Co;                 // samples per chunk (Co <= 32)
+    const int p = p0 + tx;
+    for (int b0 = 0; b0 < nb; b0 += bc) {
+        const int nbc = min(bc, nb - b0), E = nbc * Co;
+        for (int j = ty; j < 32; j += blockDim.y) {
+            const int i1 = I1[j];
+            const float2* y = Y + (long long)(i1 < 0 ? 0 : i1) * rowY + (long long)b0 * Co;
+            for (int e = tx; e < E; e += 32) s1[j][e] = i1 >= 0 ? y[e] : make_float2(0.f, 0.f);
+        }
+        __syncthreads();
+        if (p < np) {
+            const int form = FM[tx], i2 = I2[tx];
+            for (int g = ty; g < nbc * Q; g += blockDim.y) {
+                const int bl = g / Q, q = g - bl * Q, b = b0 + bl;
+                float2 h[2];
+#pragma unroll
+                for (int t = 0; t < 2; ++t) {
+                    const int c = 2 * q + t;
+                    h[t] = make_float2(0.f, 0.f);
+                    if (c >= Co) continue;
+                    const float2 u = s1[tx][bl * Co + c];
+                    if (form == 0) {
+                        const float2 v = i2 >= 0 ? Y[(long long)i2 * rowY + (long long)b * Co + c] : make_float2(0.f, 0.f);
+                        h[t] = make_float2(0.5f * (u.x + v.x), 0.5f * (u.y - v.y));
+                    } else {
+                        h[t] = form == 1 ? u : make_float2(u.x, -u.y);
+                    }
+                }
+                Z[((long long)b * Q + q) * np + p] = make_float2(h[0].x - h[1].y, h[0].y + h[1].x);
+            }
+        }
+        __syncthreads();
     }
 }
 
 // ------------------------------------------------------------- gradients
 
-// dW[i][o][k] += c_kx / n^2 sum_b G[b][o][k] conj(X[b][i][k]) for kModesPerBlock
-// modes per block, one thread per channel pair.
+// dW[i][o][k] += c_kx / n^2 sum_b G[k][b][o] conj(X[k][b][i]) (mode-major
+// spectra) for kModesPerBlock modes per block, one thread per channel pair.
 __global__ void k_wgrad_modes(int nb, int n, int Kx, int K, const float2* G, const float2* X, int Ci, int Co,
                               float* dW) {
     // rows padded by one element: a warp reads gs[o][q] for up to kMaxC channels o at one q
@@ -317,10 +516,13 @@ __global__ void k_wgrad_modes(int nb, int n, int Kx, int K, const float2* G, con
     for (int q = 0; q < kModesPerBlock; ++q) acc[q] = make_float2(0.f, 0.f);
     for (int b = 0; b < nb; ++b) {
         for (int e = t; e < (Ci + Co) * kModesPerBlock; e += blockDim.x) {
-            const int c = e / kModesPerBlock, q = e - c * kModesPerBlock;
+            // consecutive threads take consecutive channels of one mode
+            const int q = e / (Ci + Co), c = e - q * (Ci + Co);
             const int k = k0 + q;
-            if (c < Ci) xs[c][q] = k < K ? X[((long long)b * Ci + c) * K + k] : make_float2(0.f, 0.f);
-            else gs[c - Ci][q] = k < K ? G[((long long)b * Co + (c - Ci)) * K + k] : make_float2(0.f, 0.f);
+            if (c < Ci) xs[c][q] = k < K ? X[(long long)k * xstride(nb, Ci) + (long long)c * nbp(nb) + b]
+                                         : make_float2(0.f, 0.f);
+            else gs[c - Ci][q] = k < K ? G[(long long)k * xstride(nb, Co) + (long long)(c - Ci) * nbp(nb) + b]
+                                       : make_float2(0.f, 0.f);
         }
         __syncthreads();
         if (mine) {
@@ -561,7 +763,7 @@ size_t ws_layout(const FnoDef& d, int nb, bool train, FnoWS* w, char* base) {
     t.z = f(d.C * plane);
     t.z1 = f(d.C * plane);
     t.Zp = c2((long long)nb * P * np);
-    t.Xc = c2((long long)nb * d.C * K);
+    t.Xc = c2(xstride(nb, d.C) * K);
     t.Yc = c2((long long)nb * d.C * K);
     if (train) {
         t.gp = f(2 * plane);
@@ -570,7 +772,7 @@ size_t ws_layout(const FnoDef& d, int nb, bool train, FnoWS* w, char* base) {
         t.g2 = f(d.C * plane);
         t.g3 = f(d.C * plane);
         t.dc = f(d.C * plane);
-        t.Gc = c2((long long)nb * d.C * K);
+        t.Gc = c2(xstride(nb, d.C) * K);
     }
     if (w) *w = t;
     return o;
@@ -583,56 +785,92 @@ cudaError_t fft2(const FnoDef& d, float2* Z, long long fields, int dir, cudaStre
     return fft2d::run(Z, nullptr, fields, d.n, dir, d.plan, d.tw, st);
 }
 
-// Retained-mode spectra of the real channel planes x [nb][Ci][np] into X [nb][Ci][K].
+// Spectral layer j's block of the mode-major weight copy: j < L the NLFL
+// layers, j = L the residual layer, j = L + 1 the fusion layer.
+long long wt_modes(const FnoDef& d, int j) {
+    return j == d.L ? (long long)d.fy * d.fx : (long long)d.ky * d.kx;
+}
+long long wt_canon(const FnoDef& d, int j) { return j < d.L ? d.spec[j] : j == d.L ? d.spec_r : d.spec_f; }
+const float2* wt_of(const FnoDef& d, int j) {
+    long long o = 0;
+    for (int q = 0; q < j; ++q) o += wt_modes(d, q) * wstride(d.C);
+    return d.wt + o;
+}
+
+// Refresh the mode-major weight copy from the parameters when they changed
+// (allocated on first use; never called inside a graph capture with stale
+// weights: every run is prepared first, and preparing refreshes it).
+cudaError_t ensure_wt(const FnoDef& d, const float* P, long long version, cudaStream_t st) {
+    if (d.wt && d.wt_version == version) return cudaSuccess;
+    const int IO = d.C * d.C;
+    if (!d.wt) {
+        long long tot = 0;
+        for (int j = 0; j < d.L + 2; ++j) tot += wt_modes(d, j) * wstride(d.C);
+        cudaError_t e = cudaMalloc(&d.wt, sizeof(float2) * tot);
+        if (e != cudaSuccess) {
+            d.wt = nullptr;
+            return e;
+        }
+    }
+    for (int j = 0; j < d.L + 2; ++j) {
+        const long long K = wt_modes(d, j);
+        k_wt_transpose<<<dim3((unsigned)((K + 31) / 32), (unsigned)((IO + 31) / 32)), dim3(32, 8), 0, st>>>(
+            P + wt_canon(d, j), (int)K, IO, wstride(d.C), const_cast<float2*>(wt_of(d, j)));
+    }
+    d.wt_version = version;
+    return cudaGetLastError();
+}
+
+// Retained-mode spectra of the real channel planes x [nb][Ci][np] into the
+// mode-major X [K][xstride(nb, Ci)] (row b * Ci + i of mode k).
 cudaError_t spectra(const FnoDef& d, const FnoWS& w, int nb, const float* x, int Ci, int m, float2* X,
                     cudaStream_t st, long long* kc) {
     const long long np = (long long)d.n * d.n;
     const int P = (Ci + 1) / 2;
     const int Kx = std::min(m, d.n / 2 + 1), K = rows_kept(d.n, m) * Kx;
-    k_pack<<<grid_of((long long)nb * P * np), 256, 0, st>>>(nb, np, x, Ci, w.Zp);
+    k_pack<<<grid2(np, nb * P), 256, 0, st>>>(nb, (int)np, x, Ci, w.Zp);
     cudaError_t e = fft2(d, w.Zp, (long long)nb * P, -1, st);
     if (e != cudaSuccess) return e;
-    k_extract<<<grid_of((long long)nb * Ci * K), 256, 0, st>>>(nb, d.n, m, Kx, K, w.Zp, Ci, X);
+    k_extract<<<dim3((unsigned)((K + 31) / 32), (unsigned)((nb * Ci + 31) / 32)), dim3(32, 8), 0, st>>>(
+        nb, d.n, m, Kx, K, w.Zp, Ci, X);
     *kc += 4;
     return cudaGetLastError();
 }
 
-// out = act(irfft2(mix(Y)) / ... + M x + bias): Y [nb][Co][K] already mixed;
+// out = act(irfft2(mix(Y)) / ... + M x + bias): Y [K][nb][Co] already mixed;
 // the local matrix M(o, i) = wl[o * so + i * si] acts on x [nb][Ci][np].
 cudaError_t synthesize(const FnoDef& d, const FnoWS& w, int nb, const float2* Y, int Co, int m, const float* x,
                        int Ci, const float* wl, int so, int si, const float* bias, int act, float* pre, float* out,
-                       int add, cudaStream_t st, long long* kc) {
+                       int add, cudaStream_t st, long long* kc, const float* mul = nullptr) {
     const long long np = (long long)d.n * d.n;
     const int Q = (Co + 1) / 2;
     const int Kx = std::min(m, d.n / 2 + 1), K = rows_kept(d.n, m) * Kx;
-    k_hermite<<<grid_of((long long)nb * Q * np), 256, 0, st>>>(nb, d.n, m, Kx, K, Y, Co, w.Zp);
+    k_hermite<<<(unsigned)((np + 31) / 32), dim3(32, 8), 0, st>>>(nb, d.n, m, Kx, K, Y, Co, w.Zp);
     cudaError_t e = fft2(d, w.Zp, (long long)nb * Q, 1, st);
     if (e != cudaSuccess) return e;
     k_mix_points<<<grid_of((long long)nb * np / 2), 256, 0, st>>>(nb, np, x, Ci, wl, so, si, bias, w.Zp,
-                                                              1.f / (float)np, Co, act, pre, out, add);
+                                                              1.f / (float)np, Co, act, pre, mul, out, add);
     *kc += 4;
     return cudaGetLastError();
 }
 
-dim3 mix_grid(int K, int O) { return dim3((unsigned)((K + 31) / 32), (unsigned)((O + 7) / 8)); }
-
-// One Fourier layer: out = act(irfft2(W * R(rfft2(x))) + W^loc x + b)
-cudaError_t layer_fwd(const FnoDef& d, const FnoWS& w, int nb, const float* x, const float* Wsp, int m,
+// One Fourier layer: out = act(irfft2(W * R(rfft2(x))) + W^loc x + b), times mul (nullable)
+cudaError_t layer_fwd(const FnoDef& d, const FnoWS& w, int nb, const float* x, const float2* Wt, int m,
                       const float* wl, const float* bias, int act, float* pre, float* out, cudaStream_t st,
-                      long long* kc) {
+                      long long* kc, const float* mul = nullptr) {
     const int C = d.C;
     const int K = rows_kept(d.n, m) * std::min(m, d.n / 2 + 1);
     cudaError_t e = spectra(d, w, nb, x, C, m, w.Xc, st, kc);
     if (e != cudaSuccess) return e;
-    k_mix_modes<<<mix_grid(K, C), 256, 0, st>>>(nb, K, w.Xc, Wsp, C, C, 0, w.Yc);
+    e = mix_modes(nb, K, w.Xc, Wt, C, 0, w.Yc, st);
     *kc += 1;
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    return synthesize(d, w, nb, w.Yc, C, m, x, C, wl, C, 1, bias, act, pre, out, 0, st, kc);
+    if (e != cudaSuccess) return e;
+    return synthesize(d, w, nb, w.Yc, C, m, x, C, wl, C, 1, bias, act, pre, out, 0, st, kc, mul);
 }
 
 // Backward of one Fourier layer from G = dL/d(pre-activation): accumulates the
 // spectral, local and bias gradients; dx = adjoint(G) (nullable).
-cudaError_t layer_bwd(const FnoDef& d, const FnoWS& w, int nb, const float* x, const float* Wsp, float* dWsp, int m,
+cudaError_t layer_bwd(const FnoDef& d, const FnoWS& w, int nb, const float* x, const float2* Wt, float* dWsp, int m,
                       const float* wl, float* dwl, float* dbias, const float* G, float* dx, cudaStream_t st,
                       long long* kc) {
     const int C = d.C;
@@ -648,9 +886,9 @@ cudaError_t layer_bwd(const FnoDef& d, const FnoWS& w, int nb, const float* x, c
     *kc += 2;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (!dx) return cudaSuccess;
-    k_mix_modes<<<mix_grid(K, C), 256, 0, st>>>(nb, K, w.Gc, Wsp, C, C, 1, w.Yc);
+    e = mix_modes(nb, K, w.Gc, Wt, C, 1, w.Yc, st);
     *kc += 1;
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (e != cudaSuccess) return e;
     return synthesize(d, w, nb, w.Yc, C, m, G, C, wl, 1, C, nullptr, 0, nullptr, dx, 0, st, kc);
 }
 
@@ -664,11 +902,11 @@ cudaError_t coefficient_branch(const FnoDef& d, const float* P, const FnoWS& w, 
     k_ln_plane<<<grid_of((long long)nb * d.ca * np), 256, 0, st>>>(sd, a, d.ca, astride, w.stats, w.lnp);
     k_mix_points<<<grid_of((long long)nb * np / 2), 256, 0, st>>>(nb, np, w.lnp, d.ca, P + d.lift_a_w, d.ca, 1,
                                                               P + d.lift_a_b, nullptr, 0.f, C, 0, nullptr,
-                                                              coef(w, d, 0, train), 0);
+                                                              nullptr, coef(w, d, 0, train), 0);
     *kc += 3;
     cudaError_t e = cudaGetLastError();
     for (int l = 0; l < d.L && e == cudaSuccess; ++l)
-        e = layer_fwd(d, w, nb, coef(w, d, l, train), P + d.spec[l], d.m, P + d.loc_w[l], P + d.loc_b[l], 1,
+        e = layer_fwd(d, w, nb, coef(w, d, l, train), wt_of(d, l), d.m, P + d.loc_w[l], P + d.loc_b[l], 1,
                       train ? w.pre[l] : nullptr, coef(w, d, l + 1, train), st, kc);
     return e;
 }
@@ -689,13 +927,19 @@ cudaError_t forward_group(const FnoDef& d, const float* P, const FnoWS& w, const
     }
     k_complex_planes<<<grid_of((long long)nb * np), 256, 0, st>>>(sd, r, w.rp);
     k_mix_points<<<grid_of((long long)nb * np / 2), 256, 0, st>>>(nb, np, w.rp, 2, P + d.lift_r, 2, 1, nullptr, nullptr,
-                                                              0.f, C, 0, nullptr, w.x0, 0);
+                                                              0.f, C, 0, nullptr, nullptr, w.x0, 0);
     *kc += 2;
-    e = layer_fwd(d, w, nb, w.x0, P + d.spec_r, d.fx, P + d.loc_r, nullptr, 0, nullptr, w.x1, st, kc);
-    if (e != cudaSuccess) return e;
-    k_mul<<<grid_of((long long)nb * C * np), 256, 0, st>>>((long long)nb * C * np, cf, w.x1, w.z);
-    *kc += 1;
-    e = layer_fwd(d, w, nb, w.z, P + d.spec_f, d.m, P + d.loc_f, nullptr, 0, nullptr, w.z1, st, kc);
+    if (train) {
+        // the backward needs x1 = the residual layer's output as well as z = c x1
+        e = layer_fwd(d, w, nb, w.x0, wt_of(d, d.L), d.fx, P + d.loc_r, nullptr, 0, nullptr, w.x1, st, kc);
+        if (e != cudaSuccess) return e;
+        k_mul<<<grid_of((long long)nb * C * np), 256, 0, st>>>((long long)nb * C * np, cf, w.x1, w.z);
+        *kc += 1;
+    } else {
+        e = layer_fwd(d, w, nb, w.x0, wt_of(d, d.L), d.fx, P + d.loc_r, nullptr, 0, nullptr, w.z, st, kc, cf);
+        if (e != cudaSuccess) return e;
+    }
+    e = layer_fwd(d, w, nb, w.z, wt_of(d, d.L + 1), d.m, P + d.loc_f, nullptr, 0, nullptr, w.z1, st, kc);
     if (e != cudaSuccess) return e;
     if (!out) return cudaSuccess;  // a recomputation for the backward needs the activations only
     k_proj<<<grid_of((long long)nb * np), 256, 0, st>>>(sd, w.z1, C, P + d.proj, out, add, d.skip ? r : nullptr);
@@ -703,7 +947,13 @@ cudaError_t forward_group(const FnoDef& d, const float* P, const FnoWS& w, const
     return cudaGetLastError();
 }
 
-cudaError_t set_fft_attrs() { return fft2d::set_attrs(); }
+// kernel attributes of the current device: the FFT kernels' and the mixing
+// kernel's shared-memory limits
+cudaError_t set_fft_attrs() {
+    cudaError_t e = fft2d::set_attrs();
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_mix_modes, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mix_smem(kMaxC));
+}
 
 }  // namespace
 
@@ -725,6 +975,7 @@ npbs_status fno_prepare(npbs_ctx* ctx, const Net& net, const Plan& pl, const std
     }
     if (off.empty()) return NPBS_OK;
     NPBS_CK(ctx, set_fft_attrs());
+    NPBS_CK(ctx, ensure_wt(d, net.params, net.version, st));
     NPBS_CK(ctx, ctx->net_ws.ensure(ws_layout(d, (int)off.size(), train, nullptr, nullptr)));
     NPBS_CK(ctx, ctx->work[5].ensure(sizeof(long long) * off.size()));
     long long* doff = static_cast<long long*>(ctx->work[5].p);
@@ -773,6 +1024,7 @@ npbs_status fno_prepare(npbs_ctx* ctx, const Net& net, const Plan& pl, const std
 npbs_status fno_run_forward(npbs_ctx* ctx, const Net& net, const NetRun& run, const float2* r, const float* a,
                             float2* out, int add, cudaStream_t st) {
     const FnoDef& d = *net.fno;
+    if (!run.groups.empty()) NPBS_CK(ctx, ensure_wt(d, net.params, net.version, st));
     for (const NetGroup& g : run.groups) {
         FnoWS w;
         ws_layout(d, g.sd.nb, run.train, &w, static_cast<char*>(ctx->net_ws.p));
@@ -794,6 +1046,7 @@ npbs_status fno_run_backward(npbs_ctx* ctx, Net& net, const NetRun& run, const f
     const int C = d.C;
     const float* P = net.params;
     float* dP = net.grads;
+    if (!run.groups.empty()) NPBS_CK(ctx, ensure_wt(d, P, net.version, st));
     for (const NetGroup& g : run.groups) {
         FnoWS w;
         ws_layout(d, g.sd.nb, true, &w, static_cast<char*>(ctx->net_ws.p));
@@ -809,12 +1062,12 @@ npbs_status fno_run_backward(npbs_ctx* ctx, Net& net, const NetRun& run, const f
         kc += 3;
         NPBS_CK(ctx, cudaGetLastError());
         // fusion layer, then the product
-        NPBS_CK(ctx, layer_bwd(d, w, nb, w.z, P + d.spec_f, dP + d.spec_f, d.m, P + d.loc_f, dP + d.loc_f, nullptr,
+        NPBS_CK(ctx, layer_bwd(d, w, nb, w.z, wt_of(d, d.L + 1), dP + d.spec_f, d.m, P + d.loc_f, dP + d.loc_f, nullptr,
                                w.g1, w.g2, st, &kc));
         k_mul_back<<<grid_of(cnt), 256, 0, st>>>(cnt, w.g2, w.c[d.L], w.x1, w.g1, w.dc);
         kc += 1;
         // residual layer and the lifting of r
-        NPBS_CK(ctx, layer_bwd(d, w, nb, w.x0, P + d.spec_r, dP + d.spec_r, d.fx, P + d.loc_r, dP + d.loc_r,
+        NPBS_CK(ctx, layer_bwd(d, w, nb, w.x0, wt_of(d, d.L), dP + d.spec_r, d.fx, P + d.loc_r, dP + d.loc_r,
                                nullptr, w.g1, w.g3, st, &kc));
         k_wgrad_points<<<304, 256, 0, st>>>(nb, np, w.g3, C, w.rp, 2, dP + d.lift_r, nullptr);
         k_lift_r_back<<<grid_of((long long)nb * np), 256, 0, st>>>(sd, w.g3, C, P + d.lift_r, gr, add,
@@ -825,7 +1078,7 @@ npbs_status fno_run_backward(npbs_ctx* ctx, Net& net, const NetRun& run, const f
         for (int l = d.L - 1; l >= 0; --l) {
             k_gelu_back<<<grid_of(cnt), 256, 0, st>>>(cnt, w.dc, w.pre[l], w.g1);
             kc += 1;
-            NPBS_CK(ctx, layer_bwd(d, w, nb, w.c[l], P + d.spec[l], dP + d.spec[l], d.m, P + d.loc_w[l],
+            NPBS_CK(ctx, layer_bwd(d, w, nb, w.c[l], wt_of(d, l), dP + d.spec[l], d.m, P + d.loc_w[l],
                                    dP + d.loc_w[l], dP + d.loc_b[l], w.g1, w.dc, st, &kc));
         }
         k_wgrad_points<<<304, 256, 0, st>>>(nb, np, w.dc, C, w.lnp, d.ca, dP + d.lift_a_w, dP + d.lift_a_b);

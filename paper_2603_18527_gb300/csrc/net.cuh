@@ -43,6 +43,12 @@ struct FnoDef {
     mutable const float* cache_a = nullptr;
     mutable unsigned long long cache_key = 0;
     mutable long long cache_version = -1;
+    // Mode-major copy of every spectral weight block, Wt[k][i][o] (complex;
+    // each mode's C x C block padded to an even length), layers in the order
+    // spec[0..L), spec_r, spec_f; valid for Net::version
+    // == wt_version (refreshed when a network run is prepared).
+    mutable float2* wt = nullptr;
+    mutable long long wt_version = -1;
 };
 FnoDef fno_def(int n, int C, int m, int L, int ca = 1);
 

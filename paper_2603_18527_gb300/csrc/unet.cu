@@ -536,6 +536,7 @@ Net::~Net() {
     if (fno) {
         cudaFree(fno->tw);
         cudaFree(fno->cache);
+        cudaFree(fno->wt);
         delete fno;
     }
 }
