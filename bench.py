@@ -305,11 +305,18 @@ def bench_extensions(capi, ctx, args, stream):
     na()
     ms = timed(stream, na, 20)
     fl = 16.0 * 64 ** 3 * len(ninst)
-    fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12  # SMs x FP32 lanes x FMA x maximum SM clock (TFLOP/s)
+    # side 64 runs on the tensor cores in TF32 with a three-term split: each useful flop costs three
+    # TF32 flops, against the TF32 dense rate (half the BF16 rate: measured BF16 x the nominal ratio)
+    bf16_burst, _, pk_kind = tensor_peak()
+    tf32x3_peak = bf16_burst * 0.5 / 3.0
+    hbm, hbm_kind = peaks()
+    gbs = 28.0 * 64 * 64 * len(ninst) / (ms * 1e-3) / 1e9  # read x, r (8 B), u (4 B); write out (8 B)
     out["newton_apply_64"] = {"instances": len(ninst), "mode": "RESIDUAL", "ms": ms,
-                              "tflops": fl / (ms * 1e-3) / 1e12, "fp32_peak_tflops": fp32_peak,
-                              "frac_of_fp32_peak": fl / (ms * 1e-3) / 1e12 / fp32_peak,
-                              "flop_per_instance": 16 * 64 ** 3}
+                              "kernel": "tcgen05 TF32 x3 (k_nt_apply_tc)",
+                              "tflops": fl / (ms * 1e-3) / 1e12, "tf32x3_peak_tflops": tf32x3_peak,
+                              "frac_of_tf32x3_peak": fl / (ms * 1e-3) / 1e12 / tf32x3_peak,
+                              "algorithmic_gbs": gbs, "frac_of_hbm": gbs / hbm, "peak_kind": pk_kind,
+                              "flop_per_instance": 16 * 64 ** 3, "bytes_per_point": 28}
     test = ninst[:100]
     tb = capi.Batch([(64, 64)] * len(test), h=[1.0 / 65] * len(test))
     tf = tb.pack([i.f for i in test], dtype=torch.float64)

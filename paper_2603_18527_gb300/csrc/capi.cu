@@ -635,8 +635,9 @@ npbs_status npbs_device_status(npbs_ctx* ctx) {
     if (!ctx) return NPBS_ERR_INVALID_ARG;
     NPBS_CK(ctx, cudaSetDevice(ctx->device));
     NPBS_CK(ctx, cudaDeviceSynchronize());
-    if (conv_tc_timeout_flag()) {
+    if (conv_tc_timeout_flag() || newton_tc_timeout_flag()) {
         conv_tc_clear_timeout();
+        newton_tc_clear_timeout();
         return set_err(ctx, NPBS_ERR_DEVICE_TIMEOUT,
                        "a bounded device wait gave up (a TMA or tensor-core stage never completed); the kernel "
                        "returned early and its results are invalid");

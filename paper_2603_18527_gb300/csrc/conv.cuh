@@ -59,6 +59,8 @@ cudaError_t conv_wgrad_tc(const ConvWgrad& a, cudaStream_t st);
 cudaError_t prepare_conv_tc();
 int conv_tc_timeout_flag();   // 1 once a bounded device wait gave up (synchronous read)
 void conv_tc_clear_timeout();
+int newton_tc_timeout_flag();  // the same for the tensor-core Newton apply (newton.cu)
+void newton_tc_clear_timeout();
 // One CTA waits on an mbarrier nothing arrives at for `seconds`, then gives up.
 cudaError_t wait_selftest(double seconds, cudaStream_t st);
 

@@ -24,6 +24,7 @@
 
 #include "ctx.cuh"
 #include "net.cuh"
+#include "umma.cuh"
 
 namespace npbs {
 namespace {
@@ -308,6 +309,263 @@ __global__ void k_nt_axpy(const NtInst* ins, const int* ids, const int* frozen, 
     }
 }
 
+// ---------------------------------------------------------------- tensor cores
+
+// The same apply on the 5th-generation tensor cores for side 64 (modes
+// RESIDUAL, OP_B, ADJ_B and kNtGreen).  G = S diag(w) (S q S) S is four real
+// 64 x 64 sine-matrix products of a complex tile, each one MMA of M = 128
+// (rows: real parts of 64 rows, then imaginary parts), N = 64, K = 64 against
+// S in TF32 with a three-term split (hi hi + hi lo + lo hi, hi = tf32(v), lo =
+// tf32(v - hi)), which keeps float32 accuracy.  The accumulator sits in TMEM,
+// lane = operand row; between products every thread moves its lane into the
+// next operand transposed (lane (p, a) holding columns b becomes column a of
+// rows (p, b)), which is a conflict-free row write of the swizzled tile, so
+// S q S, the symbol and S Z S chain without a separate transpose:
+//   A0 = q        -> D0[(p,i)][j] = (q S)[i][j]
+//   A1 = D0^T     -> D1[(p,j)][i] = (S q S)[i][j]   (scaled by w[i][j] on the way out)
+//   A2 = D1^T     -> D2[(p,i)][j] = (Z S)[i][j]
+//   A3 = D2^T     -> D3[(p,j)][i] = (S Z S)[i][j] = (G q)[i][j]
+// One CTA (eight warps: warp w reads TMEM lanes 32 (w % 4) .. + 31, columns
+// 32 (w / 4) .. + 31) walks instances blockIdx.x, blockIdx.x + gridDim.x, ...;
+// thread 0 issues the MMAs and waits (bounded) on their commit; a wait that
+// gives up sets g_nt_tc_timeout and the CTA stops.
+constexpr int kNtTcN = 64;
+constexpr int kNtTcBytes = 98304 + 1024 + 512;  // A hi/lo, S hi/lo, alignment slack, eig / flags
+__device__ int g_nt_tc_timeout = 0;
+
+// v = hi + lo as two TF32 values, each rounded to nearest (ties away from
+// zero) by adding half a unit of the 10-bit mantissa to the magnitude bits and
+// clearing the 13 bits below it; v - hi is exact in float32
+__device__ __forceinline__ uint32_t tf32_round(uint32_t b) { return (b + 0x1000u) & 0xffffe000u; }
+__device__ __forceinline__ void put_split(unsigned char* hi, unsigned char* lo, uint32_t off, float v) {
+    const uint32_t h = tf32_round(__float_as_uint(v));
+    const uint32_t l = tf32_round(__float_as_uint(v - __uint_as_float(h)));
+    *reinterpret_cast<uint32_t*>(hi + off) = h;
+    *reinterpret_cast<uint32_t*>(lo + off) = l;
+}
+
+constexpr int kNtTcThreads = 256;
+__global__ void __launch_bounds__(kNtTcThreads, 2) k_nt_apply_tc(const NtInst* ins, const int* ids, int cnt, const float* tab,
+                                                     const double* shift, const float* u, const float2* r,
+                                                     const float2* x, float2* out, double* norm2, int mode,
+                                                     long long wait_limit) {
+    using namespace umma;
+    extern __shared__ unsigned char smraw_tc[];
+    unsigned char* base = reinterpret_cast<unsigned char*>(((uintptr_t)smraw_tc + 1023) & ~(uintptr_t)1023);
+    unsigned char* Ah = base;           // operand A: 128 rows x 64, tf32 high parts (2 x 16 KB)
+    unsigned char* Al = base + 32768;   // low parts
+    unsigned char* Sh = base + 65536;   // the sine matrix as operand B: 64 rows x 64 (2 x 8 KB)
+    unsigned char* Sl = base + 81920;
+    float* eig = reinterpret_cast<float*>(base + 98304);
+    double* red = reinterpret_cast<double*>(eig + kNtTcN);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(red + kNtTcThreads / 32);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 1);
+    int* okflag = reinterpret_cast<int*>(tslot + 1);
+    float2* O = reinterpret_cast<float2*>(base);  // result staging over A once the last product is done
+    constexpr int n = kNtTcN, np = kNtTcN * kNtTcN;
+    const int t = threadIdx.x, w = t >> 5, lane = t & 31;
+    if (t == 0) {
+        mbar_init(su32(bar), 1);
+        *okflag = 1;
+    }
+    if (w == 0) tmem_alloc(tslot, 64);
+    {
+        // the table as float4 (4 per thread, all loads in flight before the stores)
+        float4 tv[np / 4 / kNtTcThreads];
+#pragma unroll
+        for (int m = 0; m < np / 4 / kNtTcThreads; ++m) tv[m] = reinterpret_cast<const float4*>(tab)[t + kNtTcThreads * m];
+#pragma unroll
+        for (int m = 0; m < np / 4 / kNtTcThreads; ++m) {
+            const int e = 4 * (t + kNtTcThreads * m), row = e >> 6, k = e & 63;
+            put_split(Sh, Sl, sw128_off(row, k, n), tv[m].x);
+            put_split(Sh, Sl, sw128_off(row, k + 1, n), tv[m].y);
+            put_split(Sh, Sl, sw128_off(row, k + 2, n), tv[m].z);
+            put_split(Sh, Sl, sw128_off(row, k + 3, n), tv[m].w);
+        }
+    }
+    if (t < n) eig[t] = tab[np + t];
+    fence_async_smem();
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    const uint32_t tmem = *tslot;
+    const uint32_t idesc = idesc_tf32(128, n);
+    // operand descriptors at the tile bases (shared addresses < 256 KB: the 14-bit
+    // start field never carries when a K sub-step is added)
+    const uint64_t dAh = desc_sw128(su32(Ah)), dAl = desc_sw128(su32(Al));
+    const uint64_t dSh = desc_sw128(su32(Sh)), dSl = desc_sw128(su32(Sl));
+    const float inv_h2 = (float)(n + 1) * (float)(n + 1);
+    const float sc = 4.f / inv_h2;
+    const int lrow = 32 * (w & 3) + lane;  // this thread's TMEM lane = operand row (part p, index a)
+    const int p = lrow >> 6, a = lrow & 63;
+    const int col0 = 32 * (w >> 2);          // and its half of the accumulator columns
+    uint32_t phase = 0;
+    bool ok = true;
+    for (int q = blockIdx.x; q < cnt && ok; q += gridDim.x) {
+        const NtInst in = ins[q];
+        const int j = ids[q];
+        const float c = (float)shift[j];
+        // the first operand in natural order: rows (part, i), column k.  Warp w
+        // takes the band of rows 8 w .. 8 w + 7, lanes = columns k and k + 32;
+        // the band's rows (with a halo row on each side), u and r are loaded
+        // before any is used, and the left / right neighbours come from the
+        // adjacent lanes.
+        const bool stencil = mode == NPBS_RESIDUAL || mode == NPBS_OP_B;
+        const bool with_r = mode == NPBS_RESIDUAL && r != nullptr;
+        {
+            const int i0 = 8 * w;
+            float2 X[10][2];
+            float U[8][2];
+            float2 R[8][2];
+#pragma unroll
+            for (int rr = 0; rr < 10; ++rr) {
+                const int i = i0 - 1 + rr;
+#pragma unroll
+                for (int h = 0; h < 2; ++h)
+                    X[rr][h] = (i >= 0 && i < n && (stencil || (rr >= 1 && rr <= 8)))
+                                   ? x[in.off + (long long)i * n + lane + 32 * h]
+                                   : make_float2(0.f, 0.f);
+            }
+#pragma unroll
+            for (int rr = 0; rr < 8; ++rr)
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const long long e = in.off + (long long)(i0 + rr) * n + lane + 32 * h;
+                    U[rr][h] = stencil ? u[e] : 0.f;
+                    R[rr][h] = with_r ? r[e] : make_float2(0.f, 0.f);
+                }
+#pragma unroll
+            for (int rr = 0; rr < 8; ++rr) {
+                const int i = i0 + rr;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int k = lane + 32 * h;
+                    const float2 cc = X[rr + 1][h];
+                    float2 v = cc;
+                    if (stencil) {
+                        // neighbours in the row: lanes +-1, across the two column halves at lanes 0 / 31
+                        const float2 o0 = X[rr + 1][0], o1 = X[rr + 1][1];
+                        float2 lf, rt;
+                        const float2 up0 = make_float2(__shfl_up_sync(0xffffffffu, o0.x, 1), __shfl_up_sync(0xffffffffu, o0.y, 1));
+                        const float2 up1 = make_float2(__shfl_up_sync(0xffffffffu, o1.x, 1), __shfl_up_sync(0xffffffffu, o1.y, 1));
+                        const float2 dn0 = make_float2(__shfl_down_sync(0xffffffffu, o0.x, 1), __shfl_down_sync(0xffffffffu, o0.y, 1));
+                        const float2 dn1 = make_float2(__shfl_down_sync(0xffffffffu, o1.x, 1), __shfl_down_sync(0xffffffffu, o1.y, 1));
+                        const float2 l31 = make_float2(__shfl_sync(0xffffffffu, o0.x, 31), __shfl_sync(0xffffffffu, o0.y, 31));
+                        const float2 r0 = make_float2(__shfl_sync(0xffffffffu, o1.x, 0), __shfl_sync(0xffffffffu, o1.y, 0));
+                        if (h == 0) {
+                            lf = lane == 0 ? make_float2(0.f, 0.f) : up0;
+                            rt = lane == 31 ? r0 : dn0;
+                        } else {
+                            lf = lane == 0 ? l31 : up1;
+                            rt = lane == 31 ? make_float2(0.f, 0.f) : dn1;
+                        }
+                        const float2 a1 = X[rr][h], a2 = X[rr + 2][h];
+                        const float sx = 4.f * cc.x - a1.x - a2.x - lf.x - rt.x;
+                        const float sy = 4.f * cc.y - a1.y - a2.y - lf.y - rt.y;
+                        const float uv = U[rr][h];
+                        v = make_float2(sx * inv_h2 - 2.f * uv * cc.x, sy * inv_h2 - 2.f * uv * cc.y);
+                        if (mode == NPBS_RESIDUAL) v = make_float2(R[rr][h].x - v.x, R[rr][h].y - v.y);
+                    }
+                    put_split(Ah, Al, sw128_off(i, k, 128), v.x);
+                    put_split(Ah, Al, sw128_off(n + i, k, 128), v.y);
+                }
+            }
+        }
+        for (int st = 0; st < 4; ++st) {
+            fence_async_smem();
+            fence_before_sync();
+            __syncthreads();
+            if (t == 0) {
+                fence_after_sync();
+                // a K sub-step moves the start address field (bytes / 16) of the base descriptors
+#pragma unroll
+                for (int kb = 0; kb < 2; ++kb)
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk) {
+                        const uint64_t ao = (uint64_t)((kb * 16384 + kk * 32) >> 4);
+                        const uint64_t bo = (uint64_t)((kb * 8192 + kk * 32) >> 4);
+                        mma_tf32(tmem, dAl + ao, dSh + bo, idesc, (kb | kk) ? 1u : 0u);
+                        mma_tf32(tmem, dAh + ao, dSl + bo, idesc, 1u);
+                        mma_tf32(tmem, dAh + ao, dSh + bo, idesc, 1u);
+                    }
+                commit(su32(bar));
+                if (!mbar_wait(su32(bar), phase, wait_limit)) {
+                    atomicExch(&g_nt_tc_timeout, 1);
+                    *okflag = 0;
+                }
+            }
+            phase ^= 1;
+            __syncthreads();
+            if (!*okflag) {
+                ok = false;
+                break;
+            }
+            fence_after_sync();
+            // this lane's 32 accumulator columns, 16 at a time
+            const float ea = eig[a] + c;
+#pragma unroll
+            for (int cq = 0; cq < 2; ++cq) {
+                const int cb = (col0 >> 4) + cq;
+                float v[16];
+                tmem_ld16(tmem + ((uint32_t)(32 * (w & 3)) << 16) + (uint32_t)(cb * 16), v);
+                if (st == 1) {
+                    // lane (p, j = a) holds (S q S)[i][a] over i: the Green symbol
+#pragma unroll
+                    for (int q2 = 0; q2 < 16; ++q2) v[q2] *= sc / (eig[cb * 16 + q2] + ea);
+                }
+                if (st < 3) {
+#pragma unroll
+                    for (int q2 = 0; q2 < 16; ++q2) put_split(Ah, Al, sw128_off(p * n + cb * 16 + q2, a, 128), v[q2]);
+                } else {
+                    // lane (p, j = a) holds (G q)[i][a] over i: stage it in natural order
+                    float* Of = reinterpret_cast<float*>(O);
+#pragma unroll
+                    for (int q2 = 0; q2 < 16; ++q2) Of[2 * ((cb * 16 + q2) * n + a) + p] = v[q2];
+                }
+            }
+        }
+        if (!ok) break;
+        fence_before_sync();
+        __syncthreads();
+        double acc = 0.0;
+#pragma unroll 8
+        for (int e = t; e < np; e += blockDim.x) {
+            float2 vv = O[e];
+            if (mode == NPBS_ADJ_B) {
+                // J (G x): the stencil on the staged tile
+                const int i = e >> 6, k = e & 63;
+                float2 s = make_float2(4.f * vv.x, 4.f * vv.y);
+                if (i > 0) { const float2 y = O[e - n]; s.x -= y.x; s.y -= y.y; }
+                if (i < n - 1) { const float2 y = O[e + n]; s.x -= y.x; s.y -= y.y; }
+                if (k > 0) { const float2 y = O[e - 1]; s.x -= y.x; s.y -= y.y; }
+                if (k < n - 1) { const float2 y = O[e + 1]; s.x -= y.x; s.y -= y.y; }
+                const float uv = u[in.off + e];
+                vv = make_float2(s.x * inv_h2 - 2.f * uv * vv.x, s.y * inv_h2 - 2.f * uv * vv.y);
+            }
+            out[in.off + e] = vv;
+            acc += (double)vv.x * vv.x + (double)vv.y * vv.y;
+        }
+        if (norm2) {
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            if (lane == 0) red[w] = acc;
+            __syncthreads();
+            if (t == 0) {
+                double tot = 0.0;
+                for (int q2 = 0; q2 < kNtTcThreads / 32; ++q2) tot += red[q2];
+                atomicAdd(norm2 + j, tot);
+            }
+        }
+        __syncthreads();  // the staging tile is the next instance's operand
+    }
+    if (!ok && t == 0) {
+        // a wait gave up: give the MMAs in flight one more bounded wait before TMEM is released
+        (void)mbar_wait(su32(bar), phase ^ 1, wait_limit);
+    }
+    fence_before_sync();
+    __syncthreads();
+    if (w == 0) tmem_dealloc(tmem, 64);
+}
+
 }  // namespace
 }  // namespace npbs
 
@@ -324,7 +582,16 @@ struct NtGroup {
 struct NtPrep {
     std::vector<NtGroup> groups;
     long long extent = 0;
+    int tc_ctas = 0;             // CTAs of the tensor-core apply (two per SM)
+    long long wait_limit = 0;    // its bounded waits, in clock cycles (about two seconds)
 };
+
+// The tensor-core apply serves side-64 groups unless NPBS_NEWTON_TC=0 (read
+// at each apply, so that the two kernels can be compared in one process).
+bool nt_tc_enabled() {
+    const char* e = getenv("NPBS_NEWTON_TC");
+    return !(e && e[0] == '0');
+}
 
 size_t nt_smem(int n) { return sizeof(float) * ((size_t)n * n + ((n + 3) & ~3)) + 2 * sizeof(float2) * (size_t)n * n; }
 
@@ -412,6 +679,15 @@ npbs_status nt_prepare(npbs_ctx* ctx, const npbs_batch* batch, NtPrep* P, cudaSt
     }
     NPBS_CK(ctx, cudaFuncSetAttribute(k_nt_apply, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)nt_smem(kNtMaxN)));
+    NPBS_CK(ctx, cudaFuncSetAttribute(k_nt_apply_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kNtTcBytes));
+    {
+        int dev = 0, sms = 0, khz = 0;
+        NPBS_CK(ctx, cudaGetDevice(&dev));
+        NPBS_CK(ctx, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        NPBS_CK(ctx, cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev));
+        P->tc_ctas = 2 * std::max(1, sms);
+        P->wait_limit = 2LL * std::max(1, khz) * 1000;
+    }
     auto cached = std::make_shared<NtCached>();
     cached->desc = std::move(desc);
     cached->P = *P;
@@ -423,8 +699,13 @@ npbs_status nt_prepare(npbs_ctx* ctx, const npbs_batch* batch, NtPrep* P, cudaSt
 npbs_status nt_run(npbs_ctx* ctx, const NtPrep& P, int mode, const double* shift, const float* u, const float2* r,
                    const float2* x, float2* out, double* norm2, int count, cudaStream_t st) {
     if (norm2) NPBS_CK(ctx, cudaMemsetAsync(norm2, 0, sizeof(double) * count, st));
+    const bool tc = mode != NPBS_TRUE_RESIDUAL && nt_tc_enabled();
     for (const NtGroup& g : P.groups) {
-        k_nt_apply<<<g.cnt, 256, nt_smem(g.n), st>>>(g.ins, g.ids, g.tab, shift, u, r, x, out, norm2, mode);
+        if (tc && g.n == kNtTcN)
+            k_nt_apply_tc<<<std::min(g.cnt, P.tc_ctas), kNtTcThreads, kNtTcBytes, st>>>(g.ins, g.ids, g.cnt, g.tab, shift, u,
+                                                                             r, x, out, norm2, mode, P.wait_limit);
+        else
+            k_nt_apply<<<g.cnt, 256, nt_smem(g.n), st>>>(g.ins, g.ids, g.tab, shift, u, r, x, out, norm2, mode);
         NPBS_CK(ctx, cudaGetLastError());
         ctx->count(st, 1);
     }
@@ -444,6 +725,21 @@ const Plan* nt_net_plan(npbs_ctx* ctx, const npbs_batch* batch, npbs_status* st)
 }
 
 }  // namespace
+}  // namespace npbs
+
+namespace npbs {
+
+// 1 once a bounded wait of the tensor-core apply gave up (synchronous read), and its reset
+int newton_tc_timeout_flag() {
+    int v = 0;
+    cudaMemcpyFromSymbol(&v, g_nt_tc_timeout, sizeof(int));
+    return v;
+}
+void newton_tc_clear_timeout() {
+    const int z = 0;
+    cudaMemcpyToSymbol(g_nt_tc_timeout, &z, sizeof(int));
+}
+
 }  // namespace npbs
 
 using namespace npbs;

@@ -211,3 +211,42 @@ def test_newton_step_in_the_direct_format_follows_the_oracle():
     # eps32 ||J|| ||delta|| (||J|| ~ 8/h^2 = 8.7e3 at N = 32) before the network
     # amplifies it: three steps give a few 1e-5 relative to u
     assert rel_l2(u.cpu().numpy().reshape(32, 32), ref.numpy()) <= 1e-4
+
+
+@pytest.mark.parametrize("mode", ["RESIDUAL", "OP_B", "ADJ_B"])
+def test_newton_tensor_core_apply_matches_cuda_core_apply(mode, monkeypatch):
+    """Side-64 groups run on the tensor cores (TF32 with a three-term split);
+    NPBS_NEWTON_TC=0 selects the float32 CUDA-core kernel.  On 400 instances
+    (more than the persistent grid, so CTAs walk several instances) the two
+    agree to float32 accuracy instance by instance, with their norms, and a
+    sample of instances matches the oracle."""
+    capi, c = ctx()
+    sizes = [64] * 400
+    b = _batch(capi, sizes)
+    st = _states(sizes[:4], 70)
+    rng = np.random.default_rng(5)
+    shifts = [st[j % 4].shift for j in range(len(sizes))]
+    u32 = b.pack([st[j % 4].u.numpy() for j in range(len(sizes))], dtype=torch.float32)
+    xs = [random_field((64, 64), 100 + j) for j in range(len(sizes))]
+    rs = [random_field((64, 64), 900 + j) * 100.0 for j in range(len(sizes))]
+    x, r = b.pack(xs), b.pack(rs)
+    outs, norms = [], []
+    for flag in ("1", "0"):
+        monkeypatch.setenv("NPBS_NEWTON_TC", flag)
+        out = torch.zeros_like(x)
+        n2 = torch.zeros(b.count, dtype=torch.float64, device="cuda")
+        capi.newton_apply(c, b, shifts, u32, r, x, out, getattr(capi, mode), n2)
+        torch.cuda.synchronize()
+        outs.append(b.unpack(out))
+        norms.append(n2.cpu().numpy())
+    assert capi.npbs_device_status(c) == capi.OK
+    for j in range(len(sizes)):
+        assert rel_l2(outs[0][j], outs[1][j]) <= 2e-5, (j, rel_l2(outs[0][j], outs[1][j]))
+    assert np.allclose(norms[0], norms[1], rtol=5e-5)
+    for j in rng.choice(len(sizes), size=4, replace=False):
+        s = st[j % 4]
+        X = torch.from_numpy(xs[j].astype(np.complex64).astype(np.complex128))
+        R = torch.from_numpy(rs[j].astype(np.complex64).astype(np.complex128))
+        ref = {"RESIDUAL": lambda: NW.born_residual(s, X, R), "OP_B": lambda: NW.op_B(s, X),
+               "ADJ_B": lambda: NW.op_BH(s, X)}[mode]().numpy()
+        assert rel_l2(outs[0][j], ref) <= 2e-4, (j, rel_l2(outs[0][j], ref))
