@@ -9,8 +9,11 @@
 //
 // Three launches per apply over the whole batch (every instance of every
 // size in the same launch, one work item per band of rows or columns).  The
-// intermediate spectrum lives in a context-owned scratch buffer.
+// intermediate spectrum lives in a context-owned scratch buffer.  The float64
+// refresh (kTrueRes64) instantiates the same kernels with the double-single
+// real type of dsfloat.cuh.
 #include "apply.cuh"
+#include "dsfloat.cuh"
 #include "fft.cuh"
 
 namespace npbs {
@@ -31,7 +34,9 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
 
 template <typename R> __device__ __forceinline__ const cpx<R>* twiddles(const BatchDev& bd, int off);
 template <> __device__ __forceinline__ const float2* twiddles<float>(const BatchDev& bd, int off) { return bd.tw32 + off; }
-template <> __device__ __forceinline__ const double2* twiddles<double>(const BatchDev& bd, int off) { return bd.tw64 + off; }
+template <> __device__ __forceinline__ const dscpx* twiddles<dsf>(const BatchDev& bd, int off) {
+    return reinterpret_cast<const dscpx*>(bd.twds + off);
+}
 
 // ---------------------------------------------------------------- kernel 1
 template <typename R, int MODE>
@@ -60,7 +65,7 @@ __global__ void __launch_bounds__(kThreads) k_rows_forward(BatchDev bd, ApplyArg
                 u.y += (double)d.y;
                 a.uhi[g] = u;
             }
-            q = u;
+            q = from_double2<C>(u);
         } else {
             const float2 x = ld(a.x + g);
             if constexpr (MODE == NPBS_RESIDUAL || MODE == NPBS_CBS_STEP) {
@@ -179,8 +184,8 @@ __global__ void __launch_bounds__(kThreads) k_rows_inverse(BatchDev bd, ApplyArg
                 kr = (double)v.x + in.k0sq;
                 ki = (double)v.y + in.eps;
             }
-            const double rr = (double)f.x + kr * u.x - ki * u.y - zr;
-            const double ri = (double)f.y + kr * u.y + ki * u.x - zi;
+            const double rr = (double)f.x + kr * u.x - ki * u.y - to_double(zr);
+            const double ri = (double)f.y + kr * u.y + ki * u.x - to_double(zi);
             if (a.out) a.out[g] = make_float2((float)rr, (float)ri);
             acc += rr * rr + ri * ri;
             acc2 += (double)f.x * f.x + (double)f.y * f.y;
@@ -257,7 +262,7 @@ cudaError_t prepare_apply() {
     if (e == cudaSuccess) e = set_attrs<float, NPBS_ADJ_B>();
     if (e == cudaSuccess) e = set_attrs<float, NPBS_TRUE_RESIDUAL>();
     if (e == cudaSuccess) e = set_attrs<float, NPBS_PREC_SWEEP>();
-    if (e == cudaSuccess) e = set_attrs<double, kTrueRes64>();
+    if (e == cudaSuccess) e = set_attrs<dsf, kTrueRes64>();
     return e;
 }
 
@@ -280,7 +285,7 @@ cudaError_t launch_apply(int mode, const BatchDev& bd, int nrow_items, int ncol_
         case NPBS_ADJ_B: return launch3<float, NPBS_ADJ_B>(bd, nrow_items, ncol_items, a, st);
         case NPBS_TRUE_RESIDUAL: return launch3<float, NPBS_TRUE_RESIDUAL>(bd, nrow_items, ncol_items, a, st);
         case NPBS_PREC_SWEEP: return launch3<float, NPBS_PREC_SWEEP>(bd, nrow_items, ncol_items, a, st);
-        case kTrueRes64: return launch3<double, kTrueRes64>(bd, nrow_items, ncol_items, a, st);
+        case kTrueRes64: return launch3<dsf, kTrueRes64>(bd, nrow_items, ncol_items, a, st);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -278,7 +278,7 @@ extern "C" npbs_status cbs_apply_static(const npbs_batch* batch, const void* V, 
     bd.inst = dp->inst;
     bd.plans = dp->plans;
     bd.tw32 = dp->tw32;
-    bd.tw64 = nullptr;
+    bd.twds = nullptr;
     bd.rows = dp->rows;
     bd.cols = dp->cols;
     bd.active = nullptr;

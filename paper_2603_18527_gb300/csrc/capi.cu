@@ -14,7 +14,7 @@ Plan::~Plan() {
     cudaFree(inst);
     cudaFree(plans);
     cudaFree(tw32);
-    cudaFree(tw64);
+    cudaFree(twds);
     cudaFree(rows32);
     cudaFree(cols32);
     cudaFree(rows64);
@@ -90,7 +90,7 @@ const Plan* get_plan(npbs_ctx* ctx, const npbs_batch* batch, npbs_status* st) {
     std::map<int, int> plan_of, tw_of;
     std::vector<RadixPlan> plans;
     std::vector<float2> tw32;
-    std::vector<double2> tw64;
+    std::vector<float4> twds;
     auto add_n = [&](int n) -> bool {
         if (plan_of.count(n)) return true;
         RadixPlan rp;
@@ -100,7 +100,9 @@ const Plan* get_plan(npbs_ctx* ctx, const npbs_batch* batch, npbs_status* st) {
         tw_of[n] = (int)tw32.size();
         for (int k = 0; k < n; ++k) {
             const double a = -2.0 * M_PI * (double)k / (double)n;
-            tw64.push_back(make_double2(std::cos(a), std::sin(a)));
+            const double c = std::cos(a), s = std::sin(a);
+            const float ch = (float)c, sh = (float)s;
+            twds.push_back(make_float4(ch, (float)(c - (double)ch), sh, (float)(s - (double)sh)));
             tw32.push_back(make_float2((float)std::cos(a), (float)std::sin(a)));
         }
         return true;
@@ -165,7 +167,7 @@ const Plan* get_plan(npbs_ctx* ctx, const npbs_batch* batch, npbs_status* st) {
     if (e == cudaSuccess) e = upload(&pl->inst, pl->inst_h);
     if (e == cudaSuccess) e = upload(&pl->plans, plans);
     if (e == cudaSuccess) e = upload(&pl->tw32, tw32);
-    if (e == cudaSuccess) e = upload(&pl->tw64, tw64);
+    if (e == cudaSuccess) e = upload(&pl->twds, twds);
     if (e == cudaSuccess) e = upload(&pl->rows32, r32);
     if (e == cudaSuccess) e = upload(&pl->cols32, c32);
     if (e == cudaSuccess) e = upload(&pl->rows64, r64);

@@ -64,7 +64,7 @@ struct BatchDev {
     const InstDev* inst;
     const RadixPlan* plans;
     const float2* tw32;      // W_N^k = exp(-2 pi i k / N), per distinct N
-    const double2* tw64;
+    const float4* twds;      // the same in double-single (re hi, re lo, im hi, im lo): float64 refresh
     const RowItem* rows;
     const ColItem* cols;
     const int* active;       // nullable: per-instance mask (0 = skip)

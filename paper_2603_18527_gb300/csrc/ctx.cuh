@@ -22,7 +22,7 @@ struct Plan {
     InstDev* inst = nullptr;
     RadixPlan* plans = nullptr;
     float2* tw32 = nullptr;
-    double2* tw64 = nullptr;
+    float4* twds = nullptr;
     RowItem* rows32 = nullptr;
     ColItem* cols32 = nullptr;
     RowItem* rows64 = nullptr;
@@ -53,7 +53,7 @@ struct Plan {
         b.inst = inst;
         b.plans = plans;
         b.tw32 = tw32;
-        b.tw64 = tw64;
+        b.twds = twds;
         b.rows = f64 ? rows64 : rows32;
         b.cols = f64 ? cols64 : cols32;
         b.active = active;

@@ -83,3 +83,22 @@ def test_warm_start_from_a_converged_solution():
     st, rep2 = capi.cbs_solve(c, b, k2, f, u, rtol=1e-5, max_iter=20000, check_every=16)
     assert st == capi.OK and rep2["iters"] == [0, 0]
     assert torch.equal(u, u0)
+
+
+def test_refresh_precision_reaches_1e9():
+    """The float64 refresh (double-single transforms, float64 epilogue) stays
+    the arbiter well below the float32 floor: two small instances solved to
+    rTol 1e-9 meet it by the oracle's complex128 residual, and the reported
+    rTol equals the oracle's to 1e-3 relative (a 48-bit transform errs by about
+    1e-13 of ||f||, 1e-4 of a 1e-9 residual)."""
+    capi, c = ctx()
+    insts = [synth.small_instance(64, 64, seed=41, layer=8), synth.small_instance(48, 96, seed=42)]
+    b, k2, f, n, V = setup_batch(capi, c, insts)
+    u = torch.zeros(b.extent, dtype=torch.complex128, device="cuda")
+    st, rep = capi.cbs_solve(c, b, k2, f, u, rtol=1e-9, max_iter=40000, check_every=16)
+    assert st == capi.OK, rep
+    got = b.unpack(u)
+    for j, inst in enumerate(insts):
+        r = H.rtol(oracle_problem(inst), torch.from_numpy(got[j]))
+        assert r <= 1e-9, (j, r)
+        assert rep["rtol"][j] == pytest.approx(r, rel=1e-3), (j, r, rep["rtol"][j])
