@@ -44,16 +44,20 @@ __global__ void __launch_bounds__(256) k_rows(C* data, const long long* off, int
     for (int e = threadIdx.x; e < cnt; e += blockDim.x) p[e] = res[e];
 }
 
-// cb columns of one field per block, the transform along each column
+// cb columns of one field per block, the transform along each column; only
+// the first nlo and the last nhi column blocks of every field (all of them
+// when nlo + nhi covers the field)
 template <typename C, int DIR, int N = 0, int CB = 0>
 __global__ void __launch_bounds__(256) k_cols(C* data, const long long* off, int n_, int cb_, RadixPlan plan,
-                                              const C* tw) {
+                                              const C* tw, int nlo, int nhi) {
     extern __shared__ __align__(16) unsigned char smraw[];
     C* sm = reinterpret_cast<C*>(smraw);
     const int n = N ? N : n_, cb = N ? CB : cb_;
-    const int nb = n / cb;
-    const long long field = blockIdx.x / nb;
-    C* p = data + (off ? off[field] : field * n * n) + (long long)(blockIdx.x % nb) * cb;
+    const int nb = n / cb, nsel = nlo + nhi;
+    const long long field = blockIdx.x / nsel;
+    const int bi = (int)(blockIdx.x % nsel);
+    const int blk = bi < nlo ? bi : nb - nhi + (bi - nlo);
+    C* p = data + (off ? off[field] : field * n * n) + (long long)blk * cb;
     const int cnt = cb * n;
     for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
         const int i = e / cb, b = e - i * cb;
@@ -96,31 +100,48 @@ template <typename C> inline cudaError_t set_attrs_of() {
 
 inline cudaError_t set_attrs() { return set_attrs_of<float2>(); }
 
+// Forward: rows, then the selected column blocks.  Inverse: the selected
+// column blocks first (the others must hold zeros), then rows.  The two
+// orders give the same 2D transform where every column is transformed.
 template <typename C, int N, int RB, int CB>
-inline void launch(C* data, const long long* off, long long fields, int n, int rb, int cb, int dir,
-                   const RadixPlan& plan, const C* tw, cudaStream_t st) {
+inline void launch(C* data, const long long* off, long long fields, int n, int rb, int cb, int dir, int nlo,
+                   int nhi, const RadixPlan& plan, const C* tw, cudaStream_t st) {
     const size_t sm = 2 * kTile * sizeof(C);
+    const unsigned gr = (unsigned)(fields * (n / rb)), gc = (unsigned)(fields * (nlo + nhi));
     if (dir < 0) {
-        k_rows<C, -1, N, RB><<<(unsigned)(fields * (n / rb)), 256, sm, st>>>(data, off, n, rb, plan, tw);
-        k_cols<C, -1, N, CB><<<(unsigned)(fields * (n / cb)), 256, sm, st>>>(data, off, n, cb, plan, tw);
+        k_rows<C, -1, N, RB><<<gr, 256, sm, st>>>(data, off, n, rb, plan, tw);
+        k_cols<C, -1, N, CB><<<gc, 256, sm, st>>>(data, off, n, cb, plan, tw, nlo, nhi);
     } else {
-        k_rows<C, 1, N, RB><<<(unsigned)(fields * (n / rb)), 256, sm, st>>>(data, off, n, rb, plan, tw);
-        k_cols<C, 1, N, CB><<<(unsigned)(fields * (n / cb)), 256, sm, st>>>(data, off, n, cb, plan, tw);
+        k_cols<C, 1, N, CB><<<gc, 256, sm, st>>>(data, off, n, cb, plan, tw, nlo, nhi);
+        k_rows<C, 1, N, RB><<<gr, 256, sm, st>>>(data, off, n, rb, plan, tw);
     }
 }
 
-// 2D transform of `fields` fields in place (dir < 0 forward, > 0 inverse)
+// 2D transform of `fields` fields in place (dir < 0 forward, > 0 inverse).
+// kx > 0: only columns 0 .. kx - 1 and n - kx + 1 .. n - 1 matter (the
+// retained modes of a real field's half-plane spectrum and their mirrors):
+// a forward transform computes those columns only (the others hold row
+// spectra), an inverse one requires the others to be zero.
 template <typename C>
 inline cudaError_t run(C* data, const long long* off, long long fields, int n, int dir, const RadixPlan& plan,
-                       const C* tw, cudaStream_t st) {
+                       const C* tw, cudaStream_t st, int kx = 0) {
     const int rb = largest_divisor_at_most(n, kTile / n), cb = largest_divisor_at_most(n, std::min(16, kTile / n));
+    const int nb = n / cb;
+    int nlo = nb, nhi = 0;
+    if (kx > 0) {
+        const int lo = (kx + cb - 1) / cb, hi = (kx - 1 + cb - 1) / cb;
+        if (lo + hi < nb) {
+            nlo = lo;
+            nhi = hi;
+        }
+    }
     if constexpr (std::is_same<C, float2>::value) {
-        if (n == 64 && rb == 64 && cb == 16) launch<C, 64, 64, 16>(data, off, fields, n, rb, cb, dir, plan, tw, st);
-        else if (n == 128 && rb == 32 && cb == 16) launch<C, 128, 32, 16>(data, off, fields, n, rb, cb, dir, plan, tw, st);
-        else if (n == 256 && rb == 16 && cb == 16) launch<C, 256, 16, 16>(data, off, fields, n, rb, cb, dir, plan, tw, st);
-        else launch<C, 0, 0, 0>(data, off, fields, n, rb, cb, dir, plan, tw, st);
+        if (n == 64 && rb == 64 && cb == 16) launch<C, 64, 64, 16>(data, off, fields, n, rb, cb, dir, nlo, nhi, plan, tw, st);
+        else if (n == 128 && rb == 32 && cb == 16) launch<C, 128, 32, 16>(data, off, fields, n, rb, cb, dir, nlo, nhi, plan, tw, st);
+        else if (n == 256 && rb == 16 && cb == 16) launch<C, 256, 16, 16>(data, off, fields, n, rb, cb, dir, nlo, nhi, plan, tw, st);
+        else launch<C, 0, 0, 0>(data, off, fields, n, rb, cb, dir, nlo, nhi, plan, tw, st);
     } else {
-        launch<C, 0, 0, 0>(data, off, fields, n, rb, cb, dir, plan, tw, st);
+        launch<C, 0, 0, 0>(data, off, fields, n, rb, cb, dir, nlo, nhi, plan, tw, st);
     }
     return cudaGetLastError();
 }

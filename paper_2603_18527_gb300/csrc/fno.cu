@@ -781,8 +781,10 @@ size_t ws_layout(const FnoDef& d, int nb, bool train, FnoWS* w, char* base) {
 // the coefficient activation after layer l (inference keeps two buffers)
 float* coef(const FnoWS& w, const FnoDef& d, int l, bool train) { return train ? w.c[l] : w.c[l & 1]; }
 
-cudaError_t fft2(const FnoDef& d, float2* Z, long long fields, int dir, cudaStream_t st) {
-    return fft2d::run(Z, nullptr, fields, d.n, dir, d.plan, d.tw, st);
+// 2D transforms of Z; kx: the retained columns (and their mirrors) of the
+// layer, so that a layer with few modes transforms only those columns
+cudaError_t fft2(const FnoDef& d, float2* Z, long long fields, int dir, cudaStream_t st, int kx) {
+    return fft2d::run(Z, nullptr, fields, d.n, dir, d.plan, d.tw, st, kx);
 }
 
 // Spectral layer j's block of the mode-major weight copy: j < L the NLFL
@@ -829,7 +831,7 @@ cudaError_t spectra(const FnoDef& d, const FnoWS& w, int nb, const float* x, int
     const int P = (Ci + 1) / 2;
     const int Kx = std::min(m, d.n / 2 + 1), K = rows_kept(d.n, m) * Kx;
     k_pack<<<grid2(np, nb * P), 256, 0, st>>>(nb, (int)np, x, Ci, w.Zp);
-    cudaError_t e = fft2(d, w.Zp, (long long)nb * P, -1, st);
+    cudaError_t e = fft2(d, w.Zp, (long long)nb * P, -1, st, Kx);
     if (e != cudaSuccess) return e;
     k_extract<<<dim3((unsigned)((K + 31) / 32), (unsigned)((nb * Ci + 31) / 32)), dim3(32, 8), 0, st>>>(
         nb, d.n, m, Kx, K, w.Zp, Ci, X);
@@ -846,7 +848,7 @@ cudaError_t synthesize(const FnoDef& d, const FnoWS& w, int nb, const float2* Y,
     const int Q = (Co + 1) / 2;
     const int Kx = std::min(m, d.n / 2 + 1), K = rows_kept(d.n, m) * Kx;
     k_hermite<<<(unsigned)((np + 31) / 32), dim3(32, 8), 0, st>>>(nb, d.n, m, Kx, K, Y, Co, w.Zp);
-    cudaError_t e = fft2(d, w.Zp, (long long)nb * Q, 1, st);
+    cudaError_t e = fft2(d, w.Zp, (long long)nb * Q, 1, st, Kx);
     if (e != cudaSuccess) return e;
     k_mix_points<<<grid_of((long long)nb * np / 2), 256, 0, st>>>(nb, np, x, Ci, wl, so, si, bias, w.Zp,
                                                               1.f / (float)np, Co, act, pre, mul, out, add);
