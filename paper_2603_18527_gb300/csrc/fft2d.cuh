@@ -26,19 +26,42 @@ __device__ __forceinline__ C* tile(C* a, C* b, const RadixPlan& plan, int nb, in
     else return fft_tile<C, DIR, COLS>(a, b, plan, nb, si, sb, tw, threadIdx.x, blockDim.x);
 }
 
+// Real channel planes feeding a forward transform: field f = b * P + j of
+// the transform is (channel 2 j) + i (channel 2 j + 1) of sample b of planes
+// x [nb][ci][n n] (P = ceil(ci / 2); a missing odd channel is zero).
+struct RealPairs {
+    const float* x = nullptr;
+    int ci = 0;
+};
+
 // rb rows of one field per block, the transform along each row (N > 0: the
-// side and RB = rb are compile-time constants)
+// side and RB = rb are compile-time constants); src.x non-null: the rows are
+// loaded from real channel pairs instead of the field
 template <typename C, int DIR, int N = 0, int RB = 0>
 __global__ void __launch_bounds__(256) k_rows(C* data, const long long* off, int n_, int rb_, RadixPlan plan,
-                                              const C* tw) {
+                                              const C* tw, RealPairs src) {
     extern __shared__ __align__(16) unsigned char smraw[];
     C* sm = reinterpret_cast<C*>(smraw);
     const int n = N ? N : n_, rb = N ? RB : rb_;
     const int nb = n / rb;
     const long long field = blockIdx.x / nb;
-    C* p = data + (off ? off[field] : field * n * n) + (long long)(blockIdx.x % nb) * rb * n;
+    const long long r0 = (long long)(blockIdx.x % nb) * rb * n;
+    C* p = data + (off ? off[field] : field * n * n) + r0;
     const int cnt = rb * n;
-    for (int e = threadIdx.x; e < cnt; e += blockDim.x) sm[e] = p[e];
+    if (src.x) {
+        const int P = (src.ci + 1) / 2;
+        const long long b = field / P, j = field - b * P, np = (long long)n * n;
+        const float* re = src.x + (b * src.ci + 2 * j) * np + r0;
+        const bool has_im = 2 * j + 1 < src.ci;
+        for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+            C v;
+            v.x = re[e];
+            v.y = has_im ? re[np + e] : 0.f;
+            sm[e] = v;
+        }
+    } else {
+        for (int e = threadIdx.x; e < cnt; e += blockDim.x) sm[e] = p[e];
+    }
     __syncthreads();
     C* res = tile<C, N, RB, 1, N, DIR, false>(sm, sm + kTile, plan, rb, 1, n, tw);
     for (int e = threadIdx.x; e < cnt; e += blockDim.x) p[e] = res[e];
@@ -105,15 +128,15 @@ inline cudaError_t set_attrs() { return set_attrs_of<float2>(); }
 // orders give the same 2D transform where every column is transformed.
 template <typename C, int N, int RB, int CB>
 inline void launch(C* data, const long long* off, long long fields, int n, int rb, int cb, int dir, int nlo,
-                   int nhi, const RadixPlan& plan, const C* tw, cudaStream_t st) {
+                   int nhi, const RadixPlan& plan, const C* tw, cudaStream_t st, RealPairs src) {
     const size_t sm = 2 * kTile * sizeof(C);
     const unsigned gr = (unsigned)(fields * (n / rb)), gc = (unsigned)(fields * (nlo + nhi));
     if (dir < 0) {
-        k_rows<C, -1, N, RB><<<gr, 256, sm, st>>>(data, off, n, rb, plan, tw);
+        k_rows<C, -1, N, RB><<<gr, 256, sm, st>>>(data, off, n, rb, plan, tw, src);
         k_cols<C, -1, N, CB><<<gc, 256, sm, st>>>(data, off, n, cb, plan, tw, nlo, nhi);
     } else {
         k_cols<C, 1, N, CB><<<gc, 256, sm, st>>>(data, off, n, cb, plan, tw, nlo, nhi);
-        k_rows<C, 1, N, RB><<<gr, 256, sm, st>>>(data, off, n, rb, plan, tw);
+        k_rows<C, 1, N, RB><<<gr, 256, sm, st>>>(data, off, n, rb, plan, tw, RealPairs{});
     }
 }
 
@@ -121,10 +144,11 @@ inline void launch(C* data, const long long* off, long long fields, int n, int r
 // kx > 0: only columns 0 .. kx - 1 and n - kx + 1 .. n - 1 matter (the
 // retained modes of a real field's half-plane spectrum and their mirrors):
 // a forward transform computes those columns only (the others hold row
-// spectra), an inverse one requires the others to be zero.
+// spectra), an inverse one requires the others to be zero.  src (forward,
+// float2 fields without offsets only): read the input from real channel pairs.
 template <typename C>
 inline cudaError_t run(C* data, const long long* off, long long fields, int n, int dir, const RadixPlan& plan,
-                       const C* tw, cudaStream_t st, int kx = 0) {
+                       const C* tw, cudaStream_t st, int kx = 0, RealPairs src = RealPairs{}) {
     const int rb = largest_divisor_at_most(n, kTile / n), cb = largest_divisor_at_most(n, std::min(16, kTile / n));
     const int nb = n / cb;
     int nlo = nb, nhi = 0;
@@ -136,12 +160,12 @@ inline cudaError_t run(C* data, const long long* off, long long fields, int n, i
         }
     }
     if constexpr (std::is_same<C, float2>::value) {
-        if (n == 64 && rb == 64 && cb == 16) launch<C, 64, 64, 16>(data, off, fields, n, rb, cb, dir, nlo, nhi, plan, tw, st);
-        else if (n == 128 && rb == 32 && cb == 16) launch<C, 128, 32, 16>(data, off, fields, n, rb, cb, dir, nlo, nhi, plan, tw, st);
-        else if (n == 256 && rb == 16 && cb == 16) launch<C, 256, 16, 16>(data, off, fields, n, rb, cb, dir, nlo, nhi, plan, tw, st);
-        else launch<C, 0, 0, 0>(data, off, fields, n, rb, cb, dir, nlo, nhi, plan, tw, st);
+        if (n == 64 && rb == 64 && cb == 16) launch<C, 64, 64, 16>(data, off, fields, n, rb, cb, dir, nlo, nhi, plan, tw, st, src);
+        else if (n == 128 && rb == 32 && cb == 16) launch<C, 128, 32, 16>(data, off, fields, n, rb, cb, dir, nlo, nhi, plan, tw, st, src);
+        else if (n == 256 && rb == 16 && cb == 16) launch<C, 256, 16, 16>(data, off, fields, n, rb, cb, dir, nlo, nhi, plan, tw, st, src);
+        else launch<C, 0, 0, 0>(data, off, fields, n, rb, cb, dir, nlo, nhi, plan, tw, st, src);
     } else {
-        launch<C, 0, 0, 0>(data, off, fields, n, rb, cb, dir, nlo, nhi, plan, tw, st);
+        launch<C, 0, 0, 0>(data, off, fields, n, rb, cb, dir, nlo, nhi, plan, tw, st, RealPairs{});
     }
     return cudaGetLastError();
 }

@@ -44,11 +44,6 @@ constexpr int kMaxC = 32;     // channel bound of the register-blocked kernels
 constexpr int kModesPerBlock = 8;
 
 int grid_of(long long n, int per = 256) { return (int)std::min<long long>((n + per - 1) / per, 152LL * 64); }
-// grid of the points x fields kernels: 256-thread blocks along the points,
-// one field per block row (fields past 65535 are looped over)
-dim3 grid2(long long points, long long fields) {
-    return dim3((unsigned)((points + 255) / 256), (unsigned)std::max(1LL, std::min<long long>(fields, 65535)));
-}
 
 // rows of the compact mode list for m retained modes: min(ky, n - ky) < m
 __host__ __device__ inline int rows_kept(int n, int m) {
@@ -226,21 +221,6 @@ __global__ void __launch_bounds__(256) k_mix_points(int nb, long long np, const 
                 *reinterpret_cast<float2*>(out + oi) = make_float2(v0, v1);
             }
         }
-    }
-}
-
-// pack real channel planes [nb][Ci][np] into complex pair fields [nb][P][np]
-// (grid: points x fields, field f = b * P + j)
-__global__ void k_pack(int nb, int np, const float* __restrict__ x, int Ci, float2* __restrict__ Z) {
-    const int P = (Ci + 1) / 2;
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= np) return;
-    for (int f = blockIdx.y; f < nb * P; f += gridDim.y) {
-        const int b = f / P, j = f - b * P;
-        const float* xb = x + ((long long)b * Ci + 2 * j) * np + p;
-        const float re = xb[0];
-        const float im = 2 * j + 1 < Ci ? xb[np] : 0.f;
-        Z[(long long)f * np + p] = make_float2(re, im);
     }
 }
 
@@ -783,8 +763,9 @@ float* coef(const FnoWS& w, const FnoDef& d, int l, bool train) { return train ?
 
 // 2D transforms of Z; kx: the retained columns (and their mirrors) of the
 // layer, so that a layer with few modes transforms only those columns
-cudaError_t fft2(const FnoDef& d, float2* Z, long long fields, int dir, cudaStream_t st, int kx) {
-    return fft2d::run(Z, nullptr, fields, d.n, dir, d.plan, d.tw, st, kx);
+cudaError_t fft2(const FnoDef& d, float2* Z, long long fields, int dir, cudaStream_t st, int kx,
+                 fft2d::RealPairs src = fft2d::RealPairs{}) {
+    return fft2d::run(Z, nullptr, fields, d.n, dir, d.plan, d.tw, st, kx, src);
 }
 
 // Spectral layer j's block of the mode-major weight copy: j < L the NLFL
@@ -827,15 +808,14 @@ cudaError_t ensure_wt(const FnoDef& d, const float* P, long long version, cudaSt
 // mode-major X [K][xstride(nb, Ci)] (row b * Ci + i of mode k).
 cudaError_t spectra(const FnoDef& d, const FnoWS& w, int nb, const float* x, int Ci, int m, float2* X,
                     cudaStream_t st, long long* kc) {
-    const long long np = (long long)d.n * d.n;
     const int P = (Ci + 1) / 2;
     const int Kx = std::min(m, d.n / 2 + 1), K = rows_kept(d.n, m) * Kx;
-    k_pack<<<grid2(np, nb * P), 256, 0, st>>>(nb, (int)np, x, Ci, w.Zp);
-    cudaError_t e = fft2(d, w.Zp, (long long)nb * P, -1, st, Kx);
+    // the row transforms read the channel pairs of x directly (no packed copy)
+    cudaError_t e = fft2(d, w.Zp, (long long)nb * P, -1, st, Kx, fft2d::RealPairs{x, Ci});
     if (e != cudaSuccess) return e;
     k_extract<<<dim3((unsigned)((K + 31) / 32), (unsigned)((nb * Ci + 31) / 32)), dim3(32, 8), 0, st>>>(
         nb, d.n, m, Kx, K, w.Zp, Ci, X);
-    *kc += 4;
+    *kc += 3;
     return cudaGetLastError();
 }
 
