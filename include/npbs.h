@@ -264,7 +264,9 @@ npbs_status cbs_apply_static(const npbs_batch* batch, const void* V, const void*
  * All solvers iterate in complex64 on a correction delta and fold it into the
  * solution u held in complex128 every refinement cycle, where the true
  * residual f - A u is recomputed in float64 (mixed-precision iterative
- * refinement).  Linear stationary iterations restarted from delta = 0 on the
+ * refinement; the transforms of that residual run in double-single
+ * arithmetic, pairs of floats with about 48 significant bits, and its
+ * pointwise terms and norms in float64).  Linear stationary iterations restarted from delta = 0 on the
  * correction equation A delta = f - A u produce the same iterates as the
  * uninterrupted iteration, so iteration counts are those of the method; the
  * float64 residual removes the float32 floor (about 1e-5 for complex64 CBS).
@@ -507,7 +509,11 @@ npbs_status cdr_solve_direct(npbs_ctx* ctx, const npbs_net* net, const npbs_batc
  * TRUE_RESIDUAL out = r - J x (r nullable: -J x); ADJ_B out = (G J)^* x =
  * J G x (J and G are real symmetric).  r, x, out: DEVICE complex64 (out may
  * alias x); norm2 (nullable, DEVICE double [count]) receives ||out||^2.
- * Asynchronous. */
+ * Side 64 runs its sine-matrix products on the tensor cores (TF32 with a
+ * three-term split, float32-class accuracy); other sides, TRUE_RESIDUAL and
+ * the environment setting NPBS_NEWTON_TC=0 use the CUDA-core kernel.  A
+ * bounded wait of the tensor-core kernel that gives up is reported by
+ * npbs_device_status.  Asynchronous. */
 npbs_status newton_apply(npbs_ctx* ctx, const npbs_batch* batch, const double* shift, const float* u,
                          const void* r, const void* x, void* out, npbs_mode mode, double* norm2,
                          npbs_stream stream);
