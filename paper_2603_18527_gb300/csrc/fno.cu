@@ -401,81 +401,61 @@ __global__ void k_wt_transpose(const float* __restrict__ W, int K, int IO, long 
 
 // Hermitian completion of the retained half-plane spectra, two channels per
 // complex field: Z[b][q] = H(Y[.][b][2q]) + i H(Y[.][b][2q + 1]), Y mode-major
-// [K][nb][Co].  A block takes 32 points; where each point takes its value
-// from (one or two) retained modes is decided once.  Samples go in chunks:
-// the (sample, channel) rows of the points' source modes are read into a
-// shared tile along the rows, then Z is written along the points.
-constexpr int kHermE = 128;  // (sample, channel) entries of one chunk
-__global__ void k_hermite(int nb, int n, int m, int Kx, int K, const float2* __restrict__ Y, int Co,
-                          float2* __restrict__ Z) {
-    __shared__ float2 s1[32][kHermE + 1];
-    __shared__ int I1[32], I2[32], FM[32];
+// [K][nb][Co].  Grid: points x chunks of kHermF fields (f = b * Q + q); where
+// a point takes its value from (one or two) retained modes is decided once per
+// thread, its fields' two channel values are read straight from the
+// (L2-resident) spectra, and Z is written along the points, without shared
+// memory or barriers.
+constexpr int kHermF = 8;
+__global__ void __launch_bounds__(256) k_hermite(int nb, int n, int m, int Kx, int K, const float2* __restrict__ Y,
+                                                 int Co, float2* __restrict__ Z) {
     const int Q = (Co + 1) / 2;
     const int np = n * n;
-    const int p0 = blockIdx.x * 32;
-    const int tx = threadIdx.x, ty = threadIdx.y;
-    if (ty == 0) {
-        // value = the mode itself (form 1, kx < n/2), the conjugate of the
-        // mirrored mode (form 2, kx > n/2), or half the sum of the mode and the
-        // conjugate of its mirror (form 0, kx = 0 or n/2)
-        const int p = p0 + tx;
-        int i1 = -1, i2 = -1, form = 1;
-        auto idx = [&](int yy, int xx) -> int {
-            const int ri = row_index(yy, n, m);
-            return (ri < 0 || xx >= Kx) ? -1 : ri * Kx + xx;
-        };
-        if (p < np) {
-            const int ky = p / n, kx = p - ky * n;
-            const int mky = ky == 0 ? 0 : n - ky;
-            if (kx == 0 || 2 * kx == n) {
-                form = 0;
-                i1 = idx(ky, kx);
-                i2 = idx(mky, kx);
-            } else if (2 * kx < n) {
-                i1 = idx(ky, kx);
-            } else {
-                form = 2;
-                i1 = idx(mky, n - kx);
-            }
-        }
-        I1[tx] = i1;
-        I2[tx] = i2;
-        FM[tx] = form;
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= np) return;
+    // value = the mode itself (form 1, kx < n/2), the conjugate of the
+    // mirrored mode (form 2, kx > n/2), or half the sum of the mode and the
+    // conjugate of its mirror (form 0, kx = 0 or n/2)
+    const int ky = p / n, kx = p - ky * n;
+    const int mky = ky == 0 ? 0 : n - ky;
+    auto idx = [&](int yy, int xx) -> int {
+        const int ri = row_index(yy, n, m);
+        return (ri < 0 || xx >= Kx) ? -1 : ri * Kx + xx;
+    };
+    int i1, i2 = -1, form = 1;
+    if (kx == 0 || 2 * kx == n) {
+        form = 0;
+        i1 = idx(ky, kx);
+        i2 = idx(mky, kx);
+    } else if (2 * kx < n) {
+        i1 = idx(ky, kx);
+    } else {
+        form = 2;
+        i1 = idx(mky, n - kx);
     }
-    __syncthreads();
     const long long rowY = (long long)nb * Co;  // entries per mode
-    const int bc = kHermE / Co;                 // samples per chunk (Co <= 32)
-    const int p = p0 + tx;
-    for (int b0 = 0; b0 < nb; b0 += bc) {
-        const int nbc = min(bc, nb - b0), E = nbc * Co;
-        for (int j = ty; j < 32; j += blockDim.y) {
-            const int i1 = I1[j];
-            const float2* y = Y + (long long)(i1 < 0 ? 0 : i1) * rowY + (long long)b0 * Co;
-            for (int e = tx; e < E; e += 32) s1[j][e] = i1 >= 0 ? y[e] : make_float2(0.f, 0.f);
+    const float2* y1 = Y + (long long)(i1 < 0 ? 0 : i1) * rowY;
+    const float2* y2 = Y + (long long)(i2 < 0 ? 0 : i2) * rowY;
+    const float2 zero = make_float2(0.f, 0.f);
+    const int f0 = blockIdx.y * kHermF, f1 = min(nb * Q, f0 + kHermF);
+#pragma unroll 4
+    for (int f = f0; f < f1; ++f) {
+        const int b = f / Q, q = f - b * Q;
+        const int c0 = 2 * q, c1 = 2 * q + 1;
+        const long long e0 = (long long)b * Co + c0;
+        const bool has1 = c1 < Co;
+        float2 u0 = i1 >= 0 ? y1[e0] : zero;
+        float2 u1 = (i1 >= 0 && has1) ? y1[e0 + 1] : zero;
+        if (form == 0) {
+            const float2 v0 = i2 >= 0 ? y2[e0] : zero;
+            const float2 v1 = (i2 >= 0 && has1) ? y2[e0 + 1] : zero;
+            u0 = make_float2(0.5f * (u0.x + v0.x), 0.5f * (u0.y - v0.y));
+            u1 = make_float2(0.5f * (u1.x + v1.x), 0.5f * (u1.y - v1.y));
+        } else if (form == 2) {
+            u0.y = -u0.y;
+            u1.y = -u1.y;
         }
-        __syncthreads();
-        if (p < np) {
-            const int form = FM[tx], i2 = I2[tx];
-            for (int g = ty; g < nbc * Q; g += blockDim.y) {
-                const int bl = g / Q, q = g - bl * Q, b = b0 + bl;
-                float2 h[2];
-#pragma unroll
-                for (int t = 0; t < 2; ++t) {
-                    const int c = 2 * q + t;
-                    h[t] = make_float2(0.f, 0.f);
-                    if (c >= Co) continue;
-                    const float2 u = s1[tx][bl * Co + c];
-                    if (form == 0) {
-                        const float2 v = i2 >= 0 ? Y[(long long)i2 * rowY + (long long)b * Co + c] : make_float2(0.f, 0.f);
-                        h[t] = make_float2(0.5f * (u.x + v.x), 0.5f * (u.y - v.y));
-                    } else {
-                        h[t] = form == 1 ? u : make_float2(u.x, -u.y);
-                    }
-                }
-                Z[((long long)b * Q + q) * np + p] = make_float2(h[0].x - h[1].y, h[0].y + h[1].x);
-            }
-        }
-        __syncthreads();
+        Z[(long long)f * np + p] = make_float2(u0.x - u1.y, u0.y + u1.x);
     }
 }
 
@@ -827,7 +807,8 @@ cudaError_t synthesize(const FnoDef& d, const FnoWS& w, int nb, const float2* Y,
     const long long np = (long long)d.n * d.n;
     const int Q = (Co + 1) / 2;
     const int Kx = std::min(m, d.n / 2 + 1), K = rows_kept(d.n, m) * Kx;
-    k_hermite<<<(unsigned)((np + 31) / 32), dim3(32, 8), 0, st>>>(nb, d.n, m, Kx, K, Y, Co, w.Zp);
+    k_hermite<<<dim3((unsigned)((np + 255) / 256), (unsigned)((nb * Q + kHermF - 1) / kHermF)), 256, 0, st>>>(
+        nb, d.n, m, Kx, K, Y, Co, w.Zp);
     cudaError_t e = fft2(d, w.Zp, (long long)nb * Q, 1, st, Kx);
     if (e != cudaSuccess) return e;
     k_mix_points<<<grid_of((long long)nb * np / 2), 256, 0, st>>>(nb, np, x, Ci, wl, so, si, bias, w.Zp,
