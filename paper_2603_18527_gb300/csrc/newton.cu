@@ -246,8 +246,12 @@ __global__ void k_nt_linearise(const NtInst* ins, const int* ids, const int* fro
 // The inner solve's float64 check per instance (one CTA): delta += eps
 // (complex), eps = 0, rho = r - J delta in float64 (rounded to complex64 into
 // rho32) and out4[4 j + 2] = ||rho||^2.  Instances with frozen set are skipped.
-__global__ void k_nt_check(const NtInst* ins, const int* ids, const int* frozen, const double* u, const double* r,
-                           float2* eps, double2* delta, float2* rho32, double* out4) {
+// its_out non-null: the check also freezes the instance on the device when
+// it passes (||rho||^2 <= rtol2 ||r||^2, ||r||^2 from out4[4 j]), is not
+// finite, or it >= max_it, recording it in its_out[j].
+__global__ void k_nt_check(const NtInst* ins, const int* ids, int* frozen, const double* u, const double* r,
+                           float2* eps, double2* delta, float2* rho32, double* out4, int* its_out, double rtol2,
+                           int it, int max_it) {
     __shared__ double red[8];
     const NtInst in = ins[blockIdx.x];
     const int j = ids[blockIdx.x];
@@ -276,7 +280,16 @@ __global__ void k_nt_check(const NtInst* ins, const int* ids, const int* frozen,
         s2 += px * px + py * py;
     }
     s2 = block_sum(s2, red);
-    if (threadIdx.x == 0) out4[4 * j + 2] = s2;
+    if (threadIdx.x == 0) {
+        out4[4 * j + 2] = s2;
+        if (its_out) {
+            const double q = s2 / fmax(out4[4 * j], 1e-300);
+            if (!isfinite(q) || q <= rtol2 || it >= max_it) {
+                frozen[j] = 1;
+                its_out[j] = it;
+            }
+        }
+    }
 }
 
 // u += Re delta, delta = 0 (instances with active set)
@@ -814,7 +827,7 @@ npbs_status newton_solve(npbs_ctx* ctx, const npbs_net* net, const npbs_batch* b
     const size_t ext = (size_t)std::max<long long>(P.extent, 1);
     // delta (double2), r (double), eps, rho32, rr (float2), u32 (float), shift, out4 (double), flags (int)
     const size_t bytes = ext * (16 + 8 + 3 * 8) + ((ext * 4 + 255) & ~size_t(255)) + sizeof(double) * 5 * cnt +
-                         sizeof(int) * 3 * cnt + 1024;
+                         sizeof(int) * 4 * cnt + 1024;
     NPBS_CK(ctx, ctx->work[19].ensure(bytes));
     char* w = static_cast<char*>(ctx->work[19].p);
     double2* delta = reinterpret_cast<double2*>(w);
@@ -828,6 +841,7 @@ npbs_status newton_solve(npbs_ctx* ctx, const npbs_net* net, const npbs_batch* b
     int* nfrozen = reinterpret_cast<int*>(out4 + 4 * cnt);
     int* ifrozen = nfrozen + cnt;
     int* active = ifrozen + cnt;
+    int* itsd = active + cnt;
     NPBS_CK(ctx, cudaMemsetAsync(delta, 0, sizeof(double2) * ext, s));
     NPBS_CK(ctx, cudaMemsetAsync(out4, 0, sizeof(double) * 4 * cnt, s));
     const Net* N = reinterpret_cast<const Net*>(net);
@@ -887,7 +901,8 @@ npbs_status newton_solve(npbs_ctx* ctx, const npbs_net* net, const npbs_batch* b
             npbs_status s2 = upload(ifrozen, hi);
             if (s2 != NPBS_OK) return s2;
             for (const NtGroup& g : P.groups)
-                k_nt_check<<<g.cnt, 256, 0, s>>>(g.ins, g.ids, ifrozen, u, r64, eps, delta, rho32, out4);
+                k_nt_check<<<g.cnt, 256, 0, s>>>(g.ins, g.ids, ifrozen, u, r64, eps, delta, rho32, out4, nullptr,
+                                                 0.0, 0, 0);
             NPBS_CK(ctx, cudaGetLastError());
             ctx->count(s, (long long)P.groups.size());
             if ((s2 = read4()) != NPBS_OK) return s2;
@@ -899,8 +914,49 @@ npbs_status newton_solve(npbs_ctx* ctx, const npbs_net* net, const npbs_batch* b
             }
             return upload(ifrozen, hi);
         };
-        if ((st = check()) != NPBS_OK) return st;
-        for (;;) {
+        if (!N) {
+            // Born inner solves: the check freezes each instance on the device at
+            // its first passing check, so the host reads the flags only every
+            // kNtSyncChecks checks (iterations on frozen instances after that are
+            // never folded in, and the update skips them)
+            constexpr int kNtSyncChecks = 4;
+            const double rtol2 = opts->inner_rtol * opts->inner_rtol;
+            if ((st = upload(ifrozen, hi)) != NPBS_OK) return st;
+            auto check_dev = [&]() -> npbs_status {
+                for (const NtGroup& g : P.groups)
+                    k_nt_check<<<g.cnt, 256, 0, s>>>(g.ins, g.ids, ifrozen, u, r64, eps, delta, rho32, out4, itsd,
+                                                     rtol2, it, opts->inner_max_iter);
+                NPBS_CK(ctx, cudaGetLastError());
+                ctx->count(s, (long long)P.groups.size());
+                return NPBS_OK;
+            };
+            if ((st = check_dev()) != NPBS_OK) return st;
+            for (;;) {
+                NPBS_CK(ctx, cudaMemcpyAsync(hi.data(), ifrozen, sizeof(int) * cnt, cudaMemcpyDeviceToHost, s));
+                NPBS_CK(ctx, cudaStreamSynchronize(s));
+                bool busy = false;
+                for (int j = 0; j < cnt; ++j) busy |= !hi[j];
+                if (!busy) break;
+                for (int sc = 0; sc < kNtSyncChecks; ++sc) {
+                    for (int k = 0; k < opts->check_every && it < opts->inner_max_iter; ++k, ++it) {
+                        st = nt_run(ctx, P, NPBS_RESIDUAL, shift, u32, rho32, eps, rr, nullptr, cnt, s);
+                        if (st != NPBS_OK) return st;
+                        for (const NtGroup& g : P.groups)
+                            k_nt_axpy<<<g.cnt, 256, 0, s>>>(g.ins, g.ids, ifrozen, rr, eps);
+                        NPBS_CK(ctx, cudaGetLastError());
+                        ctx->count(s, (long long)P.groups.size());
+                    }
+                    if ((st = check_dev()) != NPBS_OK) return st;
+                }
+            }
+            std::vector<int> hits(cnt);
+            NPBS_CK(ctx, cudaMemcpyAsync(hits.data(), itsd, sizeof(int) * cnt, cudaMemcpyDeviceToHost, s));
+            NPBS_CK(ctx, cudaStreamSynchronize(s));
+            for (int j = 0; j < cnt; ++j)
+                if (!hn[j]) its[j] = hits[j];
+        }
+        if (N && (st = check()) != NPBS_OK) return st;
+        for (; N;) {
             bool busy = false;
             for (int j = 0; j < cnt; ++j) busy |= !hi[j];
             if (!busy) break;
